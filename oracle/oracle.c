@@ -1,0 +1,669 @@
+/*
+ * Oracle for Gen. ParRep dynamics — TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Plain FP64 C, no blocking, fusion or reordering beyond what the definitions state.  Each function
+ * names the passage of the paper (Hedin & Lelievre, gen.parRep) or the published method it follows.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct orc_ctx {
+  orc_system s;
+  uint8_t *excluded; /* [n][n] 1 when the nonbonded pair is excluded */
+};
+
+orc_ctx *orc_create(const orc_system *sys) {
+  orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  if (!c) return NULL;
+  c->s = *sys;
+  int n = sys->n_atoms;
+  c->excluded = (uint8_t *)calloc((size_t)n * (size_t)n, 1);
+  if (!c->excluded) { free(c); return NULL; }
+  for (int e = 0; e < sys->n_excl; ++e) {
+    int i = sys->excl[2 * e], j = sys->excl[2 * e + 1];
+    c->excluded[(size_t)i * n + j] = 1;
+    c->excluded[(size_t)j * n + i] = 1;
+  }
+  return c;
+}
+
+void orc_destroy(orc_ctx *c) {
+  if (!c) return;
+  free(c->excluded);
+  free(c);
+}
+
+/* ---------------------------------------------------------------- vector helpers (3-D) */
+static void sub3(const double *a, const double *b, double *r) { r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2]; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+/* Dihedral angle of atoms (i, j, k, l) in radians, (-pi, pi]: the signed angle between the planes
+ * (i, j, k) and (j, k, l), positive for a right-handed rotation about j->k. */
+static double dihedral_angle(const double *qi, const double *qj, const double *qk, const double *ql) {
+  double b1[3], b2[3], b3[3], n1[3], n2[3];
+  sub3(qj, qi, b1); sub3(qk, qj, b2); sub3(ql, qk, b3);
+  cross3(b1, b2, n1); cross3(b2, b3, n2);
+  return atan2(norm3(b2) * dot3(b1, n2), dot3(n1, n2));
+}
+
+static void group_com(const orc_ctx *c, int g, const double *q, double *com) {
+  const orc_system *s = &c->s;
+  double mt = 0, acc[3] = {0, 0, 0};
+  for (int t = s->group_offsets[g]; t < s->group_offsets[g + 1]; ++t) {
+    int a = s->group_atoms[t];
+    double m = s->mass[a];
+    mt += m;
+    for (int d = 0; d < 3; ++d) acc[d] += m * q[3 * a + d];
+  }
+  for (int d = 0; d < 3; ++d) com[d] = acc[d] / mt;
+}
+
+/* ---------------------------------------------------------------- potential V(q), Eq. 1 */
+double orc_potential(const orc_ctx *c, const double *q) {
+  const orc_system *s = &c->s;
+  if (s->potential == ORC_POT_DOUBLE_WELL_2D) {
+    double x = q[0], y = q[1];
+    return s->dw_a * (x * x - 1.0) * (x * x - 1.0) + s->dw_b * y * y;
+  }
+  int n = s->n_atoms;
+  double e = 0.0;
+  for (int b = 0; b < s->n_bonds; ++b) {
+    const int *a = s->bond_atoms + 2 * b;
+    double d[3];
+    sub3(q + 3 * a[0], q + 3 * a[1], d);
+    double r = norm3(d);
+    e += 0.5 * s->bond_k[b] * (r - s->bond_r0[b]) * (r - s->bond_r0[b]);
+  }
+  for (int t = 0; t < s->n_angles; ++t) {
+    const int *a = s->angle_atoms + 3 * t;
+    double u[3], v[3], w[3];
+    sub3(q + 3 * a[0], q + 3 * a[1], u);
+    sub3(q + 3 * a[2], q + 3 * a[1], v);
+    cross3(u, v, w);
+    double th = atan2(norm3(w), dot3(u, v));
+    e += 0.5 * s->angle_k[t] * (th - s->angle_theta0[t]) * (th - s->angle_theta0[t]);
+  }
+  for (int t = 0; t < s->n_dihedrals; ++t) {
+    const int *a = s->dihedral_atoms + 4 * t;
+    double phi = dihedral_angle(q + 3 * a[0], q + 3 * a[1], q + 3 * a[2], q + 3 * a[3]);
+    e += s->dihedral_k[t] * (1.0 + cos(s->dihedral_n[t] * phi - s->dihedral_delta[t]));
+  }
+  for (int i = 0; i < n; ++i) {
+    for (int j = i + 1; j < n; ++j) {
+      if (c->excluded[(size_t)i * n + j]) continue;
+      double d[3];
+      sub3(q + 3 * i, q + 3 * j, d);
+      double r2 = dot3(d, d);
+      if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
+      double sig = 0.5 * (s->sigma[i] + s->sigma[j]);
+      double eps = sqrt(s->epsilon[i] * s->epsilon[j]);
+      double sr6 = pow(sig * sig / r2, 3);
+      e += 4.0 * eps * (sr6 * sr6 - sr6);
+      /* dielectric eps(r) = 4 r: E = k_e q_i q_j / (4 r * r) */
+      e += s->coulomb_k * s->charge[i] * s->charge[j] / (4.0 * r2);
+    }
+  }
+  return e;
+}
+
+/* ---------------------------------------------------------------- forces F = -grad V */
+void orc_forces(const orc_ctx *c, const double *q, double *f) {
+  const orc_system *s = &c->s;
+  if (s->potential == ORC_POT_DOUBLE_WELL_2D) {
+    double x = q[0], y = q[1];
+    f[0] = -s->dw_a * 4.0 * x * (x * x - 1.0);
+    f[1] = -s->dw_b * 2.0 * y;
+    return;
+  }
+  int n = s->n_atoms;
+  memset(f, 0, sizeof(double) * 3 * (size_t)n);
+  /* bonds: dE/dr = k (r - r0); F_i = -dE/dr * (q_i - q_j)/r */
+  for (int b = 0; b < s->n_bonds; ++b) {
+    const int *a = s->bond_atoms + 2 * b;
+    double d[3];
+    sub3(q + 3 * a[0], q + 3 * a[1], d);
+    double r = norm3(d);
+    double g = s->bond_k[b] * (r - s->bond_r0[b]) / r;
+    for (int x = 0; x < 3; ++x) {
+      f[3 * a[0] + x] -= g * d[x];
+      f[3 * a[1] + x] += g * d[x];
+    }
+  }
+  /* angles: theta = atan2(|u x v|, u.v) with u = q_i - q_j, v = q_k - q_j;
+   * d theta / d q_i = (cos(theta) u/|u| - v/|v|) / (|u| sin(theta)), likewise for q_k. */
+  for (int t = 0; t < s->n_angles; ++t) {
+    const int *a = s->angle_atoms + 3 * t;
+    double u[3], v[3], w[3];
+    sub3(q + 3 * a[0], q + 3 * a[1], u);
+    sub3(q + 3 * a[2], q + 3 * a[1], v);
+    cross3(u, v, w);
+    double lu = norm3(u), lv = norm3(v);
+    double th = atan2(norm3(w), dot3(u, v));
+    double ct = cos(th), st = sin(th);
+    if (st < 1e-12) st = 1e-12;
+    double dedth = s->angle_k[t] * (th - s->angle_theta0[t]);
+    for (int x = 0; x < 3; ++x) {
+      double dthi = (ct * u[x] / lu - v[x] / lv) / (lu * st);
+      double dthk = (ct * v[x] / lv - u[x] / lu) / (lv * st);
+      f[3 * a[0] + x] -= dedth * dthi;
+      f[3 * a[2] + x] -= dedth * dthk;
+      f[3 * a[1] + x] += dedth * (dthi + dthk);
+    }
+  }
+  /* dihedrals (Blondel & Karplus 1996 gradient of the dihedral angle):
+   * d phi/d q_i = -|b2| n1/|n1|^2, d phi/d q_l = |b2| n2/|n2|^2,
+   * d phi/d q_j = -(1 + b1.b2/|b2|^2) d phi/d q_i + (b3.b2/|b2|^2) d phi/d q_l,
+   * d phi/d q_k = (b1.b2/|b2|^2) d phi/d q_i - (1 + b3.b2/|b2|^2) d phi/d q_l
+   * (the four gradients sum to zero: translation invariance). */
+  for (int t = 0; t < s->n_dihedrals; ++t) {
+    const int *a = s->dihedral_atoms + 4 * t;
+    const double *qi = q + 3 * a[0], *qj = q + 3 * a[1], *qk = q + 3 * a[2], *ql = q + 3 * a[3];
+    double b1[3], b2[3], b3[3], n1[3], n2[3];
+    sub3(qj, qi, b1); sub3(qk, qj, b2); sub3(ql, qk, b3);
+    cross3(b1, b2, n1); cross3(b2, b3, n2);
+    double lb2 = norm3(b2);
+    double phi = atan2(lb2 * dot3(b1, n2), dot3(n1, n2));
+    double dedphi = -s->dihedral_k[t] * s->dihedral_n[t] * sin(s->dihedral_n[t] * phi - s->dihedral_delta[t]);
+    double n1sq = dot3(n1, n1), n2sq = dot3(n2, n2);
+    double f12 = dot3(b1, b2) / (lb2 * lb2), f32 = dot3(b3, b2) / (lb2 * lb2);
+    for (int x = 0; x < 3; ++x) {
+      double gi = -lb2 * n1[x] / n1sq;
+      double gl = lb2 * n2[x] / n2sq;
+      double gj = -(1.0 + f12) * gi + f32 * gl;
+      double gk = f12 * gi - (1.0 + f32) * gl;
+      f[3 * a[0] + x] -= dedphi * gi;
+      f[3 * a[1] + x] -= dedphi * gj;
+      f[3 * a[2] + x] -= dedphi * gk;
+      f[3 * a[3] + x] -= dedphi * gl;
+    }
+  }
+  /* Lennard-Jones (Lorentz-Berthelot) and Coulomb with eps(r) = 4r over non-excluded pairs */
+  for (int i = 0; i < n; ++i) {
+    for (int j = i + 1; j < n; ++j) {
+      if (c->excluded[(size_t)i * n + j]) continue;
+      double d[3];
+      sub3(q + 3 * i, q + 3 * j, d);
+      double r2 = dot3(d, d);
+      if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
+      double sig = 0.5 * (s->sigma[i] + s->sigma[j]);
+      double eps = sqrt(s->epsilon[i] * s->epsilon[j]);
+      double sr6 = pow(sig * sig / r2, 3);
+      /* -dE_LJ/dr / r = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 */
+      double g = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
+      /* -dE_C/dr / r = 2 k_e q_i q_j / (4 r^3) / r */
+      g += 2.0 * s->coulomb_k * s->charge[i] * s->charge[j] / (4.0 * r2 * r2);
+      for (int x = 0; x < 3; ++x) {
+        f[3 * i + x] += g * d[x];
+        f[3 * j + x] -= g * d[x];
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------- Philox4x32-10 */
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo) {
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(0xD2511F53u, x0, &hi0, &lo0);
+    mulhilo32(0xCD9E8D57u, x2, &hi1, &lo1);
+    uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += 0x9E3779B9u; /* Weyl sequence key schedule */
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Counter layout: (step low 32 bits, step bits 32..55 | stream << 24, replica, atom); key = seed. */
+static void philox_words(uint64_t seed, int64_t step, uint32_t stream, int32_t replica, int32_t atom,
+                         uint32_t out[4]) {
+  uint64_t st = (uint64_t)step;
+  uint32_t ctr[4] = {(uint32_t)st, (uint32_t)((st >> 32) & 0x00FFFFFFu) | (stream << 24),
+                     (uint32_t)replica, (uint32_t)atom};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  orc_philox4x32_10(ctr, key, out);
+}
+
+/* Box-Muller (1958): (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2) with
+ * u = (w + 1/2) 2^-32 for a 32-bit word w, so u is in (0, 1). */
+void orc_normals(uint64_t seed, int64_t step, int32_t replica, int32_t atom, double xi[4]) {
+  uint32_t w[4];
+  philox_words(seed, step, 0u, replica, atom, w);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int pair = 0; pair < 2; ++pair) {
+    double u1 = ((double)w[2 * pair] + 0.5) * 0x1p-32;
+    double u2 = ((double)w[2 * pair + 1] + 0.5) * 0x1p-32;
+    double r = sqrt(-2.0 * log(u1));
+    xi[2 * pair] = r * cos(two_pi * u2);
+    xi[2 * pair + 1] = r * sin(two_pi * u2);
+  }
+}
+
+uint32_t orc_branch_word(uint64_t seed, int64_t step, int32_t replica) {
+  uint32_t w[4];
+  philox_words(seed, step, 1u, replica, 0, w);
+  return w[0];
+}
+
+/* ---------------------------------------------------------------- BAOAB step of Eq. 1
+ * B: p += dt/2 F; A: q += dt/2 M^-1 p; O: p = c1 p + sqrt((1 - c1^2) m kT) xi with c1 = exp(-gamma dt)
+ * (gamma read as a collision rate); A: q += dt/2 M^-1 p; F = F(q); B: p += dt/2 F. */
+void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t seed,
+                    int32_t replica, int64_t step) {
+  const orc_system *s = &c->s;
+  int n = s->n_atoms, dim = s->dim;
+  double h = 0.5 * s->dt;
+  double c1 = exp(-s->gamma * s->dt);
+  for (int a = 0; a < n; ++a) {
+    double m = s->mass[a];
+    double sd = sqrt((1.0 - c1 * c1) * m * s->kT);
+    double xi[4];
+    orc_normals(seed, step, replica, a, xi);
+    for (int x = 0; x < dim; ++x) {
+      int i = dim * a + x;
+      p[i] += h * f[i];
+      q[i] += h * p[i] / m;
+      p[i] = c1 * p[i] + sd * xi[x];
+      q[i] += h * p[i] / m;
+    }
+  }
+  orc_forces(c, q, f);
+  for (int i = 0; i < n * dim; ++i) p[i] += h * f[i];
+}
+
+/* ---------------------------------------------------------------- states (Sections 2.2, 3.3) */
+void orc_cv(const orc_ctx *c, const double *q, double cv[2]) {
+  const orc_system *s = &c->s;
+  cv[0] = cv[1] = 0.0;
+  if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
+    cv[0] = q[0];
+  } else if (s->cv_kind == ORC_CV_DIHEDRAL_RECT) {
+    const int *a = s->cv_atoms;
+    const double deg = 180.0 / 3.14159265358979323846;
+    cv[0] = deg * dihedral_angle(q + 3 * a[0], q + 3 * a[1], q + 3 * a[2], q + 3 * a[3]);
+    cv[1] = deg * dihedral_angle(q + 3 * a[1], q + 3 * a[2], q + 3 * a[3], q + 3 * a[4]);
+  } else if (s->cv_kind == ORC_CV_COM_DISTANCE) {
+    double c0[3], c1[3], d[3];
+    group_com(c, 0, q, c0);
+    group_com(c, 1, q, c1);
+    sub3(c0, c1, d);
+    cv[0] = norm3(d);
+  }
+}
+
+/* Double well: states are the cores x < -w (state 0) and x > w (state 1), w = cv_params[0];
+ * the state 0 is left when x >= 0, the state 1 when x < 0.
+ * Dihedral rectangle: state 0 = {phi in [p0, p1] and psi in [p2, p3]} (degrees), state 1 = the
+ * complement: a two-state partition.
+ * Centre-of-mass distance: state 0 = {d < cv_params[0]}, state 1 = the complement. */
+int32_t orc_state_of(const orc_ctx *c, const double *q) {
+  const orc_system *s = &c->s;
+  double cv[2];
+  orc_cv(c, q, cv);
+  if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
+    if (cv[0] < -s->cv_params[0]) return 0;
+    if (cv[0] > s->cv_params[0]) return 1;
+    return -1;
+  }
+  if (s->cv_kind == ORC_CV_DIHEDRAL_RECT) {
+    int in = cv[0] >= s->cv_params[0] && cv[0] <= s->cv_params[1] && cv[1] >= s->cv_params[2] &&
+             cv[1] <= s->cv_params[3];
+    return in ? 0 : 1;
+  }
+  return cv[0] < s->cv_params[0] ? 0 : 1;
+}
+
+int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega) {
+  const orc_system *s = &c->s;
+  if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
+    double x = q[0];
+    return omega == 0 ? (x >= 0.0) : (x < 0.0);
+  }
+  return orc_state_of(c, q) != omega;
+}
+
+/* ---------------------------------------------------------------- observables (Section 2.4.1) */
+double orc_observable(const orc_ctx *c, int32_t j, const double *q, const double *p) {
+  const orc_system *s = &c->s;
+  const int32_t *arg = s->obs_arg[j];
+  int n = s->n_atoms, dim = s->dim;
+  switch (s->obs_kind[j]) {
+    case ORC_OBS_COORD: return q[dim * arg[0] + arg[1]];
+    case ORC_OBS_POTENTIAL: return orc_potential(c, q);
+    case ORC_OBS_KINETIC: {
+      double k = 0;
+      for (int a = 0; a < n; ++a)
+        for (int x = 0; x < dim; ++x) k += 0.5 * p[dim * a + x] * p[dim * a + x] / s->mass[a];
+      return k;
+    }
+    case ORC_OBS_DIHEDRAL:
+      return dihedral_angle(q + 3 * arg[0], q + 3 * arg[1], q + 3 * arg[2], q + 3 * arg[3]);
+    case ORC_OBS_GROUP_DISTANCE: {
+      double c0[3], c1[3], d[3];
+      group_com(c, arg[0], q, c0);
+      group_com(c, arg[1], q, c1);
+      sub3(c0, c1, d);
+      return norm3(d);
+    }
+    case ORC_OBS_RMS_VELOCITY: {
+      double acc = 0;
+      int cnt = 0;
+      for (int t = s->group_offsets[arg[0]]; t < s->group_offsets[arg[0] + 1]; ++t) {
+        int a = s->group_atoms[t];
+        for (int x = 0; x < 3; ++x) {
+          double v = p[3 * a + x] / s->mass[a];
+          acc += v * v;
+        }
+        cnt++;
+      }
+      return sqrt(acc / cnt);
+    }
+  }
+  return 0.0;
+}
+
+/* ---------------------------------------------------------------- Gelman-Rubin, Eqs. 2-3
+ * Obar^k = mean over the samples of replica k, Obar = mean over k of Obar^k;
+ * R = [1/N sum_k 1/n sum_s (O_s^k - Obar)^2] / [1/N sum_k 1/n sum_s (O_s^k - Obar^k)^2]. */
+double orc_gelman_rubin(int32_t n_rep, int32_t n_samp, const double *samples) {
+  if (n_rep < 1 || n_samp < 1) return INFINITY;
+  double *mk = (double *)malloc(sizeof(double) * (size_t)n_rep);
+  double grand = 0;
+  for (int k = 0; k < n_rep; ++k) {
+    double sum = 0;
+    for (int t = 0; t < n_samp; ++t) sum += samples[(size_t)k * n_samp + t];
+    mk[k] = sum / n_samp;
+    grand += mk[k];
+  }
+  grand /= n_rep;
+  double num = 0, den = 0;
+  for (int k = 0; k < n_rep; ++k) {
+    double a = 0, b = 0;
+    for (int t = 0; t < n_samp; ++t) {
+      double o = samples[(size_t)k * n_samp + t];
+      a += (o - grand) * (o - grand);
+      b += (o - mk[k]) * (o - mk[k]);
+    }
+    num += a / n_samp;
+    den += b / n_samp;
+  }
+  free(mk);
+  num /= n_rep;
+  den /= n_rep;
+  if (!(den > 0)) return INFINITY;
+  return num / den;
+}
+
+/* ---------------------------------------------------------------- Fleming-Viot branching */
+int32_t orc_fv_branch(uint64_t seed, int64_t step, int32_t n_rep, const uint8_t *exited,
+                      int32_t *src) {
+  int32_t *surv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_rep > 0 ? n_rep : 1));
+  int ns = 0, nb = 0;
+  for (int r = 1; r < n_rep; ++r)
+    if (!exited[r]) surv[ns++] = r;
+  src[0] = -1;
+  for (int r = 1; r < n_rep; ++r) {
+    if (!exited[r]) { src[r] = -1; continue; }
+    if (ns == 0) {
+      src[r] = 0;
+    } else {
+      uint32_t w = orc_branch_word(seed, step, r);
+      src[r] = surv[((uint64_t)w * (uint64_t)ns) >> 32];
+    }
+    nb++;
+  }
+  free(surv);
+  return nb;
+}
+
+/* ---------------------------------------------------------------- k steps with sampling */
+int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
+                   uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
+                   double *samples, int32_t cap) {
+  const orc_system *s = &c->s;
+  int nd = s->n_atoms * s->dim, no = s->n_obs;
+  int ns = 0;
+  for (int64_t i = 0; i < k; ++i) {
+    for (int r = 0; r < n_rep; ++r)
+      orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, seed, r, t0 + i);
+    if (t_gr > 0 && (tp0 + i + 1) % t_gr == 0) {
+      if (samples && ns < cap)
+        for (int r = 0; r < n_rep; ++r)
+          for (int j = 0; j < no; ++j)
+            samples[((size_t)r * cap + ns) * no + j] =
+                orc_observable(c, j, q + (size_t)r * nd, p + (size_t)r * nd);
+      ns++;
+    }
+  }
+  return ns;
+}
+
+/* ---------------------------------------------------------------- parallel dynamics step, Eq. 5 */
+int32_t orc_parallel_phase(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
+                           uint64_t seed, int64_t t0, int32_t omega, int32_t t_check,
+                           int64_t max_checks, orc_exit *out) {
+  int nd = c->s.n_atoms * c->s.dim;
+  int64_t t = t0;
+  for (int64_t M = 1; M <= max_checks; ++M) {
+    orc_step_k(c, n_rep, q, p, f, seed, t, 0, t_check, 0, NULL, 0);
+    t += t_check;
+    for (int r = 0; r < n_rep; ++r) {
+      if (orc_exited(c, q + (size_t)r * nd, omega)) {
+        out->M = M;
+        out->k = r + 1;
+        out->label_to = orc_state_of(c, q + (size_t)r * nd);
+        out->tau_steps = ((int64_t)n_rep * (M - 1) + (r + 1)) * (int64_t)t_check;
+        return 1;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------- the loop of Fig. 1 */
+typedef struct {
+  double *v;   /* [n_rep][n_obs][cap] */
+  int32_t cap, n;
+} history;
+
+static void hist_reserve(history *h, int n_rep, int n_obs, int need) {
+  if (need <= h->cap) return;
+  int ncap = h->cap ? h->cap : 64;
+  while (ncap < need) ncap *= 2;
+  double *nv = (double *)malloc(sizeof(double) * (size_t)n_rep * n_obs * ncap);
+  for (int r = 0; r < n_rep; ++r)
+    for (int j = 0; j < n_obs; ++j)
+      for (int t = 0; t < h->n; ++t)
+        nv[((size_t)r * n_obs + j) * ncap + t] = h->v[((size_t)r * n_obs + j) * h->cap + t];
+  free(h->v);
+  h->v = nv;
+  h->cap = ncap;
+}
+
+int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const double *q0,
+                          const double *p0, orc_event *events, int32_t max_events,
+                          int64_t *t_global_out) {
+  const orc_system *s = &c->s;
+  int N = rp->n_rep, nd = s->n_atoms * s->dim, no = s->n_obs;
+  double *q = (double *)malloc(sizeof(double) * (size_t)N * nd);
+  double *p = (double *)malloc(sizeof(double) * (size_t)N * nd);
+  double *f = (double *)malloc(sizeof(double) * (size_t)N * nd);
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(N > 1 ? N - 1 : 1) * 1);
+  uint8_t *ex = (uint8_t *)malloc((size_t)N);
+  int32_t *src = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  history h = {NULL, 0, 0};
+  memcpy(q, q0, sizeof(double) * nd);
+  memcpy(p, p0, sizeof(double) * nd);
+  orc_forces(c, q, f);
+  int64_t tg = 0, tsim = 0;
+  int nev = 0, nexit = 0;
+#define LOG_EVENT(KIND, OM, TO, KK, MM, STEPS, NB)                                          \
+  do {                                                                                     \
+    if (nev < max_events) {                                                                \
+      orc_event e_ = {(KIND), (OM), (TO), (KK), (MM), (STEPS), tsim, (NB)};                \
+      events[nev] = e_;                                                                    \
+    }                                                                                      \
+    nev++;                                                                                 \
+  } while (0)
+
+  while (nexit < rp->max_exits && tg < rp->max_steps && nev < max_events) {
+    /* 1. transient propagation of the reference walker until it is in some state */
+    int64_t treach = 0;
+    int omega = orc_state_of(c, q);
+    while (omega < 0 && tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) orc_baoab_step(c, q, p, f, rp->seed, 0, tg++);
+      treach += rp->t_check;
+      omega = orc_state_of(c, q);
+    }
+    if (omega < 0) break;
+    if (treach > 0) {
+      tsim += treach;
+      LOG_EVENT(ORC_EV_TRANSIENT, -1, omega, 0, 0, treach, 0);
+    }
+    /* 2. convergence step: Fleming-Viot process from the broadcast reference, Gelman-Rubin test */
+    for (int r = 1; r < N; ++r) {
+      memcpy(q + (size_t)r * nd, q, sizeof(double) * nd);
+      memcpy(p + (size_t)r * nd, p, sizeof(double) * nd);
+      memcpy(f + (size_t)r * nd, f, sizeof(double) * nd);
+    }
+    h.n = 0;
+    int64_t t = 0, nbranch = 0;
+    int converged = 0, ref_exit = 0;
+    while (tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) {
+        for (int r = 0; r < N; ++r)
+          orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, rp->seed, r, tg);
+        tg++;
+        t++;
+        if (t % rp->t_gr == 0) {
+          hist_reserve(&h, N, no, h.n + 1);
+          for (int r = 0; r < N; ++r)
+            for (int j = 0; j < no; ++j)
+              h.v[((size_t)r * no + j) * h.cap + h.n] =
+                  orc_observable(c, j, q + (size_t)r * nd, p + (size_t)r * nd);
+          h.n++;
+        }
+      }
+      /* (a) the reference walker left omega: kill the F-V workers, clock += t_ref */
+      if (orc_exited(c, q, omega)) {
+        tsim += t;
+        LOG_EVENT(ORC_EV_REF_EXIT, omega, orc_state_of(c, q), 0, 0, t, nbranch);
+        nexit++;
+        ref_exit = 1;
+        break;
+      }
+      /* (b) branching of the exited workers */
+      for (int r = 0; r < N; ++r) ex[r] = (uint8_t)(r > 0 && orc_exited(c, q + (size_t)r * nd, omega));
+      int nb = orc_fv_branch(rp->seed, tg, N, ex, src);
+      if (nb > 0) {
+        int all = 1;
+        for (int r = 1; r < N; ++r) all &= ex[r];
+        if (all) LOG_EVENT(ORC_EV_FV_ALL_EXITED, omega, omega, 0, 0, t, nb);
+        for (int r = 1; r < N; ++r) {
+          if (src[r] < 0) continue;
+          int sr = src[r];
+          memcpy(q + (size_t)r * nd, q + (size_t)sr * nd, sizeof(double) * nd);
+          memcpy(p + (size_t)r * nd, p + (size_t)sr * nd, sizeof(double) * nd);
+          memcpy(f + (size_t)r * nd, f + (size_t)sr * nd, sizeof(double) * nd);
+          for (int j = 0; j < no; ++j)
+            memcpy(h.v + ((size_t)r * no + j) * h.cap, h.v + ((size_t)sr * no + j) * h.cap,
+                   sizeof(double) * (size_t)h.n);
+        }
+        nbranch += nb;
+      }
+      /* (c) Gelman-Rubin over the F-V workers, Eq. 4 */
+      if (t >= rp->min_fv_steps && N > 1) {
+        int all_ok = 1;
+        buf = (double *)realloc(buf, sizeof(double) * (size_t)(N - 1) * (h.n > 0 ? h.n : 1));
+        for (int j = 0; j < no && all_ok; ++j) {
+          for (int r = 1; r < N; ++r)
+            for (int u = 0; u < h.n; ++u)
+              buf[(size_t)(r - 1) * h.n + u] = h.v[((size_t)r * no + j) * h.cap + u];
+          double R = orc_gelman_rubin(N - 1, h.n, buf);
+          if (!(R < 1.0 + rp->tol)) all_ok = 0;
+        }
+        if (all_ok) { converged = 1; break; }
+      }
+    }
+    if (ref_exit) continue;
+    if (!converged) break;
+    tsim += t;
+    LOG_EVENT(ORC_EV_FV_CONVERGED, omega, omega, 0, 0, t, nbranch);
+    /* 3. parallel dynamics step, Eqs. 5-6 */
+    int64_t M = 0;
+    int found = -1;
+    while (tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) {
+        for (int r = 0; r < N; ++r)
+          orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, rp->seed, r, tg);
+        tg++;
+      }
+      M++;
+      for (int r = 0; r < N; ++r)
+        if (orc_exited(c, q + (size_t)r * nd, omega)) { found = r; break; }
+      if (found >= 0) break;
+    }
+    if (found < 0) break;
+    int64_t tau = ((int64_t)N * (M - 1) + (found + 1)) * (int64_t)rp->t_check;
+    tsim += tau;
+    LOG_EVENT(ORC_EV_PARALLEL_EXIT, omega, orc_state_of(c, q + (size_t)found * nd), found + 1, M, tau, 0);
+    nexit++;
+    /* the exit configuration X_tau^k becomes the reference walker */
+    memcpy(q, q + (size_t)found * nd, sizeof(double) * nd);
+    memcpy(p, p + (size_t)found * nd, sizeof(double) * nd);
+    memcpy(f, f + (size_t)found * nd, sizeof(double) * nd);
+  }
+#undef LOG_EVENT
+  if (t_global_out) *t_global_out = tg;
+  free(q); free(p); free(f); free(buf); free(ex); free(src); free(h.v);
+  return nev < max_events ? nev : max_events;
+}
+
+/* ---------------------------------------------------------------- brute-force reference dynamics */
+int32_t orc_run_bruteforce(const orc_ctx *c, uint64_t seed, int32_t t_check, const double *q0,
+                           const double *p0, int64_t max_steps, int64_t *residence,
+                           int32_t *from_state, int32_t max_res) {
+  int nd = c->s.n_atoms * c->s.dim;
+  double *q = (double *)malloc(sizeof(double) * nd);
+  double *p = (double *)malloc(sizeof(double) * nd);
+  double *f = (double *)malloc(sizeof(double) * nd);
+  memcpy(q, q0, sizeof(double) * nd);
+  memcpy(p, p0, sizeof(double) * nd);
+  orc_forces(c, q, f);
+  int64_t t = 0, t_enter = 0;
+  int state = orc_state_of(c, q), nres = 0;
+  while (t < max_steps && nres < max_res) {
+    for (int i = 0; i < t_check; ++i) orc_baoab_step(c, q, p, f, seed, 0, t++);
+    if (state >= 0) {
+      if (orc_exited(c, q, state)) {
+        residence[nres] = t - t_enter;
+        from_state[nres] = state;
+        nres++;
+        state = orc_state_of(c, q);
+        t_enter = t;
+      }
+    } else {
+      state = orc_state_of(c, q);
+      t_enter = t;
+    }
+  }
+  free(q); free(p); free(f);
+  return nres;
+}

@@ -1,0 +1,180 @@
+/*
+ * Oracle for Generalized Parallel Replica (Gen. ParRep) dynamics — TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64, single-threaded-per-call C implementation of what the method computes:
+ * Langevin dynamics (Section 2.1, Eq. 1) discretised by BAOAB, the state functions of Sections 2.2
+ * and 3.3, the Fleming-Viot convergence step with the Gelman-Rubin statistic (Section 2.4.1,
+ * Eqs. 2-4), the parallel dynamics step and its exit-time formula (Section 2.4.2, Eqs. 5-6) and the
+ * three-step loop of Fig. 1.  It shares no code, header, table or constant generator with the CUDA
+ * library; only tests, the smoke entry point and the CPU-baseline leg of the benchmark may load it.
+ *
+ * Layouts: positions and momenta of one replica are [n_atoms][dim] row-major FP64; several
+ * replicas are stacked as [n_replicas][n_atoms][dim].  Units are those of the system description.
+ *
+ * Parity status: every function here is pinned by a CPU test except where "parity unpinned" is
+ * written beside it.
+ */
+#ifndef GRP_ORACLE_H
+#define GRP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_POT_DOUBLE_WELL_2D = 0, ORC_POT_FORCE_FIELD = 1 };
+enum { ORC_CV_DOUBLE_WELL = 0, ORC_CV_DIHEDRAL_RECT = 1, ORC_CV_COM_DISTANCE = 2 };
+enum {
+  ORC_OBS_COORD = 0,        /* arg0 = atom, arg1 = axis */
+  ORC_OBS_POTENTIAL = 1,    /* V(q) */
+  ORC_OBS_KINETIC = 2,      /* K(p) = 1/2 p^T M^-1 p */
+  ORC_OBS_DIHEDRAL = 3,     /* arg0..3 = atoms, radians in (-pi, pi] */
+  ORC_OBS_GROUP_DISTANCE = 4, /* arg0, arg1 = groups; distance between their centres of mass */
+  ORC_OBS_RMS_VELOCITY = 5  /* arg0 = group; sqrt(mean |p_i/m_i|^2) over the group */
+};
+#define ORC_MAX_OBS 8
+#define ORC_MAX_GROUPS 4
+
+typedef struct {
+  int32_t n_atoms;
+  int32_t dim;        /* 2 for the analytic double well, 3 for a force-field system */
+  int32_t potential;  /* ORC_POT_* */
+  const double *mass; /* [n_atoms] */
+  double dw_a, dw_b;  /* V(x,y) = dw_a (x^2-1)^2 + dw_b y^2 */
+  /* nonbonded: Lennard-Jones (Lorentz-Berthelot) + Coulomb with distance-dependent dielectric 4r */
+  const double *sigma, *epsilon, *charge; /* [n_atoms] */
+  int32_t n_excl;
+  const int32_t *excl; /* [n_excl][2] excluded nonbonded pairs */
+  double cutoff;       /* 0: every pair; else pairs with r < cutoff (plain truncation) */
+  double coulomb_k;    /* k_e in energy*length/charge^2 */
+  /* bonded */
+  int32_t n_bonds;
+  const int32_t *bond_atoms; /* [n_bonds][2] */
+  const double *bond_k, *bond_r0; /* E = 1/2 k (r - r0)^2 */
+  int32_t n_angles;
+  const int32_t *angle_atoms; /* [n_angles][3], vertex in the middle */
+  const double *angle_k, *angle_theta0; /* E = 1/2 k (theta - theta0)^2, radians */
+  int32_t n_dihedrals;  /* one entry per periodic term */
+  const int32_t *dihedral_atoms; /* [n_dihedrals][4] */
+  const int32_t *dihedral_n;
+  const double *dihedral_k, *dihedral_delta; /* E = k (1 + cos(n phi - delta)) */
+  /* Langevin parameters */
+  double kT, gamma, dt;
+  /* state definition (Sections 2.2 and 3.3) */
+  int32_t cv_kind;
+  int32_t cv_atoms[8];
+  double cv_params[8];
+  /* atom groups (centres of mass for CVs and observables) */
+  int32_t n_groups;
+  int32_t group_offsets[ORC_MAX_GROUPS + 1];
+  const int32_t *group_atoms;
+  /* Gelman-Rubin observables (Section 2.4.1) */
+  int32_t n_obs;
+  int32_t obs_kind[ORC_MAX_OBS];
+  int32_t obs_arg[ORC_MAX_OBS][4];
+} orc_system;
+
+typedef struct orc_ctx orc_ctx;
+
+orc_ctx *orc_create(const orc_system *sys);
+void orc_destroy(orc_ctx *c);
+
+/* Potential and forces (-grad V), Eq. 1. */
+double orc_potential(const orc_ctx *c, const double *q);
+void orc_forces(const orc_ctx *c, const double *q, double *f);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the Philox S-box on a 128-bit
+ * counter with a 64-bit key. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Four standard normals for (seed, replica, step, atom): Box-Muller on the four Philox words of
+ * stream 0. */
+void orc_normals(uint64_t seed, int64_t step, int32_t replica, int32_t atom, double xi[4]);
+/* First Philox word of stream 1 for (seed, step, replica): the Fleming-Viot branching draw. */
+uint32_t orc_branch_word(uint64_t seed, int64_t step, int32_t replica);
+
+/* One BAOAB step of Eq. 1 for one replica; f holds F(q) on entry and on exit. */
+void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t seed,
+                    int32_t replica, int64_t step);
+
+/* State functions of Section 3.3: (i) index of the state containing q, -1 if none;
+ * (ii) whether q is outside the state omega. */
+int32_t orc_state_of(const orc_ctx *c, const double *q);
+int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega);
+/* Collective variables of the state definition: cv[0..1] (phi/psi in degrees, x, or distance). */
+void orc_cv(const orc_ctx *c, const double *q, double cv[2]);
+/* Observable j of Section 2.4.1 (iii). */
+double orc_observable(const orc_ctx *c, int32_t j, const double *q, const double *p);
+
+/* Gelman-Rubin ratio, Eq. 3, with the time integrals of Eq. 2 replaced by sample means over
+ * samples[n_rep][n_samp].  +inf when the denominator is not positive. */
+double orc_gelman_rubin(int32_t n_rep, int32_t n_samp, const double *samples);
+
+/* Fleming-Viot branching (Section 2.4.1, task 2): for every exited worker r >= 1, src[r] = a
+ * survivor drawn uniformly among the non-exited workers; src[r] = -1 otherwise; src[0] = -1.
+ * When no worker survives, every exited worker takes src = 0 (the reference walker).
+ * Returns the number of branched workers. */
+int32_t orc_fv_branch(uint64_t seed, int64_t step, int32_t n_rep, const uint8_t *exited,
+                      int32_t *src);
+
+/* Advance n_rep replicas by k BAOAB steps starting at global step t0 and phase step tp0; after
+ * every step where (tp0 + i + 1) % t_gr == 0 (t_gr > 0) the observables of every replica are
+ * appended to samples[r][s][j] (s counted from 0; capacity cap per replica).  Returns the number
+ * of samples taken per replica. */
+int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
+                   uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
+                   double *samples, int32_t cap);
+
+/* Parallel dynamics step (Section 2.4.2): every replica advances t_check steps at a time until
+ * one has exited omega.  M = number of checks, k = lowest 1-based index exited at check M,
+ * tau_steps = [N (M-1) + k] t_check (Eq. 5).  Returns 1 on exit, 0 if max_checks passed. */
+typedef struct {
+  int64_t M;
+  int32_t k;
+  int32_t label_to;
+  int64_t tau_steps;
+} orc_exit;
+int32_t orc_parallel_phase(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
+                           uint64_t seed, int64_t t0, int32_t omega, int32_t t_check,
+                           int64_t max_checks, orc_exit *out);
+
+/* Events of the whole loop of Fig. 1. */
+enum { ORC_EV_TRANSIENT = 0, ORC_EV_REF_EXIT = 1, ORC_EV_FV_CONVERGED = 2, ORC_EV_PARALLEL_EXIT = 3,
+       ORC_EV_FV_ALL_EXITED = 4 };
+typedef struct {
+  int32_t kind;
+  int32_t omega;     /* state the event belongs to (-1 for a transient) */
+  int32_t label_to;  /* state index after the event (-1: none) */
+  int32_t k;         /* parallel exit: 1-based replica index */
+  int64_t M;         /* parallel exit: number of checks */
+  int64_t steps;     /* t_reach, t_ref, t_FV or tau, in steps */
+  int64_t t_sim;     /* simulation clock after the event, in steps */
+  int64_t n_branch;  /* F-V: number of branchings during the phase */
+} orc_event;
+
+typedef struct {
+  int32_t n_rep;
+  uint64_t seed;
+  int32_t t_gr, t_check;
+  double tol;
+  int64_t min_fv_steps;
+  int64_t max_steps;   /* bound on the global step counter */
+  int32_t max_exits;   /* stop after this many parallel exits or reference exits */
+} orc_run_params;
+
+/* Whole Gen. ParRep loop of Fig. 1 from the reference configuration (q0, p0).  Writes at most
+ * max_events events; returns the number written, and the global step counter in *t_global. */
+int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const double *q0,
+                          const double *p0, orc_event *events, int32_t max_events,
+                          int64_t *t_global);
+
+/* Plain Langevin trajectory (replica index 0) checked every t_check steps; residence times (in
+ * steps) from the check at which a state is entered to the check at which it is exited.  Returns
+ * the number recorded. */
+int32_t orc_run_bruteforce(const orc_ctx *c, uint64_t seed, int32_t t_check, const double *q0,
+                           const double *p0, int64_t max_steps, int64_t *residence,
+                           int32_t *from_state, int32_t max_res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,245 @@
+"""Seeded synthetic workloads shaped like the paper's systems.
+
+This module is shared by the CUDA binding, the oracle, the tests and the benchmark.  It holds none
+of the method's arithmetic: it only builds geometries (a chain from internal coordinates) and draws
+force-field parameters, initial momenta and system sizes from seeded numpy generators.
+
+Systems (stand-ins for the paper's workloads, whose force fields and structures are not available):
+  * ``double_well_2d``  - one particle in V(x, y) = 5 (x^2 - 1)^2 + 2.5 y^2 (dimensionless, kT = 1),
+    two states = the cores |x| > 0.3 of the two basins; used for the brute-force exit-time check.
+  * ``chain``           - a 22-bead (or n-bead) peptide-like chain shaped like alanine dipeptide
+    (Section 4.1): harmonic bonds and angles, periodic dihedrals, LJ + Coulomb with eps = 4r; the
+    two states are the paper's (phi, psi) rectangle and its complement.
+  * ``batched_chains``  - independent chains of uneven sizes for the batched path.
+  * ``ligand_receptor`` - a packed-globule receptor with an elastic network and a short ligand chain
+    in a surface pocket, shaped like the FKBP-DMSO dissociation problem (Section 4.2).
+
+Units for the particle systems: nm, ps, amu, kJ/mol, elementary charge.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+KB_KJ_PER_MOL_K = 0.0083144626
+COULOMB_K = 138.935458  # kJ mol^-1 nm e^-2
+
+POT_DOUBLE_WELL_2D = 0
+POT_FORCE_FIELD = 1
+
+CV_DOUBLE_WELL = 0
+CV_DIHEDRAL_RECT = 1
+CV_COM_DISTANCE = 2
+
+OBS_COORD = 0
+OBS_POTENTIAL = 1
+OBS_KINETIC = 2
+OBS_DIHEDRAL = 3
+OBS_GROUP_DISTANCE = 4
+OBS_RMS_VELOCITY = 5
+
+
+@dataclasses.dataclass
+class System:
+    name: str
+    n_atoms: int
+    dim: int
+    potential: int
+    mass: np.ndarray
+    kT: float
+    gamma: float
+    dt: float
+    dw_a: float = 0.0
+    dw_b: float = 0.0
+    sigma: np.ndarray | None = None
+    epsilon: np.ndarray | None = None
+    charge: np.ndarray | None = None
+    excl: np.ndarray | None = None          # [m, 2] int32
+    cutoff: float = 0.0
+    coulomb_k: float = 0.0
+    bonds: np.ndarray | None = None         # [nb, 2]
+    bond_k: np.ndarray | None = None
+    bond_r0: np.ndarray | None = None
+    angles: np.ndarray | None = None        # [na, 3]
+    angle_k: np.ndarray | None = None
+    angle_theta0: np.ndarray | None = None
+    dihedrals: np.ndarray | None = None     # [nd, 4]
+    dihedral_n: np.ndarray | None = None
+    dihedral_k: np.ndarray | None = None
+    dihedral_delta: np.ndarray | None = None
+    cv_kind: int = CV_DOUBLE_WELL
+    cv_atoms: tuple = ()
+    cv_params: tuple = ()
+    groups: list = dataclasses.field(default_factory=list)
+    observables: list = dataclasses.field(default_factory=list)  # (kind, (args...))
+    q0: np.ndarray | None = None            # [n, dim]
+    p0: np.ndarray | None = None            # [n, dim]
+    # Gen. ParRep parameters (Sections 2.4.1 and 3.4)
+    n_replicas: int = 32
+    t_gr: int = 10
+    t_check: int = 100
+    tol: float = 0.01
+    min_fv_steps: int = 0
+
+    def empty_arrays(self):
+        """Return zero-length arrays for the force-field fields a system does not use."""
+        z_i2 = np.zeros((0, 2), np.int32)
+        out = {}
+        out["sigma"] = self.sigma if self.sigma is not None else np.zeros(self.n_atoms)
+        out["epsilon"] = self.epsilon if self.epsilon is not None else np.zeros(self.n_atoms)
+        out["charge"] = self.charge if self.charge is not None else np.zeros(self.n_atoms)
+        out["excl"] = self.excl if self.excl is not None else z_i2
+        out["bonds"] = self.bonds if self.bonds is not None else z_i2
+        out["bond_k"] = self.bond_k if self.bond_k is not None else np.zeros(0)
+        out["bond_r0"] = self.bond_r0 if self.bond_r0 is not None else np.zeros(0)
+        out["angles"] = self.angles if self.angles is not None else np.zeros((0, 3), np.int32)
+        out["angle_k"] = self.angle_k if self.angle_k is not None else np.zeros(0)
+        out["angle_theta0"] = self.angle_theta0 if self.angle_theta0 is not None else np.zeros(0)
+        out["dihedrals"] = self.dihedrals if self.dihedrals is not None else np.zeros((0, 4), np.int32)
+        out["dihedral_n"] = self.dihedral_n if self.dihedral_n is not None else np.zeros(0, np.int32)
+        out["dihedral_k"] = self.dihedral_k if self.dihedral_k is not None else np.zeros(0)
+        out["dihedral_delta"] = self.dihedral_delta if self.dihedral_delta is not None else np.zeros(0)
+        return out
+
+
+def maxwell_boltzmann(mass: np.ndarray, kT: float, dim: int, rng: np.random.Generator) -> np.ndarray:
+    """Momenta p_i ~ N(0, m_i kT) per component."""
+    return rng.standard_normal((mass.shape[0], dim)) * np.sqrt(mass * kT)[:, None]
+
+
+def double_well_2d(seed: int = 2431, n_replicas: int = 32) -> System:
+    """One particle, V = 5 (x^2-1)^2 + 2.5 y^2, kT = 1, m = 1, gamma = 1, dt = 1e-3, q0 = (-1, 0)."""
+    rng = np.random.default_rng(seed)
+    mass = np.ones(1)
+    s = System(
+        name="double_well_2d", n_atoms=1, dim=2, potential=POT_DOUBLE_WELL_2D, mass=mass,
+        kT=1.0, gamma=1.0, dt=1e-3, dw_a=5.0, dw_b=2.5,
+        cv_kind=CV_DOUBLE_WELL, cv_params=(0.3,),
+        observables=[(OBS_COORD, (0, 0)), (OBS_POTENTIAL, ())],
+        n_replicas=n_replicas, t_gr=10, t_check=100, tol=0.01, min_fv_steps=2000,
+    )
+    s.q0 = np.array([[-1.0, 0.0]])
+    s.p0 = maxwell_boltzmann(mass, s.kT, 2, rng)
+    return s
+
+
+def _place(a, b, c, bond, angle, torsion):
+    """Natural-extension reference frame: the point d with |cd| = bond, angle(b, c, d) = angle and
+    dihedral(a, b, c, d) = torsion (radians)."""
+    bc = c - b
+    bc /= np.linalg.norm(bc)
+    n = np.cross(b - a, bc)
+    n /= np.linalg.norm(n)
+    m = np.cross(n, bc)
+    d2 = np.array([-bond * math.cos(angle),
+                   bond * math.sin(angle) * math.cos(torsion),
+                   bond * math.sin(angle) * math.sin(torsion)])
+    return c + d2[0] * bc + d2[1] * m + d2[2] * n
+
+
+def _chain_geometry(n, bond, angle, torsions):
+    x = np.zeros((n, 3))
+    x[1] = [bond, 0.0, 0.0]
+    x[2] = x[1] + bond * np.array([-math.cos(angle), math.sin(angle), 0.0])
+    for i in range(3, n):
+        x[i] = _place(x[i - 3], x[i - 2], x[i - 1], bond, angle, torsions[i - 3])
+    return x
+
+
+def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas: int = 256,
+          temperature: float = 300.0) -> System:
+    """Peptide-like bead chain shaped like alanine dipeptide (Section 4.1 stand-in).
+
+    Bonds k = 3e5 kJ/mol/nm^2, r0 = 0.15 nm; angles k = 400 kJ/mol/rad^2, theta0 = 110 deg; each
+    dihedral (i, i+1, i+2, i+3) has terms n = 1, 2, 3 with k ~ U[0, 8] kJ/mol, delta in {0, pi};
+    LJ sigma ~ U[0.25, 0.35] nm, eps ~ U[0.2, 0.8] kJ/mol (Lorentz-Berthelot); charges ~ N(0, 0.3)
+    shifted to zero net; Coulomb with eps = 4r; 1-2 and 1-3 pairs excluded; no cutoff; mass 12 amu;
+    gamma = 1/ps, dt = 2 fs.  States: phi = dihedral(c-2, c-1, c, c+1), psi = dihedral(c-1, c, c+1,
+    c+2) around the central bead c = n//2 - 1 (beads 9..13 for n = 22); state 0 is the paper's
+    rectangle phi in [0, 120], psi in [-170, 0] (degrees), state 1 its complement.  The initial
+    central angles are the paper's starting point (phi, psi) = (-81, 70) degrees, in state 1.
+    """
+    rng = np.random.default_rng(seed)
+    n = n_atoms
+    mass = np.full(n, 12.0)
+    sigma = rng.uniform(0.25, 0.35, n)
+    epsilon = rng.uniform(0.2, 0.8, n)
+    charge = rng.normal(0.0, 0.3, n)
+    charge -= charge.mean()
+    bonds = np.array([[i, i + 1] for i in range(n - 1)], np.int32)
+    angles = np.array([[i, i + 1, i + 2] for i in range(n - 2)], np.int32)
+    dih, dn, dk, dd = [], [], [], []
+    for i in range(n - 3):
+        for mult in (1, 2, 3):
+            dih.append([i, i + 1, i + 2, i + 3])
+            dn.append(mult)
+            dk.append(rng.uniform(0.0, 8.0))
+            dd.append(math.pi * rng.integers(0, 2))
+    excl = np.array([[i, j] for i in range(n) for j in range(i + 1, min(n, i + 3))], np.int32)
+    c = n // 2 - 1
+    phi_idx, psi_idx = c - 2, c - 1  # torsion index t describes dihedral (t, t+1, t+2, t+3)
+    bond, angle = 0.15, math.radians(110.0)
+    while True:
+        tors = []
+        for t in range(n - 3):
+            if rng.random() < 0.7:
+                tors.append(math.radians(180.0 + rng.uniform(-20.0, 20.0)))
+            else:
+                tors.append(math.radians(rng.choice([-65.0, 65.0]) + rng.uniform(-10.0, 10.0)))
+        if n - 3 > psi_idx:
+            tors[phi_idx] = math.radians(-81.0)
+            tors[psi_idx] = math.radians(70.0)
+        x = _chain_geometry(n, bond, angle, tors)
+        ok = True
+        for i in range(n):
+            for j in range(i + 3, n):
+                if np.linalg.norm(x[i] - x[j]) < 0.8 * 0.5 * (sigma[i] + sigma[j]):
+                    ok = False
+        if ok:
+            break
+    x -= x.mean(axis=0)
+    kT = KB_KJ_PER_MOL_K * temperature
+    s = System(
+        name=f"chain{n}", n_atoms=n, dim=3, potential=POT_FORCE_FIELD, mass=mass,
+        kT=kT, gamma=1.0, dt=0.002, sigma=sigma, epsilon=epsilon, charge=charge, excl=excl,
+        cutoff=0.0, coulomb_k=COULOMB_K,
+        bonds=bonds, bond_k=np.full(n - 1, 3.0e5), bond_r0=np.full(n - 1, bond),
+        angles=angles, angle_k=np.full(n - 2, 400.0), angle_theta0=np.full(n - 2, angle),
+        dihedrals=np.array(dih, np.int32).reshape(-1, 4), dihedral_n=np.array(dn, np.int32),
+        dihedral_k=np.array(dk), dihedral_delta=np.array(dd),
+        cv_kind=CV_DIHEDRAL_RECT, cv_atoms=(c - 2, c - 1, c, c + 1, c + 2),
+        cv_params=(0.0, 120.0, -170.0, 0.0),
+        observables=[(OBS_POTENTIAL, ()), (OBS_KINETIC, ()),
+                     (OBS_DIHEDRAL, (c - 2, c - 1, c, c + 1)),
+                     (OBS_DIHEDRAL, (c - 1, c, c + 1, c + 2))],
+        n_replicas=n_replicas, t_gr=10, t_check=500, tol=0.01, min_fv_steps=0,
+    )
+    s.q0 = x
+    s.p0 = maxwell_boltzmann(mass, kT, 3, np.random.default_rng(dyn_seed))
+    return s
+
+
+def batched_sizes(n_runs: int = 64, seed: int = 1807, lo: int = 22, hi: int = 400) -> np.ndarray:
+    """Chain sizes drawn uniformly in [lo, hi] for the batched workload."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, n_runs)
+
+
+def batched_chains(n_runs: int = 64, seed: int = 1807, n_replicas: int = 128, lo: int = 22,
+                   hi: int = 400) -> list[System]:
+    """Independent chains of uneven sizes, one Gen. ParRep run each (seeds 1807 + run)."""
+    sizes = batched_sizes(n_runs, seed, lo, hi)
+    return [chain(int(nb), seed=seed + r, dyn_seed=2431 + r, n_replicas=n_replicas)
+            for r, nb in enumerate(sizes)]
+
+
+def replica_states(s: System, n_replicas: int, seed: int, spread: float = 0.0):
+    """Per-replica (q, p) [R, n, dim]: the system's q0 plus optional Gaussian displacement of scale
+    `spread`, and Maxwell-Boltzmann momenta; used by parity tests that need distinct replicas."""
+    rng = np.random.default_rng(seed)
+    q = np.repeat(s.q0[None], n_replicas, axis=0).astype(np.float64)
+    if spread > 0:
+        q = q + spread * rng.standard_normal(q.shape)
+    p = np.stack([maxwell_boltzmann(s.mass, s.kT, s.dim, rng) for _ in range(n_replicas)])
+    return np.ascontiguousarray(q), np.ascontiguousarray(p)
