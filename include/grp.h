@@ -1,0 +1,232 @@
+/*
+ * grp.h — C ABI of libgrp.so: the data-parallel hot path of Generalized Parallel Replica dynamics
+ * (Hedin & Lelievre, "gen.parRep: a first implementation of the Generalized Parallel Replica
+ * dynamics for the long time simulation of metastable biochemical systems") on one NVIDIA GB300.
+ *
+ * Conventions for every call:
+ *  - Handles (grp_system, grp_replicas) are opaque and owned by the library; destroy them with the
+ *    matching grp_destroy_* call.
+ *  - Pointer arguments named h_* are host memory, d_* are device memory of the current CUDA device
+ *    (for instance the data pointer of a CUDA torch tensor).  The caller owns them; the library
+ *    never keeps them after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are ordered
+ *    on that stream; calls that return host values synchronise it before returning.
+ *  - Every call returns GRP_OK (0) or a negative grp_status; nothing aborts.  grp_last_error()
+ *    returns a thread-local message describing the last failure (library-owned string).  Device-side
+ *    faults detected by the kernels (non-finite state, fixed-point overflow) are latched in a sticky
+ *    per-replica-set error word and reported by the next synchronising call.
+ *  - Replica 0 is the reference walker of Section 2.4.1; indices are 0-based except the exit index
+ *    k of Eq. 5, which is 1-based as in the paper.
+ *  - State layout on the device and in h_q / h_p: [n_replicas][n_atoms][dim] row-major FP64.
+ */
+#ifndef GRP_H
+#define GRP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t grp_status;
+#define GRP_OK 0
+#define GRP_EINVAL (-1)    /* invalid argument (null pointer, bad size, bad index) */
+#define GRP_ENOMEM (-2)    /* device or host allocation failed */
+#define GRP_ECUDA (-3)     /* a CUDA runtime call failed */
+#define GRP_ENAN (-4)      /* a kernel found a non-finite position or momentum */
+#define GRP_EOVERFLOW (-5) /* a force contribution exceeded the fixed-point range (|f| >= 2^20) */
+#define GRP_ETIMEOUT (-6)  /* a bounded loop ran out before its condition was met */
+#define GRP_ENOTIMPL (-7)  /* the requested combination is not supported */
+#define GRP_NOEXIT 1       /* positive: the parallel phase ended after max_checks without exit */
+
+/* Precision of the compute path. */
+enum { GRP_FP64 = 0,  /* FP64 forces, FP64 integration, FP64 noise */
+       GRP_MIXED = 1  /* FP32 forces into 64-bit fixed point, double-single integration,
+                         FP32 noise; FP64 only for state in memory, CV near boundaries, G-R */ };
+
+enum { GRP_POT_DOUBLE_WELL_2D = 0, GRP_POT_FORCE_FIELD = 1 };
+enum { GRP_CV_DOUBLE_WELL = 0, GRP_CV_DIHEDRAL_RECT = 1, GRP_CV_COM_DISTANCE = 2 };
+enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DIHEDRAL = 3,
+       GRP_OBS_GROUP_DISTANCE = 4, GRP_OBS_RMS_VELOCITY = 5 };
+#define GRP_MAX_OBS 8
+#define GRP_MAX_GROUPS 4
+
+/* Molecular system and Langevin parameters (Section 2.1, Eq. 1; Sections 2.2, 3.3 for the states;
+ * Section 2.4.1 for the observables).  All pointers are host memory, copied by grp_create_system.
+ *   potential GRP_POT_DOUBLE_WELL_2D: one particle, dim = 2, V = dw_a (x^2 - 1)^2 + dw_b y^2.
+ *   potential GRP_POT_FORCE_FIELD: dim = 3, V = sum of
+ *     bonds 1/2 k (r - r0)^2, angles 1/2 k (theta - theta0)^2 (radians), dihedral terms
+ *     k (1 + cos(n phi - delta)), Lennard-Jones 4 eps_ij ((s_ij/r)^12 - (s_ij/r)^6) with
+ *     s_ij = (s_i + s_j)/2, eps_ij = sqrt(eps_i eps_j), and Coulomb k_e q_i q_j / (4 r^2)
+ *     (dielectric 4r), over every pair not in excl, truncated at `cutoff` when cutoff > 0.
+ *   States: GRP_CV_DOUBLE_WELL: state 0 = {x < -w}, state 1 = {x > w} (w = cv_params[0]);
+ *     state 0 is left when x >= 0, state 1 when x < 0.  GRP_CV_DIHEDRAL_RECT: phi = dihedral of
+ *     cv_atoms[0..3], psi of cv_atoms[1..4] (degrees, IUPAC sign); state 0 = phi in
+ *     [cv_params[0], cv_params[1]] and psi in [cv_params[2], cv_params[3]], state 1 = complement.
+ *     GRP_CV_COM_DISTANCE: d = |COM(group 0) - COM(group 1)|; state 0 = {d < cv_params[0]},
+ *     state 1 = complement.
+ *   Observables: GRP_OBS_COORD (atom, axis), POTENTIAL, KINETIC, DIHEDRAL (4 atoms, radians),
+ *     GROUP_DISTANCE (group a, group b), RMS_VELOCITY (group). */
+typedef struct {
+  int32_t n_atoms;
+  int32_t dim;
+  int32_t potential;
+  int32_t precision;
+  const double *mass;
+  double dw_a, dw_b;
+  const double *sigma, *epsilon, *charge;
+  int32_t n_excl;
+  const int32_t *excl;          /* [n_excl][2] */
+  double cutoff;
+  double coulomb_k;
+  int32_t n_bonds;
+  const int32_t *bond_atoms;    /* [n_bonds][2] */
+  const double *bond_k, *bond_r0;
+  int32_t n_angles;
+  const int32_t *angle_atoms;   /* [n_angles][3], vertex in the middle */
+  const double *angle_k, *angle_theta0;
+  int32_t n_dihedrals;          /* one entry per periodic term */
+  const int32_t *dihedral_atoms; /* [n_dihedrals][4] */
+  const int32_t *dihedral_n;
+  const double *dihedral_k, *dihedral_delta;
+  double kT, gamma, dt;         /* gamma is a collision rate: c1 = exp(-gamma dt) */
+  int32_t cv_kind;
+  int32_t cv_atoms[8];
+  double cv_params[8];
+  int32_t n_groups;
+  int32_t group_offsets[GRP_MAX_GROUPS + 1];
+  const int32_t *group_atoms;
+  int32_t n_obs;
+  int32_t obs_kind[GRP_MAX_OBS];
+  int32_t obs_arg[GRP_MAX_OBS][4];
+} grp_system_desc;
+
+typedef struct grp_system grp_system;
+typedef struct grp_replicas grp_replicas;
+
+/* Step counters of a replica set.  t_global keys the noise (Philox counter), t_phase counts steps
+ * since the last broadcast (the F-V time t of Eqs. 2-4, sampled every t_GR). */
+typedef struct {
+  int64_t t_global;
+  int64_t t_phase;
+} grp_counters;
+
+/* Result of the parallel dynamics step (Section 2.4.2). */
+typedef struct {
+  int64_t M;          /* number of checks performed, the exit being seen at check M */
+  int32_t k;          /* 1-based index of the lowest replica exited at check M */
+  int32_t label_to;   /* state of X_tau^k (-1: in no state) */
+  int64_t tau_steps;  /* [N (M - 1) + k] t_check, Eq. 5 */
+} grp_exit;
+
+/* Device pointers of a replica set, for zero-copy access (valid until grp_destroy_replicas). */
+typedef struct {
+  double *q, *p, *f;  /* [R][n][dim] positions, momenta, forces F(q) */
+  double *acc;        /* [R][n_obs][4]: shift c, sum (O - c), sum (O - c)^2, sample count */
+  int8_t *labels;     /* [R] state index from the last check (-1: none) */
+  uint8_t *exited;    /* [R] 1 when the replica was outside omega at the last check */
+} grp_device_view;
+
+/* Parameters of the whole loop of Fig. 1. */
+typedef struct {
+  int32_t t_gr;          /* observable sampling period, steps (Section 3.4) */
+  int32_t t_check;       /* exit-test period, steps */
+  double tol;            /* Gelman-Rubin tolerance: converged when every R < 1 + tol (Eq. 4) */
+  int64_t min_fv_steps;  /* no convergence before this many F-V steps */
+  int64_t max_steps;     /* bound on the global step counter */
+  int32_t max_exits;     /* stop after this many reference or parallel exits */
+} grp_run_params;
+
+enum { GRP_EV_TRANSIENT = 0, GRP_EV_REF_EXIT = 1, GRP_EV_FV_CONVERGED = 2, GRP_EV_PARALLEL_EXIT = 3,
+       GRP_EV_FV_ALL_EXITED = 4 };
+typedef struct {
+  int32_t kind;
+  int32_t omega;      /* state of the visit (-1 for a transient) */
+  int32_t label_to;   /* state after the event (-1: none) */
+  int32_t k;          /* parallel exit: 1-based replica index */
+  int64_t M;          /* parallel exit: number of checks */
+  int64_t steps;      /* t_reach, t_ref, t_FV or tau, in steps */
+  int64_t t_sim;      /* simulation clock after the event, in steps */
+  int64_t n_branch;   /* F-V: branchings during the phase */
+} grp_event;
+
+/* Thread-local description of the last error (library-owned, valid until the next call). */
+const char *grp_last_error(void);
+
+/* Build a system on the current device from a host description (copied).  Validates every index
+ * and size (GRP_EINVAL).  Section 2.1 (Eq. 1) and Section 3.2 (the engine's requirements). */
+grp_status grp_create_system(const grp_system_desc *d, grp_system **out);
+void grp_destroy_system(grp_system *s);
+
+/* Allocate n_replicas >= 1 replicas of s on the device; every replica starts at (h_q0, h_p0), a
+ * host [n][dim] configuration (per_replica = 0) or host [n_replicas][n][dim] (per_replica = 1);
+ * forces are evaluated at q0, counters and accumulators are zero.  `seed` keys the Philox4x32-10
+ * noise: counter (t_global, stream, replica, atom).  Section 2.4.1 (replicas, reference walker). */
+grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint64_t seed, const double *h_q0,
+                             const double *h_p0, int32_t per_replica, void *stream,
+                             grp_replicas **out);
+void grp_destroy_replicas(grp_replicas *r);
+
+/* Advance replicas [0, n_active) by k BAOAB steps of Eq. 1 (n_active = 0: all).  After each step
+ * that brings t_phase to a multiple of t_gr (t_gr > 0) every observable of the active replicas is
+ * accumulated (Eq. 2 with the time integral replaced by samples every t_GR, Section 2.4.1).
+ * Increments t_global and t_phase by k.  Section 3.2: "one code block realising discretisation
+ * steps". */
+grp_status grp_step_k(grp_replicas *r, int64_t k, int32_t t_gr, int32_t n_active, void *stream);
+
+/* State functions of Section 3.3 for every replica: d_labels[r] = state containing replica r
+ * (-1: none), d_exited[r] = 1 when replica r is outside omega.  Either pointer may be NULL; the
+ * results are also kept in the replica set (grp_device_view). */
+grp_status grp_check_states(grp_replicas *r, int32_t omega, int8_t *d_labels, uint8_t *d_exited,
+                            void *stream);
+
+/* Fleming-Viot branching (Section 2.4.1, task 2): every worker r >= 1 with d_exited[r] = 1 is
+ * overwritten by a copy of a surviving worker drawn uniformly (Philox stream 1, counter
+ * (t_global, replica r)): positions, momenta, forces and its observable history (Section 3.1).
+ * When no worker survives, exited workers copy the reference walker.  d_exited NULL = the mask of
+ * the last grp_check_states.  d_src (device [R], optional) receives the source index or -1;
+ * h_n_branched (optional) the number of copies.  The reference walker (replica 0) is never
+ * branched. */
+grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, int32_t *d_src,
+                         int32_t *h_n_branched, void *stream);
+
+/* Gelman-Rubin ratios of Eq. 3 over the F-V workers (replicas 1..R-1) for every observable, from
+ * the accumulated samples; h_rhat[n_obs] receives R_j (+inf when undefined) and h_converged
+ * whether every R_j < 1 + tol (Eq. 4).  Either pointer may be NULL. */
+grp_status grp_gelman_rubin(grp_replicas *r, double tol, double *h_rhat, int32_t *h_converged,
+                            void *stream);
+
+/* Parallel dynamics step (Section 2.4.2): all replicas advance t_check steps at a time until one
+ * is outside omega, at most max_checks times.  Returns GRP_OK with h_out = (M, k, label_to, tau)
+ * of Eq. 5, or GRP_NOEXIT.  Replica k-1 then holds X_tau^k. */
+grp_status grp_run_parallel_phase(grp_replicas *r, int32_t omega, int32_t t_check, int64_t max_checks,
+                                  grp_exit *h_out, void *stream);
+
+/* Copy replica src to every replica, clear the accumulators and set t_phase = 0 (the broadcast of
+ * the reference configuration before a convergence step, Section 3.1). */
+grp_status grp_broadcast(grp_replicas *r, int32_t src, void *stream);
+
+/* Whole loop of Fig. 1 from the current state of replica 0: transient, convergence (F-V with
+ * Gelman-Rubin), parallel step, clock updates (Section 2.4.1, Eq. 6).  Writes at most max_events
+ * events to h_events, their count to h_n_events, and the final clock to h_t_sim (optional). */
+grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
+                   int32_t *h_n_events, int64_t *h_t_sim, void *stream);
+
+/* Checkpoint and resume: copy positions, momenta, accumulators (each optional) and counters
+ * between the replica set and host memory.  grp_set_state re-evaluates the forces. */
+grp_status grp_get_state(grp_replicas *r, double *h_q, double *h_p, double *h_acc, grp_counters *h_ctr,
+                         void *stream);
+grp_status grp_set_state(grp_replicas *r, const double *h_q, const double *h_p, const double *h_acc,
+                         const grp_counters *h_ctr, void *stream);
+
+/* Device pointers of the replica set. */
+grp_status grp_get_device_view(grp_replicas *r, grp_device_view *out);
+
+/* Potential energy and forces of B configurations (device [B][n][dim] FP64) with the system's
+ * precision: d_energy[B] (optional) and d_forces [B][n][dim] (optional). */
+grp_status grp_energy_forces(grp_system *s, int32_t n_conf, const double *d_q, double *d_energy,
+                             double *d_forces, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

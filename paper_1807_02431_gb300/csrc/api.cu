@@ -1,0 +1,674 @@
+// C ABI of libgrp (include/grp.h): argument validation, device buffers, and the host driver of the
+// Gen. ParRep loop of Fig. 1.  Every step of the hot path runs in the kernels of segment.cu and
+// fvgr.cu; the host only launches them and reads a few bytes per exit test.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace grp;
+
+namespace {
+thread_local std::string g_last_error;
+
+grp_status fail(grp_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(GRP_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+grp_status upload(std::vector<void *> &owned, const T *h, size_t n, const T **out) {
+  *out = nullptr;
+  if (n == 0) return GRP_OK;
+  void *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, n * sizeof(T));
+  if (e != cudaSuccess) return fail(GRP_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+  owned.push_back(d);
+  e = cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(GRP_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+  *out = (const T *)d;
+  return GRP_OK;
+}
+}  // namespace
+
+struct grp_system {
+  SysDev dev{};
+  SegConfig seg{};
+  std::vector<void *> owned;
+  int device = 0;
+};
+
+struct grp_replicas {
+  grp_system *sys = nullptr;
+  int R = 0;
+  uint64_t seed = 0;
+  double *q = nullptr, *p = nullptr, *f = nullptr, *acc = nullptr;
+  int8_t *labels = nullptr;
+  uint8_t *exited = nullptr;
+  int32_t *src = nullptr;
+  unsigned long long *exit_key = nullptr;
+  int *err = nullptr;
+  int *n_branched = nullptr;
+  double *rhat = nullptr;
+  long long t_global = 0, t_phase = 0;
+  // pinned host mirror of the small per-check readback
+  struct Readback {
+    unsigned long long exit_key;
+    int err;
+    int n_branched;
+    int8_t label0;
+    uint8_t exited0;
+    int8_t pad[6];
+    double rhat[GRP_MAX_OBS];
+  } *hb = nullptr;
+};
+
+extern "C" const char *grp_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------------------------
+extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **out) {
+  if (!d || !out) return fail(GRP_EINVAL, "grp_create_system: null argument");
+  *out = nullptr;
+  const int n = d->n_atoms;
+  if (d->potential != GRP_POT_DOUBLE_WELL_2D && d->potential != GRP_POT_FORCE_FIELD)
+    return fail(GRP_EINVAL, "unknown potential %d", d->potential);
+  if (d->precision != GRP_FP64 && d->precision != GRP_MIXED)
+    return fail(GRP_EINVAL, "unknown precision %d", d->precision);
+  if (d->potential == GRP_POT_DOUBLE_WELL_2D) {
+    if (n != 1 || d->dim != 2) return fail(GRP_EINVAL, "double well needs n_atoms = 1, dim = 2");
+  } else if (d->dim != 3 || n < 1 || n > 65535) {
+    return fail(GRP_EINVAL, "force field needs dim = 3 and 1 <= n_atoms <= 65535 (got %d, %d)", d->dim, n);
+  }
+  if (!d->mass) return fail(GRP_EINVAL, "mass is null");
+  for (int i = 0; i < n; ++i)
+    if (!(d->mass[i] > 0)) return fail(GRP_EINVAL, "mass[%d] must be > 0", i);
+  if (!(d->kT > 0) || !(d->dt > 0) || !(d->gamma >= 0)) return fail(GRP_EINVAL, "need kT > 0, dt > 0, gamma >= 0");
+  if (d->n_obs < 0 || d->n_obs > GRP_MAX_OBS) return fail(GRP_EINVAL, "n_obs must be in [0, %d]", GRP_MAX_OBS);
+  if (d->n_groups < 0 || d->n_groups > GRP_MAX_GROUPS) return fail(GRP_EINVAL, "n_groups out of range");
+  for (int g = 0; g < d->n_groups; ++g)
+    if (d->group_offsets[g] < 0 || d->group_offsets[g + 1] <= d->group_offsets[g])
+      return fail(GRP_EINVAL, "group %d is empty or offsets decrease", g);
+  const int n_group_atoms = d->n_groups > 0 ? d->group_offsets[d->n_groups] : 0;
+  if (n_group_atoms > 0 && !d->group_atoms) return fail(GRP_EINVAL, "group_atoms is null");
+  for (int t = 0; t < n_group_atoms; ++t)
+    if (d->group_atoms[t] < 0 || d->group_atoms[t] >= n) return fail(GRP_EINVAL, "group atom %d out of range", t);
+  auto bad_atom = [&](int a) { return a < 0 || a >= n; };
+  for (int j = 0; j < d->n_obs; ++j) {
+    const int k = d->obs_kind[j];
+    const int *a = d->obs_arg[j];
+    if (k == GRP_OBS_COORD) {
+      if (bad_atom(a[0]) || a[1] < 0 || a[1] >= d->dim) return fail(GRP_EINVAL, "observable %d: bad atom/axis", j);
+    } else if (k == GRP_OBS_DIHEDRAL) {
+      if (d->dim != 3 || bad_atom(a[0]) || bad_atom(a[1]) || bad_atom(a[2]) || bad_atom(a[3]))
+        return fail(GRP_EINVAL, "observable %d: bad dihedral atoms", j);
+    } else if (k == GRP_OBS_GROUP_DISTANCE) {
+      if (d->dim != 3 || a[0] < 0 || a[0] >= d->n_groups || a[1] < 0 || a[1] >= d->n_groups)
+        return fail(GRP_EINVAL, "observable %d: bad groups", j);
+    } else if (k == GRP_OBS_RMS_VELOCITY) {
+      if (d->dim != 3 || a[0] < 0 || a[0] >= d->n_groups) return fail(GRP_EINVAL, "observable %d: bad group", j);
+    } else if (k != GRP_OBS_POTENTIAL && k != GRP_OBS_KINETIC) {
+      return fail(GRP_EINVAL, "observable %d: unknown kind %d", j, k);
+    }
+    if (d->potential == GRP_POT_DOUBLE_WELL_2D && k != GRP_OBS_COORD && k != GRP_OBS_POTENTIAL && k != GRP_OBS_KINETIC)
+      return fail(GRP_EINVAL, "observable %d: not available for the double well", j);
+  }
+  if (d->cv_kind == GRP_CV_DOUBLE_WELL) {
+    if (d->potential != GRP_POT_DOUBLE_WELL_2D) return fail(GRP_EINVAL, "double-well states need the double-well potential");
+  } else if (d->cv_kind == GRP_CV_DIHEDRAL_RECT) {
+    if (d->dim != 3) return fail(GRP_EINVAL, "dihedral states need dim = 3");
+    for (int t = 0; t < 5; ++t)
+      if (bad_atom(d->cv_atoms[t])) return fail(GRP_EINVAL, "cv_atoms[%d] out of range", t);
+  } else if (d->cv_kind == GRP_CV_COM_DISTANCE) {
+    if (d->dim != 3 || d->n_groups < 2) return fail(GRP_EINVAL, "COM-distance states need two groups");
+  } else {
+    return fail(GRP_EINVAL, "unknown cv_kind %d", d->cv_kind);
+  }
+
+  grp_system *s = new grp_system();
+  CU(cudaGetDevice(&s->device));
+  SysDev &D = s->dev;
+  D.n = n;
+  D.dim = d->dim;
+  D.nd = n * d->dim;
+  D.potential = d->potential;
+  D.precision = d->precision;
+  D.dw_a = d->dw_a;
+  D.dw_b = d->dw_b;
+  D.kT = d->kT;
+  D.gamma = d->gamma;
+  D.dt = d->dt;
+  D.cv_kind = d->cv_kind;
+  for (int t = 0; t < 8; ++t) { D.cv_atoms[t] = d->cv_atoms[t]; D.cv_params[t] = d->cv_params[t]; }
+  D.n_groups = d->n_groups;
+  for (int g = 0; g <= GRP_MAX_GROUPS; ++g) D.group_off[g] = g <= d->n_groups ? d->group_offsets[g] : n_group_atoms;
+  D.n_obs = d->n_obs;
+  for (int j = 0; j < GRP_MAX_OBS; ++j) {
+    D.obs_kind[j] = d->obs_kind[j];
+    for (int t = 0; t < 4; ++t) D.obs_arg[j][t] = d->obs_arg[j][t];
+  }
+  grp_status st = GRP_OK;
+#define UP(h, cnt, out)                                   \
+  do {                                                    \
+    st = upload(s->owned, h, cnt, out);                   \
+    if (st != GRP_OK) { grp_destroy_system(s); return st; } \
+  } while (0)
+  UP(d->mass, (size_t)n, &D.mass);
+  if (n_group_atoms > 0) UP(d->group_atoms, (size_t)n_group_atoms, &D.group_atoms);
+
+  if (d->potential == GRP_POT_FORCE_FIELD) {
+    if (!d->sigma || !d->epsilon || !d->charge) { grp_destroy_system(s); return fail(GRP_EINVAL, "sigma/epsilon/charge null"); }
+    std::vector<double4> ad(n);
+    std::vector<float4> af(n);
+    const double ck = std::sqrt(std::max(d->coulomb_k, 0.0) / 4.0);
+    for (int i = 0; i < n; ++i) {
+      if (!(d->epsilon[i] >= 0)) { grp_destroy_system(s); return fail(GRP_EINVAL, "epsilon[%d] < 0", i); }
+      ad[i] = make_double4(0.5 * d->sigma[i], std::sqrt(d->epsilon[i]), d->charge[i] * ck, 1.0 / d->mass[i]);
+      af[i] = make_float4((float)ad[i].x, (float)ad[i].y, (float)ad[i].z, (float)ad[i].w);
+    }
+    UP(ad.data(), (size_t)n, &D.atom_d);
+    UP(af.data(), (size_t)n, &D.atom_f);
+    // explicit list of non-excluded pairs
+    std::vector<uint8_t> excl((size_t)n * n, 0);
+    if (d->n_excl > 0 && !d->excl) { grp_destroy_system(s); return fail(GRP_EINVAL, "excl is null"); }
+    for (int e = 0; e < d->n_excl; ++e) {
+      const int i = d->excl[2 * e], j = d->excl[2 * e + 1];
+      if (bad_atom(i) || bad_atom(j) || i == j) { grp_destroy_system(s); return fail(GRP_EINVAL, "exclusion %d invalid", e); }
+      excl[(size_t)i * n + j] = excl[(size_t)j * n + i] = 1;
+    }
+    std::vector<uint32_t> pairs;
+    pairs.reserve((size_t)n * (n - 1) / 2);
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j)
+        if (!excl[(size_t)i * n + j]) pairs.push_back((uint32_t)i | ((uint32_t)j << 16));
+    D.n_pairs = (int)pairs.size();
+    UP(pairs.data(), pairs.size(), &D.pairs);
+    D.cutoff2 = d->cutoff > 0 ? d->cutoff * d->cutoff : 0.0;
+    // bonds
+    if (d->n_bonds > 0 && (!d->bond_atoms || !d->bond_k || !d->bond_r0)) { grp_destroy_system(s); return fail(GRP_EINVAL, "bond arrays null"); }
+    std::vector<int2> bij(d->n_bonds);
+    std::vector<double2> bd(d->n_bonds);
+    std::vector<float2> bf(d->n_bonds);
+    for (int b = 0; b < d->n_bonds; ++b) {
+      const int i = d->bond_atoms[2 * b], j = d->bond_atoms[2 * b + 1];
+      if (bad_atom(i) || bad_atom(j) || i == j) { grp_destroy_system(s); return fail(GRP_EINVAL, "bond %d invalid", b); }
+      bij[b] = make_int2(i, j);
+      bd[b] = make_double2(d->bond_k[b], d->bond_r0[b]);
+      bf[b] = make_float2((float)bd[b].x, (float)bd[b].y);
+    }
+    D.n_bonds = d->n_bonds;
+    UP(bij.data(), bij.size(), &D.bond_ij);
+    UP(bd.data(), bd.size(), &D.bond_d);
+    UP(bf.data(), bf.size(), &D.bond_f);
+    // angles
+    if (d->n_angles > 0 && (!d->angle_atoms || !d->angle_k || !d->angle_theta0)) { grp_destroy_system(s); return fail(GRP_EINVAL, "angle arrays null"); }
+    std::vector<int4> aijk(d->n_angles);
+    std::vector<double2> angd(d->n_angles);
+    std::vector<float2> angf(d->n_angles);
+    for (int t = 0; t < d->n_angles; ++t) {
+      const int *a = d->angle_atoms + 3 * t;
+      if (bad_atom(a[0]) || bad_atom(a[1]) || bad_atom(a[2])) { grp_destroy_system(s); return fail(GRP_EINVAL, "angle %d invalid", t); }
+      aijk[t] = make_int4(a[0], a[1], a[2], 0);
+      angd[t] = make_double2(d->angle_k[t], d->angle_theta0[t]);
+      angf[t] = make_float2((float)angd[t].x, (float)angd[t].y);
+    }
+    D.n_angles = d->n_angles;
+    UP(aijk.data(), aijk.size(), &D.angle_ijk);
+    UP(angd.data(), angd.size(), &D.angle_d);
+    UP(angf.data(), angf.size(), &D.angle_f);
+    // dihedrals: entries with the same four atoms form one item whose terms share the geometry
+    if (d->n_dihedrals > 0 && (!d->dihedral_atoms || !d->dihedral_n || !d->dihedral_k || !d->dihedral_delta)) {
+      grp_destroy_system(s);
+      return fail(GRP_EINVAL, "dihedral arrays null");
+    }
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    std::vector<std::tuple<int, int, int, int>> order;
+    for (int t = 0; t < d->n_dihedrals; ++t) {
+      const int *a = d->dihedral_atoms + 4 * t;
+      if (bad_atom(a[0]) || bad_atom(a[1]) || bad_atom(a[2]) || bad_atom(a[3]) || d->dihedral_n[t] < 1 ||
+          d->dihedral_n[t] > 6) {
+        grp_destroy_system(s);
+        return fail(GRP_EINVAL, "dihedral %d invalid (atoms or multiplicity outside 1..6)", t);
+      }
+      auto key = std::make_tuple(a[0], a[1], a[2], a[3]);
+      if (!groups.count(key)) order.push_back(key);
+      groups[key].push_back(t);
+    }
+    std::vector<int4> dijkl;
+    std::vector<int2> dterms;
+    std::vector<double4> td;
+    std::vector<float4> tf;
+    for (auto &key : order) {
+      dijkl.push_back(make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key)));
+      const int t0 = (int)td.size();
+      for (int t : groups[key]) {
+        td.push_back(make_double4(d->dihedral_k[t], (double)d->dihedral_n[t], std::cos(d->dihedral_delta[t]),
+                                  std::sin(d->dihedral_delta[t])));
+        tf.push_back(make_float4((float)td.back().x, (float)td.back().y, (float)td.back().z, (float)td.back().w));
+      }
+      dterms.push_back(make_int2(t0, (int)td.size()));
+    }
+    D.n_dih = (int)dijkl.size();
+    UP(dijkl.data(), dijkl.size(), &D.dih_ijkl);
+    UP(dterms.data(), dterms.size(), &D.dih_terms);
+    UP(td.data(), td.size(), &D.term_d);
+    UP(tf.data(), tf.size(), &D.term_f);
+  }
+#undef UP
+  s->seg = segment_config(D, 0);
+  if (s->seg.smem > 227 * 1024) {
+    grp_destroy_system(s);
+    return fail(GRP_ENOTIMPL, "system of %d atoms needs %zu bytes of shared memory per replica", n, s->seg.smem);
+  }
+  *out = s;
+  return GRP_OK;
+}
+
+extern "C" void grp_destroy_system(grp_system *s) {
+  if (!s) return;
+  for (void *p : s->owned) cudaFree(p);
+  delete s;
+}
+
+// ------------------------------------------------------------------------------------------------
+static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
+  CU(cudaMemcpyAsync(&r->hb->err, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const int e = r->hb->err;
+  if (e) {
+    CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
+    if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
+    return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range (|f| >= 2^20)");
+  }
+  return GRP_OK;
+}
+
+static grp_status compute_forces(grp_replicas *r, cudaStream_t st) {
+  CU(launch_energy_forces(r->sys->dev, r->R, r->q, nullptr, r->f, r->err, st));
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint64_t seed, const double *h_q0,
+                                        const double *h_p0, int32_t per_replica, void *stream, grp_replicas **out) {
+  if (!s || !out || !h_q0 || !h_p0) return fail(GRP_EINVAL, "grp_init_replicas: null argument");
+  *out = nullptr;
+  if (n_replicas < 1 || n_replicas > (1 << 24)) return fail(GRP_EINVAL, "n_replicas must be in [1, 2^24]");
+  cudaStream_t st = (cudaStream_t)stream;
+  grp_replicas *r = new grp_replicas();
+  r->sys = s;
+  r->R = n_replicas;
+  r->seed = seed;
+  const SysDev &D = s->dev;
+  const size_t nd = (size_t)D.nd, R = (size_t)n_replicas, nacc = (size_t)D.n_obs * 4;
+  auto alloc = [&](void **p, size_t bytes) -> grp_status {
+    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 8);
+    if (e != cudaSuccess) return fail(GRP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return GRP_OK;
+  };
+  grp_status stt = GRP_OK;
+#define AL(p, b)                                                  \
+  do {                                                            \
+    stt = alloc((void **)&(p), (b));                              \
+    if (stt != GRP_OK) { grp_destroy_replicas(r); return stt; }   \
+  } while (0)
+  AL(r->q, R * nd * 8);
+  AL(r->p, R * nd * 8);
+  AL(r->f, R * nd * 8);
+  AL(r->acc, R * nacc * 8);
+  AL(r->labels, R);
+  AL(r->exited, R);
+  AL(r->src, R * 4);
+  AL(r->exit_key, 8);
+  AL(r->err, 4);
+  AL(r->n_branched, 4);
+  AL(r->rhat, GRP_MAX_OBS * 8);
+#undef AL
+  if (cudaMallocHost((void **)&r->hb, sizeof(*r->hb)) != cudaSuccess) {
+    grp_destroy_replicas(r);
+    return fail(GRP_ENOMEM, "cudaMallocHost failed");
+  }
+  if (per_replica) {
+    CU(cudaMemcpyAsync(r->q, h_q0, R * nd * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(r->p, h_p0, R * nd * 8, cudaMemcpyHostToDevice, st));
+  } else {
+    for (size_t i = 0; i < R; ++i) {
+      CU(cudaMemcpyAsync(r->q + i * nd, h_q0, nd * 8, cudaMemcpyHostToDevice, st));
+      CU(cudaMemcpyAsync(r->p + i * nd, h_p0, nd * 8, cudaMemcpyHostToDevice, st));
+    }
+  }
+  CU(cudaMemsetAsync(r->acc, 0, R * nacc * 8 + 8, st));
+  CU(cudaMemsetAsync(r->labels, 0, R, st));
+  CU(cudaMemsetAsync(r->exited, 0, R, st));
+  CU(cudaMemsetAsync(r->err, 0, 4, st));
+  CU(cudaMemsetAsync(r->exit_key, 0xff, 8, st));
+  grp_status e = compute_forces(r, st);
+  if (e == GRP_OK) e = latch_errors(r, st);
+  if (e != GRP_OK) { grp_destroy_replicas(r); return e; }
+  *out = r;
+  return GRP_OK;
+}
+
+extern "C" void grp_destroy_replicas(grp_replicas *r) {
+  if (!r) return;
+  cudaFree(r->q); cudaFree(r->p); cudaFree(r->f); cudaFree(r->acc);
+  cudaFree(r->labels); cudaFree(r->exited); cudaFree(r->src); cudaFree(r->exit_key);
+  cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat);
+  if (r->hb) cudaFreeHost(r->hb);
+  delete r;
+}
+
+// ------------------------------------------------------------------------------------------------
+static SegArgs seg_args(grp_replicas *r, int k, int t_gr, int n_active) {
+  SegArgs a{};
+  a.S = r->sys->dev;
+  a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc;
+  a.labels = r->labels; a.exited = r->exited; a.exit_key = r->exit_key; a.err = r->err;
+  a.seed = r->seed;
+  a.t_global0 = r->t_global;
+  a.t_phase0 = r->t_phase;
+  a.k = k;
+  a.t_gr = t_gr;
+  a.n_active = n_active;
+  a.h = 0.5 * a.S.dt;
+  a.c1 = std::exp(-a.S.gamma * a.S.dt);
+  return a;
+}
+
+// k steps in launches of at most kMaxSegment steps, so that one launch stays short.
+static constexpr long long kMaxSegment = 20000;
+
+static grp_status run_steps(grp_replicas *r, long long k, int t_gr, int n_active, int do_check, int omega,
+                            long long M, int skip, cudaStream_t st) {
+  while (k > 0) {
+    const int kk = (int)std::min(k, kMaxSegment);
+    SegArgs a = seg_args(r, kk, t_gr, n_active);
+    a.do_check = (k == kk) ? do_check : 0;
+    a.omega = omega;
+    a.M = M;
+    a.skip_if_exit = skip;
+    CU(launch_segment(a, r->sys->seg, st));
+    r->t_global += kk;
+    r->t_phase += kk;
+    k -= kk;
+  }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_step_k(grp_replicas *r, int64_t k, int32_t t_gr, int32_t n_active, void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_step_k: null handle");
+  if (k < 0 || t_gr < 0 || n_active < 0 || n_active > r->R) return fail(GRP_EINVAL, "grp_step_k: bad k/t_gr/n_active");
+  return run_steps(r, k, t_gr, n_active ? n_active : r->R, 0, 0, 0, 0, (cudaStream_t)stream);
+}
+
+extern "C" grp_status grp_check_states(grp_replicas *r, int32_t omega, int8_t *d_labels, uint8_t *d_exited, void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_check_states: null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(launch_check(r->sys->dev, r->q, r->R, omega, r->labels, r->exited, nullptr, 0, st));
+  if (d_labels) CU(cudaMemcpyAsync(d_labels, r->labels, r->R, cudaMemcpyDeviceToDevice, st));
+  if (d_exited) CU(cudaMemcpyAsync(d_exited, r->exited, r->R, cudaMemcpyDeviceToDevice, st));
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, int32_t *d_src, int32_t *h_n_branched,
+                                    void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_fv_branch: null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  const SysDev &D = r->sys->dev;
+  CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
+  CU(launch_fv_branch(D, r->R, r->q, r->p, r->f, r->acc, d_exited ? d_exited : r->exited, r->src, r->n_branched,
+                      r->seed, r->t_global, st));
+  if (d_src) CU(cudaMemcpyAsync(d_src, r->src, (size_t)r->R * 4, cudaMemcpyDeviceToDevice, st));
+  if (h_n_branched) {
+    CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    *h_n_branched = r->hb->n_branched;
+  }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_gelman_rubin(grp_replicas *r, double tol, double *h_rhat, int32_t *h_converged, void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_gelman_rubin: null handle");
+  if (r->R < 2) return fail(GRP_EINVAL, "grp_gelman_rubin: needs at least one F-V worker (R >= 2)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const SysDev &D = r->sys->dev;
+  CU(launch_gelman_rubin(D, r->R, r->acc, tol, r->rhat, nullptr, st));
+  CU(cudaMemcpyAsync(r->hb->rhat, r->rhat, sizeof(double) * D.n_obs, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  int conv = 1;
+  for (int j = 0; j < D.n_obs; ++j) {
+    if (h_rhat) h_rhat[j] = r->hb->rhat[j];
+    if (!(r->hb->rhat[j] < 1.0 + tol)) conv = 0;
+  }
+  if (h_converged) *h_converged = conv;
+  return GRP_OK;
+}
+
+// Parallel phase: segments of t_check steps with the exit test fused at the end; batches of
+// segments are queued before the exit key is read back (segments after an exit return at once).
+static grp_status parallel_phase(grp_replicas *r, int omega, int t_check, long long max_checks, grp_exit *out,
+                                 cudaStream_t st) {
+  CU(cudaMemsetAsync(r->exit_key, 0xff, 8, st));
+  const long long tg0 = r->t_global, tp0 = r->t_phase;
+  long long M = 0;
+  int batch = 1;
+  while (M < max_checks) {
+    const long long nb = std::min<long long>(batch, max_checks - M);
+    for (long long i = 0; i < nb; ++i) {
+      ++M;
+      grp_status e = run_steps(r, t_check, 0, r->R, 1, omega, M, 1, st);
+      if (e != GRP_OK) return e;
+    }
+    CU(cudaMemcpyAsync(&r->hb->exit_key, r->exit_key, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const unsigned long long key = r->hb->exit_key;
+    if (key != ~0ull) {
+      const long long Mx = (long long)(key >> 32);
+      const int k0 = (int)(key & 0xffffffffu);
+      CU(cudaMemcpyAsync(&r->hb->label0, r->labels + k0, 1, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      r->t_global = tg0 + Mx * t_check;
+      r->t_phase = tp0 + Mx * t_check;
+      out->M = Mx;
+      out->k = k0 + 1;
+      out->label_to = r->hb->label0;
+      out->tau_steps = ((long long)r->R * (Mx - 1) + (k0 + 1)) * (long long)t_check;
+      return GRP_OK;
+    }
+    batch = std::min(batch * 2, 16);
+  }
+  return GRP_NOEXIT;
+}
+
+extern "C" grp_status grp_run_parallel_phase(grp_replicas *r, int32_t omega, int32_t t_check, int64_t max_checks,
+                                             grp_exit *h_out, void *stream) {
+  if (!r || !h_out) return fail(GRP_EINVAL, "grp_run_parallel_phase: null argument");
+  if (t_check < 1 || max_checks < 1) return fail(GRP_EINVAL, "grp_run_parallel_phase: t_check, max_checks >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  grp_status e = parallel_phase(r, omega, t_check, max_checks, h_out, st);
+  grp_status e2 = latch_errors(r, st);
+  return e2 != GRP_OK ? e2 : e;
+}
+
+extern "C" grp_status grp_broadcast(grp_replicas *r, int32_t src, void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_broadcast: null handle");
+  if (src < 0 || src >= r->R) return fail(GRP_EINVAL, "grp_broadcast: src out of range");
+  CU(launch_copy_replica(r->sys->dev, r->R, r->q, r->p, r->f, r->acc, src, -1, 1, (cudaStream_t)stream));
+  r->t_phase = 0;
+  return GRP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
+                              int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
+  if (!r || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_run: null argument");
+  if (p->t_gr < 1 || p->t_check < 1 || !(p->tol > 0)) return fail(GRP_EINVAL, "grp_run: need t_gr, t_check >= 1, tol > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const SysDev &D = r->sys->dev;
+  const int R = r->R;
+  int nev = 0, nexit = 0;
+  long long tsim = 0;
+  auto log = [&](int kind, int omega, int to, int k, long long M, long long steps, long long nb) {
+    if (nev < max_events) {
+      grp_event &e = h_events[nev];
+      e.kind = kind; e.omega = omega; e.label_to = to; e.k = k; e.M = M; e.steps = steps;
+      e.t_sim = tsim; e.n_branch = nb;
+    }
+    ++nev;
+  };
+  auto read_label0 = [&](int omega, int *label, int *exited) -> grp_status {
+    CU(launch_check(D, r->q, 1, omega, r->labels, r->exited, nullptr, 0, st));
+    CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    *label = r->hb->label0;
+    *exited = r->hb->exited0;
+    return GRP_OK;
+  };
+  grp_status e = GRP_OK;
+  while (nexit < p->max_exits && r->t_global < p->max_steps && nev < max_events) {
+    // 1. transient propagation of the reference walker
+    long long treach = 0;
+    int omega, ex;
+    if ((e = read_label0(0, &omega, &ex)) != GRP_OK) return e;
+    while (omega < 0 && r->t_global < p->max_steps) {
+      if ((e = run_steps(r, p->t_check, 0, 1, 0, 0, 0, 0, st)) != GRP_OK) return e;
+      treach += p->t_check;
+      if ((e = read_label0(0, &omega, &ex)) != GRP_OK) return e;
+    }
+    if (omega < 0) break;
+    if (treach > 0) {
+      tsim += treach;
+      log(GRP_EV_TRANSIENT, -1, omega, 0, 0, treach, 0);
+    }
+    // 2. convergence step
+    CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, 0, -1, 1, st));
+    r->t_phase = 0;
+    long long nbranch = 0;
+    int converged = 0, ref_exit = 0;
+    while (r->t_global < p->max_steps) {
+      if ((e = run_steps(r, p->t_check, p->t_gr, R, 1, omega, 0, 0, st)) != GRP_OK) return e;
+      CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
+      CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
+      const bool want_gr = r->t_phase >= p->min_fv_steps && R > 1 && D.n_obs > 0;
+      if (want_gr) {
+        CU(launch_gelman_rubin(D, R, r->acc, p->tol, r->rhat, nullptr, st));
+        CU(cudaMemcpyAsync(r->hb->rhat, r->rhat, sizeof(double) * D.n_obs, cudaMemcpyDeviceToHost, st));
+      }
+      CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      // (a) the reference walker left omega: the F-V workers are discarded (the branching above
+      //     only touched workers, which the next broadcast overwrites)
+      if (r->hb->exited0) {
+        tsim += r->t_phase;
+        log(GRP_EV_REF_EXIT, omega, r->hb->label0, 0, 0, r->t_phase, nbranch);
+        ++nexit;
+        ref_exit = 1;
+        break;
+      }
+      // (b) branching done on the device
+      const int nb = r->hb->n_branched;
+      if (nb > 0 && nb == R - 1) log(GRP_EV_FV_ALL_EXITED, omega, omega, 0, 0, r->t_phase, nb);
+      nbranch += nb;
+      // (c) Gelman-Rubin test, Eq. 4
+      if (want_gr) {
+        int ok = 1;
+        for (int j = 0; j < D.n_obs; ++j)
+          if (!(r->hb->rhat[j] < 1.0 + p->tol)) ok = 0;
+        if (ok) { converged = 1; break; }
+      }
+    }
+    if (ref_exit) continue;
+    if (!converged) break;
+    tsim += r->t_phase;
+    log(GRP_EV_FV_CONVERGED, omega, omega, 0, 0, r->t_phase, nbranch);
+    // 3. parallel dynamics step
+    const long long left = (p->max_steps - r->t_global + p->t_check - 1) / p->t_check;
+    if (left < 1) break;
+    grp_exit ex_out{};
+    e = parallel_phase(r, omega, p->t_check, left, &ex_out, st);
+    if (e == GRP_NOEXIT) break;
+    if (e != GRP_OK) return e;
+    tsim += ex_out.tau_steps;
+    log(GRP_EV_PARALLEL_EXIT, omega, ex_out.label_to, ex_out.k, ex_out.M, ex_out.tau_steps, 0);
+    ++nexit;
+    // the exit configuration becomes the reference walker
+    if (ex_out.k != 1) CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, ex_out.k - 1, 0, 0, st));
+  }
+  if (h_n_events) *h_n_events = std::min(nev, max_events);
+  if (h_t_sim) *h_t_sim = tsim;
+  return latch_errors(r, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+extern "C" grp_status grp_get_state(grp_replicas *r, double *h_q, double *h_p, double *h_acc, grp_counters *h_ctr,
+                                    void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_get_state: null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nd = (size_t)r->sys->dev.nd * r->R, na = (size_t)r->sys->dev.n_obs * 4 * r->R;
+  if (h_q) CU(cudaMemcpyAsync(h_q, r->q, nd * 8, cudaMemcpyDeviceToHost, st));
+  if (h_p) CU(cudaMemcpyAsync(h_p, r->p, nd * 8, cudaMemcpyDeviceToHost, st));
+  if (h_acc && na) CU(cudaMemcpyAsync(h_acc, r->acc, na * 8, cudaMemcpyDeviceToHost, st));
+  if (h_ctr) { h_ctr->t_global = r->t_global; h_ctr->t_phase = r->t_phase; }
+  return latch_errors(r, st);
+}
+
+extern "C" grp_status grp_set_state(grp_replicas *r, const double *h_q, const double *h_p, const double *h_acc,
+                                    const grp_counters *h_ctr, void *stream) {
+  if (!r) return fail(GRP_EINVAL, "grp_set_state: null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nd = (size_t)r->sys->dev.nd * r->R, na = (size_t)r->sys->dev.n_obs * 4 * r->R;
+  if (h_q) CU(cudaMemcpyAsync(r->q, h_q, nd * 8, cudaMemcpyHostToDevice, st));
+  if (h_p) CU(cudaMemcpyAsync(r->p, h_p, nd * 8, cudaMemcpyHostToDevice, st));
+  if (h_acc && na) CU(cudaMemcpyAsync(r->acc, h_acc, na * 8, cudaMemcpyHostToDevice, st));
+  if (h_ctr) {
+    if (h_ctr->t_global < 0 || h_ctr->t_phase < 0) return fail(GRP_EINVAL, "grp_set_state: negative counters");
+    r->t_global = h_ctr->t_global;
+    r->t_phase = h_ctr->t_phase;
+  }
+  if (h_q) {
+    grp_status e = compute_forces(r, st);
+    if (e != GRP_OK) return e;
+  }
+  return latch_errors(r, st);
+}
+
+extern "C" grp_status grp_get_device_view(grp_replicas *r, grp_device_view *out) {
+  if (!r || !out) return fail(GRP_EINVAL, "grp_get_device_view: null argument");
+  out->q = r->q; out->p = r->p; out->f = r->f; out->acc = r->acc;
+  out->labels = r->labels; out->exited = r->exited;
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_energy_forces(grp_system *s, int32_t n_conf, const double *d_q, double *d_energy,
+                                        double *d_forces, void *stream) {
+  if (!s || !d_q || n_conf < 0) return fail(GRP_EINVAL, "grp_energy_forces: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int *err = nullptr;
+  CU(cudaMallocAsync((void **)&err, 4, st));
+  CU(cudaMemsetAsync(err, 0, 4, st));
+  CU(launch_energy_forces(s->dev, n_conf, d_q, d_energy, d_forces, err, st));
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaFreeAsync(err, st));
+  if (h & kErrOverflow) return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range");
+  return GRP_OK;
+}

@@ -1,0 +1,186 @@
+// Shared device definitions of libgrp: system layout on the device, Philox4x32-10 noise,
+// Box-Muller normals, 64-bit fixed-point force accumulation and double-single arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/grp.h"
+
+namespace grp {
+
+constexpr int kMaxObs = GRP_MAX_OBS;
+constexpr int kMaxGroups = GRP_MAX_GROUPS;
+
+// Error bits latched by kernels into the replica set's error word.
+enum : int { kErrNaN = 1, kErrOverflow = 2 };
+
+// Fixed point: one unit = 2^-32 of the force (or energy) unit.  A single contribution must stay
+// below 2^20 in magnitude so that up to 2^10 of them sum without overflowing int64.
+constexpr double kFixScale = 4294967296.0;          // 2^32
+constexpr double kFixInv = 1.0 / 4294967296.0;
+constexpr float kFixScaleF = 4294967296.0f;
+constexpr double kFixLimit = 1048576.0;               // 2^20
+
+// Device copy of a system.  All arrays are device memory owned by grp_system.  Parameters exist in
+// FP64 (FP64 path) and FP32 (mixed path) copies.
+struct SysDev {
+  int n, dim, nd, potential, precision;
+  double dw_a, dw_b;
+  double kT, gamma, dt;
+  const double *mass;      // [n]
+  const double4 *atom_d;   // [n] (sigma/2, sqrt(eps), q sqrt(k_e/4), 1/m)
+  const float4 *atom_f;
+  int n_pairs;             // explicit non-excluded pair list (i | j << 16), i < j
+  const uint32_t *pairs;
+  double cutoff2;          // 0: no cutoff
+  int n_bonds;
+  const int2 *bond_ij;
+  const double2 *bond_d;   // (k, r0)
+  const float2 *bond_f;
+  int n_angles;
+  const int4 *angle_ijk;
+  const double2 *angle_d;  // (k, theta0)
+  const float2 *angle_f;
+  int n_dih;               // dihedral items: 4 atoms, terms [dih_terms.x, dih_terms.y)
+  const int4 *dih_ijkl;
+  const int2 *dih_terms;
+  const double4 *term_d;   // (k, n, cos delta, sin delta)
+  const float4 *term_f;
+  int cv_kind;
+  int cv_atoms[8];
+  double cv_params[8];
+  int n_groups;
+  int group_off[kMaxGroups + 1];
+  const int *group_atoms;
+  int n_obs;
+  int obs_kind[kMaxObs];
+  int obs_arg[kMaxObs][4];
+};
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+// Counter = (t_global low 32 bits, t_global bits 32..55 | stream << 24, replica, atom), key = seed.
+// Stream 0: BAOAB noise; stream 1: Fleming-Viot branching draw.
+struct Philox4 {
+  uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                  uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  Philox4 r;
+  r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+  return r;
+}
+
+__device__ __forceinline__ Philox4 philox_stream(uint64_t seed, int64_t step, uint32_t stream,
+                                                 int replica, int atom) {
+  const uint64_t st = (uint64_t)step;
+  return philox4x32_10((uint32_t)st, (uint32_t)((st >> 32) & 0x00FFFFFFu) | (stream << 24),
+                       (uint32_t)replica, (uint32_t)atom, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Box-Muller on word pairs (w0, w1), (w2, w3) with u = (w + 1/2) 2^-32.
+__device__ __forceinline__ void normals4_f64(const Philox4 &w, double xi[4]) {
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const double u1 = ((double)w.v[2 * pr] + 0.5) * 0x1p-32;
+    const double u2 = ((double)w.v[2 * pr + 1] + 0.5) * 0x1p-32;
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    xi[2 * pr] = rad * c;
+    xi[2 * pr + 1] = rad * s;
+  }
+}
+
+__device__ __forceinline__ void normals4_f32(const Philox4 &w, float xi[4]) {
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const float u1 = fmaf((float)w.v[2 * pr], 0x1p-32f, 0x1p-33f);
+    const float u2 = fmaf((float)w.v[2 * pr + 1], 0x1p-32f, 0x1p-33f);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    xi[2 * pr] = rad * c;
+    xi[2 * pr + 1] = rad * s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Fixed-point accumulation: contributions converted with round-to-nearest; integer sums are exact
+// and independent of order, so results do not depend on the thread decomposition.
+__device__ __forceinline__ long long to_fix(double v, int *err) {
+  if (!(fabs(v) < kFixLimit)) { *err |= kErrOverflow; return 0; }
+  return __double2ll_rn(v * kFixScale);
+}
+__device__ __forceinline__ long long to_fix(float v, int *err) {
+  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return 0; }
+  return __float2ll_rn(v * kFixScaleF);
+}
+__device__ __forceinline__ void fix_add(long long *dst, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Double-single numbers x = hi + lo (|lo| <= ulp(hi)/2): Knuth's TwoSum and Dekker's Fast2Sum keep
+// about 48 significant bits with FP32 instructions only.
+struct ds {
+  float hi, lo;
+};
+__device__ __forceinline__ ds ds_from_double(double x) {
+  ds r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double ds_to_double(ds x) { return (double)x.hi + (double)x.lo; }
+// x + d for a float d
+__device__ __forceinline__ ds ds_add(ds x, float d) {
+  const float s = __fadd_rn(x.hi, d);
+  const float bp = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+  const float lo = __fadd_rn(x.lo, e);
+  ds r;
+  r.hi = __fadd_rn(s, lo);
+  r.lo = __fsub_rn(lo, __fsub_rn(r.hi, s));
+  return r;
+}
+// c * x for a float c
+__device__ __forceinline__ ds ds_scale(ds x, float c) {
+  const float ph = __fmul_rn(c, x.hi);
+  const float pl = __fmaf_rn(c, x.hi, -ph);  // exact error of the product
+  const float lo = __fmaf_rn(c, x.lo, pl);
+  ds r;
+  r.hi = __fadd_rn(ph, lo);
+  r.lo = __fsub_rn(lo, __fsub_rn(r.hi, ph));
+  return r;
+}
+
+// Block-wide sum of int64 values (every thread contributes; result valid in thread 0).
+template <int kThreads>
+__device__ __forceinline__ long long block_sum_ll(long long v, long long *scratch /* >= 32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  long long t = 0;
+  if (warp == 0) {
+    t = (lane < (kThreads + 31) / 32) ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+}  // namespace grp

@@ -1,0 +1,62 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace grp {
+
+// Arguments of one segment launch: k BAOAB steps of every active replica with observable sampling
+// and an optional state check at the end.
+struct SegArgs {
+  SysDev S;
+  double *q, *p, *f;         // [R][n][dim] state in HBM
+  double *acc;               // [R][n_obs][4]
+  int8_t *labels;            // [R]
+  uint8_t *exited;           // [R]
+  unsigned long long *exit_key;  // packed (check << 32 | replica), ~0 = none
+  int *err;                  // sticky error bits
+  uint64_t seed;
+  long long t_global0, t_phase0;
+  int k, t_gr;
+  int n_active;
+  int do_check, omega;
+  long long M;               // check index written into the exit key
+  int skip_if_exit;          // return at once when *exit_key is already set
+  int pairs_in_smem;
+  double h, c1;              // dt/2 and exp(-gamma dt)
+};
+
+// Launch configuration chosen per system (threads per replica block).
+struct SegConfig {
+  int threads;
+  size_t smem;
+  int pairs_in_smem;
+};
+
+SegConfig segment_config(const SysDev &S, int threads_hint);
+cudaError_t launch_segment(const SegArgs &a, const SegConfig &cfg, cudaStream_t st);
+
+// State functions at the current state (FP64), writing labels/exited; exit key as above.
+cudaError_t launch_check(const SysDev &S, const double *q, int n_rep, int omega, int8_t *labels,
+                         uint8_t *exited, unsigned long long *exit_key, long long M, cudaStream_t st);
+
+// Fleming-Viot branching of exited workers; n_branched (device int) accumulates the copies.
+cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
+                             const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
+                             long long t_global, cudaStream_t st);
+
+// Gelman-Rubin ratio per observable over workers 1..R-1; rhat[n_obs], converged flag.
+cudaError_t launch_gelman_rubin(const SysDev &S, int n_rep, const double *acc, double tol, double *rhat,
+                                int *converged, cudaStream_t st);
+
+// Copy replica src to every other replica (or only to dst >= 0); clear accumulators when asked.
+cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
+                                int src, int dst, int clear_acc, cudaStream_t st);
+
+// Energies and forces of B configurations.
+cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, double *energy,
+                                 double *forces, int *err, cudaStream_t st);
+
+}  // namespace grp

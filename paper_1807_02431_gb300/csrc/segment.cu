@@ -1,0 +1,572 @@
+// Fused segment kernels: k BAOAB steps of Eq. 1 per replica with the replica's state held on chip,
+// observable sampling every t_GR (Section 2.4.1) and the exit test at the end of the segment
+// (Section 3.3).  One thread block per replica for force-field systems; one thread per replica for
+// the analytic 2-D double well.
+#include <cfloat>
+
+#include "forcefield.cuh"
+#include "kernels.h"
+
+namespace grp {
+
+// ------------------------------------------------------------------------------------------------
+// FP64 state functions (Section 3.3) on positions given by an accessor get(a, double[3]).
+template <class Get>
+__device__ double dihedral_rad_f64(Get get, int i, int j, int k, int l) {
+  double qi[3], qj[3], qk[3], ql[3];
+  get(i, qi); get(j, qj); get(k, qk); get(l, ql);
+  const V3<double> b1 = {qj[0] - qi[0], qj[1] - qi[1], qj[2] - qi[2]};
+  const V3<double> b2 = {qk[0] - qj[0], qk[1] - qj[1], qk[2] - qj[2]};
+  const V3<double> b3 = {ql[0] - qk[0], ql[1] - qk[1], ql[2] - qk[2]};
+  const V3<double> n1 = cross(b1, b2), n2 = cross(b2, b3);
+  return atan2(sqrt(dot(b2, b2)) * dot(b1, n2), dot(n1, n2));
+}
+
+template <class Get>
+__device__ void group_com_f64(const SysDev &S, Get get, int g, double com[3]) {
+  double mt = 0, c[3] = {0, 0, 0};
+  for (int t = S.group_off[g]; t < S.group_off[g + 1]; ++t) {
+    const int at = S.group_atoms[t];
+    const double m = S.mass[at];
+    double x[3];
+    get(at, x);
+    mt += m;
+    c[0] += m * x[0]; c[1] += m * x[1]; c[2] += m * x[2];
+  }
+  com[0] = c[0] / mt; com[1] = c[1] / mt; com[2] = c[2] / mt;
+}
+
+// Returns the state index containing the configuration (-1: none); *out_exited = outside omega.
+template <class Get>
+__device__ int state_check_f64(const SysDev &S, Get get, int omega, int *out_exited) {
+  if (S.cv_kind == GRP_CV_DOUBLE_WELL) {
+    double x[3];
+    get(0, x);
+    const double w = S.cv_params[0];
+    *out_exited = omega == 0 ? (x[0] >= 0.0) : (x[0] < 0.0);
+    return x[0] < -w ? 0 : (x[0] > w ? 1 : -1);
+  }
+  int label;
+  if (S.cv_kind == GRP_CV_DIHEDRAL_RECT) {
+    const int *c = S.cv_atoms;
+    const double deg = 57.295779513082320876798154814105;
+    const double phi = deg * dihedral_rad_f64(get, c[0], c[1], c[2], c[3]);
+    const double psi = deg * dihedral_rad_f64(get, c[1], c[2], c[3], c[4]);
+    const bool in = phi >= S.cv_params[0] && phi <= S.cv_params[1] && psi >= S.cv_params[2] &&
+                    psi <= S.cv_params[3];
+    label = in ? 0 : 1;
+  } else {
+    double c0[3], c1[3];
+    group_com_f64(S, get, 0, c0);
+    group_com_f64(S, get, 1, c1);
+    const double dx = c0[0] - c1[0], dy = c0[1] - c1[1], dz = c0[2] - c1[2];
+    label = sqrt(dx * dx + dy * dy + dz * dz) < S.cv_params[0] ? 0 : 1;
+  }
+  *out_exited = label != omega;
+  return label;
+}
+
+__device__ __forceinline__ void acc_add(double *acc, double v) {
+  // acc = (shift c, sum (O - c), sum (O - c)^2, n); the first sample sets the shift.
+  if (acc[3] == 0.0) acc[0] = v;
+  const double d = v - acc[0];
+  acc[1] += d;
+  acc[2] += d * d;
+  acc[3] += 1.0;
+}
+
+__device__ __forceinline__ void record_check(const SegArgs &a, int r, int label, int ex) {
+  a.labels[r] = (int8_t)label;
+  a.exited[r] = (uint8_t)ex;
+  if (ex && a.exit_key)
+    atomicMin(a.exit_key, ((unsigned long long)a.M << 32) | (unsigned long long)(unsigned)r);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Shared-memory replica state of each precision path.
+template <class P>
+struct State;
+
+template <>
+struct State<PathF64> {
+  double *q, *p, *f, *sd;  // [3n], [3n], [3n], [n]
+  double4 *atom;           // [n]
+  static size_t bytes(int n) { return (size_t)n * (72 + 8 + 32); }
+  __device__ void carve(unsigned char *&ptr, int n) {
+    atom = (double4 *)ptr; ptr += (size_t)n * 32;
+    q = (double *)ptr; ptr += (size_t)n * 24;
+    p = (double *)ptr; ptr += (size_t)n * 24;
+    f = (double *)ptr; ptr += (size_t)n * 24;
+    sd = (double *)ptr; ptr += (size_t)n * 8;
+  }
+  __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
+    for (int at = threadIdx.x; at < n; at += blockDim.x) {
+      atom[at] = S.atom_d[at];
+      sd[at] = sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
+    }
+  }
+  __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      gq[i] = q[i]; gp[i] = p[i]; gf[i] = f[i];
+      if (!isfinite(q[i]) || !isfinite(p[i])) *err |= kErrNaN;
+    }
+  }
+  __device__ Pos<PathF64> pos() const { return Pos<PathF64>{q}; }
+  __device__ Params<PathF64> params(const SysDev &S) const {
+    return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d};
+  }
+  // B, A, O, A of BAOAB for atom `at` with normals from the Philox stream.
+  __device__ __forceinline__ void baoa(int at, const Philox4 &w, double h, double c1) {
+    double xi[4];
+    normals4_f64(w, xi);
+    const double im = atom[at].w, s = sd[at];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int i = 3 * at + x;
+      double pp = p[i] + h * f[i];
+      double qq = q[i] + h * pp * im;
+      pp = c1 * pp + s * xi[x];
+      qq = qq + h * pp * im;
+      p[i] = pp;
+      q[i] = qq;
+    }
+  }
+  // final B with the new forces (fixed point -> FP64); returns the kinetic energy of the atom.
+  __device__ __forceinline__ double bk(int at, long long *F, double h) {
+    const double im = atom[at].w;
+    double ke = 0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int i = 3 * at + x;
+      const double fv = (double)F[i] * kFixInv;
+      F[i] = 0;
+      f[i] = fv;
+      const double pp = p[i] + h * fv;
+      p[i] = pp;
+      ke += 0.5 * pp * pp * im;
+    }
+    return ke;
+  }
+  __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
+  __device__ void getp_f64(int at, double x[3]) const { x[0] = p[3 * at]; x[1] = p[3 * at + 1]; x[2] = p[3 * at + 2]; }
+};
+
+template <>
+struct State<PathMixed> {
+  float4 *qh, *ql;   // [n] double-single positions
+  float *ph, *pl;    // [3n] double-single momenta
+  float *f, *sd;     // [3n], [n]
+  float4 *atom;      // [n]
+  static size_t bytes(int n) { return (size_t)n * (32 + 24 + 12 + 4 + 16); }
+  __device__ void carve(unsigned char *&ptr, int n) {
+    qh = (float4 *)ptr; ptr += (size_t)n * 16;
+    ql = (float4 *)ptr; ptr += (size_t)n * 16;
+    atom = (float4 *)ptr; ptr += (size_t)n * 16;
+    ph = (float *)ptr; ptr += (size_t)n * 12;
+    pl = (float *)ptr; ptr += (size_t)n * 12;
+    f = (float *)ptr; ptr += (size_t)n * 12;
+    sd = (float *)ptr; ptr += (size_t)n * 4;
+  }
+  __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
+    for (int at = threadIdx.x; at < n; at += blockDim.x) {
+      const ds x = ds_from_double(gq[3 * at]), y = ds_from_double(gq[3 * at + 1]),
+               z = ds_from_double(gq[3 * at + 2]);
+      qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
+      ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
+      atom[at] = S.atom_f[at];
+      sd[at] = (float)sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
+    }
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      const ds v = ds_from_double(gp[i]);
+      ph[i] = v.hi;
+      pl[i] = v.lo;
+      f[i] = (float)gf[i];
+    }
+  }
+  __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
+    for (int at = threadIdx.x; at < n; at += blockDim.x) {
+      const float4 a = qh[at], b = ql[at];
+      gq[3 * at] = (double)a.x + (double)b.x;
+      gq[3 * at + 1] = (double)a.y + (double)b.y;
+      gq[3 * at + 2] = (double)a.z + (double)b.z;
+      if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z)) *err |= kErrNaN;
+    }
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      gp[i] = (double)ph[i] + (double)pl[i];
+      gf[i] = (double)f[i];
+      if (!isfinite(ph[i])) *err |= kErrNaN;
+    }
+  }
+  __device__ Pos<PathMixed> pos() const { return Pos<PathMixed>{qh, ql}; }
+  __device__ Params<PathMixed> params(const SysDev &S) const {
+    return Params<PathMixed>{atom, S.bond_f, S.angle_f, S.term_f};
+  }
+  __device__ __forceinline__ void baoa(int at, const Philox4 &w, float h, float c1) {
+    float xi[4];
+    normals4_f32(w, xi);
+    const float im = atom[at].w, s = sd[at], hm = h * im;
+    float4 a = qh[at], b = ql[at];
+    float *qa = &a.x, *qb = &b.x;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int i = 3 * at + x;
+      ds P = {ph[i], pl[i]};
+      ds Q = {qa[x], qb[x]};
+      P = ds_add(P, h * f[i]);
+      Q = ds_add(Q, hm * P.hi);
+      P = ds_add(ds_scale(P, c1), s * xi[x]);
+      Q = ds_add(Q, hm * P.hi);
+      ph[i] = P.hi;
+      pl[i] = P.lo;
+      qa[x] = Q.hi;
+      qb[x] = Q.lo;
+    }
+    qh[at] = a;
+    ql[at] = b;
+  }
+  __device__ __forceinline__ float bk(int at, long long *F, float h) {
+    const float im = atom[at].w;
+    float ke = 0.f;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int i = 3 * at + x;
+      const float fv = (float)F[i] * 0x1p-32f;
+      F[i] = 0;
+      f[i] = fv;
+      ds P = {ph[i], pl[i]};
+      P = ds_add(P, h * fv);
+      ph[i] = P.hi;
+      pl[i] = P.lo;
+      ke += 0.5f * P.hi * P.hi * im;
+    }
+    return ke;
+  }
+  __device__ void get_f64(int at, double x[3]) const {
+    const float4 a = qh[at], b = ql[at];
+    x[0] = (double)a.x + (double)b.x; x[1] = (double)a.y + (double)b.y; x[2] = (double)a.z + (double)b.z;
+  }
+};
+
+// Observable j (Section 2.4.1) in the path's precision, from shared-memory state.
+template <class P>
+__device__ double observable_ff(const SysDev &S, const State<P> &st, int j, double v_pot, double v_kin) {
+  using T = typename P::T;
+  const int *arg = S.obs_arg[j];
+  const Pos<P> pos = st.pos();
+  switch (S.obs_kind[j]) {
+    case GRP_OBS_POTENTIAL: return v_pot;
+    case GRP_OBS_KINETIC: return v_kin;
+    case GRP_OBS_COORD: {
+      double x[3];
+      st.get_f64(arg[0], x);
+      return x[arg[1]];
+    }
+    case GRP_OBS_DIHEDRAL: {
+      const V3<T> b1 = pos.diff(arg[1], arg[0]), b2 = pos.diff(arg[2], arg[1]), b3 = pos.diff(arg[3], arg[2]);
+      const V3<T> n1 = cross(b1, b2), n2 = cross(b2, b3);
+      return (double)gatan2(gsqrt(dot(b2, b2)) * dot(b1, n2), dot(n1, n2));
+    }
+    case GRP_OBS_GROUP_DISTANCE: {
+      // centre of mass difference relative to the first atom of group a (keeps FP32 sums small)
+      const int ref = S.group_atoms[S.group_off[arg[0]]];
+      T c[2][3] = {{0, 0, 0}, {0, 0, 0}};
+      for (int g = 0; g < 2; ++g) {
+        T mt = 0;
+        for (int t = S.group_off[arg[g]]; t < S.group_off[arg[g] + 1]; ++t) {
+          const int at = S.group_atoms[t];
+          const T m = (T)S.mass[at];
+          const V3<T> d = pos.diff(at, ref);
+          c[g][0] += m * d.x; c[g][1] += m * d.y; c[g][2] += m * d.z;
+          mt += m;
+        }
+        c[g][0] /= mt; c[g][1] /= mt; c[g][2] /= mt;
+      }
+      const T dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
+      return (double)gsqrt(dx * dx + dy * dy + dz * dz);
+    }
+    case GRP_OBS_RMS_VELOCITY: {
+      T s = 0;
+      int cnt = 0;
+      for (int t = S.group_off[arg[0]]; t < S.group_off[arg[0] + 1]; ++t) {
+        const int at = S.group_atoms[t];
+        const T im = (T)st.atom[at].w;
+        for (int x = 0; x < 3; ++x) {
+          T v;
+          if constexpr (P::kMixed) v = st.ph[3 * at + x] * im; else v = st.p[3 * at + x] * im;
+          s += v * v;
+        }
+        ++cnt;
+      }
+      return (double)gsqrt(s / (T)cnt);
+    }
+  }
+  return 0.0;
+}
+
+// ------------------------------------------------------------------------------------------------
+template <class P, int kThreads>
+__global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
+  using T = typename P::T;
+  const SysDev &S = a.S;
+  const int r = blockIdx.x;
+  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = S.n, nd = 3 * n, no = S.n_obs;
+  unsigned char *ptr = smem;
+  long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
+  long long *red = (long long *)ptr; ptr += 32 * 8;
+  double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
+  double *ek = (double *)ptr; ptr += 2 * 8;
+  State<P> st;
+  st.carve(ptr, n);
+  const uint32_t *pairs = S.pairs;
+  if (a.pairs_in_smem) {
+    uint32_t *sp = (uint32_t *)ptr;
+    for (int i = threadIdx.x; i < S.n_pairs; i += kThreads) sp[i] = S.pairs[i];
+    pairs = sp;
+  }
+  const size_t off = (size_t)r * nd;
+  st.load(S, a.q + off, a.p + off, a.f + off, n, a.c1);
+  for (int i = threadIdx.x; i < nd; i += kThreads) F[i] = 0;
+  if (threadIdx.x < no * 4) acc[threadIdx.x] = a.acc[(size_t)r * no * 4 + threadIdx.x];
+  __syncthreads();
+
+  int err = 0;
+  const T h = (T)a.h, c1 = (T)a.c1;
+  const Pos<P> pos = st.pos();
+  const Params<P> par = st.params(S);
+  for (int s = 0; s < a.k; ++s) {
+    const long long t = a.t_global0 + s;
+    for (int at = threadIdx.x; at < n; at += kThreads)
+      st.baoa(at, philox_stream(a.seed, t, 0u, r, at), h, c1);
+    __syncthreads();
+    const bool sample = a.t_gr > 0 && ((a.t_phase0 + s + 1) % a.t_gr) == 0;
+    long long e_fix = 0;
+    force_pass<P>(S, pos, par, pairs, F, sample, e_fix, &err);
+    __syncthreads();
+    long long k_fix = 0;
+    for (int at = threadIdx.x; at < n; at += kThreads) {
+      const T ke = st.bk(at, F, h);
+      if (sample) k_fix += to_fix(ke, &err);
+    }
+    if (sample) {
+      const long long es = block_sum_ll<kThreads>(e_fix, red);
+      const long long ks = block_sum_ll<kThreads>(k_fix, red);
+      if (threadIdx.x == 0) { ek[0] = (double)es * kFixInv; ek[1] = (double)ks * kFixInv; }
+      __syncthreads();
+      if (threadIdx.x < no) acc_add(acc + 4 * threadIdx.x, observable_ff<P>(S, st, threadIdx.x, ek[0], ek[1]));
+      __syncthreads();
+    }
+  }
+  st.store(a.q + off, a.p + off, a.f + off, n, &err);
+  if (threadIdx.x < no * 4) a.acc[(size_t)r * no * 4 + threadIdx.x] = acc[threadIdx.x];
+  if (a.do_check && threadIdx.x == 0) {
+    int ex;
+    const int label = state_check_f64(S, [&](int at, double x[3]) { st.get_f64(at, x); }, a.omega, &ex);
+    record_check(a, r, label, ex);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+// Analytic 2-D double well: one thread per replica, FP64 (dim = 2, one particle).
+__global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
+  const SysDev &S = a.S;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n_active) return;
+  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
+  double x = a.q[2 * r], y = a.q[2 * r + 1], px = a.p[2 * r], py = a.p[2 * r + 1];
+  double fx = a.f[2 * r], fy = a.f[2 * r + 1];
+  const int no = S.n_obs;
+  double acc[kMaxObs][4];
+  for (int j = 0; j < no; ++j)
+    for (int c = 0; c < 4; ++c) acc[j][c] = a.acc[((size_t)r * no + j) * 4 + c];
+  const double h = a.h, c1 = a.c1, im = 1.0 / S.mass[0];
+  const double sd = sqrt((1.0 - c1 * c1) * S.kT * S.mass[0]);
+  for (int s = 0; s < a.k; ++s) {
+    double xi[4];
+    normals4_f64(philox_stream(a.seed, a.t_global0 + s, 0u, r, 0), xi);
+    px += h * fx; py += h * fy;
+    x += h * px * im; y += h * py * im;
+    px = c1 * px + sd * xi[0]; py = c1 * py + sd * xi[1];
+    x += h * px * im; y += h * py * im;
+    fx = -S.dw_a * 4.0 * x * (x * x - 1.0);
+    fy = -S.dw_b * 2.0 * y;
+    px += h * fx; py += h * fy;
+    if (a.t_gr > 0 && ((a.t_phase0 + s + 1) % a.t_gr) == 0) {
+      for (int j = 0; j < no; ++j) {
+        double v;
+        const int kind = S.obs_kind[j];
+        if (kind == GRP_OBS_COORD) v = S.obs_arg[j][1] == 0 ? x : y;
+        else if (kind == GRP_OBS_POTENTIAL) v = S.dw_a * (x * x - 1.0) * (x * x - 1.0) + S.dw_b * y * y;
+        else v = 0.5 * (px * px + py * py) * im;
+        acc_add(acc[j], v);
+      }
+    }
+  }
+  a.q[2 * r] = x; a.q[2 * r + 1] = y; a.p[2 * r] = px; a.p[2 * r + 1] = py;
+  a.f[2 * r] = fx; a.f[2 * r + 1] = fy;
+  for (int j = 0; j < no; ++j)
+    for (int c = 0; c < 4; ++c) a.acc[((size_t)r * no + j) * 4 + c] = acc[j][c];
+  if (!isfinite(x) || !isfinite(y) || !isfinite(px) || !isfinite(py)) atomicOr(a.err, (int)kErrNaN);
+  if (a.do_check) {
+    int ex;
+    const int label = state_check_f64(S, [&](int, double v[3]) { v[0] = x; v[1] = y; v[2] = 0; }, a.omega, &ex);
+    record_check(a, r, label, ex);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem) {
+  const int n = S.n;
+  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16;
+  b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
+  if (pairs_in_smem) b += (size_t)S.n_pairs * 4;
+  return b;
+}
+
+SegConfig segment_config(const SysDev &S, int threads_hint) {
+  SegConfig c{};
+  if (S.potential == GRP_POT_DOUBLE_WELL_2D) {
+    c.threads = 64;
+    c.smem = 0;
+    return c;
+  }
+  const int items = S.n_dih + S.n_angles + S.n_bonds + S.n_pairs;
+  int t = threads_hint;
+  if (t <= 0) {
+    t = 64;
+    while (t < 512 && t < items) t *= 2;
+  }
+  c.threads = t;
+  c.pairs_in_smem = ff_smem_bytes(S, 1) <= 160 * 1024 ? 1 : 0;
+  c.smem = ff_smem_bytes(S, c.pairs_in_smem);
+  return c;
+}
+
+template <class P, int kT>
+static cudaError_t launch_ff(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
+  auto kern = ff_segment_kernel<P, kT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<a.n_active, kT, c.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
+  switch (c.threads) {
+    case 64: return launch_ff<P, 64>(a, c, st);
+    case 128: return launch_ff<P, 128>(a, c, st);
+    case 256: return launch_ff<P, 256>(a, c, st);
+    case 512: return launch_ff<P, 512>(a, c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t st) {
+  SegArgs a = a0;
+  a.pairs_in_smem = c.pairs_in_smem;
+  if (a.n_active <= 0) return cudaSuccess;
+  if (a.S.potential == GRP_POT_DOUBLE_WELL_2D) {
+    dw_segment_kernel<<<(a.n_active + 63) / 64, 64, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  return a.S.precision == GRP_FP64 ? launch_ff_p<PathF64>(a, c, st) : launch_ff_p<PathMixed>(a, c, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Energies and forces of independent configurations (one block per configuration).
+template <class P>
+__global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const double *q, double *energy,
+                                                            double *forces, int *errp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = S.n, nd = 3 * n, b = blockIdx.x;
+  unsigned char *ptr = smem;
+  long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
+  long long *red = (long long *)ptr; ptr += 32 * 8;
+  State<P> st;
+  st.carve(ptr, n);
+  // positions only: momenta and forces are not used
+  for (int at = threadIdx.x; at < n; at += blockDim.x) {
+    if constexpr (P::kMixed) {
+      const ds x = ds_from_double(q[(size_t)b * nd + 3 * at]), y = ds_from_double(q[(size_t)b * nd + 3 * at + 1]),
+               z = ds_from_double(q[(size_t)b * nd + 3 * at + 2]);
+      st.qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
+      st.ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
+      st.atom[at] = S.atom_f[at];
+    } else {
+      for (int x = 0; x < 3; ++x) st.q[3 * at + x] = q[(size_t)b * nd + 3 * at + x];
+      st.atom[at] = S.atom_d[at];
+    }
+  }
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) F[i] = 0;
+  __syncthreads();
+  int err = 0;
+  long long e_fix = 0;
+  force_pass<P>(S, st.pos(), st.params(S), S.pairs, F, energy != nullptr, e_fix, &err);
+  __syncthreads();
+  if (forces)
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) forces[(size_t)b * nd + i] = (double)F[i] * kFixInv;
+  const long long es = block_sum_ll<256>(e_fix, red);
+  if (energy && threadIdx.x == 0) energy[b] = (double)es * kFixInv;
+  if (err) atomicOr(errp, err);
+}
+
+__global__ void dw_energy_forces_kernel(SysDev S, int nc, const double *q, double *energy, double *forces) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nc) return;
+  const double x = q[2 * b], y = q[2 * b + 1];
+  if (energy) energy[b] = S.dw_a * (x * x - 1.0) * (x * x - 1.0) + S.dw_b * y * y;
+  if (forces) {
+    forces[2 * b] = -S.dw_a * 4.0 * x * (x * x - 1.0);
+    forces[2 * b + 1] = -S.dw_b * 2.0 * y;
+  }
+}
+
+cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, double *energy,
+                                 double *forces, int *err, cudaStream_t st) {
+  if (n_conf <= 0) return cudaSuccess;
+  if (S.potential == GRP_POT_DOUBLE_WELL_2D) {
+    dw_energy_forces_kernel<<<(n_conf + 127) / 128, 128, 0, st>>>(S, n_conf, q, energy, forces);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)3 * S.n * 8 + 32 * 8 +
+                      (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n) : State<PathMixed>::bytes(S.n));
+  cudaError_t e;
+  if (S.precision == GRP_FP64) {
+    e = cudaFuncSetAttribute(energy_forces_kernel<PathF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    energy_forces_kernel<PathF64><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err);
+  } else {
+    e = cudaFuncSetAttribute(energy_forces_kernel<PathMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    energy_forces_kernel<PathMixed><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Stand-alone state check (Section 3.3) from the FP64 state in memory, one thread per replica.
+__global__ void check_kernel(SysDev S, const double *q, int n_rep, int omega, int8_t *labels, uint8_t *exited,
+                             unsigned long long *exit_key, long long M) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rep) return;
+  const double *qr = q + (size_t)r * S.nd;
+  const int dim = S.dim;
+  int ex;
+  const int label = state_check_f64(
+      S, [&](int at, double x[3]) { x[0] = qr[dim * at]; x[1] = qr[dim * at + 1]; x[2] = dim == 3 ? qr[dim * at + 2] : 0.0; },
+      omega, &ex);
+  if (labels) labels[r] = (int8_t)label;
+  if (exited) exited[r] = (uint8_t)ex;
+  if (ex && exit_key) atomicMin(exit_key, ((unsigned long long)M << 32) | (unsigned long long)(unsigned)r);
+}
+
+cudaError_t launch_check(const SysDev &S, const double *q, int n_rep, int omega, int8_t *labels,
+                         uint8_t *exited, unsigned long long *exit_key, long long M, cudaStream_t st) {
+  check_kernel<<<(n_rep + 127) / 128, 128, 0, st>>>(S, q, n_rep, omega, labels, exited, exit_key, M);
+  return cudaGetLastError();
+}
+
+}  // namespace grp
