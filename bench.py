@@ -1,0 +1,360 @@
+"""Benchmark of the Gen. ParRep hot path on one GB300 (or N ranks, one GPU each, replicas only).
+
+Workload: the 22-bead peptide-like chain (alanine-dipeptide stand-in, Section 4.1 shape), 256
+replicas, mixed precision, t_check = 500 steps, t_GR = 10 steps.  One benchmark step is one pass of
+the convergence-step loop body over the whole replica set: a 500-step BAOAB segment with force-field
+evaluation, observable sampling every 10 steps and the fused exit test, the Fleming-Viot branching of
+exited workers, the Gelman-Rubin reduction, and the host readback of the per-check status — i.e. one
+exit test of the method (Section 2.4.1).  Metric: replica-atom-steps/s (whole job).
+
+Also reported: the same step on the plain FP64 GPU path, accelerated simulation speed (ns/day of
+simulated clock, Tables 2 and 4) from a bounded run of the whole loop, the oracle on the host cores,
+the roofline of the dominant kernel and the SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1807_02431_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "chain22_r256"
+SEED = 2431
+
+
+def algorithmic_flops_per_replica_step(s: W.System) -> float:
+    """FP32 flops per replica-step of the force kernel: 40 per non-excluded pair, 15 per bond,
+    40 per angle and 100 per three-term dihedral (33 per term), FMA counted as 2."""
+    n = s.n_atoms
+    excl = {tuple(sorted(x)) for x in s.excl.tolist()}
+    n_pairs = n * (n - 1) // 2 - len(excl)
+    return 40.0 * n_pairs + 15.0 * len(s.bonds) + 40.0 * len(s.angles) + 33.3 * len(s.dihedral_k)
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def _oracle_worker(args):
+    r0, r1, steps, seed = args
+    import oracle
+
+    s = W.chain()
+    o = oracle.Oracle(s)
+    q, p = W.replica_states(s, r1 - r0, seed=seed + r0, spread=0.002)
+    f = np.stack([o.forces(q[i]) for i in range(r1 - r0)])
+    t = time.time()
+    o.step_k(q, p, f, SEED, 0, 0, steps, s.t_gr, cap=steps // s.t_gr)
+    ex = np.array([o.exited(q[i], 1) for i in range(r1 - r0)], np.uint8)
+    return time.time() - t, int(ex.sum())
+
+
+def cpu_oracle(n_replicas: int, steps: int, cores: int):
+    """The FP64 oracle on the host cores: the replicas of the sample split over `cores` spawned
+    processes (each single-threaded).  Returns replica-atom-steps/s and the wall time."""
+    s = W.chain()
+    chunks = np.array_split(np.arange(n_replicas), cores)
+    tasks = [(int(c[0]), int(c[-1]) + 1, steps, 7) for c in chunks if len(c)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(tasks)) as pool:
+        pool.map(_oracle_worker, [(0, 1, 1, 7)] * len(tasks))  # start-up and build outside the clock
+        t = time.time()
+        pool.map(_oracle_worker, tasks)
+        wall = time.time() - t
+    return n_replicas * steps * s.n_atoms / wall, wall
+
+
+# ----------------------------------------------------------------------------- GPU step
+class Step:
+    """One convergence-step check of the method over the whole replica set (see module doc)."""
+
+    def __init__(self, B, s: W.System, precision: int, R: int, seed: int, device_index: int):
+        import torch
+
+        self.B, self.s, self.R = B, s, R
+        self.sysh = B.grp_create_system(s, precision)
+        q0, p0 = W.replica_states(s, R, seed=seed, spread=0.002)
+        self.q0, self.p0 = q0, p0
+        self.stream = torch.cuda.current_stream()
+        self.rep = B.grp_init_replicas(self.sysh, R, seed, q0, p0, per_replica=True, stream=self.stream)
+        self.launches_per_step = 3  # segment, branching, Gelman-Rubin
+        self.status = B.FvStatus()
+
+    def __call__(self):
+        s = self.s
+        # omega = 1: the chain starts in state 1 (outside the paper's rectangle); min_fv_steps = 0 so
+        # that every check also evaluates the Gelman-Rubin ratios
+        return self.B.grp_fv_check(self.rep, 1, s.t_check, s.t_gr, s.tol, 0, self.stream, self.status)
+
+    def reset(self):
+        self.B.grp_set_state(self.rep, self.q0, self.p0, np.zeros((self.R, len(self.s.observables), 4)),
+                             {"t_global": 0, "t_phase": 0}, self.stream)
+
+
+def time_steps(step, K, W_, flush, events_stream):
+    import torch
+
+    for _ in range(W_):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()  # write 256 MB > L2 between timed iterations (outside the events)
+        ev[i][0].record(events_stream)
+        step()
+        ev[i][1].record(events_stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def segment_kernel_ms(B, step, n):
+    """Average duration of the segment kernel alone (CUDA events on the launching stream)."""
+    import torch
+
+    s = step.s
+    st = step.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    B.grp_step_k(step.rep, s.t_check, s.t_gr, 0, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(n):
+        B.grp_step_k(step.rep, s.t_check, s.t_gr, 0, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def e2e_steps(B, step, K):
+    """The same step through the public API with host buffers: H2D of the replica state from pinned
+    host memory, the step, D2H of positions and the Gelman-Rubin ratios, every step."""
+    import torch
+
+    s, R = step.s, step.R
+    nd = R * s.n_atoms * s.dim
+    hq = torch.from_numpy(step.q0.copy()).pin_memory()
+    hp = torch.from_numpy(step.p0.copy()).pin_memory()
+    hout = torch.empty(nd, dtype=torch.float64).pin_memory()
+    ctr = {"t_global": 0, "t_phase": 0}
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(K):
+        B.grp_set_state(step.rep, hq.numpy(), hp.numpy(), None, ctr, step.stream)
+        step()
+        B.grp_get_state(step.rep, step.stream, q=hout.numpy().reshape(R, s.n_atoms, s.dim),
+                        p=np.empty((R, s.n_atoms, s.dim)))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    return wall, 2 * nd * 8, nd * 8 + 8 * len(s.observables)
+
+
+def accelerated_speed(B, s, precision, R, seed, max_steps):
+    """Simulated clock per wall time of the whole loop (Fig. 1) on the same system."""
+    import torch
+
+    sysh = B.grp_create_system(s, precision)
+    rep = B.grp_init_replicas(sysh, R, seed, s.q0, s.p0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ev, tsim = B.grp_run(rep, s.t_gr, s.t_check, s.tol, s.min_fv_steps, max_steps, 10 ** 6)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    ns = tsim * s.dt * 1e-3
+    return {"ns_per_day": ns / (wall / 86400.0), "t_sim_ns": ns, "wall_s": wall,
+            "events": {k: sum(1 for e in ev if e["kind"] == v) for k, v in
+                       (("fv_converged", 2), ("ref_exit", 1), ("parallel_exit", 3))}}
+
+
+def run_reference(args):
+    """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
+    bounded sample: the 256 replicas advanced 20 steps with sampling and the exit test."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    s = W.chain()
+    R, steps = s.n_replicas, 20
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, wall = cpu_oracle(R, steps, cores)
+        if i >= args.warmup:
+            vals.append((v, wall))
+    value = float(np.mean([v for v, _ in vals]))
+    ms = float(np.mean([w for _, w in vals])) * 1e3
+    line = {"metric": "replica-atom-steps/s", "value": value, "unit": "replica-atom-steps/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "n_replicas": R, "steps_per_sample": steps},
+            "cpu_baseline": {"value": value, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{R} replicas x {steps} BAOAB steps (sampling every {s.t_gr}) + exit test, "
+                                       f"split over {cores} processes"},
+            "e2e": {"value": value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="grp", choices=["grp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--accel-steps", type=int, default=200000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1807_02431_gb300 import binding as B
+    from paper_1807_02431_gb300 import build as build_mod
+
+    if rank == 0 or not os.path.exists(build_mod.LIB):
+        build_mod.build()
+    if world > 1:
+        torch.distributed.barrier()
+    B.load()
+    s = W.chain()
+    R = s.n_replicas
+    seed = SEED + 1000 * rank
+    step = Step(B, s, B.GRP_MIXED, R, seed, local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times = time_steps(step, args.steps, args.warmup, flush, step.stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t_total = float(np.sum(times)) / 1e3
+    units_per_step = R * s.n_atoms * s.t_check
+    if world > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * units_per_step * args.steps / t_total
+    clocks = clk.summary()
+    out = None
+    if rank == 0:
+        # dominant kernel: the fused segment kernel, timed alone on its stream
+        seg_ms = segment_kernel_ms(B, step, 10)
+        flops = algorithmic_flops_per_replica_step(s) * R * s.t_check
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        peak = fp32_peak_tflops(2070.0)
+        achieved = flops / (seg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "ff_segment_kernel<PathMixed,256>",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
+                "kernel_ms": seg_ms, "flops_per_launch": flops, "median_sm_mhz": sm_mhz}
+        # plain FP64 GPU path, same step
+        step64 = Step(B, s, B.GRP_FP64, R, seed, local)
+        t64 = time_steps(step64, args.fp64_steps, 1, flush, step64.stream)
+        fp64_value = units_per_step * len(t64) / (float(np.sum(t64)) / 1e3)
+        # end to end through the public API with host buffers
+        step.reset()
+        e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
+        e2e_value = units_per_step * args.steps / e2e_wall
+        accel = accelerated_speed(B, s, B.GRP_MIXED, R, seed, args.accel_steps) if args.accel_steps > 0 else None
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cores = os.cpu_count() or 1
+            cv, cwall = cpu_oracle(R, 500, cores)
+            cpu = {"value": cv, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{R} replicas x 500 BAOAB steps (one t_check segment, sampling every {s.t_gr}) "
+                             f"+ exit test, split over {cores} spawned processes; wall {cwall:.2f} s"}
+        out = {"metric": "replica-atom-steps/s", "value": value, "unit": "replica-atom-steps/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "n_replicas": R, "t_check": s.t_check,
+                          "t_gr": s.t_gr, "precision": "mixed (FP32 forces, int64 fixed point, double-single "
+                          "integration)", "parallelism": f"replicas-only x{world}",
+                          "l2": "flushed between timed steps (256 MB write outside the events)"},
+               "gpu_launches": step.launches_per_step * args.steps,
+               "roofline": roof, "clocks": clocks,
+               "fp64_path": {"value": fp64_value, "unit": "replica-atom-steps/s",
+                             "ms_per_step": float(np.mean(t64)), "speedup_of_mixed": value / world / fp64_value},
+               "accelerated": accel,
+               "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
+                       "d2h_bytes_per_step": bo},
+               "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

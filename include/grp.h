@@ -33,7 +33,7 @@ typedef int32_t grp_status;
 #define GRP_ENOMEM (-2)    /* device or host allocation failed */
 #define GRP_ECUDA (-3)     /* a CUDA runtime call failed */
 #define GRP_ENAN (-4)      /* a kernel found a non-finite position or momentum */
-#define GRP_EOVERFLOW (-5) /* a force contribution exceeded the fixed-point range (|f| >= 2^20) */
+#define GRP_EOVERFLOW (-5) /* a force contribution exceeded the fixed-point range (|f| >= 2^15) */
 #define GRP_ETIMEOUT (-6)  /* a bounded loop ran out before its condition was met */
 #define GRP_ENOTIMPL (-7)  /* the requested combination is not supported */
 #define GRP_NOEXIT 1       /* positive: the parallel phase ended after max_checks without exit */
@@ -204,6 +204,26 @@ grp_status grp_run_parallel_phase(grp_replicas *r, int32_t omega, int32_t t_chec
 /* Copy replica src to every replica, clear the accumulators and set t_phase = 0 (the broadcast of
  * the reference configuration before a convergence step, Section 3.1). */
 grp_status grp_broadcast(grp_replicas *r, int32_t src, void *stream);
+
+/* Status of one exit test of the convergence step. */
+typedef struct {
+  int32_t ref_exited;   /* the reference walker left omega at this check */
+  int32_t label0;       /* state of the reference walker (-1: none) */
+  int32_t n_branched;   /* F-V workers overwritten at this check */
+  int32_t converged;    /* Gelman-Rubin criterion met (only when evaluated) */
+  int32_t gr_evaluated; /* t_phase >= min_fv_steps, so the ratios were computed */
+  int32_t pad;
+  int64_t t_phase;      /* F-V time after the check, steps */
+  double rhat[GRP_MAX_OBS];
+} grp_fv_status;
+
+/* One exit test of the convergence step (Section 2.4.1): every replica advances t_check BAOAB steps
+ * sampling observables every t_gr, the exit test runs on every replica, exited workers are branched,
+ * and when t_phase >= min_fv_steps the Gelman-Rubin ratios are evaluated; one small readback fills
+ * h_out.  When the reference walker exited, the caller abandons the phase (the branching done on the
+ * workers is then irrelevant). */
+grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_check, int32_t t_gr, double tol,
+                        int64_t min_fv_steps, grp_fv_status *h_out, void *stream);
 
 /* Whole loop of Fig. 1 from the current state of replica 0: transient, convergence (F-V with
  * Gelman-Rubin), parallel step, clock updates (Section 2.4.1, Eq. 6).  Writes at most max_events

@@ -73,6 +73,12 @@ class RunParams(C.Structure):
                 ("max_steps", C.c_int64), ("max_exits", C.c_int32)]
 
 
+class FvStatus(C.Structure):
+    _fields_ = [("ref_exited", C.c_int32), ("label0", C.c_int32), ("n_branched", C.c_int32),
+                ("converged", C.c_int32), ("gr_evaluated", C.c_int32), ("pad", C.c_int32),
+                ("t_phase", C.c_int64), ("rhat", C.c_double * GRP_MAX_OBS)]
+
+
 class Event(C.Structure):
     _fields_ = [("kind", C.c_int32), ("omega", C.c_int32), ("label_to", C.c_int32), ("k", C.c_int32),
                 ("M", C.c_int64), ("steps", C.c_int64), ("t_sim", C.c_int64), ("n_branch", C.c_int64)]
@@ -92,6 +98,8 @@ SIGNATURES = {
     "grp_gelman_rubin": (C.c_int32, [_VP, C.c_double, _D, _I32P, _VP]),
     "grp_run_parallel_phase": (C.c_int32, [_VP, C.c_int32, C.c_int32, C.c_int64, C.POINTER(Exit), _VP]),
     "grp_broadcast": (C.c_int32, [_VP, C.c_int32, _VP]),
+    "grp_fv_check": (C.c_int32, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int64,
+                                 C.POINTER(FvStatus), _VP]),
     "grp_run": (C.c_int32, [_VP, C.POINTER(RunParams), C.POINTER(Event), C.c_int32, _I32P,
                             C.POINTER(C.c_int64), _VP]),
     "grp_get_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
@@ -268,6 +276,14 @@ def grp_run_parallel_phase(r: ReplicasHandle, omega: int, t_check: int, max_chec
 
 def grp_broadcast(r: ReplicasHandle, src: int = 0, stream=None):
     _check(_lib.grp_broadcast(r.handle, src, _stream(stream)))
+
+
+def grp_fv_check(r: ReplicasHandle, omega: int, t_check: int, t_gr: int, tol: float, min_fv_steps: int = 0,
+                 stream=None, out: FvStatus | None = None) -> FvStatus:
+    """One exit test of the convergence step; returns the status structure (reused when given)."""
+    out = FvStatus() if out is None else out
+    _check(_lib.grp_fv_check(r.handle, omega, t_check, t_gr, tol, min_fv_steps, C.byref(out), _stream(stream)))
+    return out
 
 
 def grp_run(r: ReplicasHandle, t_gr: int, t_check: int, tol: float, min_fv_steps: int, max_steps: int,

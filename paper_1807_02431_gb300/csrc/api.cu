@@ -294,7 +294,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
   if (e) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
-    return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range (|f| >= 2^20)");
+    return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range (|f| >= 2^15)");
   }
   return GRP_OK;
 }
@@ -352,7 +352,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
       CU(cudaMemcpyAsync(r->p + i * nd, h_p0, nd * 8, cudaMemcpyHostToDevice, st));
     }
   }
-  CU(cudaMemsetAsync(r->acc, 0, R * nacc * 8 + 8, st));
+  if (nacc > 0) CU(cudaMemsetAsync(r->acc, 0, R * nacc * 8, st));
   CU(cudaMemsetAsync(r->labels, 0, R, st));
   CU(cudaMemsetAsync(r->exited, 0, R, st));
   CU(cudaMemsetAsync(r->err, 0, 4, st));
@@ -513,6 +513,47 @@ extern "C" grp_status grp_broadcast(grp_replicas *r, int32_t src, void *stream) 
   return GRP_OK;
 }
 
+// One exit test of the convergence step: segment with the fused exit test, branching of exited
+// workers, Gelman-Rubin ratios when t_phase >= min_fv_steps, and one readback of the status.
+static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, double tol, long long min_fv_steps,
+                           grp_fv_status *out, cudaStream_t st) {
+  const SysDev &D = r->sys->dev;
+  const int R = r->R;
+  grp_status e = run_steps(r, t_check, t_gr, R, 1, omega, 0, 0, st);
+  if (e != GRP_OK) return e;
+  CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
+  CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
+  const bool want_gr = r->t_phase >= min_fv_steps && R > 1 && D.n_obs > 0;
+  if (want_gr) {
+    CU(launch_gelman_rubin(D, R, r->acc, tol, r->rhat, nullptr, st));
+    CU(cudaMemcpyAsync(r->hb->rhat, r->rhat, sizeof(double) * D.n_obs, cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  out->ref_exited = r->hb->exited0;
+  out->label0 = r->hb->label0;
+  out->n_branched = r->hb->n_branched;
+  out->gr_evaluated = want_gr ? 1 : 0;
+  out->t_phase = r->t_phase;
+  out->pad = 0;
+  int conv = want_gr ? 1 : 0;
+  for (int j = 0; j < GRP_MAX_OBS; ++j) {
+    out->rhat[j] = (want_gr && j < D.n_obs) ? r->hb->rhat[j] : 0.0;
+    if (want_gr && j < D.n_obs && !(r->hb->rhat[j] < 1.0 + tol)) conv = 0;
+  }
+  out->converged = conv;
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_check, int32_t t_gr, double tol,
+                                   int64_t min_fv_steps, grp_fv_status *h_out, void *stream) {
+  if (!r || !h_out) return fail(GRP_EINVAL, "grp_fv_check: null argument");
+  if (t_check < 1 || t_gr < 0) return fail(GRP_EINVAL, "grp_fv_check: need t_check >= 1, t_gr >= 0");
+  return fv_check(r, omega, t_check, t_gr, tol, min_fv_steps, h_out, (cudaStream_t)stream);
+}
+
 // ------------------------------------------------------------------------------------------------
 extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
                               int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
@@ -562,38 +603,21 @@ extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_even
     long long nbranch = 0;
     int converged = 0, ref_exit = 0;
     while (r->t_global < p->max_steps) {
-      if ((e = run_steps(r, p->t_check, p->t_gr, R, 1, omega, 0, 0, st)) != GRP_OK) return e;
-      CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
-      CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
-      const bool want_gr = r->t_phase >= p->min_fv_steps && R > 1 && D.n_obs > 0;
-      if (want_gr) {
-        CU(launch_gelman_rubin(D, R, r->acc, p->tol, r->rhat, nullptr, st));
-        CU(cudaMemcpyAsync(r->hb->rhat, r->rhat, sizeof(double) * D.n_obs, cudaMemcpyDeviceToHost, st));
-      }
-      CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
-      CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
-      CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      // (a) the reference walker left omega: the F-V workers are discarded (the branching above
-      //     only touched workers, which the next broadcast overwrites)
-      if (r->hb->exited0) {
+      grp_fv_status fs;
+      if ((e = fv_check(r, omega, p->t_check, p->t_gr, p->tol, p->min_fv_steps, &fs, st)) != GRP_OK) return e;
+      // (a) the reference walker left omega: the F-V workers are discarded
+      if (fs.ref_exited) {
         tsim += r->t_phase;
-        log(GRP_EV_REF_EXIT, omega, r->hb->label0, 0, 0, r->t_phase, nbranch);
+        log(GRP_EV_REF_EXIT, omega, fs.label0, 0, 0, r->t_phase, nbranch);
         ++nexit;
         ref_exit = 1;
         break;
       }
-      // (b) branching done on the device
-      const int nb = r->hb->n_branched;
-      if (nb > 0 && nb == R - 1) log(GRP_EV_FV_ALL_EXITED, omega, omega, 0, 0, r->t_phase, nb);
-      nbranch += nb;
+      // (b) branching (done on the device)
+      if (fs.n_branched > 0 && fs.n_branched == R - 1) log(GRP_EV_FV_ALL_EXITED, omega, omega, 0, 0, r->t_phase, fs.n_branched);
+      nbranch += fs.n_branched;
       // (c) Gelman-Rubin test, Eq. 4
-      if (want_gr) {
-        int ok = 1;
-        for (int j = 0; j < D.n_obs; ++j)
-          if (!(r->hb->rhat[j] < 1.0 + p->tol)) ok = 0;
-        if (ok) { converged = 1; break; }
-      }
+      if (fs.gr_evaluated && fs.converged) { converged = 1; break; }
     }
     if (ref_exit) continue;
     if (!converged) break;

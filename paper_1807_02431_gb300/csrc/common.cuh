@@ -14,12 +14,14 @@ constexpr int kMaxGroups = GRP_MAX_GROUPS;
 // Error bits latched by kernels into the replica set's error word.
 enum : int { kErrNaN = 1, kErrOverflow = 2 };
 
-// Fixed point: one unit = 2^-32 of the force (or energy) unit.  A single contribution must stay
-// below 2^20 in magnitude so that up to 2^10 of them sum without overflowing int64.
-constexpr double kFixScale = 4294967296.0;          // 2^32
-constexpr double kFixInv = 1.0 / 4294967296.0;
-constexpr float kFixScaleF = 4294967296.0f;
-constexpr double kFixLimit = 1048576.0;               // 2^20
+// Fixed point: one unit = 2^-40 of the force (or energy) unit, so that quantisation (9e-13) stays
+// below FP64 rounding of typical forces.  A single contribution must stay below 2^15 in magnitude,
+// so that 2^8 contributions at that bound still sum inside int64.
+constexpr double kFixScale = 1099511627776.0;       // 2^40
+constexpr double kFixInv = 1.0 / 1099511627776.0;
+constexpr float kFixScaleF = 1099511627776.0f;
+constexpr float kFixInvF = 1.0f / 1099511627776.0f;
+constexpr double kFixLimit = 32768.0;                 // 2^15
 
 // Device copy of a system.  All arrays are device memory owned by grp_system.  Parameters exist in
 // FP64 (FP64 path) and FP32 (mixed path) copies.

@@ -94,15 +94,61 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
   if (want_e) e_fix += to_fix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
 }
 
+// r - r0 of a bond for the mixed path in double-single arithmetic: the FP32 distance of a stiff bond
+// (k = 3e5) loses ~1e-8 nm to rounding before the subtraction of r0, which would dominate the force
+// error; here the difference vector, r^2 (exact products by fma) and one Newton step on sqrt keep
+// r - r0 accurate to ~1e-7 of itself.  Returns r - r0 and the FP32 distance r.
+__device__ __forceinline__ float bond_dr_ds(const Pos<PathMixed> &pos, int i, int j, float r0, float &r_out,
+                                            V3<float> &d_out) {
+  const float4 a = pos.qh[i], b = pos.qh[j], c = pos.ql[i], e = pos.ql[j];
+  const float *ah = &a.x, *bh = &b.x, *al = &c.x, *bl = &e.x;
+  float dh[3], dl[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const float s = __fsub_rn(ah[x], bh[x]);
+    const float bp = __fsub_rn(s, ah[x]);
+    const float err = __fadd_rn(__fsub_rn(ah[x], __fsub_rn(s, bp)), __fsub_rn(-bh[x], bp));  // TwoSum(a, -b)
+    const float lo = __fadd_rn(err, __fsub_rn(al[x], bl[x]));
+    dh[x] = __fadd_rn(s, lo);
+    dl[x] = __fsub_rn(lo, __fsub_rn(dh[x], s));
+  }
+  // r^2 = sum (dh + dl)^2 as hi + lo
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const float p = __fmul_rn(dh[x], dh[x]);
+    const float pe = __fmaf_rn(dh[x], dh[x], -p);
+    const float t = __fadd_rn(sh, p);
+    const float tb = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, tb)), __fsub_rn(p, tb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, __fmaf_rn(2.f * dh[x], dl[x], pe)));
+  }
+  const float r = sqrtf(sh);
+  const float rr = __fmul_rn(r, r);
+  const float rre = __fmaf_rn(r, r, -rr);
+  const float resid = __fadd_rn(__fsub_rn(__fsub_rn(sh, rr), rre), sl);  // r^2 - r*r, exactly-ish
+  const float rlo = resid / (2.f * r);
+  r_out = r;
+  d_out = {dh[0], dh[1], dh[2]};
+  return __fadd_rn(__fsub_rn(r, r0), rlo);
+}
+
 // Harmonic bond 1/2 k (r - r0)^2.
 template <class P>
 __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
                                           long long *F, bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
   const auto kp = par.bond[b];
-  const V3<T> d = pos.diff(i, j);
-  const T r = gsqrt(dot(d, d));
-  const T dr = r - T(kp.y);
+  V3<T> d;
+  T r, dr;
+  if constexpr (P::kMixed) {
+    dr = bond_dr_ds(pos, i, j, kp.y, r, d);
+  } else {
+    d = pos.diff(i, j);
+    r = gsqrt(dot(d, d));
+    dr = r - T(kp.y);
+  }
   const T g = -T(kp.x) * dr / r;
   const V3<T> fi = {g * d.x, g * d.y, g * d.z};
   add_force(F, i, fi, err);

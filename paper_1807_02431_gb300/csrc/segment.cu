@@ -82,6 +82,10 @@ __device__ __forceinline__ void record_check(const SegArgs &a, int r, int label,
     atomicMin(a.exit_key, ((unsigned long long)a.M << 32) | (unsigned long long)(unsigned)r);
 }
 
+__device__ __forceinline__ unsigned char *align32(unsigned char *p) {
+  return (unsigned char *)(((uintptr_t)p + 31) & ~(uintptr_t)31);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Shared-memory replica state of each precision path.
 template <class P>
@@ -231,7 +235,7 @@ struct State<PathMixed> {
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const int i = 3 * at + x;
-      const float fv = (float)F[i] * 0x1p-32f;
+      const float fv = (float)F[i] * kFixInvF;
       F[i] = 0;
       f[i] = fv;
       ds P = {ph[i], pl[i]};
@@ -319,9 +323,11 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
   double *ek = (double *)ptr; ptr += 2 * 8;
   State<P> st;
+  ptr = align32(ptr);
   st.carve(ptr, n);
   const uint32_t *pairs = S.pairs;
   if (a.pairs_in_smem) {
+    ptr = align32(ptr);
     uint32_t *sp = (uint32_t *)ptr;
     for (int i = threadIdx.x; i < S.n_pairs; i += kThreads) sp[i] = S.pairs[i];
     pairs = sp;
@@ -419,7 +425,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 // ------------------------------------------------------------------------------------------------
 static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem) {
   const int n = S.n;
-  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16;
+  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 64;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
   if (pairs_in_smem) b += (size_t)S.n_pairs * 4;
   return b;
@@ -486,6 +492,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
   long long *red = (long long *)ptr; ptr += 32 * 8;
   State<P> st;
+  ptr = align32(ptr);
   st.carve(ptr, n);
   // positions only: momenta and forces are not used
   for (int at = threadIdx.x; at < n; at += blockDim.x) {
@@ -531,7 +538,7 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
     dw_energy_forces_kernel<<<(n_conf + 127) / 128, 128, 0, st>>>(S, n_conf, q, energy, forces);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)3 * S.n * 8 + 32 * 8 +
+  const size_t smem = (size_t)3 * S.n * 8 + 32 * 8 + 32 +
                       (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n) : State<PathMixed>::bytes(S.n));
   cudaError_t e;
   if (S.precision == GRP_FP64) {
