@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
       __syncthreads();
     }
   }
+  __syncthreads();  // the write-back reads coordinates owned by other threads
   st.store(a.q + off, a.p + off, a.f + off, n, &err);
   if (threadIdx.x < no * 4) a.acc[(size_t)r * no * 4 + threadIdx.x] = acc[threadIdx.x];
   if (a.do_check && threadIdx.x == 0) {
