@@ -319,9 +319,13 @@ def main():
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
                 "kernel_ms": seg_ms, "flops_per_launch": flops, "median_sm_mhz": sm_mhz}
         # plain FP64 GPU path, same step
-        step64 = Step(B, s, B.GRP_FP64, R, seed, local)
-        t64 = time_steps(step64, args.fp64_steps, 1, flush, step64.stream)
-        fp64_value = units_per_step * len(t64) / (float(np.sum(t64)) / 1e3)
+        fp64 = None
+        if args.fp64_steps > 0:
+            step64 = Step(B, s, B.GRP_FP64, R, seed, local)
+            t64 = time_steps(step64, args.fp64_steps, 1, flush, step64.stream)
+            fp64_value = units_per_step * len(t64) / (float(np.sum(t64)) / 1e3)
+            fp64 = {"value": fp64_value, "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(t64)),
+                    "speedup_of_mixed": value / world / fp64_value}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
@@ -344,8 +348,7 @@ def main():
                           "l2": "flushed between timed steps (256 MB write outside the events)"},
                "gpu_launches": step.launches_per_step * args.steps,
                "roofline": roof, "clocks": clocks,
-               "fp64_path": {"value": fp64_value, "unit": "replica-atom-steps/s",
-                             "ms_per_step": float(np.mean(t64)), "speedup_of_mixed": value / world / fp64_value},
+               "fp64_path": fp64,
                "accelerated": accel,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},
