@@ -124,9 +124,36 @@ __device__ __forceinline__ long long to_fix(double v, int *err) {
   if (!(fabs(v) < kFixLimit)) { *err |= kErrOverflow; return 0; }
   return __double2ll_rn(v * kFixScale);
 }
-__device__ __forceinline__ long long to_fix(float v, int *err) {
-  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return 0; }
-  return __float2ll_rn(v * kFixScaleF);
+// FP32 -> 64-bit fixed point built from 32-bit conversions only: the 64-bit int<->float conversions
+// execute on the FP64 pipe, which on GB300 runs at 1/64 of the FP32 rate.  With a = v 2^8 (exact),
+// hi = floor(a) and the fraction r = a - hi in [0, 1), the fixed-point value is hi 2^32 + r 2^32.
+struct Fix2 {
+  int hi;
+  unsigned int lo;
+};
+__device__ __forceinline__ Fix2 to_fix2(float v, int *err) {
+  Fix2 f{0, 0u};
+  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return f; }
+  const float a = v * 256.0f;
+  const float hf = floorf(a);
+  const float r = a - hf;  // exact except for tiny negative a, where it may round up to 1
+  f.hi = (int)hf;
+  if (r >= 1.0f) {
+    f.hi += 1;
+  } else {
+    f.lo = __float2uint_rn(r * 4294967296.0f);
+  }
+  return f;
+}
+__device__ __forceinline__ long long fix2_value(Fix2 f) {
+  return (long long)(((unsigned long long)(unsigned int)f.hi << 32) | f.lo);
+}
+__device__ __forceinline__ long long to_fix(float v, int *err) { return fix2_value(to_fix2(v, err)); }
+// int64 fixed point -> FP32 from two 32-bit conversions.
+__device__ __forceinline__ float fix_to_float(long long x) {
+  const int hi = (int)(x >> 32);
+  const unsigned int lo = (unsigned int)x;
+  return fmaf((float)hi, 4294967296.0f, (float)lo) * kFixInvF;
 }
 // 64-bit shared-memory atomics are not native on sm_103a (measured: 5x slower than 32-bit, 140x
 // under a 32-way address conflict), so the int64 accumulator is updated as two 32-bit words: the low
@@ -139,6 +166,12 @@ __device__ __forceinline__ void fix_add(long long *dst, long long v) {
   const unsigned int old = atomicAdd(&w[0], lo);
   const unsigned int carry = (unsigned int)(old + lo < old);
   atomicAdd(&w[1], hi + carry);
+}
+__device__ __forceinline__ void fix_add(long long *dst, Fix2 f) {
+  unsigned int *w = reinterpret_cast<unsigned int *>(dst);
+  const unsigned int old = atomicAdd(&w[0], f.lo);
+  const unsigned int carry = (unsigned int)(old + f.lo < old);
+  atomicAdd(&w[1], (unsigned int)f.hi + carry);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -65,11 +65,15 @@ struct Params<PathMixed> {
   const float4 *term;
 };
 
-template <class T>
-__device__ __forceinline__ void add_force(long long *F, int a, V3<T> g, int *err) {
+__device__ __forceinline__ void add_force(long long *F, int a, V3<double> g, int *err) {
   fix_add(&F[3 * a + 0], to_fix(g.x, err));
   fix_add(&F[3 * a + 1], to_fix(g.y, err));
   fix_add(&F[3 * a + 2], to_fix(g.z, err));
+}
+__device__ __forceinline__ void add_force(long long *F, int a, V3<float> g, int *err) {
+  fix_add(&F[3 * a + 0], to_fix2(g.x, err));
+  fix_add(&F[3 * a + 1], to_fix2(g.y, err));
+  fix_add(&F[3 * a + 2], to_fix2(g.z, err));
 }
 
 // Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j).

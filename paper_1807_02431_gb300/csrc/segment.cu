@@ -235,7 +235,7 @@ struct State<PathMixed> {
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const int i = 3 * at + x;
-      const float fv = (float)F[i] * kFixInvF;
+      const float fv = fix_to_float(F[i]);
       F[i] = 0;
       f[i] = fv;
       ds P = {ph[i], pl[i]};
@@ -342,12 +342,15 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   const T h = (T)a.h, c1 = (T)a.c1;
   const Pos<P> pos = st.pos();
   const Params<P> par = st.params(S);
+  // steps until the next sample: (t_phase0 + s + 1) % t_gr == 0
+  int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
   for (int s = 0; s < a.k; ++s) {
     const long long t = a.t_global0 + s;
     for (int at = threadIdx.x; at < n; at += kThreads)
       st.baoa(at, philox_stream(a.seed, t, 0u, r, at), h, c1);
     __syncthreads();
-    const bool sample = a.t_gr > 0 && ((a.t_phase0 + s + 1) % a.t_gr) == 0;
+    const bool sample = --until == 0;
+    if (sample) until = a.t_gr;
     long long e_fix = 0;
     force_pass<P>(S, pos, par, pairs, F, sample, e_fix, &err);
     __syncthreads();
