@@ -155,6 +155,38 @@ __device__ __forceinline__ float fix_to_float(long long x) {
   const unsigned int lo = (unsigned int)x;
   return fmaf((float)hi, 4294967296.0f, (float)lo) * kFixInvF;
 }
+
+// Mixed-path force accumulator: fixed point with 2^-32 units kept as two 32-bit words that are
+// summed separately with non-returning atomics (no carry between them): a contribution v 2^32 is
+// split as hi 2^20 + lo with lo in [0, 2^20).  The lo word holds up to 4,096 contributions without
+// wrapping; the hi word is summed modulo 2^32, exact as long as the total |F| < 2^19.  The value is
+// hi_sum 2^20 + lo_sum, the same integer whatever the order of the additions.
+constexpr float kSplitHiScale = 4096.0f;       // 2^32 / 2^20
+constexpr float kSplitLoScale = 1048576.0f;    // 2^20
+constexpr float kSplitInv = 2.3283064365386963e-10f;  // 2^-32
+struct Split {
+  int hi;
+  unsigned int lo;
+};
+__device__ __forceinline__ Split to_split(float v, int *err) {
+  Split s{0, 0u};
+  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return s; }
+  const float a = v * kSplitHiScale;
+  const float hf = floorf(a);
+  s.hi = (int)hf;
+  unsigned int lo = __float2uint_rn((a - hf) * kSplitLoScale);
+  if (lo >= (1u << 20)) { lo -= (1u << 20); s.hi += 1; }
+  s.lo = lo;
+  return s;
+}
+__device__ __forceinline__ long long split_value(Split s) { return (long long)s.hi * (1ll << 20) + (long long)s.lo; }
+__device__ __forceinline__ void split_add(int *hi, unsigned int *lo, int idx, Split s) {
+  atomicAdd(&hi[idx], s.hi);
+  atomicAdd(&lo[idx], s.lo);
+}
+__device__ __forceinline__ float split_to_float(int hi_sum, unsigned int lo_sum) {
+  return fmaf((float)hi_sum, kSplitLoScale, (float)lo_sum) * kSplitInv;
+}
 // 64-bit shared-memory atomics are not native on sm_103a (measured: 5x slower than 32-bit, 140x
 // under a 32-way address conflict), so the int64 accumulator is updated as two 32-bit words: the low
 // word's atomic returns its previous value, which gives this addition's carry into the high word.

@@ -1,5 +1,5 @@
 // Force-field terms of the potential V of Eq. 1 evaluated by one thread per term, accumulated into
-// 64-bit fixed point in shared memory.  T = double (FP64 path) or float (mixed path).
+// fixed point in shared memory.  T = double (FP64 path) or float (mixed path).
 #pragma once
 #include "common.cuh"
 
@@ -19,18 +19,49 @@ __device__ __forceinline__ double gsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float gsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double gatan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float gatan2(float y, float x) { return atan2f(y, x); }
+// reciprocal and quotient: IEEE in FP64, the fast hardware approximations (about 1 ulp) in FP32
+__device__ __forceinline__ double grcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float gdiv(float a, float b) { return __fdividef(a, b); }
 
-// Precision traits: parameter arrays and shared-memory position layout of each path.
+// FP64 path: int64 accumulators in 2^-40 units, updated as two 32-bit words with carry.
+struct AccF64 {
+  long long *F;  // [3n]
+  static constexpr double kInv = kFixInv;
+  __device__ __forceinline__ void add(int a, V3<double> g, int *err) const {
+    fix_add(&F[3 * a + 0], to_fix(g.x, err));
+    fix_add(&F[3 * a + 1], to_fix(g.y, err));
+    fix_add(&F[3 * a + 2], to_fix(g.z, err));
+  }
+  __device__ __forceinline__ long long efix(double e, int *err) const { return to_fix(e, err); }
+};
+// Mixed path: split hi/lo words in 2^-32 units (see Split).
+struct AccMixed {
+  int *hi;           // [3n]
+  unsigned int *lo;  // [3n]
+  static constexpr double kInv = 2.3283064365386963e-10;  // 2^-32
+  __device__ __forceinline__ void add(int a, V3<float> g, int *err) const {
+    split_add(hi, lo, 3 * a + 0, to_split(g.x, err));
+    split_add(hi, lo, 3 * a + 1, to_split(g.y, err));
+    split_add(hi, lo, 3 * a + 2, to_split(g.z, err));
+  }
+  __device__ __forceinline__ long long efix(float e, int *err) const { return split_value(to_split(e, err)); }
+};
+
+// Precision traits.
 struct PathF64 {
   using T = double;
+  using Acc = AccF64;
   static constexpr bool kMixed = false;
 };
 struct PathMixed {
   using T = float;
+  using Acc = AccMixed;
   static constexpr bool kMixed = true;
 };
 
-// Shared-memory view of one replica's positions and fixed-point force accumulators.
+// Shared-memory view of one replica's positions.
 template <class P>
 struct Pos;
 template <>
@@ -65,21 +96,10 @@ struct Params<PathMixed> {
   const float4 *term;
 };
 
-__device__ __forceinline__ void add_force(long long *F, int a, V3<double> g, int *err) {
-  fix_add(&F[3 * a + 0], to_fix(g.x, err));
-  fix_add(&F[3 * a + 1], to_fix(g.y, err));
-  fix_add(&F[3 * a + 2], to_fix(g.z, err));
-}
-__device__ __forceinline__ void add_force(long long *F, int a, V3<float> g, int *err) {
-  fix_add(&F[3 * a + 0], to_fix2(g.x, err));
-  fix_add(&F[3 * a + 1], to_fix2(g.y, err));
-  fix_add(&F[3 * a + 2], to_fix2(g.z, err));
-}
-
 // Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j).
 template <class P>
 __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &par, int i, int j,
-                                          typename P::T cutoff2, long long *F, bool want_e,
+                                          typename P::T cutoff2, const typename P::Acc &acc, bool want_e,
                                           long long &e_fix, int *err) {
   using T = typename P::T;
   const V3<T> d = pos.diff(i, j);
@@ -87,15 +107,15 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
   if (cutoff2 > T(0) && r2 >= cutoff2) return;
   const auto ai = par.atom[i], aj = par.atom[j];
   const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
-  const T inv_r2 = T(1) / r2;
+  const T inv_r2 = grcp(r2);
   const T s2 = sig * sig * inv_r2;
   const T s6 = s2 * s2 * s2;
   // -dE/dr / r: 24 eps (2 s^12 - s^6) / r^2 + 2 k_e q_i q_j / (4 r^4)
   const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
   const V3<T> fi = {g * d.x, g * d.y, g * d.z};
-  add_force(F, i, fi, err);
-  add_force(F, j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
-  if (want_e) e_fix += to_fix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
+  acc.add(i, fi, err);
+  acc.add(j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
+  if (want_e) e_fix += acc.efix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
 }
 
 // r - r0 of a bond for the mixed path in double-single arithmetic: the FP32 distance of a stiff bond
@@ -131,8 +151,8 @@ __device__ __forceinline__ float bond_dr_ds(const Pos<PathMixed> &pos, int i, in
   const float r = sqrtf(sh);
   const float rr = __fmul_rn(r, r);
   const float rre = __fmaf_rn(r, r, -rr);
-  const float resid = __fadd_rn(__fsub_rn(__fsub_rn(sh, rr), rre), sl);  // r^2 - r*r, exactly-ish
-  const float rlo = resid / (2.f * r);
+  const float resid = __fadd_rn(__fsub_rn(__fsub_rn(sh, rr), rre), sl);  // r^2 - r*r
+  const float rlo = __fdividef(resid, 2.f * r);
   r_out = r;
   d_out = {dh[0], dh[1], dh[2]};
   return __fadd_rn(__fsub_rn(r, r0), rlo);
@@ -141,7 +161,7 @@ __device__ __forceinline__ float bond_dr_ds(const Pos<PathMixed> &pos, int i, in
 // Harmonic bond 1/2 k (r - r0)^2.
 template <class P>
 __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
-                                          long long *F, bool want_e, long long &e_fix, int *err) {
+                                          const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
   const auto kp = par.bond[b];
   V3<T> d;
@@ -153,18 +173,19 @@ __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &pa
     r = gsqrt(dot(d, d));
     dr = r - T(kp.y);
   }
-  const T g = -T(kp.x) * dr / r;
+  const T g = -gdiv(T(kp.x) * dr, r);
   const V3<T> fi = {g * d.x, g * d.y, g * d.z};
-  add_force(F, i, fi, err);
-  add_force(F, j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
-  if (want_e) e_fix += to_fix(T(0.5) * T(kp.x) * dr * dr, err);
+  acc.add(i, fi, err);
+  acc.add(j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
+  if (want_e) e_fix += acc.efix(T(0.5) * T(kp.x) * dr * dr, err);
 }
 
 // Harmonic angle 1/2 k (theta - theta0)^2 at vertex j; theta = atan2(|u x v|, u.v) with
 // u = q_i - q_j, v = q_k - q_j, d theta/d q_i = ((u.v)/|u|^2 u - v) / |u x v| and likewise for q_k.
 template <class P>
 __device__ __forceinline__ void angle_term(const Pos<P> &pos, const Params<P> &par, int t, int i, int j,
-                                           int k, long long *F, bool want_e, long long &e_fix, int *err) {
+                                           int k, const typename P::Acc &acc, bool want_e, long long &e_fix,
+                                           int *err) {
   using T = typename P::T;
   const auto kp = par.angle[t];
   const V3<T> u = pos.diff(i, j), v = pos.diff(k, j);
@@ -174,29 +195,29 @@ __device__ __forceinline__ void angle_term(const Pos<P> &pos, const Params<P> &p
   const T th = gatan2(sn, c);
   sn = sn > T(1e-30) ? sn : T(1e-30);
   const T dth = th - T(kp.y);
-  const T de = T(kp.x) * dth;  // dE/dtheta
-  const T s = -de / sn;        // F = -dE/dtheta * d theta/dq
-  const T cu = c / uu, cv = c / vv;
+  const T s = -gdiv(T(kp.x) * dth, sn);  // F = -dE/dtheta * d theta/dq
+  const T cu = gdiv(c, uu), cv = gdiv(c, vv);
   const V3<T> fi = {s * (cu * u.x - v.x), s * (cu * u.y - v.y), s * (cu * u.z - v.z)};
   const V3<T> fk = {s * (cv * v.x - u.x), s * (cv * v.y - u.y), s * (cv * v.z - u.z)};
-  add_force(F, i, fi, err);
-  add_force(F, k, fk, err);
-  add_force(F, j, V3<T>{-fi.x - fk.x, -fi.y - fk.y, -fi.z - fk.z}, err);
-  if (want_e) e_fix += to_fix(T(0.5) * T(kp.x) * dth * dth, err);
+  acc.add(i, fi, err);
+  acc.add(k, fk, err);
+  acc.add(j, V3<T>{-fi.x - fk.x, -fi.y - fk.y, -fi.z - fk.z}, err);
+  if (want_e) e_fix += acc.efix(T(0.5) * T(kp.x) * dth * dth, err);
 }
 
 // Periodic dihedral terms sum_t k_t (1 + cos(n_t phi - delta_t)) of atoms (i, j, k, l), IUPAC sign;
 // cos(n phi), sin(n phi) by the angle-addition recurrence; gradient of phi after Blondel & Karplus.
 template <class P>
 __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P> &par, int4 a, int2 terms,
-                                              long long *F, bool want_e, long long &e_fix, int *err) {
+                                              const typename P::Acc &acc, bool want_e, long long &e_fix,
+                                              int *err) {
   using T = typename P::T;
   const V3<T> b1 = pos.diff(a.y, a.x), b2 = pos.diff(a.z, a.y), b3 = pos.diff(a.w, a.z);
   const V3<T> n1 = cross(b1, b2), n2 = cross(b2, b3);
   const T b2sq = dot(b2, b2), lb2 = gsqrt(b2sq);
   const T x = dot(n1, n2), y = lb2 * dot(b1, n2);
-  const T rho = gsqrt(x * x + y * y);
-  const T cph = x / rho, sph = y / rho;
+  const T irho = grcp(gsqrt(x * x + y * y));
+  const T cph = x * irho, sph = y * irho;
   T dedphi = T(0), e = T(0);
   for (int t = terms.x; t < terms.y; ++t) {
     const auto tp = par.term[t];  // (k, n, cos delta, sin delta)
@@ -212,9 +233,10 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
     if (want_e) e += T(tp.x) * (T(1) + cn * T(tp.z) + sn * T(tp.w));
   }
   const T n1sq = dot(n1, n1), n2sq = dot(n2, n2);
-  const T f12 = dot(b1, b2) / b2sq, f32 = dot(b3, b2) / b2sq;
-  const T ci = lb2 / n1sq * dedphi;   // F_i = -dE/dphi * (-|b2| n1/|n1|^2)
-  const T cl = -lb2 / n2sq * dedphi;  // F_l = -dE/dphi * ( |b2| n2/|n2|^2)
+  const T ib2 = grcp(b2sq);
+  const T f12 = dot(b1, b2) * ib2, f32 = dot(b3, b2) * ib2;
+  const T ci = gdiv(lb2, n1sq) * dedphi;   // F_i = -dE/dphi * (-|b2| n1/|n1|^2)
+  const T cl = -gdiv(lb2, n2sq) * dedphi;  // F_l = -dE/dphi * ( |b2| n2/|n2|^2)
   const V3<T> fi = {ci * n1.x, ci * n1.y, ci * n1.z};
   const V3<T> fl = {cl * n2.x, cl * n2.y, cl * n2.z};
   // F_j = -(1 + f12) F_i + f32 F_l, F_k = f12 F_i - (1 + f32) F_l
@@ -222,36 +244,38 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
                     -(T(1) + f12) * fi.z + f32 * fl.z};
   const V3<T> fk = {f12 * fi.x - (T(1) + f32) * fl.x, f12 * fi.y - (T(1) + f32) * fl.y,
                     f12 * fi.z - (T(1) + f32) * fl.z};
-  add_force(F, a.x, fi, err);
-  add_force(F, a.y, fj, err);
-  add_force(F, a.z, fk, err);
-  add_force(F, a.w, fl, err);
-  if (want_e) e_fix += to_fix(e, err);
+  acc.add(a.x, fi, err);
+  acc.add(a.y, fj, err);
+  acc.add(a.z, fk, err);
+  acc.add(a.w, fl, err);
+  if (want_e) e_fix += acc.efix(e, err);
 }
 
 // One pass over every force-field item of a replica, strided over the block's threads.  Items are
-// ordered dihedrals, angles, bonds, pairs so that the heaviest ones start first.
+// ordered dihedrals, angles, bonds, pairs so that each warp mostly runs one kind of item; thread t
+// starts at item blockDim - 1 - t, so that the heaviest items (dihedrals) land on the last warps and
+// not on warp 0, which also integrates the first 32 atoms.
 template <class P>
 __device__ __forceinline__ void force_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                           const uint32_t *pairs, long long *F, bool want_e,
+                                           const uint32_t *pairs, const typename P::Acc &acc, bool want_e,
                                            long long &e_fix, int *err) {
   using T = typename P::T;
   const int nd = S.n_dih, na = nd + S.n_angles, nb = na + S.n_bonds, ntot = nb + S.n_pairs;
   const T cut2 = (T)S.cutoff2;
-  for (int it = threadIdx.x; it < ntot; it += blockDim.x) {
+  for (int it = (int)blockDim.x - 1 - (int)threadIdx.x; it < ntot; it += blockDim.x) {
     if (it >= nb) {
       const uint32_t pk = pairs[it - nb];
-      pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, F, want_e, e_fix, err);
+      pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
     } else if (it >= na) {
       const int b = it - na;
       const int2 ij = S.bond_ij[b];
-      bond_term<P>(pos, par, b, ij.x, ij.y, F, want_e, e_fix, err);
+      bond_term<P>(pos, par, b, ij.x, ij.y, acc, want_e, e_fix, err);
     } else if (it >= nd) {
       const int t = it - nd;
       const int4 ijk = S.angle_ijk[t];
-      angle_term<P>(pos, par, t, ijk.x, ijk.y, ijk.z, F, want_e, e_fix, err);
+      angle_term<P>(pos, par, t, ijk.x, ijk.y, ijk.z, acc, want_e, e_fix, err);
     } else {
-      dihedral_term<P>(pos, par, S.dih_ijkl[it], S.dih_terms[it], F, want_e, e_fix, err);
+      dihedral_term<P>(pos, par, S.dih_ijkl[it], S.dih_terms[it], acc, want_e, e_fix, err);
     }
   }
 }

@@ -25,6 +25,7 @@ struct SegArgs {
   long long M;               // check index written into the exit key
   int skip_if_exit;          // return at once when *exit_key is already set
   int pairs_in_smem;
+  int noise_batch;           // steps of noise generated together
   double h, c1;              // dt/2 and exp(-gamma dt)
 };
 
@@ -33,6 +34,7 @@ struct SegConfig {
   int threads;
   size_t smem;
   int pairs_in_smem;
+  int noise_batch;
 };
 
 SegConfig segment_config(const SysDev &S, int threads_hint);

@@ -86,6 +86,23 @@ __device__ __forceinline__ unsigned char *align32(unsigned char *p) {
   return (unsigned char *)(((uintptr_t)p + 31) & ~(uintptr_t)31);
 }
 
+__device__ __forceinline__ void normals4(const Philox4 &w, double xi[4]) { normals4_f64(w, xi); }
+__device__ __forceinline__ void normals4(const Philox4 &w, float xi[4]) { normals4_f32(w, xi); }
+
+// Normals for `steps` consecutive steps of one replica, [step][atom][3], spread over every thread of
+// the block: the noise does not depend on the state, so it is generated off the per-step chain.
+template <class T>
+__device__ __forceinline__ void gen_noise(T *xi, int steps, long long t0, uint64_t seed, int r, int n) {
+  const int items = steps * n;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int j = it / n, at = it - j * n;
+    T z[4];
+    normals4(philox_stream(seed, t0 + j, 0u, r, at), z);
+    T *o = xi + (size_t)it * 3;
+    o[0] = z[0]; o[1] = z[1]; o[2] = z[2];
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Shared-memory replica state of each precision path.
 template <class P>
@@ -103,6 +120,7 @@ struct State<PathF64> {
     f = (double *)ptr; ptr += (size_t)n * 24;
     sd = (double *)ptr; ptr += (size_t)n * 8;
   }
+  static __device__ AccF64 acc(long long *F, int n) { return AccF64{F}; }
   __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
@@ -120,10 +138,8 @@ struct State<PathF64> {
   __device__ Params<PathF64> params(const SysDev &S) const {
     return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d};
   }
-  // B, A, O, A of BAOAB for atom `at` with normals from the Philox stream.
-  __device__ __forceinline__ void baoa(int at, const Philox4 &w, double h, double c1) {
-    double xi[4];
-    normals4_f64(w, xi);
+  // B, A, O, A of BAOAB for atom `at` with the normals xi[0..2].
+  __device__ __forceinline__ void baoa(int at, const double *xi, double h, double c1) {
     const double im = atom[at].w, s = sd[at];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -137,14 +153,14 @@ struct State<PathF64> {
     }
   }
   // final B with the new forces (fixed point -> FP64); returns the kinetic energy of the atom.
-  __device__ __forceinline__ double bk(int at, long long *F, double h) {
+  __device__ __forceinline__ double bk(int at, const AccF64 &acc, double h) {
     const double im = atom[at].w;
     double ke = 0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const int i = 3 * at + x;
-      const double fv = (double)F[i] * kFixInv;
-      F[i] = 0;
+      const double fv = (double)acc.F[i] * kFixInv;
+      acc.F[i] = 0;
       f[i] = fv;
       const double pp = p[i] + h * fv;
       p[i] = pp;
@@ -153,7 +169,7 @@ struct State<PathF64> {
     return ke;
   }
   __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
-  __device__ void getp_f64(int at, double x[3]) const { x[0] = p[3 * at]; x[1] = p[3 * at + 1]; x[2] = p[3 * at + 2]; }
+  __device__ double mom(int i) const { return p[i]; }
 };
 
 template <>
@@ -171,6 +187,10 @@ struct State<PathMixed> {
     pl = (float *)ptr; ptr += (size_t)n * 12;
     f = (float *)ptr; ptr += (size_t)n * 12;
     sd = (float *)ptr; ptr += (size_t)n * 4;
+  }
+  // the 8 bytes per force component hold the hi words [3n] then the lo words [3n]
+  static __device__ AccMixed acc(long long *F, int n) {
+    return AccMixed{(int *)F, (unsigned int *)F + 3 * n};
   }
   __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
@@ -206,9 +226,7 @@ struct State<PathMixed> {
   __device__ Params<PathMixed> params(const SysDev &S) const {
     return Params<PathMixed>{atom, S.bond_f, S.angle_f, S.term_f};
   }
-  __device__ __forceinline__ void baoa(int at, const Philox4 &w, float h, float c1) {
-    float xi[4];
-    normals4_f32(w, xi);
+  __device__ __forceinline__ void baoa(int at, const float *xi, float h, float c1) {
     const float im = atom[at].w, s = sd[at], hm = h * im;
     float4 a = qh[at], b = ql[at];
     float *qa = &a.x, *qb = &b.x;
@@ -229,14 +247,15 @@ struct State<PathMixed> {
     qh[at] = a;
     ql[at] = b;
   }
-  __device__ __forceinline__ float bk(int at, long long *F, float h) {
+  __device__ __forceinline__ float bk(int at, const AccMixed &acc, float h) {
     const float im = atom[at].w;
     float ke = 0.f;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const int i = 3 * at + x;
-      const float fv = fix_to_float(F[i]);
-      F[i] = 0;
+      const float fv = split_to_float(acc.hi[i], acc.lo[i]);
+      acc.hi[i] = 0;
+      acc.lo[i] = 0u;
       f[i] = fv;
       ds P = {ph[i], pl[i]};
       P = ds_add(P, h * fv);
@@ -250,6 +269,7 @@ struct State<PathMixed> {
     const float4 a = qh[at], b = ql[at];
     x[0] = (double)a.x + (double)b.x; x[1] = (double)a.y + (double)b.y; x[2] = (double)a.z + (double)b.z;
   }
+  __device__ float mom(int i) const { return ph[i]; }
 };
 
 // Observable j (Section 2.4.1) in the path's precision, from shared-memory state.
@@ -296,8 +316,7 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
         const int at = S.group_atoms[t];
         const T im = (T)st.atom[at].w;
         for (int x = 0; x < 3; ++x) {
-          T v;
-          if constexpr (P::kMixed) v = st.ph[3 * at + x] * im; else v = st.p[3 * at + x] * im;
+          const T v = (T)st.mom(3 * at + x) * im;
           s += v * v;
         }
         ++cnt;
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   const int r = blockIdx.x;
   if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = S.n, nd = 3 * n, no = S.n_obs;
+  const int n = S.n, nd = 3 * n, no = S.n_obs, NB = a.noise_batch;
   unsigned char *ptr = smem;
   long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
   long long *red = (long long *)ptr; ptr += 32 * 8;
@@ -325,6 +344,8 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n);
+  ptr = align32(ptr);
+  T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);
   const uint32_t *pairs = S.pairs;
   if (a.pairs_in_smem) {
     ptr = align32(ptr);
@@ -342,27 +363,32 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   const T h = (T)a.h, c1 = (T)a.c1;
   const Pos<P> pos = st.pos();
   const Params<P> par = st.params(S);
+  const typename P::Acc fa = State<P>::acc(F, n);
   // steps until the next sample: (t_phase0 + s + 1) % t_gr == 0
   int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
-  for (int s = 0; s < a.k; ++s) {
-    const long long t = a.t_global0 + s;
-    for (int at = threadIdx.x; at < n; at += kThreads)
-      st.baoa(at, philox_stream(a.seed, t, 0u, r, at), h, c1);
+  int j = 0;  // step index inside the current noise batch
+  for (int s = 0; s < a.k; ++s, ++j) {
+    if (j == NB) j = 0;
+    if (j == 0) {
+      gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r, n);
+      __syncthreads();
+    }
+    for (int at = threadIdx.x; at < n; at += kThreads) st.baoa(at, xi + ((size_t)j * n + at) * 3, h, c1);
     __syncthreads();
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    force_pass<P>(S, pos, par, pairs, F, sample, e_fix, &err);
+    force_pass<P>(S, pos, par, pairs, fa, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
     for (int at = threadIdx.x; at < n; at += kThreads) {
-      const T ke = st.bk(at, F, h);
-      if (sample) k_fix += to_fix(ke, &err);
+      const T ke = st.bk(at, fa, h);
+      if (sample) k_fix += fa.efix(ke, &err);
     }
     if (sample) {
       const long long es = block_sum_ll<kThreads>(e_fix, red);
       const long long ks = block_sum_ll<kThreads>(k_fix, red);
-      if (threadIdx.x == 0) { ek[0] = (double)es * kFixInv; ek[1] = (double)ks * kFixInv; }
+      if (threadIdx.x == 0) { ek[0] = (double)es * P::Acc::kInv; ek[1] = (double)ks * P::Acc::kInv; }
       __syncthreads();
       if (threadIdx.x < no) acc_add(acc + 4 * threadIdx.x, observable_ff<P>(S, st, threadIdx.x, ek[0], ek[1]));
       __syncthreads();
@@ -393,6 +419,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
     for (int c = 0; c < 4; ++c) acc[j][c] = a.acc[((size_t)r * no + j) * 4 + c];
   const double h = a.h, c1 = a.c1, im = 1.0 / S.mass[0];
   const double sd = sqrt((1.0 - c1 * c1) * S.kT * S.mass[0]);
+  int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
   for (int s = 0; s < a.k; ++s) {
     double xi[4];
     normals4_f64(philox_stream(a.seed, a.t_global0 + s, 0u, r, 0), xi);
@@ -403,7 +430,8 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
     fx = -S.dw_a * 4.0 * x * (x * x - 1.0);
     fy = -S.dw_b * 2.0 * y;
     px += h * fx; py += h * fy;
-    if (a.t_gr > 0 && ((a.t_phase0 + s + 1) % a.t_gr) == 0) {
+    if (--until == 0) {
+      until = a.t_gr;
       for (int j = 0; j < no; ++j) {
         double v;
         const int kind = S.obs_kind[j];
@@ -427,10 +455,12 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem) {
+static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch) {
   const int n = S.n;
-  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 64;  // + alignment padding
+  const size_t real = S.precision == GRP_FP64 ? 8 : 4;
+  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
+  b += (size_t)noise_batch * 3 * n * real;
   if (pairs_in_smem) b += (size_t)S.n_pairs * 4;
   return b;
 }
@@ -440,6 +470,7 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
   if (S.potential == GRP_POT_DOUBLE_WELL_2D) {
     c.threads = 64;
     c.smem = 0;
+    c.noise_batch = 1;
     return c;
   }
   const int items = S.n_dih + S.n_angles + S.n_bonds + S.n_pairs;
@@ -449,8 +480,13 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
     while (t < 512 && t < items) t *= 2;
   }
   c.threads = t;
-  c.pairs_in_smem = ff_smem_bytes(S, 1) <= 160 * 1024 ? 1 : 0;
-  c.smem = ff_smem_bytes(S, c.pairs_in_smem);
+  // noise for up to 16 steps at a time, within 32 KB
+  const size_t real = S.precision == GRP_FP64 ? 8 : 4;
+  int nb = 16;
+  while (nb > 1 && (size_t)nb * 3 * S.n * real > 32 * 1024) nb /= 2;
+  c.noise_batch = nb;
+  c.pairs_in_smem = ff_smem_bytes(S, 1, nb) <= 160 * 1024 ? 1 : 0;
+  c.smem = ff_smem_bytes(S, c.pairs_in_smem, nb);
   return c;
 }
 
@@ -477,6 +513,7 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
 cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t st) {
   SegArgs a = a0;
   a.pairs_in_smem = c.pairs_in_smem;
+  a.noise_batch = c.noise_batch;
   if (a.n_active <= 0) return cudaSuccess;
   if (a.S.potential == GRP_POT_DOUBLE_WELL_2D) {
     dw_segment_kernel<<<(a.n_active + 63) / 64, 64, 0, st>>>(a);
@@ -515,12 +552,19 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   __syncthreads();
   int err = 0;
   long long e_fix = 0;
-  force_pass<P>(S, st.pos(), st.params(S), S.pairs, F, energy != nullptr, e_fix, &err);
+  const typename P::Acc fa = State<P>::acc(F, n);
+  force_pass<P>(S, st.pos(), st.params(S), S.pairs, fa, energy != nullptr, e_fix, &err);
   __syncthreads();
-  if (forces)
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) forces[(size_t)b * nd + i] = (double)F[i] * kFixInv;
+  if (forces) {
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+      long long v;
+      if constexpr (P::kMixed) v = (long long)fa.hi[i] * (1ll << 20) + (long long)fa.lo[i];
+      else v = F[i];
+      forces[(size_t)b * nd + i] = (double)v * P::Acc::kInv;
+    }
+  }
   const long long es = block_sum_ll<256>(e_fix, red);
-  if (energy && threadIdx.x == 0) energy[b] = (double)es * kFixInv;
+  if (energy && threadIdx.x == 0) energy[b] = (double)es * P::Acc::kInv;
   if (err) atomicOr(errp, err);
 }
 
