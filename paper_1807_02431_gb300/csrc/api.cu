@@ -265,6 +265,22 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       dterms.push_back(make_int2(t0, (int)td.size()));
     }
     D.n_dih = (int)dijkl.size();
+    // work items: pairs, bonds, angles, dihedrals, each kind padded to a multiple of 32 entries
+    std::vector<uint32_t> items;
+    auto add_kind = [&](uint32_t kind, int count) {
+      for (int i = 0; i < count; ++i) items.push_back((kind << 28) | (uint32_t)i);
+      while (items.size() % 32) items.push_back((uint32_t)kItemNone << 28);
+    };
+    add_kind(kItemPair, D.n_pairs);
+    add_kind(kItemBond, D.n_bonds);
+    add_kind(kItemAngle, D.n_angles);
+    add_kind(kItemDihedral, D.n_dih);
+    if (D.n_pairs >= (1 << 28) || items.size() >= (size_t)1 << 31) {
+      grp_destroy_system(s);
+      return fail(GRP_ENOTIMPL, "too many force-field items (%zu)", items.size());
+    }
+    D.n_items = (int)items.size();
+    UP(items.data(), items.size(), &D.items);
     UP(dijkl.data(), dijkl.size(), &D.dih_ijkl);
     UP(dterms.data(), dterms.size(), &D.dih_terms);
     UP(td.data(), td.size(), &D.term_d);

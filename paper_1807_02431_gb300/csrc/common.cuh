@@ -14,6 +14,9 @@ constexpr int kMaxGroups = GRP_MAX_GROUPS;
 // Error bits latched by kernels into the replica set's error word.
 enum : int { kErrNaN = 1, kErrOverflow = 2 };
 
+// Kinds of force-field work items.
+enum : uint32_t { kItemPair = 0, kItemBond = 1, kItemAngle = 2, kItemDihedral = 3, kItemNone = 15 };
+
 // Fixed point: one unit = 2^-40 of the force (or energy) unit, so that quantisation (9e-13) stays
 // below FP64 rounding of typical forces.  A single contribution must stay below 2^15 in magnitude,
 // so that 2^8 contributions at that bound still sum inside int64.
@@ -34,6 +37,8 @@ struct SysDev {
   const float4 *atom_f;
   int n_pairs;             // explicit non-excluded pair list (i | j << 16), i < j
   const uint32_t *pairs;
+  int n_items;             // force-field work items, (kind << 28) | index, each kind padded to a
+  const uint32_t *items;   // multiple of 32 entries so that a warp runs a single kind of item
   double cutoff2;          // 0: no cutoff
   int n_bonds;
   const int2 *bond_ij;
@@ -158,7 +163,7 @@ __device__ __forceinline__ float fix_to_float(long long x) {
 
 // Mixed-path force accumulator: fixed point with 2^-32 units kept as two 32-bit words that are
 // summed separately with non-returning atomics (no carry between them): a contribution v 2^32 is
-// split as hi 2^20 + lo with lo in [0, 2^20).  The lo word holds up to 4,096 contributions without
+// split as hi 2^20 + lo with lo in [0, 2^20].  The lo word holds up to 4,095 contributions without
 // wrapping; the hi word is summed modulo 2^32, exact as long as the total |F| < 2^19.  The value is
 // hi_sum 2^20 + lo_sum, the same integer whatever the order of the additions.
 constexpr float kSplitHiScale = 4096.0f;       // 2^32 / 2^20
@@ -168,15 +173,16 @@ struct Split {
   int hi;
   unsigned int lo;
 };
+// hi = floor(v 2^12) (one rounding-down conversion), r = v 2^12 - hi in [0, 1) (exact: |v 2^12| <
+// 2^27 keeps hi exactly representable), lo = round(r 2^20) in [0, 2^20]; lo = 2^20 (r rounding up)
+// is a valid split of the same integer, so the lo word holds at most 4,095 contributions.  A
+// contribution at or beyond the fixed-point limit (or NaN) sets the overflow flag.
 __device__ __forceinline__ Split to_split(float v, int *err) {
-  Split s{0, 0u};
-  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return s; }
   const float a = v * kSplitHiScale;
-  const float hf = floorf(a);
-  s.hi = (int)hf;
-  unsigned int lo = __float2uint_rn((a - hf) * kSplitLoScale);
-  if (lo >= (1u << 20)) { lo -= (1u << 20); s.hi += 1; }
-  s.lo = lo;
+  Split s;
+  s.hi = __float2int_rd(a);
+  s.lo = __float2uint_rn((a - (float)s.hi) * kSplitLoScale);
+  *err |= (fabsf(v) < (float)kFixLimit) ? 0 : kErrOverflow;
   return s;
 }
 __device__ __forceinline__ long long split_value(Split s) { return (long long)s.hi * (1ll << 20) + (long long)s.lo; }
@@ -242,8 +248,8 @@ __device__ __forceinline__ ds ds_scale(ds x, float c) {
 }
 
 // Block-wide sum of int64 values (every thread contributes; result valid in thread 0).
-template <int kThreads>
 __device__ __forceinline__ long long block_sum_ll(long long v, long long *scratch /* >= 32 */) {
+  const int kThreads = (int)blockDim.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -251,31 +251,31 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   if (want_e) e_fix += acc.efix(e, err);
 }
 
-// One pass over every force-field item of a replica, strided over the block's threads.  Items are
-// ordered dihedrals, angles, bonds, pairs so that each warp mostly runs one kind of item; thread t
-// starts at item blockDim - 1 - t, so that the heaviest items (dihedrals) land on the last warps and
-// not on warp 0, which also integrates the first 32 atoms.
+// One pass over every force-field item of a replica, strided over the block's threads.  The item
+// table groups pairs, bonds, angles and dihedrals, each group padded to a multiple of 32 entries, so
+// that every warp runs a single kind of item (no serialised divergent paths) and the dihedrals, the
+// longest items, land on the last warps rather than on warp 0, which also integrates atoms 0..31.
 template <class P>
 __device__ __forceinline__ void force_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                           const uint32_t *pairs, const typename P::Acc &acc, bool want_e,
-                                           long long &e_fix, int *err) {
+                                           const uint32_t *items, const uint32_t *pairs,
+                                           const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
-  const int nd = S.n_dih, na = nd + S.n_angles, nb = na + S.n_bonds, ntot = nb + S.n_pairs;
   const T cut2 = (T)S.cutoff2;
-  for (int it = (int)blockDim.x - 1 - (int)threadIdx.x; it < ntot; it += blockDim.x) {
-    if (it >= nb) {
-      const uint32_t pk = pairs[it - nb];
+  for (int it = threadIdx.x; it < S.n_items; it += blockDim.x) {
+    const uint32_t e = items[it];
+    const uint32_t kind = e >> 28;
+    const int idx = (int)(e & 0x0FFFFFFFu);
+    if (kind == kItemPair) {
+      const uint32_t pk = pairs[idx];
       pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
-    } else if (it >= na) {
-      const int b = it - na;
-      const int2 ij = S.bond_ij[b];
-      bond_term<P>(pos, par, b, ij.x, ij.y, acc, want_e, e_fix, err);
-    } else if (it >= nd) {
-      const int t = it - nd;
-      const int4 ijk = S.angle_ijk[t];
-      angle_term<P>(pos, par, t, ijk.x, ijk.y, ijk.z, acc, want_e, e_fix, err);
-    } else {
-      dihedral_term<P>(pos, par, S.dih_ijkl[it], S.dih_terms[it], acc, want_e, e_fix, err);
+    } else if (kind == kItemBond) {
+      const int2 ij = S.bond_ij[idx];
+      bond_term<P>(pos, par, idx, ij.x, ij.y, acc, want_e, e_fix, err);
+    } else if (kind == kItemAngle) {
+      const int4 ijk = S.angle_ijk[idx];
+      angle_term<P>(pos, par, idx, ijk.x, ijk.y, ijk.z, acc, want_e, e_fix, err);
+    } else if (kind == kItemDihedral) {
+      dihedral_term<P>(pos, par, S.dih_ijkl[idx], S.dih_terms[idx], acc, want_e, e_fix, err);
     }
   }
 }

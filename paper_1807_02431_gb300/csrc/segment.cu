@@ -328,13 +328,14 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
 }
 
 // ------------------------------------------------------------------------------------------------
-template <class P, int kThreads>
-__global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
+template <class P>
+__global__ void __launch_bounds__(512) ff_segment_kernel(const SegArgs a) {
   using T = typename P::T;
   const SysDev &S = a.S;
   const int r = blockIdx.x;
   if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  const int kThreads = (int)blockDim.x;
   const int n = S.n, nd = 3 * n, no = S.n_obs, NB = a.noise_batch;
   unsigned char *ptr = smem;
   long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
@@ -346,12 +347,15 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
   st.carve(ptr, n);
   ptr = align32(ptr);
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);
-  const uint32_t *pairs = S.pairs;
+  const uint32_t *pairs = S.pairs, *items = S.items;
   if (a.pairs_in_smem) {
     ptr = align32(ptr);
     uint32_t *sp = (uint32_t *)ptr;
     for (int i = threadIdx.x; i < S.n_pairs; i += kThreads) sp[i] = S.pairs[i];
     pairs = sp;
+    uint32_t *si = sp + S.n_pairs;
+    for (int i = threadIdx.x; i < S.n_items; i += kThreads) si[i] = S.items[i];
+    items = si;
   }
   const size_t off = (size_t)r * nd;
   st.load(S, a.q + off, a.p + off, a.f + off, n, a.c1);
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    force_pass<P>(S, pos, par, pairs, fa, sample, e_fix, &err);
+    force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
     for (int at = threadIdx.x; at < n; at += kThreads) {
@@ -386,8 +390,8 @@ __global__ void __launch_bounds__(kThreads) ff_segment_kernel(const SegArgs a) {
       if (sample) k_fix += fa.efix(ke, &err);
     }
     if (sample) {
-      const long long es = block_sum_ll<kThreads>(e_fix, red);
-      const long long ks = block_sum_ll<kThreads>(k_fix, red);
+      const long long es = block_sum_ll(e_fix, red);
+      const long long ks = block_sum_ll(k_fix, red);
       if (threadIdx.x == 0) { ek[0] = (double)es * P::Acc::kInv; ek[1] = (double)ks * P::Acc::kInv; }
       __syncthreads();
       if (threadIdx.x < no) acc_add(acc + 4 * threadIdx.x, observable_ff<P>(S, st, threadIdx.x, ek[0], ek[1]));
@@ -461,7 +465,7 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch)
   size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
   b += (size_t)noise_batch * 3 * n * real;
-  if (pairs_in_smem) b += (size_t)S.n_pairs * 4;
+  if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4;
   return b;
 }
 
@@ -473,12 +477,10 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
     c.noise_batch = 1;
     return c;
   }
-  const int items = S.n_dih + S.n_angles + S.n_bonds + S.n_pairs;
+  // one thread per (padded) item up to 512 threads per replica, a multiple of 32, at least 64
   int t = threads_hint;
-  if (t <= 0) {
-    t = 64;
-    while (t < 512 && t < items) t *= 2;
-  }
+  if (t <= 0) t = ((S.n_items + 31) / 32) * 32;
+  t = t < 64 ? 64 : (t > 512 ? 512 : ((t + 31) / 32) * 32);
   c.threads = t;
   // noise for up to 16 steps at a time, within 32 KB
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
@@ -490,24 +492,14 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
   return c;
 }
 
-template <class P, int kT>
-static cudaError_t launch_ff(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
-  auto kern = ff_segment_kernel<P, kT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  if (e != cudaSuccess) return e;
-  kern<<<a.n_active, kT, c.smem, st>>>(a);
-  return cudaGetLastError();
-}
-
 template <class P>
 static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
-  switch (c.threads) {
-    case 64: return launch_ff<P, 64>(a, c, st);
-    case 128: return launch_ff<P, 128>(a, c, st);
-    case 256: return launch_ff<P, 256>(a, c, st);
-    case 512: return launch_ff<P, 512>(a, c, st);
-  }
-  return cudaErrorInvalidValue;
+  if (c.threads < 32 || c.threads > 512 || c.threads % 32) return cudaErrorInvalidValue;
+  auto kern = ff_segment_kernel<P>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<a.n_active, c.threads, c.smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t st) {
@@ -553,7 +545,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   int err = 0;
   long long e_fix = 0;
   const typename P::Acc fa = State<P>::acc(F, n);
-  force_pass<P>(S, st.pos(), st.params(S), S.pairs, fa, energy != nullptr, e_fix, &err);
+  force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, energy != nullptr, e_fix, &err);
   __syncthreads();
   if (forces) {
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
@@ -563,7 +555,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
       forces[(size_t)b * nd + i] = (double)v * P::Acc::kInv;
     }
   }
-  const long long es = block_sum_ll<256>(e_fix, red);
+  const long long es = block_sum_ll(e_fix, red);
   if (energy && threadIdx.x == 0) energy[b] = (double)es * P::Acc::kInv;
   if (err) atomicOr(errp, err);
 }
