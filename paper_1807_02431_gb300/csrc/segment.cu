@@ -328,8 +328,10 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
 }
 
 // ------------------------------------------------------------------------------------------------
-template <class P>
-__global__ void __launch_bounds__(512) ff_segment_kernel(const SegArgs a) {
+// kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
+// on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
+template <class P, int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
   using T = typename P::T;
   const SysDev &S = a.S;
   const int r = blockIdx.x;
@@ -495,7 +497,7 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
 template <class P>
 static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
   if (c.threads < 32 || c.threads > 512 || c.threads % 32) return cudaErrorInvalidValue;
-  auto kern = ff_segment_kernel<P>;
+  auto kern = c.threads <= 320 ? ff_segment_kernel<P, 320, 2> : ff_segment_kernel<P, 512, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.n_active, c.threads, c.smem, st>>>(a);
