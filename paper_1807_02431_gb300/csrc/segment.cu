@@ -274,7 +274,8 @@ struct State<PathMixed> {
 
 // Observable j (Section 2.4.1) in the path's precision, from shared-memory state.
 template <class P>
-__device__ double observable_ff(const SysDev &S, const State<P> &st, int j, double v_pot, double v_kin) {
+__device__ typename P::T observable_ff(const SysDev &S, const State<P> &st, int j, typename P::T v_pot,
+                                       typename P::T v_kin) {
   using T = typename P::T;
   const int *arg = S.obs_arg[j];
   const Pos<P> pos = st.pos();
@@ -283,13 +284,18 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
     case GRP_OBS_KINETIC: return v_kin;
     case GRP_OBS_COORD: {
       double x[3];
-      st.get_f64(arg[0], x);
-      return x[arg[1]];
+      if constexpr (P::kMixed) {
+        const float4 a = st.qh[arg[0]], b = st.ql[arg[0]];
+        return (&a.x)[arg[1]] + (&b.x)[arg[1]];
+      } else {
+        st.get_f64(arg[0], x);
+        return x[arg[1]];
+      }
     }
     case GRP_OBS_DIHEDRAL: {
       const V3<T> b1 = pos.diff(arg[1], arg[0]), b2 = pos.diff(arg[2], arg[1]), b3 = pos.diff(arg[3], arg[2]);
       const V3<T> n1 = cross(b1, b2), n2 = cross(b2, b3);
-      return (double)gatan2(gsqrt(dot(b2, b2)) * dot(b1, n2), dot(n1, n2));
+      return gatan2(gsqrt(dot(b2, b2)) * dot(b1, n2), dot(n1, n2));
     }
     case GRP_OBS_GROUP_DISTANCE: {
       // centre of mass difference relative to the first atom of group a (keeps FP32 sums small)
@@ -307,7 +313,7 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
         c[g][0] /= mt; c[g][1] /= mt; c[g][2] /= mt;
       }
       const T dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
-      return (double)gsqrt(dx * dx + dy * dy + dz * dz);
+      return gsqrt(dx * dx + dy * dy + dz * dz);
     }
     case GRP_OBS_RMS_VELOCITY: {
       T s = 0;
@@ -321,11 +327,61 @@ __device__ double observable_ff(const SysDev &S, const State<P> &st, int j, doub
         }
         ++cnt;
       }
-      return (double)gsqrt(s / (T)cnt);
+      return gsqrt(s / (T)cnt);
     }
   }
-  return 0.0;
+  return T(0);
 }
+
+// Fixed-point sum (2^-40 units on the FP64 path, 2^-32 on the mixed path) to the path's precision,
+// the mixed path with 32-bit conversions only.
+__device__ __forceinline__ double fix_value(long long x, double) { return (double)x * kFixInv; }
+__device__ __forceinline__ float fix_value(long long x, float) {
+  return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned int)x) * kSplitInv;
+}
+
+// Samples of one observable within a segment, accumulated by the thread that owns the observable.
+// FP64 path: straight into the FP64 accumulators.  Mixed path: on chip in double-single arithmetic
+// (no FP64 instruction per sample: on GB300 each costs ~64 cycles on the critical path), folded into
+// the FP64 accumulators once at the end of the segment, re-expressed relative to the stored shift:
+// sum (v - c) = S1 + n d and sum (v - c)^2 = S2 + 2 d S1 + n d^2 with d = c_chip - c.
+template <class P>
+struct ObsAcc {
+  __device__ void begin(const double *) {}
+  __device__ void add(double *acc4, double v) { acc_add(acc4, v); }
+  __device__ void end(double *) {}
+};
+template <>
+struct ObsAcc<PathMixed> {
+  float c;
+  ds s1, s2;
+  int n;
+  bool have_c;
+  __device__ void begin(const double *acc4) {
+    have_c = acc4[3] > 0.0;
+    c = have_c ? (float)acc4[0] : 0.f;
+    s1 = ds{0.f, 0.f};
+    s2 = ds{0.f, 0.f};
+    n = 0;
+  }
+  __device__ void add(double *, float v) {
+    if (!have_c) { c = v; have_c = true; }
+    const float d = v - c;
+    s1 = ds_add(s1, d);
+    s2 = ds_add(s2, d * d);
+    ++n;
+  }
+  __device__ void end(double *acc4) {
+    if (n == 0) return;
+    const double cs = acc4[3] == 0.0 ? (double)c : acc4[0];
+    const double dd = (double)c - cs;
+    const double S1 = ds_to_double(s1), S2 = ds_to_double(s2);
+    acc4[0] = cs;
+    acc4[1] += S1 + n * dd;
+    acc4[2] += S2 + 2.0 * dd * S1 + n * dd * dd;
+    acc4[3] += (double)n;
+  }
+};
 
 // ------------------------------------------------------------------------------------------------
 // kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
@@ -343,7 +399,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
   long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
   long long *red = (long long *)ptr; ptr += 32 * 8;
   double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
-  double *ek = (double *)ptr; ptr += 2 * 8;
+  long long *ek = (long long *)ptr; ptr += 2 * 8;
   State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n);
@@ -364,6 +420,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
   for (int i = threadIdx.x; i < nd; i += kThreads) F[i] = 0;
   if (threadIdx.x < no * 4) acc[threadIdx.x] = a.acc[(size_t)r * no * 4 + threadIdx.x];
   __syncthreads();
+  ObsAcc<P> oacc;
+  if (threadIdx.x < no) oacc.begin(acc + 4 * threadIdx.x);
 
   int err = 0;
   const T h = (T)a.h, c1 = (T)a.c1;
@@ -394,12 +452,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
     if (sample) {
       const long long es = block_sum_ll(e_fix, red);
       const long long ks = block_sum_ll(k_fix, red);
-      if (threadIdx.x == 0) { ek[0] = (double)es * P::Acc::kInv; ek[1] = (double)ks * P::Acc::kInv; }
+      if (threadIdx.x == 0) { ek[0] = es; ek[1] = ks; }
       __syncthreads();
-      if (threadIdx.x < no) acc_add(acc + 4 * threadIdx.x, observable_ff<P>(S, st, threadIdx.x, ek[0], ek[1]));
+      if (threadIdx.x < no)
+        oacc.add(acc + 4 * threadIdx.x,
+                 observable_ff<P>(S, st, threadIdx.x, fix_value(ek[0], T(0)), fix_value(ek[1], T(0))));
       __syncthreads();
     }
   }
+  if (threadIdx.x < no) oacc.end(acc + 4 * threadIdx.x);
   __syncthreads();  // the write-back reads coordinates owned by other threads
   st.store(a.q + off, a.p + off, a.f + off, n, &err);
   if (threadIdx.x < no * 4) a.acc[(size_t)r * no * 4 + threadIdx.x] = acc[threadIdx.x];
