@@ -246,6 +246,22 @@ grp_status grp_get_device_view(grp_replicas *r, grp_device_view *out);
 grp_status grp_energy_forces(grp_system *s, int32_t n_conf, const double *d_q, double *d_energy,
                              double *d_forces, void *stream);
 
+/* Fleming-Viot branching, as grp_fv_branch, on replica arrays the caller owns, allocating nothing.
+ * (No counterpart in the paper: this serves callers that cannot allocate device memory while they
+ * run, because their memory belongs to another allocator with a fixed budget or because the
+ * implicit synchronisation of cudaMalloc/cudaFree is not acceptable in their loop.)
+ *   d_q, d_p, d_f: device [n_rep][n][dim] FP64, updated in place; d_acc: device [n_rep][n_obs][4]
+ *   (may be NULL when the system has no observables); d_exited: device [n_rep] u8 exit flags;
+ *   seed and t_global key the branching draw exactly as in grp_fv_branch; h_n_branched (host)
+ *   receives the number of copies.  Synchronises `stream` before returning.
+ * Scratch: one source index per replica plus a counter in a static device array that every GPU which
+ * loads the library holds until exit (256 KB); n_rep above 65,536 is rejected with GRP_EINVAL.  The
+ * counter is cleared at each call; calls that overlap on the GPU share the array and race.  The first
+ * call on each device looks the array's address up (cudaGetSymbolAddress) with that device current. */
+grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, double *d_q, double *d_p, double *d_f,
+                                 double *d_acc, const uint8_t *d_exited, uint64_t seed, int64_t t_global,
+                                 int32_t *h_n_branched, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,8 @@ SIGNATURES = {
     "grp_set_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
     "grp_get_device_view": (C.c_int32, [_VP, C.POINTER(DeviceView)]),
     "grp_energy_forces": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "grp_fv_branch_noalloc": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_uint64, C.c_int64, _I32P,
+                                          _VP]),
 }
 
 
@@ -329,6 +331,15 @@ def grp_get_device_view(r: ReplicasHandle) -> dict:
 
 def grp_energy_forces(sysh: SystemHandle, n_conf: int, d_q, d_energy=None, d_forces=None, stream=None):
     _check(_lib.grp_energy_forces(sysh.handle, n_conf, _ptr(d_q), _ptr(d_energy), _ptr(d_forces), _stream(stream)))
+
+
+def grp_fv_branch_noalloc(sysh: SystemHandle, n_rep: int, d_q, d_p, d_f, d_acc, d_exited, seed: int,
+                          t_global: int, stream=None) -> int:
+    """Fleming-Viot branching on caller-owned device arrays; the library allocates nothing."""
+    nb = C.c_int32(0)
+    _check(_lib.grp_fv_branch_noalloc(sysh.handle, n_rep, _ptr(d_q), _ptr(d_p), _ptr(d_f), _ptr(d_acc),
+                                      _ptr(d_exited), seed, t_global, C.byref(nb), _stream(stream)))
+    return nb.value
 
 
 class _CudaArray:

@@ -82,6 +82,10 @@ struct grp_replicas {
 
 extern "C" const char *grp_last_error(void) { return g_last_error.c_str(); }
 
+// Shared with noalloc.cu.
+grp::SysDev grp_system_device_view(const grp_system *s) { return s->dev; }
+void grp_set_last_error(const char *msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------------------------------------------
 extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **out) {
   if (!d || !out) return fail(GRP_EINVAL, "grp_create_system: null argument");
