@@ -149,7 +149,7 @@ def _chain_geometry(n, bond, angle, torsions):
 
 
 def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas: int = 256,
-          temperature: float = 300.0) -> System:
+          temperature: float = 300.0, dihedral_terms: str = "triple") -> System:
     """Peptide-like bead chain shaped like alanine dipeptide (Section 4.1 stand-in).
 
     Bonds k = 3e5 kJ/mol/nm^2, r0 = 0.15 nm; angles k = 400 kJ/mol/rad^2, theta0 = 110 deg; each
@@ -172,7 +172,11 @@ def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas:
     angles = np.array([[i, i + 1, i + 2] for i in range(n - 2)], np.int32)
     dih, dn, dk, dd = [], [], [], []
     for i in range(n - 3):
-        for mult in (1, 2, 3):
+        if dihedral_terms == "triple":  # terms n = 1, 2, 3, each with its own k
+            mults = (1, 2, 3)
+        else:  # "single": one term whose multiplicity is drawn from 1..3
+            mults = (int(rng.integers(1, 4)),)
+        for mult in mults:
             dih.append([i, i + 1, i + 2, i + 3])
             dn.append(mult)
             dk.append(rng.uniform(0.0, 8.0))
