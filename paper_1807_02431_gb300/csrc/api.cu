@@ -196,14 +196,39 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       if (bad_atom(i) || bad_atom(j) || i == j) { grp_destroy_system(s); return fail(GRP_EINVAL, "exclusion %d invalid", e); }
       excl[(size_t)i * n + j] = excl[(size_t)j * n + i] = 1;
     }
-    std::vector<uint32_t> pairs;
-    pairs.reserve((size_t)n * (n - 1) / 2);
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j)
-        if (!excl[(size_t)i * n + j]) pairs.push_back((uint32_t)i | ((uint32_t)j << 16));
-    D.n_pairs = (int)pairs.size();
-    UP(pairs.data(), pairs.size(), &D.pairs);
     D.cutoff2 = d->cutoff > 0 ? d->cutoff * d->cutoff : 0.0;
+    // Small systems: an explicit list of non-excluded pairs, one thread per pair.  From 64 atoms on:
+    // tiles of 32 atoms, every tile pair I <= J with per-lane interaction masks.
+    D.tiled = n >= 64 ? 1 : 0;
+    std::vector<uint32_t> pairs;
+    if (!D.tiled) {
+      pairs.reserve((size_t)n * (n - 1) / 2);
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+          if (!excl[(size_t)i * n + j]) pairs.push_back((uint32_t)i | ((uint32_t)j << 16));
+    } else {
+      const int nt = (n + 31) / 32;
+      std::vector<uint32_t> tps, masks;
+      for (int I = 0; I < nt; ++I)
+        for (int J = I; J < nt; ++J) {
+          tps.push_back((uint32_t)I | ((uint32_t)J << 16));
+          for (int l = 0; l < 32; ++l) {
+            const int i = I * 32 + l;
+            uint32_t m = 0;
+            for (int k = 0; k < 32; ++k) {
+              const int j = J * 32 + k;
+              if (i < n && j < n && i != j && !excl[(size_t)i * n + j]) m |= 1u << k;
+            }
+            masks.push_back(m);
+          }
+        }
+      D.n_tiles = nt;
+      D.n_tile_pairs = (int)tps.size();
+      UP(tps.data(), tps.size(), &D.tile_pairs);
+      UP(masks.data(), masks.size(), &D.tile_masks);
+    }
+    D.n_pairs = (int)pairs.size();
+    if (!pairs.empty()) UP(pairs.data(), pairs.size(), &D.pairs);
     // bonds
     if (d->n_bonds > 0 && (!d->bond_atoms || !d->bond_k || !d->bond_r0)) { grp_destroy_system(s); return fail(GRP_EINVAL, "bond arrays null"); }
     std::vector<int2> bij(d->n_bonds);

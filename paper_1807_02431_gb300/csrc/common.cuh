@@ -39,6 +39,13 @@ struct SysDev {
   const uint32_t *pairs;
   int n_items;             // force-field work items, (kind << 28) | index, each kind padded to a
   const uint32_t *items;   // multiple of 32 entries so that a warp runs a single kind of item
+  // Tiled nonbonded path (tiled = 1): atoms in tiles of 32; every tile pair I <= J with, per lane
+  // of tile I, a 32-bit mask of the atoms of tile J it interacts with (exclusions, padding and, on
+  // the diagonal, i != j removed); the explicit pair items are then not in the item table.
+  int tiled;
+  int n_tiles, n_tile_pairs;
+  const uint32_t *tile_pairs;  // I | J << 16
+  const uint32_t *tile_masks;  // [n_tile_pairs][32]
   double cutoff2;          // 0: no cutoff
   int n_bonds;
   const int2 *bond_ij;

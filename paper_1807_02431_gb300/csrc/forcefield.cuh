@@ -96,15 +96,16 @@ struct Params<PathMixed> {
   const float4 *term;
 };
 
-// Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j).
+// Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j): force on i
+// (minus the force on j) and the pair energy; false beyond the cutoff.
 template <class P>
-__device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &par, int i, int j,
-                                          typename P::T cutoff2, const typename P::Acc &acc, bool want_e,
-                                          long long &e_fix, int *err) {
+__device__ __forceinline__ bool pair_eval(const Pos<P> &pos, const Params<P> &par, int i, int j,
+                                          typename P::T cutoff2, V3<typename P::T> &fi, typename P::T &e,
+                                          bool want_e) {
   using T = typename P::T;
   const V3<T> d = pos.diff(i, j);
   const T r2 = dot(d, d);
-  if (cutoff2 > T(0) && r2 >= cutoff2) return;
+  if (cutoff2 > T(0) && r2 >= cutoff2) return false;
   const auto ai = par.atom[i], aj = par.atom[j];
   const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
   const T inv_r2 = grcp(r2);
@@ -112,10 +113,76 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
   const T s6 = s2 * s2 * s2;
   // -dE/dr / r: 24 eps (2 s^12 - s^6) / r^2 + 2 k_e q_i q_j / (4 r^4)
   const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
-  const V3<T> fi = {g * d.x, g * d.y, g * d.z};
+  fi = {g * d.x, g * d.y, g * d.z};
+  if (want_e) e = T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  return true;
+}
+
+template <class P>
+__device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &par, int i, int j,
+                                          typename P::T cutoff2, const typename P::Acc &acc, bool want_e,
+                                          long long &e_fix, int *err) {
+  using T = typename P::T;
+  V3<T> fi;
+  T e = T(0);
+  if (!pair_eval<P>(pos, par, i, j, cutoff2, fi, e, want_e)) return;
   acc.add(i, fi, err);
   acc.add(j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
-  if (want_e) e_fix += acc.efix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
+  if (want_e) e_fix += acc.efix(e, err);
+}
+
+// Tiled nonbonded pass: each warp takes tile pairs (I, J); lane l owns atom i = 32 I + l and, at
+// rotation step s, meets atom j = 32 J + ((l + s) mod 32).  The force on i accumulates in registers;
+// the force on j accumulates in a register that moves one lane down after every step (a warp
+// shuffle), so that it always sits in the lane currently meeting atom j and ends in a known lane.
+// Off-diagonal tiles take s = 0..31; a diagonal tile takes s = 1..16 (lanes 16..31 skip s = 16), which
+// meets every unordered pair once.  Per lane and tile pair the FP32 (FP64) sums are converted to fixed
+// point once, so the result does not depend on which warp takes which tile pair, or in which order.
+// With a cutoff, tile pairs whose bounding boxes are further apart than the cutoff are skipped.
+template <class P>
+__device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
+                                          const typename P::Acc &acc, const float *boxes, bool want_e,
+                                          long long &e_fix, int *err) {
+  using T = typename P::T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const T cut2 = (T)S.cutoff2;
+  for (int tp = warp; tp < S.n_tile_pairs; tp += nwarps) {
+    const uint32_t e = S.tile_pairs[tp];
+    const int I = (int)(e & 0xFFFFu), J = (int)(e >> 16);
+    if (boxes) {  // gap between the two tiles' boxes
+      const float *a = boxes + 6 * I, *b = boxes + 6 * J;
+      const float gx = fmaxf(0.f, fmaxf(a[0] - b[3], b[0] - a[3]));
+      const float gy = fmaxf(0.f, fmaxf(a[1] - b[4], b[1] - a[4]));
+      const float gz = fmaxf(0.f, fmaxf(a[2] - b[5], b[2] - a[5]));
+      if (gx * gx + gy * gy + gz * gz >= (float)S.cutoff2) continue;
+    }
+    const uint32_t mask = S.tile_masks[(size_t)tp * 32 + lane];
+    const int i = I * 32 + lane, j0 = J * 32;
+    const bool diag = I == J;
+    const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
+    V3<T> fi = {T(0), T(0), T(0)}, fj = {T(0), T(0), T(0)};
+    T en = T(0);
+    for (int s = s0; s < s1; ++s) {
+      const int m = (lane + s) & 31;
+      const bool on = ((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16);
+      if (on) {
+        V3<T> f;
+        T ep = T(0);
+        if (pair_eval<P>(pos, par, i, j0 + m, cut2, f, ep, want_e)) {
+          fi.x += f.x; fi.y += f.y; fi.z += f.z;
+          fj.x -= f.x; fj.y -= f.y; fj.z -= f.z;
+          en += ep;
+        }
+      }
+      fj.x = __shfl_sync(0xffffffffu, fj.x, (lane + 1) & 31);
+      fj.y = __shfl_sync(0xffffffffu, fj.y, (lane + 1) & 31);
+      fj.z = __shfl_sync(0xffffffffu, fj.z, (lane + 1) & 31);
+    }
+    if (i < S.n) acc.add(i, fi, err);
+    const int ja = j0 + ((lane + s1) & 31);
+    if (ja < S.n) acc.add(ja, fj, err);
+    if (want_e) e_fix += acc.efix(en, err);
+  }
 }
 
 // r - r0 of a bond for the mixed path in double-single arithmetic: the FP32 distance of a stiff bond

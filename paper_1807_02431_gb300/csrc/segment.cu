@@ -169,6 +169,9 @@ struct State<PathF64> {
     return ke;
   }
   __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
+  __device__ void get_f32(int at, float x[3]) const {
+    x[0] = (float)q[3 * at]; x[1] = (float)q[3 * at + 1]; x[2] = (float)q[3 * at + 2];
+  }
   __device__ double mom(int i) const { return p[i]; }
 };
 
@@ -269,6 +272,10 @@ struct State<PathMixed> {
     const float4 a = qh[at], b = ql[at];
     x[0] = (double)a.x + (double)b.x; x[1] = (double)a.y + (double)b.y; x[2] = (double)a.z + (double)b.z;
   }
+  __device__ void get_f32(int at, float x[3]) const {
+    const float4 a = qh[at];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z;
+  }
   __device__ float mom(int i) const { return ph[i]; }
 };
 
@@ -331,6 +338,32 @@ __device__ typename P::T observable_ff(const SysDev &S, const State<P> &st, int 
     }
   }
   return T(0);
+}
+
+// Bounding box of every tile of 32 atoms, [n_tiles][min xyz, max xyz], padded by 1e-3 length units
+// (the boxes only decide which tile pairs to skip under a cutoff).  One warp per tile.
+template <class P>
+__device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int t = warp; t < S.n_tiles; t += nwarps) {
+    const int a = t * 32 + lane;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (a < S.n) {
+      float x[3];
+      st.get_f32(a, x);
+      for (int c = 0; c < 3; ++c) { lo[c] = x[c]; hi[c] = x[c]; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+        hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+      }
+    if (lane < 6) {
+      const float v = lane == 0 ? lo[0] : lane == 1 ? lo[1] : lane == 2 ? lo[2] : lane == 3 ? hi[0] : lane == 4 ? hi[1] : hi[2];
+      boxes[6 * t + lane] = lane < 3 ? v - 1e-3f : v + 1e-3f;
+    }
+  }
 }
 
 // Fixed-point sum (2^-40 units on the FP64 path, 2^-32 on the mixed path) to the path's precision,
@@ -405,6 +438,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
   st.carve(ptr, n);
   ptr = align32(ptr);
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);
+  float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
+  if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
   const uint32_t *pairs = S.pairs, *items = S.items;
   if (a.pairs_in_smem) {
     ptr = align32(ptr);
@@ -439,10 +474,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
     }
     for (int at = threadIdx.x; at < n; at += kThreads) st.baoa(at, xi + ((size_t)j * n + at) * 3, h, c1);
     __syncthreads();
+    if (boxes) {
+      tile_boxes<P>(S, st, boxes);
+      __syncthreads();
+    }
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
     force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
+    if (S.tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
     for (int at = threadIdx.x; at < n; at += kThreads) {
@@ -528,7 +568,8 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch)
   size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
   b += (size_t)noise_batch * 3 * n * real;
-  if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4;
+  if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
+  if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
   return b;
 }
 
@@ -540,9 +581,13 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
     c.noise_batch = 1;
     return c;
   }
-  // one thread per (padded) item up to 512 threads per replica, a multiple of 32, at least 64
+  // one thread per (padded) item, or one warp per tile pair, up to 512 threads per replica, a
+  // multiple of 32, at least 64
   int t = threads_hint;
-  if (t <= 0) t = ((S.n_items + 31) / 32) * 32;
+  if (t <= 0) {
+    t = ((S.n_items + 31) / 32) * 32;
+    if (S.tiled && 32 * S.n_tile_pairs > t) t = 32 * S.n_tile_pairs;
+  }
   t = t < 64 ? 64 : (t > 512 ? 512 : ((t + 31) / 32) * 32);
   c.threads = t;
   // noise for up to 16 steps at a time, within 32 KB
@@ -609,6 +654,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   long long e_fix = 0;
   const typename P::Acc fa = State<P>::acc(F, n);
   force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, energy != nullptr, e_fix, &err);
+  if (S.tiled) tile_pass<P>(S, st.pos(), st.params(S), fa, nullptr, energy != nullptr, e_fix, &err);
   __syncthreads();
   if (forces) {
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {

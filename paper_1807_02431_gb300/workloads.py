@@ -139,6 +139,37 @@ def _place(a, b, c, bond, angle, torsion):
     return c + d2[0] * bc + d2[1] * m + d2[2] * n
 
 
+def _grow_chain(n, bond, angle, sigma, rng, fixed):
+    """Place beads one by one from internal coordinates: torsions drawn 70 % trans (180 +- 20 deg),
+    30 % gauche (+-65 +- 10 deg), except the `fixed` ones; a bead closer than 0.8 sigma_ij to any
+    earlier bead (|i - j| >= 3) has its torsion redrawn, and the chain restarts after 100 failures."""
+    while True:
+        x = np.zeros((n, 3))
+        x[1] = [bond, 0.0, 0.0]
+        if n > 2:
+            x[2] = x[1] + bond * np.array([-math.cos(angle), math.sin(angle), 0.0])
+        ok = True
+        for i in range(3, n):
+            t = i - 3
+            for _attempt in range(100):
+                if t in fixed:
+                    tor = fixed[t]
+                elif rng.random() < 0.7:
+                    tor = math.radians(180.0 + rng.uniform(-20.0, 20.0))
+                else:
+                    tor = math.radians(rng.choice([-65.0, 65.0]) + rng.uniform(-10.0, 10.0))
+                xi = _place(x[i - 3], x[i - 2], x[i - 1], bond, angle, tor)
+                d = np.linalg.norm(x[: i - 2] - xi, axis=1)
+                if np.all(d >= 0.8 * 0.5 * (sigma[: i - 2] + sigma[i])):
+                    x[i] = xi
+                    break
+            else:
+                ok = False
+                break
+        if ok:
+            return x
+
+
 def _chain_geometry(n, bond, angle, torsions):
     x = np.zeros((n, 3))
     x[1] = [bond, 0.0, 0.0]
@@ -185,24 +216,7 @@ def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas:
     c = n // 2 - 1
     phi_idx, psi_idx = c - 2, c - 1  # torsion index t describes dihedral (t, t+1, t+2, t+3)
     bond, angle = 0.15, math.radians(110.0)
-    while True:
-        tors = []
-        for t in range(n - 3):
-            if rng.random() < 0.7:
-                tors.append(math.radians(180.0 + rng.uniform(-20.0, 20.0)))
-            else:
-                tors.append(math.radians(rng.choice([-65.0, 65.0]) + rng.uniform(-10.0, 10.0)))
-        if n - 3 > psi_idx:
-            tors[phi_idx] = math.radians(-81.0)
-            tors[psi_idx] = math.radians(70.0)
-        x = _chain_geometry(n, bond, angle, tors)
-        ok = True
-        for i in range(n):
-            for j in range(i + 3, n):
-                if np.linalg.norm(x[i] - x[j]) < 0.8 * 0.5 * (sigma[i] + sigma[j]):
-                    ok = False
-        if ok:
-            break
+    x = _grow_chain(n, bond, angle, sigma, rng, {phi_idx: math.radians(-81.0), psi_idx: math.radians(70.0)})
     x -= x.mean(axis=0)
     kT = KB_KJ_PER_MOL_K * temperature
     s = System(
