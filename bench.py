@@ -228,6 +228,37 @@ def accelerated_speed(B, s, precision, R, seed, max_steps, max_exits=10 ** 6, un
     return out
 
 
+def batched_bench(B, steps, warmup, flush, n_runs=64, R=128):
+    """64 independent runs of chains with sizes drawn uniformly in 22..400 beads, 128 replicas each,
+    mixed precision, one persistent kernel per exit test (autotuned block size)."""
+    import torch
+
+    systems = W.batched_chains(n_runs=n_runs, n_replicas=R)
+    handles, reps = [], []
+    for k, s in enumerate(systems):
+        sysh = B.grp_create_system(s, B.GRP_MIXED)
+        q0, p0 = W.replica_states(s, R, seed=3000 + k, spread=0.002)
+        handles.append(sysh)
+        reps.append(B.grp_init_replicas(sysh, R, SEED + k, q0, p0, per_replica=True))
+    b = B.grp_batch_create(reps)
+    threads = B.grp_batch_autotune(b, 10)
+    st = torch.cuda.current_stream()
+    t_check = systems[0].t_check
+    omegas = [1] * n_runs
+
+    def step():
+        B.grp_batch_fv_check(b, omegas, t_check, 10, 0.01, 0, st)
+
+    times = time_steps(step, steps, warmup, flush, st)
+    t = float(np.sum(times)) / 1e3
+    atoms = sum(s.n_atoms for s in systems)
+    flops = sum(algorithmic_flops_per_replica_step(s) for s in systems) * R * t_check
+    return {"workload": f"{n_runs} runs x {R} replicas, chains of 22..400 beads (mean {atoms / n_runs:.0f})",
+            "value": R * atoms * t_check * steps / t, "unit": "replica-atom-steps/s", "ms_per_step": t * 1e3 / steps,
+            "block_threads": threads, "fp32_tflops_achieved": flops * steps / t / 1e12,
+            "fp32_frac_of_peak": flops * steps / t / 1e12 / fp32_peak_tflops(2070.0)}
+
+
 def run_reference(args):
     """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
     bounded sample: the 256 replicas advanced 20 steps with sampling and the exit test."""
@@ -267,6 +298,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--accel-steps", type=int, default=200000)
+    ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -334,6 +366,7 @@ def main():
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
         e2e_value = units_per_step * args.steps / e2e_wall
+        batched = batched_bench(B, args.batch_steps, 2, flush) if args.batch_steps > 0 else None
         accel = None
         if args.accel_steps > 0:
             # the chain (bounded run) and the double-well validation system, where the loop cycles
@@ -359,6 +392,7 @@ def main():
                "gpu_launches": step.launches_per_step * args.steps,
                "roofline": roof, "clocks": clocks,
                "fp64_path": fp64,
+               "batched": batched,
                "accelerated": accel,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},

@@ -225,6 +225,24 @@ typedef struct {
 grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_check, int32_t t_gr, double tol,
                         int64_t min_fv_steps, grp_fv_status *h_out, void *stream);
 
+/* Batched runs: several independent Gen. ParRep runs (replica sets, of the same or of different
+ * systems, all of one precision) advanced by one persistent kernel that takes (run, replica) units
+ * from a queue sorted by decreasing system size; branching, Gelman-Rubin and the status readback are
+ * one launch each for the whole batch.  The batch refers to the replica sets (it does not own them;
+ * destroy it before them).  Each run keeps its own seed and counters. */
+typedef struct grp_batch grp_batch;
+grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs, grp_batch **out);
+void grp_batch_destroy(grp_batch *b);
+/* k BAOAB steps of every replica of every run, sampling every t_gr (grp_step_k for all runs). */
+grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, void *stream);
+/* One exit test of the convergence step for every run (grp_fv_check for all runs); h_omega[n_runs]
+ * gives each run's state, h_out[n_runs] receives each run's status. */
+grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, int32_t t_check, int32_t t_gr, double tol,
+                              int64_t min_fv_steps, grp_fv_status *h_out, void *stream);
+/* Pick the block size of the batched kernel by timing candidate sizes on a short segment (the
+ * replicas' state and counters are restored afterwards); h_threads (optional) gets the choice. */
+grp_status grp_batch_autotune(grp_batch *b, int32_t t_gr, void *stream, int32_t *h_threads);
+
 /* Whole loop of Fig. 1 from the current state of replica 0: transient, convergence (F-V with
  * Gelman-Rubin), parallel step, clock updates (Section 2.4.1, Eq. 6).  Writes at most max_events
  * events to h_events, their count to h_n_events, and the final clock to h_t_sim (optional). */

@@ -108,6 +108,12 @@ SIGNATURES = {
     "grp_energy_forces": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
     "grp_fv_branch_noalloc": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_uint64, C.c_int64, _I32P,
                                           _VP]),
+    "grp_batch_create": (C.c_int32, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
+    "grp_batch_destroy": (None, [_VP]),
+    "grp_batch_step_k": (C.c_int32, [_VP, C.c_int64, C.c_int32, _VP]),
+    "grp_batch_fv_check": (C.c_int32, [_VP, _I32P, C.c_int32, C.c_int32, C.c_double, C.c_int64,
+                                       C.POINTER(FvStatus), _VP]),
+    "grp_batch_autotune": (C.c_int32, [_VP, C.c_int32, _VP, _I32P]),
 }
 
 
@@ -331,6 +337,45 @@ def grp_get_device_view(r: ReplicasHandle) -> dict:
 
 def grp_energy_forces(sysh: SystemHandle, n_conf: int, d_q, d_energy=None, d_forces=None, stream=None):
     _check(_lib.grp_energy_forces(sysh.handle, n_conf, _ptr(d_q), _ptr(d_energy), _ptr(d_forces), _stream(stream)))
+
+
+class BatchHandle:
+    """A grp_batch over replica sets (kept alive by this object)."""
+
+    def __init__(self, runs):
+        self.runs = list(runs)
+        arr = (C.c_void_p * len(self.runs))(*[r.handle for r in self.runs])
+        h = C.c_void_p()
+        _check(_lib.grp_batch_create(arr, len(self.runs), C.byref(h)))
+        self.handle = h
+        self.status = (FvStatus * len(self.runs))()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.grp_batch_destroy(self.handle)
+            self.handle = None
+
+
+def grp_batch_create(runs) -> BatchHandle:
+    return BatchHandle(runs)
+
+
+def grp_batch_step_k(b: BatchHandle, k: int, t_gr: int = 0, stream=None):
+    _check(_lib.grp_batch_step_k(b.handle, k, t_gr, _stream(stream)))
+
+
+def grp_batch_fv_check(b: BatchHandle, omegas, t_check: int, t_gr: int, tol: float, min_fv_steps: int = 0,
+                       stream=None):
+    om = np.ascontiguousarray(omegas, dtype=np.int32)
+    _check(_lib.grp_batch_fv_check(b.handle, om.ctypes.data_as(_I32P), t_check, t_gr, tol, min_fv_steps, b.status,
+                                   _stream(stream)))
+    return b.status
+
+
+def grp_batch_autotune(b: BatchHandle, t_gr: int = 0, stream=None) -> int:
+    t = C.c_int32(0)
+    _check(_lib.grp_batch_autotune(b.handle, t_gr, _stream(stream), C.byref(t)))
+    return t.value
 
 
 def grp_fv_branch_noalloc(sysh: SystemHandle, n_rep: int, d_q, d_p, d_f, d_acc, d_exited, seed: int,

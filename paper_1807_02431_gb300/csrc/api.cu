@@ -1,6 +1,7 @@
 // C ABI of libgrp (include/grp.h): argument validation, device buffers, and the host driver of the
 // Gen. ParRep loop of Fig. 1.  Every step of the hot path runs in the kernels of segment.cu and
 // fvgr.cu; the host only launches them and reads a few bytes per exit test.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -502,6 +503,234 @@ extern "C" grp_status grp_gelman_rubin(grp_replicas *r, double tol, double *h_rh
   }
   if (h_converged) *h_converged = conv;
   return GRP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched runs.
+struct grp_batch {
+  std::vector<grp_replicas *> runs;
+  int precision = 0;
+  int threads = 0;
+  size_t smem = 0;
+  int n_units = 0, n_branch_units = 0, n_gr_units = 0;
+  SegArgs *d_args = nullptr, *h_args = nullptr;      // [n_runs], h_ pinned
+  RunArrays *d_arrays = nullptr, *h_arrays = nullptr;  // [n_runs], h_ pinned
+  uint2 *d_units = nullptr, *d_branch_units = nullptr, *d_gr_units = nullptr;
+  int *d_counter = nullptr, *d_nb = nullptr;
+  BatchStatus *d_status = nullptr, *h_status = nullptr;  // h_ pinned
+};
+
+extern "C" void grp_batch_destroy(grp_batch *b) {
+  if (!b) return;
+  cudaFree(b->d_args); cudaFree(b->d_arrays); cudaFree(b->d_units); cudaFree(b->d_branch_units);
+  cudaFree(b->d_gr_units); cudaFree(b->d_counter); cudaFree(b->d_nb); cudaFree(b->d_status);
+  if (b->h_args) cudaFreeHost(b->h_args);
+  if (b->h_arrays) cudaFreeHost(b->h_arrays);
+  if (b->h_status) cudaFreeHost(b->h_status);
+  delete b;
+}
+
+extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs, grp_batch **out) {
+  if (!runs || !out || n_runs < 1) return fail(GRP_EINVAL, "grp_batch_create: need n_runs >= 1 runs");
+  *out = nullptr;
+  for (int i = 0; i < n_runs; ++i) {
+    if (!runs[i]) return fail(GRP_EINVAL, "grp_batch_create: run %d is null", i);
+    if (runs[i]->sys->dev.potential != GRP_POT_FORCE_FIELD)
+      return fail(GRP_ENOTIMPL, "grp_batch_create: batches hold force-field systems");
+    if (runs[i]->sys->dev.precision != runs[0]->sys->dev.precision)
+      return fail(GRP_EINVAL, "grp_batch_create: runs must share one precision");
+  }
+  grp_batch *b = new grp_batch();
+  b->runs.assign(runs, runs + n_runs);
+  b->precision = runs[0]->sys->dev.precision;
+  std::vector<uint2> units, bunits, gunits;
+  for (int i = 0; i < n_runs; ++i) {
+    const grp_replicas *r = runs[i];
+    b->threads = std::max(b->threads, r->sys->seg.threads);
+    b->smem = std::max(b->smem, r->sys->seg.smem);
+    for (int k = 0; k < r->R; ++k) { units.push_back(make_uint2(i, k)); bunits.push_back(make_uint2(i, k)); }
+    for (int j = 0; j < r->sys->dev.n_obs; ++j) gunits.push_back(make_uint2(i, j));
+  }
+  // largest systems first
+  std::stable_sort(units.begin(), units.end(), [&](const uint2 &x, const uint2 &y) {
+    return runs[x.x]->sys->dev.n > runs[y.x]->sys->dev.n;
+  });
+  b->threads = std::min(512, b->threads);
+  b->n_units = (int)units.size();
+  b->n_branch_units = (int)bunits.size();
+  b->n_gr_units = (int)gunits.size();
+  auto dalloc = [&](void **p, size_t bytes) { return cudaMalloc(p, bytes > 0 ? bytes : 8) == cudaSuccess; };
+  bool ok = dalloc((void **)&b->d_args, sizeof(SegArgs) * n_runs) && dalloc((void **)&b->d_arrays, sizeof(RunArrays) * n_runs) &&
+            dalloc((void **)&b->d_units, sizeof(uint2) * units.size()) &&
+            dalloc((void **)&b->d_branch_units, sizeof(uint2) * bunits.size()) &&
+            dalloc((void **)&b->d_gr_units, sizeof(uint2) * gunits.size()) && dalloc((void **)&b->d_counter, 8) &&
+            dalloc((void **)&b->d_nb, sizeof(int) * n_runs) && dalloc((void **)&b->d_status, sizeof(BatchStatus) * n_runs) &&
+            cudaMallocHost((void **)&b->h_args, sizeof(SegArgs) * n_runs) == cudaSuccess &&
+            cudaMallocHost((void **)&b->h_arrays, sizeof(RunArrays) * n_runs) == cudaSuccess &&
+            cudaMallocHost((void **)&b->h_status, sizeof(BatchStatus) * n_runs) == cudaSuccess;
+  if (!ok) { grp_batch_destroy(b); return fail(GRP_ENOMEM, "grp_batch_create: allocation failed"); }
+  if (cudaMemcpy(b->d_units, units.data(), sizeof(uint2) * units.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_branch_units, bunits.data(), sizeof(uint2) * bunits.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!gunits.empty() &&
+       cudaMemcpy(b->d_gr_units, gunits.data(), sizeof(uint2) * gunits.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    grp_batch_destroy(b);
+    return fail(GRP_ECUDA, "grp_batch_create: upload failed");
+  }
+  *out = b;
+  return GRP_OK;
+}
+
+// One batched segment of k steps (k <= kMaxSegment) with or without the fused exit test.
+static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, const int32_t *omega, cudaStream_t st) {
+  const int nr = (int)b->runs.size();
+  CU(cudaStreamSynchronize(st));  // the pinned argument block may still be read by a queued copy
+  for (int i = 0; i < nr; ++i) {
+    grp_replicas *r = b->runs[i];
+    SegArgs a = seg_args(r, k, t_gr, r->R);
+    a.do_check = do_check;
+    a.omega = omega ? omega[i] : 0;
+    a.pairs_in_smem = r->sys->seg.pairs_in_smem;
+    a.noise_batch = r->sys->seg.noise_batch;
+    b->h_args[i] = a;
+  }
+  CU(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(SegArgs) * nr, cudaMemcpyHostToDevice, st));
+  CU(launch_segment_batch(b->d_args, b->d_units, b->n_units, b->d_counter, b->precision, b->threads, b->smem, st,
+                          nullptr));
+  for (grp_replicas *r : b->runs) {
+    r->t_global += k;
+    r->t_phase += k;
+  }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, void *stream) {
+  if (!b || k < 0 || t_gr < 0) return fail(GRP_EINVAL, "grp_batch_step_k: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  while (k > 0) {
+    const int kk = (int)std::min<long long>(k, kMaxSegment);
+    grp_status e = batch_segment(b, kk, t_gr, 0, nullptr, st);
+    if (e != GRP_OK) return e;
+    k -= kk;
+  }
+  return GRP_OK;  // device error words stay latched until the next synchronising call
+}
+
+extern "C" grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, int32_t t_check, int32_t t_gr,
+                                         double tol, int64_t min_fv_steps, grp_fv_status *h_out, void *stream) {
+  if (!b || !h_omega || !h_out || t_check < 1 || t_check > kMaxSegment || t_gr < 0)
+    return fail(GRP_EINVAL, "grp_batch_fv_check: bad argument (t_check must be in [1, %lld])", kMaxSegment);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nr = (int)b->runs.size();
+  grp_status e = batch_segment(b, t_check, t_gr, 1, h_omega, st);
+  if (e != GRP_OK) return e;
+  for (int i = 0; i < nr; ++i) {
+    grp_replicas *r = b->runs[i];
+    const SysDev &D = r->sys->dev;
+    RunArrays a;
+    a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc; a.exited = r->exited; a.labels = r->labels;
+    a.src = r->src; a.n_branched = b->d_nb + i; a.rhat = r->rhat; a.err = r->err;
+    a.nd = D.nd; a.nacc = D.n_obs * 4; a.n_rep = r->R; a.n_obs = D.n_obs;
+    a.seed = r->seed; a.t_global = r->t_global;
+    b->h_arrays[i] = a;
+  }
+  CU(cudaMemcpyAsync(b->d_arrays, b->h_arrays, sizeof(RunArrays) * nr, cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(b->d_nb, 0, sizeof(int) * nr, st));
+  CU(launch_fv_branch_batch(b->d_arrays, b->d_branch_units, b->n_branch_units, st));
+  CU(launch_gelman_rubin_batch(b->d_arrays, b->d_gr_units, b->n_gr_units, st));
+  CU(launch_collect_status(b->d_arrays, nr, b->d_status, st));
+  CU(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * nr, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < nr; ++i) {
+    const grp_replicas *r = b->runs[i];
+    const BatchStatus &s = b->h_status[i];
+    grp_fv_status &o = h_out[i];
+    const int no = r->sys->dev.n_obs;
+    const bool want_gr = r->t_phase >= min_fv_steps && r->R > 1 && no > 0;
+    o.ref_exited = s.exited0;
+    o.label0 = s.label0;
+    o.n_branched = s.n_branched;
+    o.gr_evaluated = want_gr ? 1 : 0;
+    o.t_phase = r->t_phase;
+    o.pad = 0;
+    int conv = want_gr ? 1 : 0;
+    for (int j = 0; j < GRP_MAX_OBS; ++j) {
+      o.rhat[j] = (want_gr && j < no) ? s.rhat[j] : 0.0;
+      if (want_gr && j < no && !(s.rhat[j] < 1.0 + tol)) conv = 0;
+    }
+    o.converged = conv;
+  }
+  for (int i = 0; i < nr; ++i) {
+    if (b->h_status[i].err) {  // latched by a kernel of run i: report it and clear it
+      e = latch_errors(b->runs[i], st);
+      if (e != GRP_OK) return e;
+    }
+  }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_batch_autotune(grp_batch *b, int32_t t_gr, void *stream, int32_t *h_threads) {
+  if (!b) return fail(GRP_EINVAL, "grp_batch_autotune: null batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  // snapshot every run's state and counters
+  struct Snap {
+    double *q, *p, *f, *acc;
+    size_t nq, na;
+    long long tg, tp;
+  };
+  std::vector<Snap> snaps;
+  for (grp_replicas *r : b->runs) {
+    Snap s{};
+    s.nq = (size_t)r->R * r->sys->dev.nd * 8;
+    s.na = (size_t)r->R * r->sys->dev.n_obs * 4 * 8;
+    if (cudaMalloc((void **)&s.q, s.nq) != cudaSuccess || cudaMalloc((void **)&s.p, s.nq) != cudaSuccess ||
+        cudaMalloc((void **)&s.f, s.nq) != cudaSuccess || cudaMalloc((void **)&s.acc, s.na + 8) != cudaSuccess) {
+      for (Snap &x : snaps) { cudaFree(x.q); cudaFree(x.p); cudaFree(x.f); cudaFree(x.acc); }
+      return fail(GRP_ENOMEM, "grp_batch_autotune: snapshot allocation failed");
+    }
+    cudaMemcpyAsync(s.q, r->q, s.nq, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s.p, r->p, s.nq, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s.f, r->f, s.nq, cudaMemcpyDeviceToDevice, st);
+    if (s.na) cudaMemcpyAsync(s.acc, r->acc, s.na, cudaMemcpyDeviceToDevice, st);
+    s.tg = r->t_global;
+    s.tp = r->t_phase;
+    snaps.push_back(s);
+  }
+  const int candidates[] = {128, 256, 384, 512};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = b->threads;
+  float best_ms = 1e30f;
+  grp_status status = GRP_OK;
+  for (int c : candidates) {
+    b->threads = c;
+    if (batch_segment(b, 10, t_gr, 0, nullptr, st) != GRP_OK) continue;  // warm-up
+    cudaEventRecord(e0, st);
+    status = batch_segment(b, 50, t_gr, 0, nullptr, st);
+    cudaEventRecord(e1, st);
+    if (status != GRP_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  b->threads = best;
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    grp_replicas *r = b->runs[i];
+    Snap &s = snaps[i];
+    cudaMemcpyAsync(r->q, s.q, s.nq, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(r->p, s.p, s.nq, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(r->f, s.f, s.nq, cudaMemcpyDeviceToDevice, st);
+    if (s.na) cudaMemcpyAsync(r->acc, s.acc, s.na, cudaMemcpyDeviceToDevice, st);
+    r->t_global = s.tg;
+    r->t_phase = s.tp;
+  }
+  cudaStreamSynchronize(st);
+  for (Snap &s : snaps) { cudaFree(s.q); cudaFree(s.p); cudaFree(s.f); cudaFree(s.acc); }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h_threads) *h_threads = best;
+  return status;
 }
 
 // Parallel phase: segments of t_check steps with the exit test fused at the end; batches of

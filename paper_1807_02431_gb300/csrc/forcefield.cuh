@@ -70,6 +70,12 @@ struct Pos<PathF64> {
   __device__ __forceinline__ V3<double> diff(int i, int j) const {  // q_i - q_j
     return {q[3 * i] - q[3 * j], q[3 * i + 1] - q[3 * j + 1], q[3 * i + 2] - q[3 * j + 2]};
   }
+  // one atom's position held in registers (tile loops)
+  struct At {
+    double x, y, z;
+  };
+  __device__ __forceinline__ At at(int i) const { return {q[3 * i], q[3 * i + 1], q[3 * i + 2]}; }
+  __device__ __forceinline__ static V3<double> diff(const At &a, const At &b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 };
 template <>
 struct Pos<PathMixed> {
@@ -77,6 +83,13 @@ struct Pos<PathMixed> {
   __device__ __forceinline__ V3<float> diff(int i, int j) const {
     const float4 a = qh[i], b = qh[j], c = ql[i], d = ql[j];
     return {(a.x - b.x) + (c.x - d.x), (a.y - b.y) + (c.y - d.y), (a.z - b.z) + (c.z - d.z)};
+  }
+  struct At {
+    float4 h, l;
+  };
+  __device__ __forceinline__ At at(int i) const { return {qh[i], ql[i]}; }
+  __device__ __forceinline__ static V3<float> diff(const At &a, const At &b) {
+    return {(a.h.x - b.h.x) + (a.l.x - b.l.x), (a.h.y - b.h.y) + (a.l.y - b.l.y), (a.h.z - b.h.z) + (a.l.z - b.l.z)};
   }
 };
 
@@ -162,16 +175,29 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
     const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
     V3<T> fi = {T(0), T(0), T(0)}, fj = {T(0), T(0), T(0)};
     T en = T(0);
+    // atom i in registers (padding lanes read a valid atom and have an empty mask)
+    const int ic = i < S.n ? i : S.n - 1;
+    const typename Pos<P>::At pi = pos.at(ic);
+    const auto ai = par.atom[ic];
+#pragma unroll 4
     for (int s = s0; s < s1; ++s) {
       const int m = (lane + s) & 31;
       const bool on = ((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16);
       if (on) {
-        V3<T> f;
-        T ep = T(0);
-        if (pair_eval<P>(pos, par, i, j0 + m, cut2, f, ep, want_e)) {
+        const int j = j0 + m;
+        const V3<T> d = Pos<P>::diff(pi, pos.at(j));
+        const T r2 = dot(d, d);
+        if (!(cut2 > T(0) && r2 >= cut2)) {
+          const auto aj = par.atom[j];
+          const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
+          const T inv_r2 = grcp(r2);
+          const T s2 = sig * sig * inv_r2;
+          const T s6 = s2 * s2 * s2;
+          const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+          const V3<T> f = {g * d.x, g * d.y, g * d.z};
           fi.x += f.x; fi.y += f.y; fi.z += f.z;
           fj.x -= f.x; fj.y -= f.y; fj.z -= f.z;
-          en += ep;
+          if (want_e) en += T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
         }
       }
       fj.x = __shfl_sync(0xffffffffu, fj.x, (lane + 1) & 31);

@@ -9,11 +9,9 @@ namespace grp {
 // (t_global, replica r), picks survivor number floor(u * |S| / 2^32) in ascending index order among
 // the non-exited workers S (the reference walker when S is empty) and copies q, p, F and the
 // observable accumulators from it.  Sources are never destinations, so the copies do not race.
-__global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int nacc, double *q, double *p,
-                                                        double *f, double *acc, const uint8_t *exited,
-                                                        int32_t *src, int *n_branched, uint64_t seed,
-                                                        long long t_global) {
-  const int r = blockIdx.x;
+__device__ __forceinline__ void fv_branch_one(int r, int n_rep, int nd, int nacc, double *q, double *p, double *f,
+                                              double *acc, const uint8_t *exited, int32_t *src, int *n_branched,
+                                              uint64_t seed, long long t_global) {
   __shared__ int s_src;
   __shared__ int s_cnt[8];
   if (r == 0 || !exited[r]) {
@@ -67,11 +65,32 @@ __global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int n
   }
 }
 
+__global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int nacc, double *q, double *p,
+                                                        double *f, double *acc, const uint8_t *exited,
+                                                        int32_t *src, int *n_branched, uint64_t seed,
+                                                        long long t_global) {
+  fv_branch_one(blockIdx.x, n_rep, nd, nacc, q, p, f, acc, exited, src, n_branched, seed, t_global);
+}
+
 cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                              const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
                              long long t_global, cudaStream_t st) {
   fv_branch_kernel<<<n_rep, 256, 0, st>>>(n_rep, S.nd, S.n_obs * 4, q, p, f, acc, exited, src, n_branched,
                                           seed, t_global);
+  return cudaGetLastError();
+}
+
+// Batched branching: one block per (run, replica) unit.
+__global__ void __launch_bounds__(256) fv_branch_batch_kernel(const RunArrays *runs, const uint2 *units) {
+  const uint2 u = units[blockIdx.x];
+  const RunArrays &a = runs[u.x];
+  fv_branch_one((int)u.y, a.n_rep, a.nd, a.nacc, a.q, a.p, a.f, a.acc, a.exited, a.src, a.n_branched, a.seed,
+                a.t_global);
+}
+
+cudaError_t launch_fv_branch_batch(const RunArrays *d_runs, const uint2 *d_units, int n_units, cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  fv_branch_batch_kernel<<<n_units, 256, 0, st>>>(d_runs, d_units);
   return cudaGetLastError();
 }
 
@@ -97,9 +116,8 @@ __device__ __forceinline__ double block_sum_d(double v, double *scratch) {
 // One block per observable j.  With per-worker accumulators (c, S1, S2, n): Obar^k = c + S1/n and
 // the within variance var_k = S2/n - (S1/n)^2; the numerator of Eq. 3 equals W + B with
 // W = mean_k var_k and B = mean_k (Obar^k - Obar)^2, its denominator is W, so R = 1 + B / W.
-__global__ void __launch_bounds__(256) gelman_rubin_kernel(int n_rep, int n_obs, const double *acc, double *rhat) {
+__device__ __forceinline__ void gelman_rubin_one(int j, int n_rep, int n_obs, const double *acc, double *rhat) {
   __shared__ double scratch[33];
-  const int j = blockIdx.x;
   const int nw = n_rep - 1;
   double sm = 0, bad = 0;
   for (int r = 1 + threadIdx.x; r < n_rep; r += blockDim.x) {
@@ -122,6 +140,43 @@ __global__ void __launch_bounds__(256) gelman_rubin_kernel(int n_rep, int n_obs,
   const double W = block_sum_d(sw, scratch) / nw;
   if (threadIdx.x == 0) rhat[j] = (nw < 1 || nbad > 0 || !(W > 0)) ? __longlong_as_double(0x7FF0000000000000LL)
                                                                     : 1.0 + B / W;
+}
+
+__global__ void __launch_bounds__(256) gelman_rubin_kernel(int n_rep, int n_obs, const double *acc, double *rhat) {
+  gelman_rubin_one(blockIdx.x, n_rep, n_obs, acc, rhat);
+}
+
+// Batched Gelman-Rubin: one block per (run, observable) unit.
+__global__ void __launch_bounds__(256) gelman_rubin_batch_kernel(const RunArrays *runs, const uint2 *units) {
+  const uint2 u = units[blockIdx.x];
+  const RunArrays &a = runs[u.x];
+  gelman_rubin_one((int)u.y, a.n_rep, a.n_obs, a.acc, a.rhat);
+}
+
+cudaError_t launch_gelman_rubin_batch(const RunArrays *d_runs, const uint2 *d_units, int n_units, cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  gelman_rubin_batch_kernel<<<n_units, 256, 0, st>>>(d_runs, d_units);
+  return cudaGetLastError();
+}
+
+// Per-run status of one batched exit test, gathered for a single readback.
+__global__ void collect_status_kernel(const RunArrays *runs, int n_runs, BatchStatus *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_runs) return;
+  const RunArrays &a = runs[r];
+  BatchStatus s;
+  s.n_branched = *a.n_branched;
+  s.label0 = a.labels[0];
+  s.exited0 = a.exited[0];
+  s.err = *a.err;
+  for (int j = 0; j < kMaxObs; ++j) s.rhat[j] = j < a.n_obs ? a.rhat[j] : 0.0;
+  out[r] = s;
+}
+
+cudaError_t launch_collect_status(const RunArrays *d_runs, int n_runs, BatchStatus *d_out, cudaStream_t st) {
+  if (n_runs <= 0) return cudaSuccess;
+  collect_status_kernel<<<(n_runs + 63) / 64, 64, 0, st>>>(d_runs, n_runs, d_out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gelman_rubin(const SysDev &S, int n_rep, const double *acc, double tol, double *rhat,

@@ -57,6 +57,36 @@ cudaError_t launch_gelman_rubin(const SysDev &S, int n_rep, const double *acc, d
 cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                                 int src, int dst, int clear_acc, cudaStream_t st);
 
+// ---- batched runs (many replica sets, possibly of different systems, in one launch)
+// Device arrays of one run for the batched branching / Gelman-Rubin / status kernels.
+struct RunArrays {
+  double *q, *p, *f, *acc;
+  uint8_t *exited;
+  int8_t *labels;
+  int32_t *src;
+  int *n_branched;
+  double *rhat;
+  int *err;
+  int nd, nacc, n_rep, n_obs;
+  uint64_t seed;
+  long long t_global;
+};
+struct BatchStatus {
+  int n_branched;
+  int label0;
+  int exited0;
+  int err;
+  double rhat[kMaxObs];
+};
+static_assert(sizeof(SegArgs) % sizeof(int) == 0, "SegArgs is copied word by word");
+
+// Persistent batched segment kernel over (run, replica) units; returns the number of blocks used.
+cudaError_t launch_segment_batch(const SegArgs *d_runs, const uint2 *d_units, int n_units, int *d_counter,
+                                 int precision, int threads, size_t smem, cudaStream_t st, int *blocks_used);
+cudaError_t launch_fv_branch_batch(const RunArrays *d_runs, const uint2 *d_units, int n_units, cudaStream_t st);
+cudaError_t launch_gelman_rubin_batch(const RunArrays *d_runs, const uint2 *d_units, int n_units, cudaStream_t st);
+cudaError_t launch_collect_status(const RunArrays *d_runs, int n_runs, BatchStatus *d_out, cudaStream_t st);
+
 // Energies and forces of B configurations.
 cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, double *energy,
                                  double *forces, int *err, cudaStream_t st);

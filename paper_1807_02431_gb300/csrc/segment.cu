@@ -417,15 +417,11 @@ struct ObsAcc<PathMixed> {
 };
 
 // ------------------------------------------------------------------------------------------------
-// kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
-// on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
-template <class P, int kMaxThreads, int kMinBlocks>
-__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
+// One segment of replica r by the whole thread block (the block's shared memory holds its state).
+template <class P>
+__device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsigned char *smem) {
   using T = typename P::T;
   const SysDev &S = a.S;
-  const int r = blockIdx.x;
-  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int kThreads = (int)blockDim.x;
   const int n = S.n, nd = 3 * n, no = S.n_obs, NB = a.noise_batch;
   unsigned char *ptr = smem;
@@ -510,6 +506,39 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
     record_check(a, r, label, ex);
   }
   if (err) atomicOr(a.err, err);
+}
+
+// kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
+// on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
+template <class P, int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
+  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  segment_body<P>(a, blockIdx.x, smem);
+}
+
+// Batched segments: a persistent grid of blocks takes (run, replica) units from a queue sorted by
+// decreasing system size, so that the largest replicas start first and the small ones fill in.
+// Each unit's launch arguments are copied into shared memory before its segment runs.
+template <class P>
+__global__ void __launch_bounds__(512, 1) ff_segment_batch_kernel(const SegArgs *runs, const uint2 *units,
+                                                                  int n_units, int *counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SegArgs sa;
+  __shared__ int su;
+  for (;;) {
+    if (threadIdx.x == 0) su = atomicAdd(counter, 1);
+    __syncthreads();
+    const int u = su;
+    if (u >= n_units) break;
+    const uint2 un = units[u];
+    const int *src = reinterpret_cast<const int *>(runs + un.x);
+    int *dst = reinterpret_cast<int *>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(SegArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    segment_body<P>(sa, (int)un.y, smem);
+    __syncthreads();
+  }
 }
 
 // Analytic 2-D double well: one thread per replica, FP64 (dim = 2, one particle).
@@ -607,6 +636,26 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.n_active, c.threads, c.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_batch(const SegArgs *d_runs, const uint2 *d_units, int n_units, int *d_counter,
+                                 int precision, int threads, size_t smem, cudaStream_t st, int *blocks_used) {
+  if (n_units <= 0) return cudaSuccess;
+  if (threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
+  auto kern = precision == GRP_FP64 ? ff_segment_batch_kernel<PathF64> : ff_segment_batch_kernel<PathMixed>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int blocks = sms * per_sm;
+  if (blocks > n_units) blocks = n_units;
+  if ((e = cudaMemsetAsync(d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+  kern<<<blocks, threads, smem, st>>>(d_runs, d_units, n_units, d_counter);
+  if (blocks_used) *blocks_used = blocks;
   return cudaGetLastError();
 }
 
