@@ -33,7 +33,8 @@ typedef int32_t grp_status;
 #define GRP_ENOMEM (-2)    /* device or host allocation failed */
 #define GRP_ECUDA (-3)     /* a CUDA runtime call failed */
 #define GRP_ENAN (-4)      /* a kernel found a non-finite position or momentum */
-#define GRP_EOVERFLOW (-5) /* a force contribution exceeded the fixed-point range (|f| >= 2^15) */
+#define GRP_EOVERFLOW (-5) /* a force or energy term exceeded the fixed-point range (|f| >= 2^22 on
+                              the FP64 path, 2^18 on the mixed path) or was not finite */
 #define GRP_ETIMEOUT (-6)  /* a bounded loop ran out before its condition was met */
 #define GRP_ENOTIMPL (-7)  /* the requested combination is not supported */
 #define GRP_NOEXIT 1       /* positive: the parallel phase ended after max_checks without exit */

@@ -340,7 +340,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
   if (e) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
-    return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range (|f| >= 2^15)");
+    return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
 }
@@ -805,6 +805,7 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
   CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&r->hb->err, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   out->ref_exited = r->hb->exited0;
   out->label0 = r->hb->label0;
@@ -818,6 +819,7 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
     if (want_gr && j < D.n_obs && !(r->hb->rhat[j] < 1.0 + tol)) conv = 0;
   }
   out->converged = conv;
+  if (r->hb->err) return latch_errors(r, st);  // a kernel latched an error during this check
   return GRP_OK;
 }
 

@@ -17,14 +17,13 @@ enum : int { kErrNaN = 1, kErrOverflow = 2 };
 // Kinds of force-field work items.
 enum : uint32_t { kItemPair = 0, kItemBond = 1, kItemAngle = 2, kItemDihedral = 3, kItemNone = 15 };
 
-// Fixed point: one unit = 2^-40 of the force (or energy) unit, so that quantisation (9e-13) stays
-// below FP64 rounding of typical forces.  A single contribution must stay below 2^15 in magnitude,
-// so that 2^8 contributions at that bound still sum inside int64.
+// FP64-path fixed point: one unit = 2^-40 of the force (or energy) unit, so that quantisation (9e-13)
+// stays below FP64 rounding of typical forces.  Integer sums are exact modulo 2^64, so only a single
+// contribution and the final sum must fit: contributions are bounded by 2^22 (larger ones set the
+// overflow flag), and a sum is exact while its magnitude stays below 2^23.
 constexpr double kFixScale = 1099511627776.0;       // 2^40
 constexpr double kFixInv = 1.0 / 1099511627776.0;
-constexpr float kFixScaleF = 1099511627776.0f;
-constexpr float kFixInvF = 1.0f / 1099511627776.0f;
-constexpr double kFixLimit = 32768.0;                 // 2^15
+constexpr double kFixLimit = 4194304.0;               // 2^22
 
 // Device copy of a system.  All arrays are device memory owned by grp_system.  Parameters exist in
 // FP64 (FP64 path) and FP32 (mixed path) copies.
@@ -136,46 +135,17 @@ __device__ __forceinline__ long long to_fix(double v, int *err) {
   if (!(fabs(v) < kFixLimit)) { *err |= kErrOverflow; return 0; }
   return __double2ll_rn(v * kFixScale);
 }
-// FP32 -> 64-bit fixed point built from 32-bit conversions only: the 64-bit int<->float conversions
-// execute on the FP64 pipe, which on GB300 runs at 1/64 of the FP32 rate.  With a = v 2^8 (exact),
-// hi = floor(a) and the fraction r = a - hi in [0, 1), the fixed-point value is hi 2^32 + r 2^32.
-struct Fix2 {
-  int hi;
-  unsigned int lo;
-};
-__device__ __forceinline__ Fix2 to_fix2(float v, int *err) {
-  Fix2 f{0, 0u};
-  if (!(fabsf(v) < (float)kFixLimit)) { *err |= kErrOverflow; return f; }
-  const float a = v * 256.0f;
-  const float hf = floorf(a);
-  const float r = a - hf;  // exact except for tiny negative a, where it may round up to 1
-  f.hi = (int)hf;
-  if (r >= 1.0f) {
-    f.hi += 1;
-  } else {
-    f.lo = __float2uint_rn(r * 4294967296.0f);
-  }
-  return f;
-}
-__device__ __forceinline__ long long fix2_value(Fix2 f) {
-  return (long long)(((unsigned long long)(unsigned int)f.hi << 32) | f.lo);
-}
-__device__ __forceinline__ long long to_fix(float v, int *err) { return fix2_value(to_fix2(v, err)); }
-// int64 fixed point -> FP32 from two 32-bit conversions.
-__device__ __forceinline__ float fix_to_float(long long x) {
-  const int hi = (int)(x >> 32);
-  const unsigned int lo = (unsigned int)x;
-  return fmaf((float)hi, 4294967296.0f, (float)lo) * kFixInvF;
-}
-
 // Mixed-path force accumulator: fixed point with 2^-32 units kept as two 32-bit words that are
-// summed separately with non-returning atomics (no carry between them): a contribution v 2^32 is
+// summed separately with non-returning atomics (no carry between them; the 64-bit integer
+// conversions would run on the FP64 pipe, 1/64 of the FP32 rate on GB300): a contribution v 2^32 is
 // split as hi 2^20 + lo with lo in [0, 2^20].  The lo word holds up to 4,095 contributions without
 // wrapping; the hi word is summed modulo 2^32, exact as long as the total |F| < 2^19.  The value is
-// hi_sum 2^20 + lo_sum, the same integer whatever the order of the additions.
+// hi_sum 2^20 + lo_sum, the same integer whatever the order of the additions.  Single contributions
+// are bounded by 2^18 (larger ones, or NaN, set the overflow flag).
 constexpr float kSplitHiScale = 4096.0f;       // 2^32 / 2^20
 constexpr float kSplitLoScale = 1048576.0f;    // 2^20
 constexpr float kSplitInv = 2.3283064365386963e-10f;  // 2^-32
+constexpr float kSplitLimit = 262144.0f;       // 2^18
 struct Split {
   int hi;
   unsigned int lo;
@@ -189,7 +159,7 @@ __device__ __forceinline__ Split to_split(float v, int *err) {
   Split s;
   s.hi = __float2int_rd(a);
   s.lo = __float2uint_rn((a - (float)s.hi) * kSplitLoScale);
-  *err |= (fabsf(v) < (float)kFixLimit) ? 0 : kErrOverflow;
+  *err |= (fabsf(v) < kSplitLimit) ? 0 : kErrOverflow;
   return s;
 }
 __device__ __forceinline__ long long split_value(Split s) { return (long long)s.hi * (1ll << 20) + (long long)s.lo; }
@@ -211,12 +181,6 @@ __device__ __forceinline__ void fix_add(long long *dst, long long v) {
   const unsigned int old = atomicAdd(&w[0], lo);
   const unsigned int carry = (unsigned int)(old + lo < old);
   atomicAdd(&w[1], hi + carry);
-}
-__device__ __forceinline__ void fix_add(long long *dst, Fix2 f) {
-  unsigned int *w = reinterpret_cast<unsigned int *>(dst);
-  const unsigned int old = atomicAdd(&w[0], f.lo);
-  const unsigned int carry = (unsigned int)(old + f.lo < old);
-  atomicAdd(&w[1], (unsigned int)f.hi + carry);
 }
 
 // ------------------------------------------------------------------------------------------------
