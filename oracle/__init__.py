@@ -94,6 +94,7 @@ def lib():
         L.orc_potential.restype = C.c_double
         L.orc_potential.argtypes = [C.c_void_p, _D]
         L.orc_forces.argtypes = [C.c_void_p, _D, _D]
+        L.orc_param_grad.argtypes = [C.c_void_p, _D, _D]
         L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
         L.orc_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int32, C.c_int32, _D]
         L.orc_branch_word.restype = C.c_uint32
@@ -207,6 +208,15 @@ class Oracle:
         f = np.zeros_like(q)
         lib().orc_forces(self.ctx, _dp(q), _dp(f))
         return f
+
+    def param_grad(self, q):
+        """dV/d theta: [sigma_i (n), epsilon_i (n), dihedral k_t (n_dihedrals)]."""
+        q = _c64(q)
+        s = self.system
+        nd = 0 if s.dihedrals is None else len(s.dihedrals)
+        g = np.zeros(2 * s.n_atoms + nd)
+        lib().orc_param_grad(self.ctx, _dp(q), _dp(g))
+        return g
 
     def state_of(self, q):
         return lib().orc_state_of(self.ctx, _dp(_c64(q)))

@@ -209,6 +209,42 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
   }
 }
 
+/* ---------------------------------------------------------------- dV/d theta
+ * Pair (i, j): E = 4 e (s^12 - s^6) with s = sig / r, sig = (sigma_i + sigma_j) / 2 and
+ * e = sqrt(epsilon_i epsilon_j).  dE/d sig = 4 e (12 s^12 - 6 s^6) / sig and d sig / d sigma_i = 1/2;
+ * dE/d e = 4 (s^12 - s^6) and d e / d epsilon_i = epsilon_j / (2 e).  Coulomb does not depend on
+ * theta.  Dihedral term t: E = k_t (1 + cos(n_t phi - delta_t)), so dE/dk_t = 1 + cos(n_t phi - delta_t). */
+void orc_param_grad(const orc_ctx *c, const double *q, double *g) {
+  const orc_system *s = &c->s;
+  int n = s->n_atoms;
+  int nt = 2 * n + s->n_dihedrals;
+  memset(g, 0, sizeof(double) * (size_t)nt);
+  if (s->potential != ORC_POT_FORCE_FIELD) return;
+  for (int i = 0; i < n; ++i) {
+    for (int j = i + 1; j < n; ++j) {
+      if (c->excluded[(size_t)i * n + j]) continue;
+      double d[3];
+      sub3(q + 3 * i, q + 3 * j, d);
+      double r2 = dot3(d, d);
+      if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
+      double sig = 0.5 * (s->sigma[i] + s->sigma[j]);
+      double eps = sqrt(s->epsilon[i] * s->epsilon[j]);
+      double sr6 = pow(sig * sig / r2, 3);
+      double de_dsig = 4.0 * eps * (12.0 * sr6 * sr6 - 6.0 * sr6) / sig;
+      double de_deps = 4.0 * (sr6 * sr6 - sr6);
+      g[i] += 0.5 * de_dsig;
+      g[j] += 0.5 * de_dsig;
+      g[n + i] += de_deps * s->epsilon[j] / (2.0 * eps);
+      g[n + j] += de_deps * s->epsilon[i] / (2.0 * eps);
+    }
+  }
+  for (int t = 0; t < s->n_dihedrals; ++t) {
+    const int *a = s->dihedral_atoms + 4 * t;
+    double phi = dihedral_angle(q + 3 * a[0], q + 3 * a[1], q + 3 * a[2], q + 3 * a[3]);
+    g[2 * n + t] = 1.0 + cos(s->dihedral_n[t] * phi - s->dihedral_delta[t]);
+  }
+}
+
 /* ---------------------------------------------------------------- Philox4x32-10 */
 static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo) {
   uint64_t p = (uint64_t)a * (uint64_t)b;

@@ -83,6 +83,13 @@ void orc_destroy(orc_ctx *c);
 double orc_potential(const orc_ctx *c, const double *q);
 void orc_forces(const orc_ctx *c, const double *q, double *f);
 
+/* Derivatives of V with respect to the force-field parameters theta (differentiation of the
+ * potential, outside the paper): g[0..n) = dV/d sigma_i, g[n..2n) = dV/d epsilon_i (per-atom
+ * Lennard-Jones parameters combined by the Lorentz-Berthelot rules), g[2n..2n+n_dihedrals) = dV/dk_t
+ * for every dihedral term in the order of the description.  The derivative with respect to
+ * epsilon_i does not exist where epsilon_i = 0 (the square root of the combination rule). */
+void orc_param_grad(const orc_ctx *c, const double *q, double *g);
+
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the Philox S-box on a 128-bit
  * counter with a 64-bit key. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
