@@ -265,6 +265,30 @@ grp_status grp_get_device_view(grp_replicas *r, grp_device_view *out);
 grp_status grp_energy_forces(grp_system *s, int32_t n_conf, const double *d_q, double *d_energy,
                              double *d_forces, void *stream);
 
+/* Differentiation of V (Eq. 1) with respect to positions and force-field parameters (not in the
+ * paper; for fitting the force field that drives the dynamics).  The parameters theta of a
+ * GRP_POT_FORCE_FIELD system are, in this order: sigma_i (n values), epsilon_i (n values) and k of
+ * every dihedral term in the order of grp_system_desc (n_dihedrals values); n_theta = 2 n +
+ * n_dihedrals (0 for the double well).  Lennard-Jones pairs combine them by the Lorentz-Berthelot
+ * rules, so dV/d epsilon_i does not exist where epsilon_i = 0 (GRP_EOVERFLOW is then returned). */
+grp_status grp_param_count(const grp_system *s, int32_t *h_n_theta);
+/* d_theta (device [n_theta] FP64) receives the current parameters. */
+grp_status grp_get_params(const grp_system *s, double *d_theta, void *stream);
+/* Replace the parameters by d_theta (device [n_theta] FP64, copied); later calls on every replica
+ * set of s (dynamics included) use them.  GRP_EINVAL, with nothing changed, unless every sigma_i > 0,
+ * every epsilon_i >= 0 and every value is finite.  Synchronises `stream`.  Not to be called while a
+ * kernel of a replica set of s runs on another stream. */
+grp_status grp_set_params(grp_system *s, const double *d_theta, void *stream);
+/* For B configurations d_q (device [B][n][dim] FP64) and weights d_w (device [B], NULL = all 1):
+ *   d_energy     (optional, device [B])        V(q_b), unweighted;
+ *   d_grad_q     (optional, device [B][n][dim]) w_b dV/dq (q_b) = -w_b F(q_b);
+ *   d_grad_theta (optional, device [n_theta])   sum_b w_b dV/d theta (q_b), summed in order of b.
+ * This is the vector-Jacobian product of the map q -> (V(q_b))_b for the cotangent w, as reverse-
+ * mode differentiation needs it.  Computed in the system's precision (the mixed path: FP32 terms,
+ * fixed-point sums).  Synchronises `stream`. */
+grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const double *d_q, const double *d_w,
+                           double *d_energy, double *d_grad_q, double *d_grad_theta, void *stream);
+
 /* Fleming-Viot branching, as grp_fv_branch, on replica arrays the caller owns, allocating nothing.
  * (No counterpart in the paper: this serves callers that cannot allocate device memory while they
  * run, because their memory belongs to another allocator with a fixed budget or because the

@@ -106,6 +106,10 @@ SIGNATURES = {
     "grp_set_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
     "grp_get_device_view": (C.c_int32, [_VP, C.POINTER(DeviceView)]),
     "grp_energy_forces": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "grp_param_count": (C.c_int32, [_VP, _I32P]),
+    "grp_get_params": (C.c_int32, [_VP, _VP, _VP]),
+    "grp_set_params": (C.c_int32, [_VP, _VP, _VP]),
+    "grp_energy_grad": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
     "grp_fv_branch_noalloc": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_uint64, C.c_int64, _I32P,
                                           _VP]),
     "grp_batch_create": (C.c_int32, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
@@ -337,6 +341,26 @@ def grp_get_device_view(r: ReplicasHandle) -> dict:
 
 def grp_energy_forces(sysh: SystemHandle, n_conf: int, d_q, d_energy=None, d_forces=None, stream=None):
     _check(_lib.grp_energy_forces(sysh.handle, n_conf, _ptr(d_q), _ptr(d_energy), _ptr(d_forces), _stream(stream)))
+
+
+def grp_param_count(sysh: SystemHandle) -> int:
+    n = C.c_int32(0)
+    _check(_lib.grp_param_count(sysh.handle, C.byref(n)))
+    return n.value
+
+
+def grp_get_params(sysh: SystemHandle, d_theta, stream=None):
+    _check(_lib.grp_get_params(sysh.handle, _ptr(d_theta), _stream(stream)))
+
+
+def grp_set_params(sysh: SystemHandle, d_theta, stream=None):
+    _check(_lib.grp_set_params(sysh.handle, _ptr(d_theta), _stream(stream)))
+
+
+def grp_energy_grad(sysh: SystemHandle, n_conf: int, d_q, d_w=None, d_energy=None, d_grad_q=None,
+                    d_grad_theta=None, stream=None):
+    _check(_lib.grp_energy_grad(sysh.handle, n_conf, _ptr(d_q), _ptr(d_w), _ptr(d_energy), _ptr(d_grad_q),
+                                _ptr(d_grad_theta), _stream(stream)))
 
 
 class BatchHandle:

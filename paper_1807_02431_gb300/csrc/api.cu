@@ -54,6 +54,9 @@ struct grp_system {
   SegConfig seg{};
   std::vector<void *> owned;
   int device = 0;
+  // force-field parameters theta = (sigma_i, eps_i, k of each dihedral term in description order)
+  int n_terms = 0;
+  double *theta = nullptr;  // device [2n + n_terms], owned
 };
 
 struct grp_replicas {
@@ -284,6 +287,7 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     std::vector<int2> dterms;
     std::vector<double4> td;
     std::vector<float4> tf;
+    std::vector<int> tsrc;
     for (auto &key : order) {
       dijkl.push_back(make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key)));
       const int t0 = (int)td.size();
@@ -291,6 +295,7 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
         td.push_back(make_double4(d->dihedral_k[t], (double)d->dihedral_n[t], std::cos(d->dihedral_delta[t]),
                                   std::sin(d->dihedral_delta[t])));
         tf.push_back(make_float4((float)td.back().x, (float)td.back().y, (float)td.back().z, (float)td.back().w));
+        tsrc.push_back(t);
       }
       dterms.push_back(make_int2(t0, (int)td.size()));
     }
@@ -315,6 +320,15 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     UP(dterms.data(), dterms.size(), &D.dih_terms);
     UP(td.data(), td.size(), &D.term_d);
     UP(tf.data(), tf.size(), &D.term_f);
+    UP(tsrc.data(), tsrc.size(), &D.term_src);
+    // theta as given, for grp_get_params
+    s->n_terms = (int)td.size();
+    std::vector<double> th(2 * (size_t)n + s->n_terms);
+    for (int i = 0; i < n; ++i) { th[i] = d->sigma[i]; th[n + i] = d->epsilon[i]; }
+    for (int t = 0; t < s->n_terms; ++t) th[2 * n + t] = d->dihedral_k[t];
+    const double *dth = nullptr;
+    UP(th.data(), th.size(), &dth);
+    s->theta = const_cast<double *>(dth);
   }
 #undef UP
   s->seg = segment_config(D, 0);
@@ -970,5 +984,72 @@ extern "C" grp_status grp_energy_forces(grp_system *s, int32_t n_conf, const dou
   CU(cudaStreamSynchronize(st));
   CU(cudaFreeAsync(err, st));
   if (h & kErrOverflow) return fail(GRP_EOVERFLOW, "force contribution outside the fixed-point range");
+  return GRP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Differentiation with respect to positions and force-field parameters.
+extern "C" grp_status grp_param_count(const grp_system *s, int32_t *h_n_theta) {
+  if (!s || !h_n_theta) return fail(GRP_EINVAL, "grp_param_count: null argument");
+  *h_n_theta = s->dev.potential == GRP_POT_FORCE_FIELD ? 2 * s->dev.n + s->n_terms : 0;
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_get_params(const grp_system *s, double *d_theta, void *stream) {
+  if (!s || !d_theta) return fail(GRP_EINVAL, "grp_get_params: null argument");
+  if (s->dev.potential != GRP_POT_FORCE_FIELD) return fail(GRP_EINVAL, "grp_get_params: no force-field parameters");
+  const size_t nt = 2 * (size_t)s->dev.n + s->n_terms;
+  CU(cudaMemcpyAsync(d_theta, s->theta, nt * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_set_params(grp_system *s, const double *d_theta, void *stream) {
+  if (!s || !d_theta) return fail(GRP_EINVAL, "grp_set_params: null argument");
+  if (s->dev.potential != GRP_POT_FORCE_FIELD) return fail(GRP_EINVAL, "grp_set_params: no force-field parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nt = 2 * (size_t)s->dev.n + s->n_terms;
+  int *bad = nullptr;
+  CU(cudaMallocAsync((void **)&bad, 4, st));
+  CU(launch_set_params(s->dev, s->n_terms, d_theta, bad, st));
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaFreeAsync(bad, st));
+  if (h) return fail(GRP_EINVAL, "grp_set_params: sigma must be > 0, epsilon >= 0 and every value finite");
+  CU(cudaMemcpyAsync(s->theta, d_theta, nt * 8, cudaMemcpyDeviceToDevice, st));
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const double *d_q, const double *d_w,
+                                      double *d_energy, double *d_grad_q, double *d_grad_theta, void *stream) {
+  if (!s || !d_q || n_conf < 0) return fail(GRP_EINVAL, "grp_energy_grad: bad argument");
+  if (d_grad_theta && s->dev.potential != GRP_POT_FORCE_FIELD)
+    return fail(GRP_EINVAL, "grp_energy_grad: no force-field parameters to differentiate");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nt = 2 * s->dev.n + s->n_terms;
+  if (d_grad_theta && (size_t)nt * 8 > 227 * 1024)
+    return fail(GRP_ENOTIMPL, "grp_energy_grad: %d parameters exceed one block's shared memory", nt);
+  if (n_conf == 0) {
+    if (d_grad_theta) CU(cudaMemsetAsync(d_grad_theta, 0, (size_t)nt * 8, st));
+    return GRP_OK;
+  }
+  int *err = nullptr;
+  double *partial = nullptr;
+  CU(cudaMallocAsync((void **)&err, 4, st));
+  CU(cudaMemsetAsync(err, 0, 4, st));
+  if (d_energy || d_grad_q) CU(launch_energy_forces(s->dev, n_conf, d_q, d_energy, d_grad_q, err, st));
+  if (d_grad_theta) {
+    CU(cudaMallocAsync((void **)&partial, (size_t)n_conf * nt * 8, st));
+    CU(launch_param_grad(s->dev, s->n_terms, n_conf, d_q, d_w, d_grad_q, partial, err, st));
+    CU(launch_column_sum(partial, n_conf, nt, d_grad_theta, st));
+    CU(cudaFreeAsync(partial, st));
+  } else if (d_grad_q) {
+    CU(launch_scale_rows(d_grad_q, n_conf, s->dev.nd, d_w, -1.0, st));
+  }
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaFreeAsync(err, st));
+  if (h) return fail(GRP_EOVERFLOW, "grp_energy_grad: a term outside the fixed-point range or not finite");
   return GRP_OK;
 }

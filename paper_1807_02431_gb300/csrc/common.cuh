@@ -59,6 +59,7 @@ struct SysDev {
   const int2 *dih_terms;
   const double4 *term_d;   // (k, n, cos delta, sin delta)
   const float4 *term_f;
+  const int *term_src;     // [terms] index of each term in the description's dihedral list
   int cv_kind;
   int cv_atoms[8];
   double cv_params[8];

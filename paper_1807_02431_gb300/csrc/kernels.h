@@ -91,4 +91,17 @@ cudaError_t launch_collect_status(const RunArrays *d_runs, int n_runs, BatchStat
 cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, double *energy,
                                  double *forces, int *err, cudaStream_t st);
 
+// ---- differentiation with respect to the force-field parameters theta = (sigma_i, eps_i, k_t)
+// Rewrite the parameter tables of S from theta [2n + n_terms] (device); *bad = 1 (and the tables
+// unchanged) when some sigma_i <= 0 or eps_i < 0 or a value is not finite.
+cudaError_t launch_set_params(const SysDev &S, int n_terms, const double *theta, int *bad, cudaStream_t st);
+// partial[b][t] = w_b dV/d theta_t at configuration b (w = NULL: 1); grad_q[b] (optional) holds the
+// forces on entry and w_b grad_q V = -w_b F on exit.
+cudaError_t launch_param_grad(const SysDev &S, int n_terms, int n_conf, const double *q, const double *w,
+                              double *grad_q, double *partial, int *err, cudaStream_t st);
+// x[b][i] *= alpha w_b (w = NULL: 1).
+cudaError_t launch_scale_rows(double *x, int rows, int cols, const double *w, double alpha, cudaStream_t st);
+// out[t] = sum_b partial[b][t] in order of b.
+cudaError_t launch_column_sum(const double *partial, int rows, int cols, double *out, cudaStream_t st);
+
 }  // namespace grp
