@@ -332,7 +332,7 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
   }
 #undef UP
   s->seg = segment_config(D, 0);
-  if (s->seg.smem > 227 * 1024) {
+  if (s->seg.smem > kMaxSmem) {
     grp_destroy_system(s);
     return fail(GRP_ENOTIMPL, "system of %d atoms needs %zu bytes of shared memory per replica", n, s->seg.smem);
   }
@@ -605,6 +605,7 @@ static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, con
     a.omega = omega ? omega[i] : 0;
     a.pairs_in_smem = r->sys->seg.pairs_in_smem;
     a.noise_batch = r->sys->seg.noise_batch;
+    a.lean = r->sys->seg.lean;
     b->h_args[i] = a;
   }
   CU(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(SegArgs) * nr, cudaMemcpyHostToDevice, st));
@@ -1027,7 +1028,7 @@ extern "C" grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const doubl
     return fail(GRP_EINVAL, "grp_energy_grad: no force-field parameters to differentiate");
   cudaStream_t st = (cudaStream_t)stream;
   const int nt = 2 * s->dev.n + s->n_terms;
-  if (d_grad_theta && (size_t)nt * 8 > 227 * 1024)
+  if (d_grad_theta && (size_t)nt * 8 > kMaxSmem)
     return fail(GRP_ENOTIMPL, "grp_energy_grad: %d parameters exceed one block's shared memory", nt);
   if (n_conf == 0) {
     if (d_grad_theta) CU(cudaMemsetAsync(d_grad_theta, 0, (size_t)nt * 8, st));

@@ -25,7 +25,8 @@ struct SegArgs {
   long long M;               // check index written into the exit key
   int skip_if_exit;          // return at once when *exit_key is already set
   int pairs_in_smem;
-  int noise_batch;           // steps of noise generated together
+  int noise_batch;           // steps of noise generated together (0: drawn inline per atom)
+  int lean;                  // atom parameters read from the global table (large systems)
   double h, c1;              // dt/2 and exp(-gamma dt)
 };
 
@@ -35,7 +36,11 @@ struct SegConfig {
   size_t smem;
   int pairs_in_smem;
   int noise_batch;
+  int lean;
 };
+
+// Largest dynamic shared memory of one block on sm_103a.
+constexpr size_t kMaxSmem = 227 * 1024;
 
 SegConfig segment_config(const SysDev &S, int threads_hint);
 cudaError_t launch_segment(const SegArgs &a, const SegConfig &cfg, cudaStream_t st);

@@ -111,10 +111,13 @@ struct State;
 template <>
 struct State<PathF64> {
   double *q, *p, *f, *sd;  // [3n], [3n], [3n], [n]
-  double4 *atom;           // [n]
-  static size_t bytes(int n) { return (size_t)n * (72 + 8 + 32); }
-  __device__ void carve(unsigned char *&ptr, int n) {
-    atom = (double4 *)ptr; ptr += (size_t)n * 32;
+  const double4 *atom;     // [n] parameters: a shared-memory copy, or the global table when lean
+  bool own_atom;
+  static size_t bytes(int n, bool lean) { return (size_t)n * (72 + 8 + (lean ? 0 : 32)); }
+  __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
+    own_atom = !lean;
+    if (lean) atom = S.atom_d;
+    else { atom = (const double4 *)ptr; ptr += (size_t)n * 32; }
     q = (double *)ptr; ptr += (size_t)n * 24;
     p = (double *)ptr; ptr += (size_t)n * 24;
     f = (double *)ptr; ptr += (size_t)n * 24;
@@ -124,7 +127,7 @@ struct State<PathF64> {
   __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
-      atom[at] = S.atom_d[at];
+      if (own_atom) const_cast<double4 *>(atom)[at] = S.atom_d[at];
       sd[at] = sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
     }
   }
@@ -180,12 +183,15 @@ struct State<PathMixed> {
   float4 *qh, *ql;   // [n] double-single positions
   float *ph, *pl;    // [3n] double-single momenta
   float *f, *sd;     // [3n], [n]
-  float4 *atom;      // [n]
-  static size_t bytes(int n) { return (size_t)n * (32 + 24 + 12 + 4 + 16); }
-  __device__ void carve(unsigned char *&ptr, int n) {
+  const float4 *atom;  // [n] parameters: a shared-memory copy, or the global table when lean
+  bool own_atom;
+  static size_t bytes(int n, bool lean) { return (size_t)n * (32 + 24 + 12 + 4 + (lean ? 0 : 16)); }
+  __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
+    own_atom = !lean;
     qh = (float4 *)ptr; ptr += (size_t)n * 16;
     ql = (float4 *)ptr; ptr += (size_t)n * 16;
-    atom = (float4 *)ptr; ptr += (size_t)n * 16;
+    if (lean) atom = S.atom_f;
+    else { atom = (const float4 *)ptr; ptr += (size_t)n * 16; }
     ph = (float *)ptr; ptr += (size_t)n * 12;
     pl = (float *)ptr; ptr += (size_t)n * 12;
     f = (float *)ptr; ptr += (size_t)n * 12;
@@ -201,7 +207,7 @@ struct State<PathMixed> {
                z = ds_from_double(gq[3 * at + 2]);
       qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
       ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
-      atom[at] = S.atom_f[at];
+      if (own_atom) const_cast<float4 *>(atom)[at] = S.atom_f[at];
       sd[at] = (float)sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
     }
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -431,9 +437,9 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   long long *ek = (long long *)ptr; ptr += 2 * 8;
   State<P> st;
   ptr = align32(ptr);
-  st.carve(ptr, n);
+  st.carve(ptr, n, S, a.lean != 0);
   ptr = align32(ptr);
-  T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);
+  T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);  // NB = 0: noise drawn inline per atom
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
   const uint32_t *pairs = S.pairs, *items = S.items;
@@ -463,12 +469,20 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
   int j = 0;  // step index inside the current noise batch
   for (int s = 0; s < a.k; ++s, ++j) {
-    if (j == NB) j = 0;
-    if (j == 0) {
-      gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r, n);
-      __syncthreads();
+    if (NB > 0) {
+      if (j == NB) j = 0;
+      if (j == 0) {
+        gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r, n);
+        __syncthreads();
+      }
+      for (int at = threadIdx.x; at < n; at += kThreads) st.baoa(at, xi + ((size_t)j * n + at) * 3, h, c1);
+    } else {
+      for (int at = threadIdx.x; at < n; at += kThreads) {
+        T z[4];
+        normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r, at), z);
+        st.baoa(at, z, h, c1);
+      }
     }
-    for (int at = threadIdx.x; at < n; at += kThreads) st.baoa(at, xi + ((size_t)j * n + at) * 3, h, c1);
     __syncthreads();
     if (boxes) {
       tile_boxes<P>(S, st, boxes);
@@ -591,11 +605,11 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch) {
+static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch, int lean) {
   const int n = S.n;
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
   size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
-  b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n) : State<PathMixed>::bytes(n);
+  b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n, lean) : State<PathMixed>::bytes(n, lean);
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
   if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
@@ -624,8 +638,15 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
   int nb = 16;
   while (nb > 1 && (size_t)nb * 3 * S.n * real > 32 * 1024) nb /= 2;
   c.noise_batch = nb;
-  c.pairs_in_smem = ff_smem_bytes(S, 1, nb) <= 160 * 1024 ? 1 : 0;
-  c.smem = ff_smem_bytes(S, c.pairs_in_smem, nb);
+  c.lean = 0;
+  // large systems: atom parameters read from the global table and noise drawn inline, so that the
+  // replica state alone fills the shared memory
+  if (ff_smem_bytes(S, 0, nb, 0) > kMaxSmem) {
+    c.lean = 1;
+    c.noise_batch = nb = 0;
+  }
+  c.pairs_in_smem = ff_smem_bytes(S, 1, nb, c.lean) <= 160 * 1024 ? 1 : 0;
+  c.smem = ff_smem_bytes(S, c.pairs_in_smem, nb, c.lean);
   return c;
 }
 
@@ -663,6 +684,7 @@ cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t s
   SegArgs a = a0;
   a.pairs_in_smem = c.pairs_in_smem;
   a.noise_batch = c.noise_batch;
+  a.lean = c.lean;
   if (a.n_active <= 0) return cudaSuccess;
   if (a.S.potential == GRP_POT_DOUBLE_WELL_2D) {
     dw_segment_kernel<<<(a.n_active + 63) / 64, 64, 0, st>>>(a);
@@ -675,7 +697,7 @@ cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t s
 // Energies and forces of independent configurations (one block per configuration).
 template <class P>
 __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const double *q, double *energy,
-                                                            double *forces, int *errp) {
+                                                            double *forces, int *errp, int lean) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = S.n, nd = 3 * n, b = blockIdx.x;
   unsigned char *ptr = smem;
@@ -683,7 +705,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   long long *red = (long long *)ptr; ptr += 32 * 8;
   State<P> st;
   ptr = align32(ptr);
-  st.carve(ptr, n);
+  st.carve(ptr, n, S, lean != 0);
   // positions only: momenta and forces are not used
   for (int at = threadIdx.x; at < n; at += blockDim.x) {
     if constexpr (P::kMixed) {
@@ -691,10 +713,10 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
                z = ds_from_double(q[(size_t)b * nd + 3 * at + 2]);
       st.qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
       st.ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
-      st.atom[at] = S.atom_f[at];
+      if (!lean) const_cast<float4 *>(st.atom)[at] = S.atom_f[at];
     } else {
       for (int x = 0; x < 3; ++x) st.q[3 * at + x] = q[(size_t)b * nd + 3 * at + x];
-      st.atom[at] = S.atom_d[at];
+      if (!lean) const_cast<double4 *>(st.atom)[at] = S.atom_d[at];
     }
   }
   for (int i = threadIdx.x; i < nd; i += blockDim.x) F[i] = 0;
@@ -736,17 +758,22 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
     dw_energy_forces_kernel<<<(n_conf + 127) / 128, 128, 0, st>>>(S, n_conf, q, energy, forces);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)3 * S.n * 8 + 32 * 8 + 32 +
-                      (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n) : State<PathMixed>::bytes(S.n));
+  auto bytes = [&](bool lean) {
+    return (size_t)3 * S.n * 8 + 32 * 8 + 32 +
+           (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n, lean) : State<PathMixed>::bytes(S.n, lean));
+  };
+  const int lean = bytes(false) > kMaxSmem ? 1 : 0;
+  const size_t smem = bytes(lean);
+  if (smem > kMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e;
   if (S.precision == GRP_FP64) {
     e = cudaFuncSetAttribute(energy_forces_kernel<PathF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    energy_forces_kernel<PathF64><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err);
+    energy_forces_kernel<PathF64><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean);
   } else {
     e = cudaFuncSetAttribute(energy_forces_kernel<PathMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    energy_forces_kernel<PathMixed><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err);
+    energy_forces_kernel<PathMixed><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean);
   }
   return cudaGetLastError();
 }

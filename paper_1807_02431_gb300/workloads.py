@@ -239,6 +239,138 @@ def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas:
     return s
 
 
+def _kd_order(x, leaf=32):
+    """Order of points by recursive bisection along the longest extent, each cut at a multiple of
+    `leaf` points, so that every consecutive block of `leaf` points is spatially compact."""
+    idx = np.arange(len(x))
+
+    def rec(ids):
+        if len(ids) <= leaf:
+            return [ids]
+        ext = x[ids].max(axis=0) - x[ids].min(axis=0)
+        ax = int(np.argmax(ext))
+        srt = ids[np.argsort(x[ids, ax], kind="stable")]
+        cut = max(leaf, (len(ids) // (2 * leaf)) * leaf)
+        return rec(srt[:cut]) + rec(srt[cut:])
+
+    return np.concatenate(rec(idx))
+
+
+def ligand_receptor(n_receptor: int = 2000, n_ligand: int = 30, seed: int = 1807, dyn_seed: int = 2431,
+                    n_replicas: int = 1024, temperature: float = 300.0) -> System:
+    """Ligand bound in a surface pocket of a packed globule (Section 4.2 stand-in, FKBP-DMSO shaped).
+
+    Receptor: n_receptor beads at density 7.7 nm^-3 (a jittered cubic lattice of spacing 0.506 nm,
+    jitter U[-0.05, 0.05] nm per axis) filling a sphere (radius 3.96 nm for 2,000 beads) from which a
+    pocket of radius 0.9 nm centred 0.5 nm below the surface is carved; beads are held by an elastic
+    network: a harmonic spring k = 500 kJ/mol/nm^2 with r0 = the generated distance between every pair
+    closer than 0.9 nm (those pairs are excluded from the nonbonded terms).  Beads are numbered by
+    recursive bisection, so every block of 32 consecutive beads is spatially compact.
+    Ligand: an n_ligand-bead chain grown inside the pocket (bond 0.15 nm, k = 3e5; angle 110 deg,
+    k = 400; one dihedral term per torsion with n ~ U{1,2,3}, k ~ U[0, 8] kJ/mol, delta in {0, pi};
+    1-2 and 1-3 pairs excluded), numbered after the receptor.
+    Both: LJ sigma ~ U[0.25, 0.35] nm, eps ~ U[0.2, 0.8] kJ/mol (Lorentz-Berthelot); charges
+    N(0, 0.2) (receptor) and N(0, 0.3) (ligand) shifted to zero net; Coulomb with eps = 4r; plain
+    truncation of LJ and Coulomb at 1.2 nm; mass 12 amu; gamma = 1/ps; dt = 2 fs.
+    Groups: 0 = ligand, 1 = pocket (receptor beads within 1.5 nm of the pocket centre), 2 = first and
+    3 = last ligand bead.  States: d = |COM(ligand) - COM(pocket)|; state 0 = bound (d < 1.0 nm),
+    state 1 = its complement.  Observables (sampled every 50 steps): d, the ligand's RMS velocity and
+    the distances of the two ligand ends to the pocket.
+    """
+    rng = np.random.default_rng(seed)
+    rho, a = 7.7, 0.506
+    rg = (3.0 * n_receptor / (4.0 * math.pi * rho)) ** (1.0 / 3.0)
+    cp = np.array([0.0, 0.0, rg - 0.5])
+    rp = 0.9
+    m = int(math.ceil((rg + 1.5) / a))
+    g = np.arange(-m, m + 1)
+    ijk = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = ijk * a + rng.uniform(-0.05, 0.05, ijk.shape)
+    keep = np.linalg.norm(x - cp, axis=1) >= rp
+    ijk, x = ijk[keep], x[keep]
+    order = np.argsort(np.linalg.norm(x, axis=1), kind="stable")[:n_receptor]
+    ijk, x = ijk[order], x[order]
+    xr = x[_kd_order(x)]
+    nl = n_ligand
+    n = n_receptor + nl
+    sigma = rng.uniform(0.25, 0.35, n)
+    epsilon = rng.uniform(0.2, 0.8, n)
+    charge = np.concatenate([rng.normal(0.0, 0.2, n_receptor), rng.normal(0.0, 0.3, nl)])
+    charge -= charge.mean()
+    # elastic network
+    d = np.linalg.norm(xr[:, None] - xr[None], axis=-1)
+    iu, ju = np.nonzero(np.triu(d < 0.9, 1))
+    enm = np.stack([iu, ju], 1).astype(np.int32)
+    enm_r0 = d[iu, ju]
+    # ligand chain grown inside the pocket
+    bond, angle = 0.15, math.radians(110.0)
+    sl = sigma[n_receptor:]
+
+    def clash_free(p, i, xl):
+        dr = np.linalg.norm(xr - p, axis=1)
+        if np.any(dr < 0.8 * 0.5 * (sigma[:n_receptor] + sl[i])):
+            return False
+        if i >= 3 and np.any(np.linalg.norm(xl[: i - 2] - p, axis=1) < 0.8 * 0.5 * (sl[: i - 2] + sl[i])):
+            return False
+        return np.linalg.norm(p - cp) <= rp - 0.15
+
+    for _restart in range(1000):
+        xl = np.zeros((nl, 3))
+        xl[0] = cp
+        u = rng.standard_normal(3)
+        xl[1] = cp + bond * u / np.linalg.norm(u)
+        v = np.cross(u, rng.standard_normal(3))
+        v /= np.linalg.norm(v)
+        b01 = (xl[1] - xl[0]) / bond
+        xl[2] = xl[1] + bond * (-math.cos(angle) * b01 + math.sin(angle) * v)
+        ok = clash_free(xl[1], 1, xl) and clash_free(xl[2], 2, xl)
+        for i in range(3, nl):
+            if not ok:
+                break
+            for _attempt in range(200):
+                p = _place(xl[i - 3], xl[i - 2], xl[i - 1], bond, angle, rng.uniform(-math.pi, math.pi))
+                if clash_free(p, i, xl):
+                    xl[i] = p
+                    break
+            else:
+                ok = False
+        if ok:
+            break
+    else:
+        raise RuntimeError("ligand growth failed")
+    q0 = np.concatenate([xr, xl])
+    L = n_receptor + np.arange(nl)
+    lbonds = np.stack([L[:-1], L[1:]], 1).astype(np.int32)
+    langles = np.stack([L[:-2], L[1:-1], L[2:]], 1).astype(np.int32)
+    ldih = np.stack([L[:-3], L[1:-2], L[2:-1], L[3:]], 1).astype(np.int32)
+    nt = len(ldih)
+    dn = rng.integers(1, 4, nt).astype(np.int32)
+    dk = rng.uniform(0.0, 8.0, nt)
+    dd = math.pi * rng.integers(0, 2, nt)
+    lexcl = np.array([[L[i], L[j]] for i in range(nl) for j in range(i + 1, min(nl, i + 3))], np.int32)
+    pocket = np.nonzero(np.linalg.norm(xr - cp, axis=1) < rp + 0.6)[0].astype(np.int32)
+    kT = KB_KJ_PER_MOL_K * temperature
+    mass = np.full(n, 12.0)
+    s = System(
+        name=f"ligand_receptor{n}", n_atoms=n, dim=3, potential=POT_FORCE_FIELD, mass=mass,
+        kT=kT, gamma=1.0, dt=0.002, sigma=sigma, epsilon=epsilon, charge=charge,
+        excl=np.concatenate([enm, lexcl]), cutoff=1.2, coulomb_k=COULOMB_K,
+        bonds=np.concatenate([enm, lbonds]),
+        bond_k=np.concatenate([np.full(len(enm), 500.0), np.full(nl - 1, 3.0e5)]),
+        bond_r0=np.concatenate([enm_r0, np.full(nl - 1, bond)]),
+        angles=langles, angle_k=np.full(nl - 2, 400.0), angle_theta0=np.full(nl - 2, angle),
+        dihedrals=ldih, dihedral_n=dn, dihedral_k=dk, dihedral_delta=dd,
+        cv_kind=CV_COM_DISTANCE, cv_params=(1.0,),
+        groups=[L.astype(np.int32), pocket, L[:1].astype(np.int32), L[-1:].astype(np.int32)],
+        observables=[(OBS_GROUP_DISTANCE, (0, 1)), (OBS_RMS_VELOCITY, (0,)),
+                     (OBS_GROUP_DISTANCE, (2, 1)), (OBS_GROUP_DISTANCE, (3, 1))],
+        n_replicas=n_replicas, t_gr=50, t_check=500, tol=0.01, min_fv_steps=0,
+    )
+    s.q0 = q0
+    s.p0 = maxwell_boltzmann(mass, kT, 3, np.random.default_rng(dyn_seed))
+    return s
+
+
 def batched_sizes(n_runs: int = 64, seed: int = 1807, lo: int = 22, hi: int = 400) -> np.ndarray:
     """Chain sizes drawn uniformly in [lo, hi] for the batched workload."""
     return np.random.default_rng(seed).integers(lo, hi + 1, n_runs)
