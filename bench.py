@@ -35,11 +35,19 @@ SEED = 2431
 
 
 def algorithmic_flops_per_replica_step(s: W.System) -> float:
-    """FP32 flops per replica-step of the force kernel: 40 per non-excluded pair, 15 per bond,
-    40 per angle and 100 per three-term dihedral (33 per term), FMA counted as 2."""
+    """FP32 flops per replica-step of the force kernel: 40 per non-excluded pair (with a cutoff: per
+    non-excluded pair within the cutoff in the initial configuration), 15 per bond, 40 per angle and
+    100 per three-term dihedral (33 per term), FMA counted as 2."""
     n = s.n_atoms
-    excl = {tuple(sorted(x)) for x in s.excl.tolist()}
-    n_pairs = n * (n - 1) // 2 - len(excl)
+    if s.cutoff > 0:
+        d = np.linalg.norm(s.q0[:, None] - s.q0[None], axis=-1)
+        within = np.triu(d < s.cutoff, 1)
+        within[s.excl[:, 0], s.excl[:, 1]] = False
+        within[s.excl[:, 1], s.excl[:, 0]] = False
+        n_pairs = int(within.sum())
+    else:
+        excl = {tuple(sorted(x)) for x in s.excl.tolist()}
+        n_pairs = n * (n - 1) // 2 - len(excl)
     return 40.0 * n_pairs + 15.0 * len(s.bonds) + 40.0 * len(s.angles) + 33.3 * len(s.dihedral_k)
 
 
@@ -128,10 +136,10 @@ def cpu_oracle(n_replicas: int, steps: int, cores: int):
 class Step:
     """One convergence-step check of the method over the whole replica set (see module doc)."""
 
-    def __init__(self, B, s: W.System, precision: int, R: int, seed: int, device_index: int):
+    def __init__(self, B, s: W.System, precision: int, R: int, seed: int, device_index: int, omega: int = 1):
         import torch
 
-        self.B, self.s, self.R = B, s, R
+        self.B, self.s, self.R, self.omega = B, s, R, omega
         self.sysh = B.grp_create_system(s, precision)
         q0, p0 = W.replica_states(s, R, seed=seed, spread=0.002)
         self.q0, self.p0 = q0, p0
@@ -142,9 +150,9 @@ class Step:
 
     def __call__(self):
         s = self.s
-        # omega = 1: the chain starts in state 1 (outside the paper's rectangle); min_fv_steps = 0 so
-        # that every check also evaluates the Gelman-Rubin ratios
-        return self.B.grp_fv_check(self.rep, 1, s.t_check, s.t_gr, s.tol, 0, self.stream, self.status)
+        # omega: the state the system starts in (the chain: 1, outside the paper's rectangle; the
+        # ligand: 0, bound); min_fv_steps = 0 so that every check also evaluates the Gelman-Rubin ratios
+        return self.B.grp_fv_check(self.rep, self.omega, s.t_check, s.t_gr, s.tol, 0, self.stream, self.status)
 
     def reset(self):
         self.B.grp_set_state(self.rep, self.q0, self.p0, np.zeros((self.R, len(self.s.observables), 4)),
@@ -259,6 +267,32 @@ def batched_bench(B, steps, warmup, flush, n_runs=64, R=128):
             "fp32_frac_of_peak": flops * steps / t / 1e12 / fp32_peak_tflops(2070.0)}
 
 
+def ligand_bench(B, steps, warmup, flush, fp64_steps):
+    """Ligand bound in a surface pocket of a 2,000-bead globule (2,030 atoms, elastic network, LJ and
+    Coulomb truncated at 1.2 nm), 1,024 replicas, one exit test of the convergence step per step
+    (500 BAOAB steps sampling every 50, branching, Gelman-Rubin), mixed and FP64 paths."""
+    s = W.ligand_receptor()
+    R = s.n_replicas
+    step = Step(B, s, B.GRP_MIXED, R, SEED, 0, omega=0)
+    times = time_steps(step, steps, warmup, flush, step.stream)
+    t = float(np.sum(times)) / 1e3
+    units = R * s.n_atoms * s.t_check
+    seg_ms = segment_kernel_ms(B, step, 2)
+    flops = algorithmic_flops_per_replica_step(s) * R * s.t_check
+    peak = fp32_peak_tflops(2070.0)
+    out = {"workload": f"ligand_receptor{s.n_atoms}_r{R}", "value": units * steps / t, "unit": "replica-atom-steps/s",
+           "ms_per_step": t * 1e3 / steps,
+           "roofline": {"bound": "alu", "achieved": flops / (seg_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flops / (seg_ms * 1e-3) / 1e12 / peak, "kernel_ms": seg_ms,
+                        "flops_per_launch": flops}}
+    if fp64_steps > 0:
+        step64 = Step(B, s, B.GRP_FP64, R, SEED, 0, omega=0)
+        t64 = time_steps(step64, fp64_steps, 1, flush, step64.stream)
+        v64 = units * len(t64) / (float(np.sum(t64)) / 1e3)
+        out["fp64_path"] = {"value": v64, "ms_per_step": float(np.mean(t64)), "speedup_of_mixed": out["value"] / v64}
+    return out
+
+
 def run_reference(args):
     """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
     bounded sample: the 256 replicas advanced 20 steps with sampling and the exit test."""
@@ -299,6 +333,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--accel-steps", type=int, default=200000)
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--ligand-steps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -367,6 +402,8 @@ def main():
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
         e2e_value = units_per_step * args.steps / e2e_wall
         batched = batched_bench(B, args.batch_steps, 2, flush) if args.batch_steps > 0 else None
+        ligand = (ligand_bench(B, args.ligand_steps, 1, flush, min(args.fp64_steps, 1))
+                  if args.ligand_steps > 0 else None)
         accel = None
         if args.accel_steps > 0:
             # the chain (bounded run) and the double-well validation system, where the loop cycles
@@ -393,6 +430,7 @@ def main():
                "roofline": roof, "clocks": clocks,
                "fp64_path": fp64,
                "batched": batched,
+               "ligand_receptor": ligand,
                "accelerated": accel,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},

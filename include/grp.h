@@ -277,7 +277,8 @@ grp_status grp_get_params(const grp_system *s, double *d_theta, void *stream);
 /* Replace the parameters by d_theta (device [n_theta] FP64, copied); later calls on every replica
  * set of s (dynamics included) use them.  GRP_EINVAL, with nothing changed, unless every sigma_i > 0,
  * every epsilon_i >= 0 and every value is finite.  Synchronises `stream`.  Not to be called while a
- * kernel of a replica set of s runs on another stream. */
+ * kernel of a replica set of s runs on another stream.  Replica sets keep the forces stored with
+ * their state until grp_set_state (or grp_adjoint_segment) re-evaluates them. */
 grp_status grp_set_params(grp_system *s, const double *d_theta, void *stream);
 /* For B configurations d_q (device [B][n][dim] FP64) and weights d_w (device [B], NULL = all 1):
  *   d_energy     (optional, device [B])        V(q_b), unweighted;
@@ -288,6 +289,36 @@ grp_status grp_set_params(grp_system *s, const double *d_theta, void *stream);
  * fixed-point sums).  Synchronises `stream`. */
 grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const double *d_q, const double *d_w,
                            double *d_energy, double *d_grad_q, double *d_grad_theta, void *stream);
+
+/* Loss of a dynamics segment: L = 1/(R n_s) sum over replicas and over the n_s sampling steps of
+ * g(O(q_t)), with O the system's observable `obs` (GRP_OBS_COORD, GRP_OBS_GROUP_DISTANCE or
+ * GRP_OBS_DIHEDRAL, radians) and g the identity (GRP_LOSS_IDENTITY) or the logistic function
+ * g(x) = 1 / (1 + exp(-(x - center) / width)) (GRP_LOSS_LOGISTIC: a smoothed occupancy of x > center). */
+enum { GRP_LOSS_IDENTITY = 0, GRP_LOSS_LOGISTIC = 1 };
+typedef struct {
+  int32_t obs;
+  int32_t transform;
+  double center, width;
+} grp_loss;
+
+/* Adjoint (reverse-mode) differentiation through k BAOAB steps of Eq. 1 with the noise held fixed
+ * (the same Philox stream: common random numbers; not in the paper).  Re-evaluates the forces of the
+ * current state with the system's current parameters, then advances every replica k steps exactly as
+ * grp_step_k(r, k, 0, 0) does (observable accumulators untouched),
+ * sampling O after every step that brings t_phase to a multiple of t_gr (at least one sample is
+ * required), and returns
+ *   h_loss       (optional, host)              L of the segment;
+ *   d_grad_theta (optional, device [n_theta])   dL/d theta, theta as for grp_energy_grad;
+ *   d_grad_q0, d_grad_p0 (optional, device [R][n][dim]) dL/dq and dL/dp of the state before the segment.
+ * The reverse sweep recomputes states from checkpoints saved every `checkpoint` steps and applies the
+ * transposed BAOAB step, whose Hessian-vector products and mixed parameter derivatives come from a
+ * dual-number pass of the force field.  Needs a GRP_FP64 force-field system below 64 atoms (else
+ * GRP_ENOTIMPL) and (checkpoint + 1) n dim 8 bytes of shared memory for the recomputed states (at most
+ * about 180 KB; else GRP_EINVAL).  Allocates R ceil(k / checkpoint) 3 n dim 8 bytes of device memory
+ * for the checkpoints.  Synchronises `stream`. */
+grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_gr, int32_t checkpoint,
+                               const grp_loss *loss, double *h_loss, double *d_grad_theta, double *d_grad_q0,
+                               double *d_grad_p0, void *stream);
 
 /* Fleming-Viot branching, as grp_fv_branch, on replica arrays the caller owns, allocating nothing.
  * (No counterpart in the paper: this serves callers that cannot allocate device memory while they

@@ -95,6 +95,10 @@ def lib():
         L.orc_potential.argtypes = [C.c_void_p, _D]
         L.orc_forces.argtypes = [C.c_void_p, _D, _D]
         L.orc_param_grad.argtypes = [C.c_void_p, _D, _D]
+        L.orc_adjoint_segment.restype = C.c_double
+        L.orc_adjoint_segment.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _D, _D, _D, C.c_uint64, C.c_int64, C.c_int64,
+                                          C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                          _D, _D, _D]
         L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
         L.orc_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int32, C.c_int32, _D]
         L.orc_branch_word.restype = C.c_uint32
@@ -217,6 +221,19 @@ class Oracle:
         g = np.zeros(2 * s.n_atoms + nd)
         lib().orc_param_grad(self.ctx, _dp(q), _dp(g))
         return g
+
+    def adjoint_segment(self, q, p, f, seed, t0, tp0, k, t_gr, obs, transform=0, center=0.0, width=1.0,
+                        replica0=0):
+        """Advance (q, p, f) [R, n, dim] in place by k steps (row r draws the noise of replica replica0 + r);
+        returns (L, dL/dtheta, dL/dq0, dL/dp0)."""
+        s = self.system
+        nd = 0 if s.dihedrals is None else len(s.dihedrals)
+        gth = np.zeros(2 * s.n_atoms + nd)
+        gq = np.zeros_like(q)
+        gp = np.zeros_like(p)
+        loss = lib().orc_adjoint_segment(self.ctx, q.shape[0], replica0, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr, obs,
+                                         transform, center, width, _dp(gth), _dp(gq), _dp(gp))
+        return loss, gth, gq, gp
 
     def state_of(self, q):
         return lib().orc_state_of(self.ctx, _dp(_c64(q)))

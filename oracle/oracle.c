@@ -491,6 +491,153 @@ int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double
   return ns;
 }
 
+/* ---------------------------------------------------------------- adjoint of a segment
+ * Differentiation through the dynamics (not part of the paper).  Loss
+ * L = 1/(R n_s) sum_r sum_{sampled t} g(O_j(q_t^r)) over k BAOAB steps with the noise fixed.
+ * Forward: the steps of orc_baoab_step, keeping every configuration.  Backward, one step at a time
+ * from the last, on the adjoints (lq, lp) of the state after the step, h = dt/2:
+ *   final half kick  p_{t+1} = p'' + h F(q_{t+1}):  lq += h J_F(q_{t+1}) lp;  dL/dtheta += h lp . dF/dtheta;  lp'' = lp
+ *   second drift     q_{t+1} = q' + (h/m) p'':       lq' = lq;  lp'' += (h/m) lq
+ *   friction, noise  p'' = c1 p' + s xi:             lp' = c1 lp''
+ *   first drift      q' = q_t + (h/m) p':            lq_t = lq';  lp' += (h/m) lq'
+ *   first half kick  p' = p_t + h F(q_t):            lq_t += h J_F(q_t) lp';  dL/dtheta += h lp' . dF/dtheta;  lp_t = lp'
+ * and a loss sample at q_t adds 1/(R n_s) g'(O) dO/dq to lq_t.  J_F = -Hessian of V is symmetric, so
+ * J_F^T lp = J_F lp is a central difference of the forces along lp; lp . dF/dtheta =
+ * -d/d eps [dV/dtheta (q + eps lp)] is a central difference of orc_param_grad along lp; dO/dq is a
+ * central difference of orc_observable per coordinate.  Each difference is Richardson-extrapolated
+ * from the steps e and e/2, which leaves an error of order e^4. */
+static void fd_forces_dir(const orc_ctx *c, const double *q, const double *v, double *out, double *w1, double *w2) {
+  int nd = c->s.n_atoms * c->s.dim;
+  double vmax = 0;
+  for (int i = 0; i < nd; ++i) vmax = fmax(vmax, fabs(v[i]));
+  if (vmax == 0) { memset(out, 0, sizeof(double) * (size_t)nd); return; }
+  double e = 1e-4 / vmax;
+  double *qq = (double *)malloc(sizeof(double) * (size_t)nd), *d1 = (double *)malloc(sizeof(double) * (size_t)nd);
+  for (int pass = 0; pass < 2; ++pass) {
+    double ee = pass == 0 ? e : 0.5 * e;
+    for (int i = 0; i < nd; ++i) qq[i] = q[i] + ee * v[i];
+    orc_forces(c, qq, w1);
+    for (int i = 0; i < nd; ++i) qq[i] = q[i] - ee * v[i];
+    orc_forces(c, qq, w2);
+    for (int i = 0; i < nd; ++i) {
+      double d = (w1[i] - w2[i]) / (2.0 * ee);
+      if (pass == 0) d1[i] = d;
+      else out[i] = (4.0 * d - d1[i]) / 3.0;
+    }
+  }
+  free(qq);
+  free(d1);
+}
+
+static void fd_param_dir(const orc_ctx *c, const double *q, const double *v, double *out, int nt) {
+  int nd = c->s.n_atoms * c->s.dim;
+  double vmax = 0;
+  for (int i = 0; i < nd; ++i) vmax = fmax(vmax, fabs(v[i]));
+  if (vmax == 0) { memset(out, 0, sizeof(double) * (size_t)nt); return; }
+  double e = 1e-4 / vmax;
+  double *qq = (double *)malloc(sizeof(double) * (size_t)nd);
+  double *g1 = (double *)malloc(sizeof(double) * (size_t)nt), *g2 = (double *)malloc(sizeof(double) * (size_t)nt);
+  double *d1 = (double *)malloc(sizeof(double) * (size_t)nt);
+  for (int pass = 0; pass < 2; ++pass) {
+    double ee = pass == 0 ? e : 0.5 * e;
+    for (int i = 0; i < nd; ++i) qq[i] = q[i] + ee * v[i];
+    orc_param_grad(c, qq, g1);
+    for (int i = 0; i < nd; ++i) qq[i] = q[i] - ee * v[i];
+    orc_param_grad(c, qq, g2);
+    for (int t = 0; t < nt; ++t) {
+      double d = (g1[t] - g2[t]) / (2.0 * ee);
+      if (pass == 0) d1[t] = d;
+      else out[t] = (4.0 * d - d1[t]) / 3.0;
+    }
+  }
+  free(qq); free(g1); free(g2); free(d1);
+}
+
+static double loss_g(double x, int32_t transform, double center, double width, double *gp) {
+  if (transform == 1) {
+    double g = 1.0 / (1.0 + exp(-(x - center) / width));
+    *gp = g * (1.0 - g) / width;
+    return g;
+  }
+  *gp = 1.0;
+  return x;
+}
+
+double orc_adjoint_segment(const orc_ctx *c, int32_t n_rep, int32_t replica0, double *q, double *p, double *f,
+                           uint64_t seed, int64_t t0, int64_t tp0, int32_t k, int32_t t_gr, int32_t obs, int32_t transform,
+                           double center, double width, double *grad_theta, double *grad_q0, double *grad_p0) {
+  const orc_system *s = &c->s;
+  int n = s->n_atoms, dim = s->dim, nd = n * dim;
+  int nt = 2 * n + s->n_dihedrals;
+  double h = 0.5 * s->dt, c1 = exp(-s->gamma * s->dt);
+  int64_t n_s = (tp0 + k) / t_gr - tp0 / t_gr;
+  double norm = 1.0 / ((double)n_rep * (double)n_s);
+  double *Q = (double *)malloc(sizeof(double) * (size_t)(k + 1) * nd);
+  double *lq = (double *)malloc(sizeof(double) * (size_t)nd), *lp = (double *)malloc(sizeof(double) * (size_t)nd);
+  double *jv = (double *)malloc(sizeof(double) * (size_t)nd), *w1 = (double *)malloc(sizeof(double) * (size_t)nd);
+  double *w2 = (double *)malloc(sizeof(double) * (size_t)nd), *qq = (double *)malloc(sizeof(double) * (size_t)nd);
+  double *pg = (double *)malloc(sizeof(double) * (size_t)nt);
+  double loss = 0.0;
+  if (grad_theta) memset(grad_theta, 0, sizeof(double) * (size_t)nt);
+  for (int r = 0; r < n_rep; ++r) {
+    double *qr = q + (size_t)r * nd, *pr = p + (size_t)r * nd, *fr = f + (size_t)r * nd;
+    memcpy(Q, qr, sizeof(double) * (size_t)nd);
+    for (int t = 0; t < k; ++t) {
+      orc_baoab_step(c, qr, pr, fr, seed, replica0 + r, t0 + t);
+      memcpy(Q + (size_t)(t + 1) * nd, qr, sizeof(double) * (size_t)nd);
+    }
+    memset(lq, 0, sizeof(double) * (size_t)nd);
+    memset(lp, 0, sizeof(double) * (size_t)nd);
+    for (int t = k; t >= 1; --t) {
+      const double *qt = Q + (size_t)t * nd, *qs = Q + (size_t)(t - 1) * nd;
+      /* loss sample at q_t */
+      if ((tp0 + t) % t_gr == 0) {
+        double gp;
+        loss += norm * loss_g(orc_observable(c, obs, qt, NULL), transform, center, width, &gp);
+        memcpy(qq, qt, sizeof(double) * (size_t)nd);
+        for (int i = 0; i < nd; ++i) {
+          double e = 1e-5, d1 = 0, d2 = 0;
+          for (int pass = 0; pass < 2; ++pass) {
+            double ee = pass == 0 ? e : 0.5 * e;
+            qq[i] = qt[i] + ee;
+            double op = orc_observable(c, obs, qq, NULL);
+            qq[i] = qt[i] - ee;
+            double om = orc_observable(c, obs, qq, NULL);
+            qq[i] = qt[i];
+            if (pass == 0) d1 = (op - om) / (2.0 * ee);
+            else d2 = (op - om) / (2.0 * ee);
+          }
+          lq[i] += norm * gp * (4.0 * d2 - d1) / 3.0;
+        }
+      }
+      /* final half kick of step t-1, at q_t */
+      fd_forces_dir(c, qt, lp, jv, w1, w2);
+      for (int i = 0; i < nd; ++i) lq[i] += h * jv[i];
+      if (grad_theta) {
+        fd_param_dir(c, qt, lp, pg, nt);
+        for (int u = 0; u < nt; ++u) grad_theta[u] -= h * pg[u];
+      }
+      /* second drift, friction and noise, first drift */
+      for (int i = 0; i < nd; ++i) {
+        double hm = h / s->mass[i / dim];
+        double lpp = lp[i] + hm * lq[i];
+        lp[i] = c1 * lpp + hm * lq[i];
+      }
+      /* first half kick of step t-1, at q_{t-1} */
+      fd_forces_dir(c, qs, lp, jv, w1, w2);
+      for (int i = 0; i < nd; ++i) lq[i] += h * jv[i];
+      if (grad_theta) {
+        fd_param_dir(c, qs, lp, pg, nt);
+        for (int u = 0; u < nt; ++u) grad_theta[u] -= h * pg[u];
+      }
+    }
+    if (grad_q0) memcpy(grad_q0 + (size_t)r * nd, lq, sizeof(double) * (size_t)nd);
+    if (grad_p0) memcpy(grad_p0 + (size_t)r * nd, lp, sizeof(double) * (size_t)nd);
+  }
+  free(Q); free(lq); free(lp); free(jv); free(w1); free(w2); free(qq); free(pg);
+  return loss;
+}
+
 /* ---------------------------------------------------------------- parallel dynamics step, Eq. 5 */
 int32_t orc_parallel_phase(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
                            uint64_t seed, int64_t t0, int32_t omega, int32_t t_check,

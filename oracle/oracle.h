@@ -131,6 +131,18 @@ int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double
                    uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
                    double *samples, int32_t cap);
 
+/* Adjoint of k BAOAB steps with the noise fixed (differentiation through the dynamics, not part of
+ * the paper): advances (q, p, f) [n_rep][n][dim] like orc_step_k, row r drawing the noise of replica
+ * replica0 + r, and
+ * returns L = 1/(n_rep n_s) sum over replicas and over the n_s steps with (tp0 + t) % t_gr == 0 of
+ * g(O_obs(q_t)), g(x) = x (transform 0) or 1 / (1 + exp(-(x - center) / width)) (transform 1).
+ * grad_theta [2n + n_dihedrals] (theta as for orc_param_grad), grad_q0 and grad_p0 [n_rep][n][dim]
+ * (each optional) receive dL/dtheta and dL/d(q, p) of the initial state.  Hessian-vector products
+ * and mixed derivatives are central differences with Richardson extrapolation (error ~ e^4). */
+double orc_adjoint_segment(const orc_ctx *c, int32_t n_rep, int32_t replica0, double *q, double *p, double *f,
+                           uint64_t seed, int64_t t0, int64_t tp0, int32_t k, int32_t t_gr, int32_t obs, int32_t transform,
+                           double center, double width, double *grad_theta, double *grad_q0, double *grad_p0);
+
 /* Parallel dynamics step (Section 2.4.2): every replica advances t_check steps at a time until
  * one has exited omega.  M = number of checks, k = lowest 1-based index exited at check M,
  * tau_steps = [N (M-1) + k] t_check (Eq. 5).  Returns 1 on exit, 0 if max_checks passed. */

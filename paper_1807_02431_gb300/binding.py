@@ -79,6 +79,13 @@ class FvStatus(C.Structure):
                 ("t_phase", C.c_int64), ("rhat", C.c_double * GRP_MAX_OBS)]
 
 
+class Loss(C.Structure):
+    _fields_ = [("obs", C.c_int32), ("transform", C.c_int32), ("center", C.c_double), ("width", C.c_double)]
+
+
+GRP_LOSS_IDENTITY, GRP_LOSS_LOGISTIC = 0, 1
+
+
 class Event(C.Structure):
     _fields_ = [("kind", C.c_int32), ("omega", C.c_int32), ("label_to", C.c_int32), ("k", C.c_int32),
                 ("M", C.c_int64), ("steps", C.c_int64), ("t_sim", C.c_int64), ("n_branch", C.c_int64)]
@@ -110,6 +117,8 @@ SIGNATURES = {
     "grp_get_params": (C.c_int32, [_VP, _VP, _VP]),
     "grp_set_params": (C.c_int32, [_VP, _VP, _VP]),
     "grp_energy_grad": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "grp_adjoint_segment": (C.c_int32, [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Loss), _D, _VP, _VP, _VP,
+                                        _VP]),
     "grp_fv_branch_noalloc": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_uint64, C.c_int64, _I32P,
                                           _VP]),
     "grp_batch_create": (C.c_int32, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
@@ -361,6 +370,17 @@ def grp_energy_grad(sysh: SystemHandle, n_conf: int, d_q, d_w=None, d_energy=Non
                     d_grad_theta=None, stream=None):
     _check(_lib.grp_energy_grad(sysh.handle, n_conf, _ptr(d_q), _ptr(d_w), _ptr(d_energy), _ptr(d_grad_q),
                                 _ptr(d_grad_theta), _stream(stream)))
+
+
+def grp_adjoint_segment(r: ReplicasHandle, k: int, t_gr: int, checkpoint: int, obs: int, transform: int = 0,
+                        center: float = 0.0, width: float = 1.0, d_grad_theta=None, d_grad_q0=None, d_grad_p0=None,
+                        stream=None) -> float:
+    """Advance k steps and differentiate the segment loss (see include/grp.h); returns the loss."""
+    loss = Loss(obs, transform, center, width)
+    out = C.c_double(0.0)
+    _check(_lib.grp_adjoint_segment(r.handle, k, t_gr, checkpoint, C.byref(loss), C.byref(out), _ptr(d_grad_theta),
+                                    _ptr(d_grad_q0), _ptr(d_grad_p0), _stream(stream)))
+    return out.value
 
 
 class BatchHandle:

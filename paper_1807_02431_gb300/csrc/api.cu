@@ -1054,3 +1054,105 @@ extern "C" grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const doubl
   if (h) return fail(GRP_EOVERFLOW, "grp_energy_grad: a term outside the fixed-point range or not finite");
   return GRP_OK;
 }
+
+extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_gr, int32_t checkpoint,
+                                          const grp_loss *loss, double *h_loss, double *d_grad_theta,
+                                          double *d_grad_q0, double *d_grad_p0, void *stream) {
+  if (!r || !loss || k < 1 || t_gr < 1 || checkpoint < 1 || k > (1 << 30))
+    return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
+  const grp_system *s = r->sys;
+  const SysDev &D = s->dev;
+  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled)
+    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms");
+  if (loss->obs < 0 || loss->obs >= D.n_obs) return fail(GRP_EINVAL, "grp_adjoint_segment: bad observable index");
+  const int kind = D.obs_kind[loss->obs];
+  if (kind != GRP_OBS_COORD && kind != GRP_OBS_GROUP_DISTANCE && kind != GRP_OBS_DIHEDRAL)
+    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: the loss observable must be a coordinate, a group distance or a dihedral");
+  if (loss->transform != GRP_LOSS_IDENTITY && loss->transform != GRP_LOSS_LOGISTIC)
+    return fail(GRP_EINVAL, "grp_adjoint_segment: unknown transform");
+  if (loss->transform == GRP_LOSS_LOGISTIC && !(loss->width > 0))
+    return fail(GRP_EINVAL, "grp_adjoint_segment: logistic width must be > 0");
+  const long long n_s = (r->t_phase + k) / t_gr - r->t_phase / t_gr;
+  if (n_s < 1) return fail(GRP_EINVAL, "grp_adjoint_segment: no sampling step in the segment");
+  const int ck = std::min(checkpoint, k);
+  if (adjoint_smem_bytes(D, s->n_terms, ck) > 180 * 1024)
+    return fail(GRP_EINVAL, "grp_adjoint_segment: checkpoint interval %d needs too much shared memory", ck);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int R = r->R, nd = D.nd, nt = 2 * D.n + s->n_terms;
+  const int n_ck = (k + ck - 1) / ck;
+  AdjArgs a{};
+  a.S = D;
+  a.n_ck = n_ck;
+  a.ck = ck;
+  a.k = k;
+  a.seed = r->seed;
+  a.t_global0 = r->t_global;
+  a.t_phase0 = r->t_phase;
+  a.t_gr = t_gr;
+  a.obs_kind = kind;
+  for (int t = 0; t < 4; ++t) a.obs_arg[t] = D.obs_arg[loss->obs][t];
+  a.transform = loss->transform;
+  a.center = loss->center;
+  a.width = loss->width;
+  a.inv_norm = 1.0 / ((double)R * (double)n_s);
+  a.h = 0.5 * D.dt;
+  a.c1 = std::exp(-D.gamma * D.dt);
+  a.n_terms = s->n_terms;
+  a.grad_q0 = d_grad_q0;
+  a.grad_p0 = d_grad_p0;
+  double *ckpt = nullptr, *partial = nullptr, *lossr = nullptr, *lsum = nullptr;
+  int *err = nullptr;
+  auto release = [&]() {
+    if (ckpt) cudaFreeAsync(ckpt, st);
+    if (partial) cudaFreeAsync(partial, st);
+    if (lossr) cudaFreeAsync(lossr, st);
+    if (lsum) cudaFreeAsync(lsum, st);
+    if (err) cudaFreeAsync(err, st);
+  };
+#define CUA(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      release();                                                                                    \
+      return fail(GRP_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));                       \
+    }                                                                                               \
+  } while (0)
+  CUA(cudaMallocAsync((void **)&ckpt, (size_t)R * n_ck * 3 * nd * 8, st));
+  CUA(cudaMallocAsync((void **)&partial, (size_t)R * nt * 8, st));
+  CUA(cudaMallocAsync((void **)&lossr, (size_t)R * 8, st));
+  CUA(cudaMallocAsync((void **)&lsum, 8, st));
+  CUA(cudaMallocAsync((void **)&err, 4, st));
+  CUA(cudaMemsetAsync(err, 0, 4, st));
+  // forces of the current parameters at the starting configurations
+  {
+    const grp_status e = compute_forces(r, st);
+    if (e != GRP_OK) { release(); return e; }
+  }
+  // forward pass: save (q, p, f) of every replica before each block of ck steps, then advance it
+  const size_t pitch = (size_t)n_ck * 3 * nd * 8;
+  for (int c = 0; c < n_ck; ++c) {
+    const double *src[3] = {r->q, r->p, r->f};
+    for (int x = 0; x < 3; ++x)
+      CUA(cudaMemcpy2DAsync(ckpt + ((size_t)c * 3 + x) * nd, pitch, src[x], (size_t)nd * 8, (size_t)nd * 8, R,
+                            cudaMemcpyDeviceToDevice, st));
+    const grp_status e = run_steps(r, std::min(ck, k - c * ck), 0, 0, 0, 0, 0, 0, st);
+    if (e != GRP_OK) { release(); return e; }
+  }
+  a.ckpt = ckpt;
+  a.partial = partial;
+  a.loss = lossr;
+  a.err = err;
+  CUA(launch_adjoint(a, R, st));
+  if (d_grad_theta) CUA(launch_column_sum(partial, R, nt, d_grad_theta, st));
+  CUA(launch_column_sum(lossr, R, 1, lsum, st));
+  double hl = 0.0;
+  int he = 0;
+  CUA(cudaMemcpyAsync(&hl, lsum, 8, cudaMemcpyDeviceToHost, st));
+  CUA(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st));
+  CUA(cudaStreamSynchronize(st));
+  release();
+#undef CUA
+  if (he) return fail(GRP_EOVERFLOW, "grp_adjoint_segment: a term outside the fixed-point range or not finite");
+  if (h_loss) *h_loss = hl;
+  return latch_errors(r, st);
+}

@@ -106,6 +106,29 @@ cudaError_t launch_param_grad(const SysDev &S, int n_terms, int n_conf, const do
                               double *grad_q, double *partial, int *err, cudaStream_t st);
 // x[b][i] *= alpha w_b (w = NULL: 1).
 cudaError_t launch_scale_rows(double *x, int rows, int cols, const double *w, double alpha, cudaStream_t st);
+// Adjoint of a k-step FP64 BAOAB segment (one block per replica), for the loss
+// L = 1/(R n_s) sum_r sum_samples g(O(q_t)) with the noise fixed: dL/d theta per replica, the loss
+// per replica and optionally dL/dq_0, dL/dp_0.
+struct AdjArgs {
+  SysDev S;
+  const double *ckpt;          // [R][n_ck][3][nd]: q, p, f at steps 0, ck, 2 ck, ...
+  int n_ck, ck, k;
+  uint64_t seed;
+  long long t_global0, t_phase0;
+  int t_gr;
+  int obs_kind, obs_arg[4];    // observable O
+  int transform;               // 0: g(x) = x; 1: g(x) = 1 / (1 + exp(-(x - center) / width))
+  double center, width;
+  double inv_norm;             // 1 / (R n_s)
+  double h, c1;
+  int n_terms;
+  double *partial;             // [R][n_theta]
+  double *loss;                // [R]
+  double *grad_q0, *grad_p0;   // [R][nd] or null
+  int *err;
+};
+size_t adjoint_smem_bytes(const SysDev &S, int n_terms, int ck);
+cudaError_t launch_adjoint(const AdjArgs &a, int n_rep, cudaStream_t st);
 // out[t] = sum_b partial[b][t] in order of b.
 cudaError_t launch_column_sum(const double *partial, int rows, int cols, double *out, cudaStream_t st);
 

@@ -6,6 +6,7 @@
 
 #include "forcefield.cuh"
 #include "kernels.h"
+#include "state.cuh"
 
 namespace grp {
 
@@ -81,209 +82,6 @@ __device__ __forceinline__ void record_check(const SegArgs &a, int r, int label,
   if (ex && a.exit_key)
     atomicMin(a.exit_key, ((unsigned long long)a.M << 32) | (unsigned long long)(unsigned)r);
 }
-
-__device__ __forceinline__ unsigned char *align32(unsigned char *p) {
-  return (unsigned char *)(((uintptr_t)p + 31) & ~(uintptr_t)31);
-}
-
-__device__ __forceinline__ void normals4(const Philox4 &w, double xi[4]) { normals4_f64(w, xi); }
-__device__ __forceinline__ void normals4(const Philox4 &w, float xi[4]) { normals4_f32(w, xi); }
-
-// Normals for `steps` consecutive steps of one replica, [step][atom][3], spread over every thread of
-// the block: the noise does not depend on the state, so it is generated off the per-step chain.
-template <class T>
-__device__ __forceinline__ void gen_noise(T *xi, int steps, long long t0, uint64_t seed, int r, int n) {
-  const int items = steps * n;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int j = it / n, at = it - j * n;
-    T z[4];
-    normals4(philox_stream(seed, t0 + j, 0u, r, at), z);
-    T *o = xi + (size_t)it * 3;
-    o[0] = z[0]; o[1] = z[1]; o[2] = z[2];
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// Shared-memory replica state of each precision path.
-template <class P>
-struct State;
-
-template <>
-struct State<PathF64> {
-  double *q, *p, *f, *sd;  // [3n], [3n], [3n], [n]
-  const double4 *atom;     // [n] parameters: a shared-memory copy, or the global table when lean
-  bool own_atom;
-  static size_t bytes(int n, bool lean) { return (size_t)n * (72 + 8 + (lean ? 0 : 32)); }
-  __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
-    own_atom = !lean;
-    if (lean) atom = S.atom_d;
-    else { atom = (const double4 *)ptr; ptr += (size_t)n * 32; }
-    q = (double *)ptr; ptr += (size_t)n * 24;
-    p = (double *)ptr; ptr += (size_t)n * 24;
-    f = (double *)ptr; ptr += (size_t)n * 24;
-    sd = (double *)ptr; ptr += (size_t)n * 8;
-  }
-  static __device__ AccF64 acc(long long *F, int n) { return AccF64{F}; }
-  __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
-    for (int at = threadIdx.x; at < n; at += blockDim.x) {
-      if (own_atom) const_cast<double4 *>(atom)[at] = S.atom_d[at];
-      sd[at] = sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
-    }
-  }
-  __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-      gq[i] = q[i]; gp[i] = p[i]; gf[i] = f[i];
-      if (!isfinite(q[i]) || !isfinite(p[i])) *err |= kErrNaN;
-    }
-  }
-  __device__ Pos<PathF64> pos() const { return Pos<PathF64>{q}; }
-  __device__ Params<PathF64> params(const SysDev &S) const {
-    return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d};
-  }
-  // B, A, O, A of BAOAB for atom `at` with the normals xi[0..2].
-  __device__ __forceinline__ void baoa(int at, const double *xi, double h, double c1) {
-    const double im = atom[at].w, s = sd[at];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      double pp = p[i] + h * f[i];
-      double qq = q[i] + h * pp * im;
-      pp = c1 * pp + s * xi[x];
-      qq = qq + h * pp * im;
-      p[i] = pp;
-      q[i] = qq;
-    }
-  }
-  // final B with the new forces (fixed point -> FP64); returns the kinetic energy of the atom.
-  __device__ __forceinline__ double bk(int at, const AccF64 &acc, double h) {
-    const double im = atom[at].w;
-    double ke = 0;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      const double fv = (double)acc.F[i] * kFixInv;
-      acc.F[i] = 0;
-      f[i] = fv;
-      const double pp = p[i] + h * fv;
-      p[i] = pp;
-      ke += 0.5 * pp * pp * im;
-    }
-    return ke;
-  }
-  __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
-  __device__ void get_f32(int at, float x[3]) const {
-    x[0] = (float)q[3 * at]; x[1] = (float)q[3 * at + 1]; x[2] = (float)q[3 * at + 2];
-  }
-  __device__ double mom(int i) const { return p[i]; }
-};
-
-template <>
-struct State<PathMixed> {
-  float4 *qh, *ql;   // [n] double-single positions
-  float *ph, *pl;    // [3n] double-single momenta
-  float *f, *sd;     // [3n], [n]
-  const float4 *atom;  // [n] parameters: a shared-memory copy, or the global table when lean
-  bool own_atom;
-  static size_t bytes(int n, bool lean) { return (size_t)n * (32 + 24 + 12 + 4 + (lean ? 0 : 16)); }
-  __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
-    own_atom = !lean;
-    qh = (float4 *)ptr; ptr += (size_t)n * 16;
-    ql = (float4 *)ptr; ptr += (size_t)n * 16;
-    if (lean) atom = S.atom_f;
-    else { atom = (const float4 *)ptr; ptr += (size_t)n * 16; }
-    ph = (float *)ptr; ptr += (size_t)n * 12;
-    pl = (float *)ptr; ptr += (size_t)n * 12;
-    f = (float *)ptr; ptr += (size_t)n * 12;
-    sd = (float *)ptr; ptr += (size_t)n * 4;
-  }
-  // the 8 bytes per force component hold the hi words [3n] then the lo words [3n]
-  static __device__ AccMixed acc(long long *F, int n) {
-    return AccMixed{(int *)F, (unsigned int *)F + 3 * n};
-  }
-  __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
-    for (int at = threadIdx.x; at < n; at += blockDim.x) {
-      const ds x = ds_from_double(gq[3 * at]), y = ds_from_double(gq[3 * at + 1]),
-               z = ds_from_double(gq[3 * at + 2]);
-      qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
-      ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
-      if (own_atom) const_cast<float4 *>(atom)[at] = S.atom_f[at];
-      sd[at] = (float)sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
-    }
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-      const ds v = ds_from_double(gp[i]);
-      ph[i] = v.hi;
-      pl[i] = v.lo;
-      f[i] = (float)gf[i];
-    }
-  }
-  __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
-    for (int at = threadIdx.x; at < n; at += blockDim.x) {
-      const float4 a = qh[at], b = ql[at];
-      gq[3 * at] = (double)a.x + (double)b.x;
-      gq[3 * at + 1] = (double)a.y + (double)b.y;
-      gq[3 * at + 2] = (double)a.z + (double)b.z;
-      if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z)) *err |= kErrNaN;
-    }
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-      gp[i] = (double)ph[i] + (double)pl[i];
-      gf[i] = (double)f[i];
-      if (!isfinite(ph[i])) *err |= kErrNaN;
-    }
-  }
-  __device__ Pos<PathMixed> pos() const { return Pos<PathMixed>{qh, ql}; }
-  __device__ Params<PathMixed> params(const SysDev &S) const {
-    return Params<PathMixed>{atom, S.bond_f, S.angle_f, S.term_f};
-  }
-  __device__ __forceinline__ void baoa(int at, const float *xi, float h, float c1) {
-    const float im = atom[at].w, s = sd[at], hm = h * im;
-    float4 a = qh[at], b = ql[at];
-    float *qa = &a.x, *qb = &b.x;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      ds P = {ph[i], pl[i]};
-      ds Q = {qa[x], qb[x]};
-      P = ds_add(P, h * f[i]);
-      Q = ds_add(Q, hm * P.hi);
-      P = ds_add(ds_scale(P, c1), s * xi[x]);
-      Q = ds_add(Q, hm * P.hi);
-      ph[i] = P.hi;
-      pl[i] = P.lo;
-      qa[x] = Q.hi;
-      qb[x] = Q.lo;
-    }
-    qh[at] = a;
-    ql[at] = b;
-  }
-  __device__ __forceinline__ float bk(int at, const AccMixed &acc, float h) {
-    const float im = atom[at].w;
-    float ke = 0.f;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      const float fv = split_to_float(acc.hi[i], acc.lo[i]);
-      acc.hi[i] = 0;
-      acc.lo[i] = 0u;
-      f[i] = fv;
-      ds P = {ph[i], pl[i]};
-      P = ds_add(P, h * fv);
-      ph[i] = P.hi;
-      pl[i] = P.lo;
-      ke += 0.5f * P.hi * P.hi * im;
-    }
-    return ke;
-  }
-  __device__ void get_f64(int at, double x[3]) const {
-    const float4 a = qh[at], b = ql[at];
-    x[0] = (double)a.x + (double)b.x; x[1] = (double)a.y + (double)b.y; x[2] = (double)a.z + (double)b.z;
-  }
-  __device__ void get_f32(int at, float x[3]) const {
-    const float4 a = qh[at];
-    x[0] = a.x; x[1] = a.y; x[2] = a.z;
-  }
-  __device__ float mom(int i) const { return ph[i]; }
-};
 
 // Observable j (Section 2.4.1) in the path's precision, from shared-memory state.
 template <class P>

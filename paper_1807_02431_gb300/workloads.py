@@ -371,6 +371,16 @@ def ligand_receptor(n_receptor: int = 2000, n_ligand: int = 30, seed: int = 1807
     return s
 
 
+def chain_gradient(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas: int = 256) -> System:
+    """The chain of ``chain`` for differentiation through the dynamics: groups 0 = first bead and
+    1 = last bead, and one more observable, their distance (the end-to-end distance, observable 4)."""
+    s = chain(n_atoms, seed=seed, dyn_seed=dyn_seed, n_replicas=n_replicas)
+    s.name = f"chain{n_atoms}_gradient"
+    s.groups = [np.array([0], np.int32), np.array([n_atoms - 1], np.int32)]
+    s.observables = s.observables + [(OBS_GROUP_DISTANCE, (0, 1))]
+    return s
+
+
 def batched_sizes(n_runs: int = 64, seed: int = 1807, lo: int = 22, hi: int = 400) -> np.ndarray:
     """Chain sizes drawn uniformly in [lo, hi] for the batched workload."""
     return np.random.default_rng(seed).integers(lo, hi + 1, n_runs)
