@@ -1135,7 +1135,7 @@ extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_
     for (int x = 0; x < 3; ++x)
       CUA(cudaMemcpy2DAsync(ckpt + ((size_t)c * 3 + x) * nd, pitch, src[x], (size_t)nd * 8, (size_t)nd * 8, R,
                             cudaMemcpyDeviceToDevice, st));
-    const grp_status e = run_steps(r, std::min(ck, k - c * ck), 0, 0, 0, 0, 0, 0, st);
+    const grp_status e = run_steps(r, std::min(ck, k - c * ck), 0, R, 0, 0, 0, 0, st);
     if (e != GRP_OK) { release(); return e; }
   }
   a.ckpt = ckpt;

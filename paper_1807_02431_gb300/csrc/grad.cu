@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
     st.load(S, base, base + nd, base + 2 * nd, n, c1);
     __syncthreads();
     for (int i = threadIdx.x; i < nd; i += blockDim.x) Qs[i] = st.q[i];
+    __syncthreads();  // the copy reads positions that the first drift below overwrites
     // forward recomputation of steps t0 .. t0 + len - 1, keeping every configuration
     for (int j = 0; j < len; ++j) {
       for (int at = threadIdx.x; at < n; at += blockDim.x) {
