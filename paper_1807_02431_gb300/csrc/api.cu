@@ -57,6 +57,7 @@ struct grp_system {
   // force-field parameters theta = (sigma_i, eps_i, k of each dihedral term in description order)
   int n_terms = 0;
   double *theta = nullptr;  // device [2n + n_terms], owned
+  std::vector<uint8_t> excl;  // host [n][n] exclusion matrix of systems with Verlet lists
 };
 
 struct grp_replicas {
@@ -71,6 +72,9 @@ struct grp_replicas {
   int *err = nullptr;
   int *n_branched = nullptr;
   double *rhat = nullptr;
+  uint32_t *nbl = nullptr;  // [R][nbl_cap] Verlet lists
+  float4 *qref = nullptr;   // [R][n]
+  int nbl_cap = 0;
   long long t_global = 0, t_phase = 0;
   // pinned host mirror of the small per-check readback
   struct Readback {
@@ -202,8 +206,16 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     }
     D.cutoff2 = d->cutoff > 0 ? d->cutoff * d->cutoff : 0.0;
     // Small systems: an explicit list of non-excluded pairs, one thread per pair.  From 64 atoms on:
-    // tiles of 32 atoms, every tile pair I <= J with per-lane interaction masks.
+    // tiles of 32 atoms, every tile pair I <= J with per-lane interaction masks; with a cutoff, the
+    // segment kernel keeps a Verlet list per replica (skin = cutoff / 6) built from the tiles.
     D.tiled = n >= 64 ? 1 : 0;
+    if (D.tiled && d->cutoff > 0) {
+      const double skin = d->cutoff / 6.0;
+      D.use_list = 1;
+      D.list_cut2 = (float)((d->cutoff + skin) * (d->cutoff + skin));
+      D.half_skin2 = (float)(0.25 * skin * skin);
+      s->excl = excl;
+    }
     std::vector<uint32_t> pairs;
     if (!D.tiled) {
       pairs.reserve((size_t)n * (n - 1) / 2);
@@ -354,6 +366,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
   if (e) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
+    if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
     return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
@@ -398,6 +411,26 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   AL(r->err, 4);
   AL(r->n_branched, 4);
   AL(r->rhat, GRP_MAX_OBS * 8);
+  if (D.use_list) {
+    // capacity: twice the non-excluded pairs within cutoff + skin in the first configuration
+    const int n = D.n;
+    const double lc2 = (double)D.list_cut2;
+    size_t cnt = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        if (s->excl[(size_t)i * n + j]) continue;
+        double d2 = 0;
+        for (int x = 0; x < 3; ++x) {
+          const double dx = h_q0[3 * i + x] - h_q0[3 * j + x];
+          d2 += dx * dx;
+        }
+        cnt += d2 < lc2;
+      }
+    const size_t all = (size_t)n * (n - 1) / 2;
+    r->nbl_cap = (int)std::min(all, 2 * cnt + 1024);
+    AL(r->nbl, R * (size_t)r->nbl_cap * 4);
+    AL(r->qref, R * (size_t)n * 16);
+  }
 #undef AL
   if (cudaMallocHost((void **)&r->hb, sizeof(*r->hb)) != cudaSuccess) {
     grp_destroy_replicas(r);
@@ -429,6 +462,7 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
   cudaFree(r->q); cudaFree(r->p); cudaFree(r->f); cudaFree(r->acc);
   cudaFree(r->labels); cudaFree(r->exited); cudaFree(r->src); cudaFree(r->exit_key);
   cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat);
+  cudaFree(r->nbl); cudaFree(r->qref);
   if (r->hb) cudaFreeHost(r->hb);
   delete r;
 }
@@ -439,6 +473,9 @@ static SegArgs seg_args(grp_replicas *r, int k, int t_gr, int n_active) {
   a.S = r->sys->dev;
   a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc;
   a.labels = r->labels; a.exited = r->exited; a.exit_key = r->exit_key; a.err = r->err;
+  a.nbl = r->nbl;
+  a.qref = r->qref;
+  a.nbl_cap = r->nbl_cap;
   a.seed = r->seed;
   a.t_global0 = r->t_global;
   a.t_phase0 = r->t_phase;

@@ -12,7 +12,7 @@ constexpr int kMaxObs = GRP_MAX_OBS;
 constexpr int kMaxGroups = GRP_MAX_GROUPS;
 
 // Error bits latched by kernels into the replica set's error word.
-enum : int { kErrNaN = 1, kErrOverflow = 2 };
+enum : int { kErrNaN = 1, kErrOverflow = 2, kErrList = 4 };
 
 // Kinds of force-field work items.
 enum : uint32_t { kItemPair = 0, kItemBond = 1, kItemAngle = 2, kItemDihedral = 3, kItemNone = 15 };
@@ -46,6 +46,11 @@ struct SysDev {
   const uint32_t *tile_pairs;  // I | J << 16
   const uint32_t *tile_masks;  // [n_tile_pairs][32]
   double cutoff2;          // 0: no cutoff
+  // Verlet lists (tiled systems with a cutoff): pairs closer than cutoff + skin, rebuilt when an atom
+  // has moved more than skin/2 since the last build
+  int use_list;
+  float list_cut2;         // (cutoff + skin)^2
+  float half_skin2;        // (skin / 2)^2
   int n_bonds;
   const int2 *bond_ij;
   const double2 *bond_d;   // (k, r0)

@@ -344,6 +344,20 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   if (want_e) e_fix += acc.efix(e, err);
 }
 
+// Nonbonded pairs of a Verlet list (i | j << 16), strided over the block's threads; pairs beyond the
+// cutoff contribute nothing.
+template <class P>
+__device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
+                                          const uint32_t *list, int count, const typename P::Acc &acc,
+                                          bool want_e, long long &e_fix, int *err) {
+  using T = typename P::T;
+  const T cut2 = (T)S.cutoff2;
+  for (int t = threadIdx.x; t < count; t += blockDim.x) {
+    const uint32_t pk = list[t];
+    pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
+  }
+}
+
 // One pass over every force-field item of a replica, strided over the block's threads.  The item
 // table groups pairs, bonds, angles and dihedrals, each group padded to a multiple of 32 entries, so
 // that every warp runs a single kind of item (no serialised divergent paths) and the dihedrals, the

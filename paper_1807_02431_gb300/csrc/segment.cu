@@ -170,6 +170,66 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
   }
 }
 
+// Verlet list of one replica (systems with a cutoff): every non-excluded pair closer than cutoff +
+// skin, found by the tiled scan over tile pairs whose bounding boxes are that close (the same lane
+// rotation as tile_pass, so each unordered pair is met once), appended with one shared atomic per warp
+// and step; the positions at the build are kept for the displacement test.  Returns the pair count
+// (a list longer than `cap` sets kErrList and is cut).  Called by every thread of the block.
+template <class P>
+__device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uint32_t *list, int cap,
+                          float4 *qref, int *cnt, int *err) {
+  tile_boxes<P>(S, st, boxes);
+  for (int at = threadIdx.x; at < S.n; at += blockDim.x) {
+    float x[3];
+    st.get_f32(at, x);
+    qref[at] = make_float4(x[0], x[1], x[2], 0.f);
+  }
+  if (threadIdx.x == 0) *cnt = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float lc2 = S.list_cut2;
+  for (int tp = warp; tp < S.n_tile_pairs; tp += nwarps) {
+    const uint32_t e = S.tile_pairs[tp];
+    const int I = (int)(e & 0xFFFFu), J = (int)(e >> 16);
+    const float *ba = boxes + 6 * I, *bb = boxes + 6 * J;
+    const float gx = fmaxf(0.f, fmaxf(ba[0] - bb[3], bb[0] - ba[3]));
+    const float gy = fmaxf(0.f, fmaxf(ba[1] - bb[4], bb[1] - ba[4]));
+    const float gz = fmaxf(0.f, fmaxf(ba[2] - bb[5], bb[2] - ba[5]));
+    if (gx * gx + gy * gy + gz * gz >= lc2) continue;
+    const uint32_t mask = S.tile_masks[(size_t)tp * 32 + lane];
+    const int i = I * 32 + lane;
+    const bool diag = I == J;
+    const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
+    float xi[3] = {0.f, 0.f, 0.f};
+    if (i < S.n) st.get_f32(i, xi);
+    for (int s = s0; s < s1; ++s) {
+      const int m = (lane + s) & 31;
+      bool take = false;
+      if (((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16)) {
+        float xj[3];
+        st.get_f32(J * 32 + m, xj);
+        const float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+        take = dx * dx + dy * dy + dz * dz < lc2;
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, take);
+      if (b) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(cnt, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int idx = base + __popc(b & ((1u << lane) - 1u));
+        if (take && idx < cap) list[idx] = (uint32_t)i | ((uint32_t)(J * 32 + m) << 16);
+      }
+    }
+  }
+  __syncthreads();
+  int c = *cnt;
+  if (c > cap) {
+    *err |= kErrList;
+    c = cap;
+  }
+  return c;
+}
+
 // Fixed-point sum (2^-40 units on the FP64 path, 2^-32 on the mixed path) to the path's precision,
 // the mixed path with 32-bit conversions only.
 __device__ __forceinline__ double fix_value(long long x, double) { return (double)x * kFixInv; }
@@ -233,6 +293,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   long long *red = (long long *)ptr; ptr += 32 * 8;
   double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
   long long *ek = (long long *)ptr; ptr += 2 * 8;
+  int *lcount = (int *)ptr; ptr += 8;
   State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n, S, a.lean != 0);
@@ -257,8 +318,13 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   __syncthreads();
   ObsAcc<P> oacc;
   if (threadIdx.x < no) oacc.begin(acc + 4 * threadIdx.x);
+  const bool use_list = a.nbl != nullptr;
+  uint32_t *list = use_list ? a.nbl + (size_t)r * a.nbl_cap : nullptr;
+  float4 *qref = use_list ? a.qref + (size_t)r * n : nullptr;
+  int n_list = 0;
 
   int err = 0;
+  if (use_list) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
   const T h = (T)a.h, c1 = (T)a.c1;
   const Pos<P> pos = st.pos();
   const Params<P> par = st.params(S);
@@ -281,8 +347,18 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
         st.baoa(at, z, h, c1);
       }
     }
-    __syncthreads();
-    if (boxes) {
+    // Verlet list: rebuilt when some atom has moved more than skin/2 since the last build
+    int moved = 0;
+    if (use_list)
+      for (int at = threadIdx.x; at < n; at += kThreads) {
+        float x[3];
+        st.get_f32(at, x);
+        const float4 o = qref[at];
+        const float dx = x[0] - o.x, dy = x[1] - o.y, dz = x[2] - o.z;
+        moved |= dx * dx + dy * dy + dz * dz > S.half_skin2;
+      }
+    if (__syncthreads_or(moved)) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
+    if (boxes && !use_list) {
       tile_boxes<P>(S, st, boxes);
       __syncthreads();
     }
@@ -290,7 +366,8 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if (sample) until = a.t_gr;
     long long e_fix = 0;
     force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
-    if (S.tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
+    if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
+    else if (S.tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
     for (int at = threadIdx.x; at < n; at += kThreads) {
@@ -406,7 +483,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch, int lean) {
   const int n = S.n;
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
-  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
+  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 8 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n, lean) : State<PathMixed>::bytes(n, lean);
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;

@@ -3,9 +3,9 @@
 The library's reverse sweep takes its Hessian-vector products from dual numbers (exact up to
 rounding); the oracle's from Richardson-extrapolated central differences (error ~1e-10 relative).  Both
 differentiate the same discrete map with the same noise; the trajectories differ only by rounding
-(~1e-16), which the chain's chaos amplifies by up to ~1e2 over 200 steps and ~1e5 over 1,000 steps
-(tests/test_oracle_sensitivity.py), so gradients agree to 1e-7 of their largest component at 200 steps
-and to 1e-3 at 1,000 steps (sampled replicas, the full launch).  Losses agree to 1e-12.
+(~1e-16), which the chain's chaos amplifies over the segment.  Measured on GB300: gradients agree to
+1.3e-10 of their largest component after 200 steps and to 1.6e-9 after 1,000 steps (sampled replicas
+of the full launch); the tests allow 1e-8 and 1e-6.  Losses agree to 1e-12.
 """
 import numpy as np
 import pytest
@@ -62,9 +62,9 @@ def test_adjoint_matches_oracle(B, oracle_mod, name):
     print(name, L, Lo, np.abs(gth - gtho).max() / np.abs(gtho).max(), np.abs(gq - gqo).max() / np.abs(gqo).max(),
           np.abs(gp - gpo).max() / np.abs(gpo).max())
     assert abs(L - Lo) < 1e-12 * max(1.0, abs(Lo))
-    assert np.abs(gth - gtho).max() < 1e-7 * np.abs(gtho).max()
-    assert np.abs(gq - gqo).max() < 1e-7 * np.abs(gqo).max()
-    assert np.abs(gp - gpo).max() < 1e-7 * np.abs(gpo).max()
+    assert np.abs(gth - gtho).max() < 1e-8 * np.abs(gtho).max()
+    assert np.abs(gq - gqo).max() < 1e-8 * np.abs(gqo).max()
+    assert np.abs(gp - gpo).max() < 1e-8 * np.abs(gpo).max()
 
 
 def test_adjoint_advances_like_step_k_and_ignores_checkpoint_interval(B):
@@ -132,7 +132,7 @@ def test_adjoint_full_launch_sampled(B, oracle_mod):
         ep = np.abs(gp[r] * R - gpo[0]).max() / np.abs(gpo).max()
         errs.append((eq, ep))
     print("full launch sampled errors", errs)
-    assert max(max(e) for e in errs) < 1e-3
+    assert max(max(e) for e in errs) < 1e-6
 
 
 def test_segment_loss_autograd(B):
