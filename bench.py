@@ -293,6 +293,59 @@ def ligand_bench(B, steps, warmup, flush, fp64_steps):
     return out
 
 
+def gradient_bench(B, reps):
+    """Differentiation through the dynamics (the gradient workload): 256 replicas of the 22-bead chain,
+    one 1,000-step fixed-noise segment with the end-to-end distance sampled every 10 steps, forward
+    pass + checkpoints every 100 steps + adjoint sweep (grp_adjoint_segment), FP64."""
+    import torch
+
+    s = W.chain_gradient()
+    R, k, t_gr, ck = s.n_replicas, 1000, 10, 100
+    q0, p0 = W.replica_states(s, R, seed=24, spread=0.002)
+    sysh = B.grp_create_system(s, B.GRP_FP64)
+    rep = B.grp_init_replicas(sysh, R, SEED, q0, p0, per_replica=True)
+    gth = torch.empty(B.grp_param_count(sysh), dtype=torch.float64, device="cuda")
+    B.grp_adjoint_segment(rep, k, t_gr, ck, 4, d_grad_theta=gth)  # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        B.grp_adjoint_segment(rep, k, t_gr, ck, 4, d_grad_theta=gth)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t) / reps
+    t = time.perf_counter()
+    B.grp_step_k(rep, k, 0)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t
+    return {"workload": f"chain{s.n_atoms}_gradient_r{R}_k{k}", "ms_per_segment": wall * 1e3,
+            "forward_ms": fwd * 1e3, "adjoint_over_forward": wall / fwd,
+            "value": R * s.n_atoms * k / wall, "unit": "replica-atom-steps/s (forward + adjoint)"}
+
+
+def profile_case(B, case, replicas, steps, launches):
+    """A small fixed case for ncu captures: `launches` launches of the case's main kernel."""
+    import torch
+
+    if case == "chain":
+        s = W.chain()
+        st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0)
+        for _ in range(launches):
+            B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
+    elif case == "ligand":
+        s = W.ligand_receptor()
+        st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0, omega=0)
+        for _ in range(launches):
+            B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
+    else:
+        s = W.chain_gradient()
+        q0, p0 = W.replica_states(s, replicas, seed=24, spread=0.002)
+        sysh = B.grp_create_system(s, B.GRP_FP64)
+        rep = B.grp_init_replicas(sysh, replicas, SEED, q0, p0, per_replica=True)
+        for _ in range(launches):
+            B.grp_adjoint_segment(rep, steps, 10, 100, 4)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "replicas": replicas, "steps": steps, "launches": launches}))
+
+
 def run_reference(args):
     """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
     bounded sample: the 256 replicas advanced 20 steps with sampling and the exit test."""
@@ -334,10 +387,25 @@ def main():
     ap.add_argument("--accel-steps", type=int, default=200000)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--ligand-steps", type=int, default=3)
+    ap.add_argument("--gradient-reps", type=int, default=2)
+    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint"], default=None,
+                    help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
+    ap.add_argument("--profile-replicas", type=int, default=152)
+    ap.add_argument("--profile-steps", type=int, default=100)
+    ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        import torch
+
+        from paper_1807_02431_gb300 import binding as B
+        from paper_1807_02431_gb300 import build as build_mod
+
+        build_mod.build()
+        B.load()
+        return profile_case(B, args.profile_case, args.profile_replicas, args.profile_steps, args.profile_launches)
 
     import torch
 
@@ -404,6 +472,7 @@ def main():
         batched = batched_bench(B, args.batch_steps, 2, flush) if args.batch_steps > 0 else None
         ligand = (ligand_bench(B, args.ligand_steps, 1, flush, min(args.fp64_steps, 1))
                   if args.ligand_steps > 0 else None)
+        gradient = gradient_bench(B, args.gradient_reps) if args.gradient_reps > 0 else None
         accel = None
         if args.accel_steps > 0:
             # the chain (bounded run) and the double-well validation system, where the loop cycles
@@ -431,6 +500,7 @@ def main():
                "fp64_path": fp64,
                "batched": batched,
                "ligand_receptor": ligand,
+               "gradient": gradient,
                "accelerated": accel,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},
