@@ -251,6 +251,9 @@ __device__ __forceinline__ float bond_dr_ds(const Pos<PathMixed> &pos, int i, in
   return __fadd_rn(__fsub_rn(r, r0), rlo);
 }
 
+// Mixed path: bonds at least this stiff (kJ/mol/nm^2) take r - r0 in double-single arithmetic.
+constexpr float kSoftBond = 1.0e4f;
+
 // Harmonic bond 1/2 k (r - r0)^2.
 template <class P>
 __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
@@ -260,7 +263,13 @@ __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &pa
   V3<T> d;
   T r, dr;
   if constexpr (P::kMixed) {
-    dr = bond_dr_ds(pos, i, j, kp.y, r, d);
+    if (kp.x >= kSoftBond) {
+      dr = bond_dr_ds(pos, i, j, kp.y, r, d);
+    } else {  // soft springs: the FP32 rounding of r moves the force by < 1e-6 of its thermal scale
+      d = pos.diff(i, j);
+      r = gsqrt(dot(d, d));
+      dr = r - T(kp.y);
+    }
   } else {
     d = pos.diff(i, j);
     r = gsqrt(dot(d, d));
@@ -345,17 +354,45 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
 }
 
 // Nonbonded pairs of a Verlet list (i | j << 16), strided over the block's threads; pairs beyond the
-// cutoff contribute nothing.
+// cutoff contribute nothing.  The list lives in global memory (L2): each thread loads its next four
+// entries before evaluating them, so that one load latency covers four pairs.
 template <class P>
 __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                           const uint32_t *list, int count, const typename P::Acc &acc,
                                           bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
   const T cut2 = (T)S.cutoff2;
-  for (int t = threadIdx.x; t < count; t += blockDim.x) {
-    const uint32_t pk = list[t];
-    pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
+  const int bd = blockDim.x;
+  for (int t = threadIdx.x; t < count; t += 4 * bd) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pk[u] = t + u * bd < count ? list[t + u * bd] : 0xFFFFFFFFu;  // written in this kernel: no .nc loads
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (pk[u] != 0xFFFFFFFFu)
+        pair_term<P>(pos, par, (int)(pk[u] & 0xFFFFu), (int)(pk[u] >> 16), cut2, acc, want_e, e_fix, err);
   }
+}
+
+// Bonded terms by kind, without the item table (large systems, whose tables stay in global memory):
+// each thread loads the indices and parameters of its next two bonds before evaluating them.
+template <class P>
+__device__ __forceinline__ void bonded_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
+                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
+  const int bd = blockDim.x;
+  for (int b = threadIdx.x; b < S.n_bonds; b += 2 * bd) {
+    const int b2 = b + bd;
+    const int2 ij0 = S.bond_ij[b];
+    const int2 ij1 = b2 < S.n_bonds ? S.bond_ij[b2] : make_int2(0, 0);
+    bond_term<P>(pos, par, b, ij0.x, ij0.y, acc, want_e, e_fix, err);
+    if (b2 < S.n_bonds) bond_term<P>(pos, par, b2, ij1.x, ij1.y, acc, want_e, e_fix, err);
+  }
+  for (int t = threadIdx.x; t < S.n_angles; t += bd) {
+    const int4 ijk = S.angle_ijk[t];
+    angle_term<P>(pos, par, t, ijk.x, ijk.y, ijk.z, acc, want_e, e_fix, err);
+  }
+  for (int t = threadIdx.x; t < S.n_dih; t += bd)
+    dihedral_term<P>(pos, par, S.dih_ijkl[t], S.dih_terms[t], acc, want_e, e_fix, err);
 }
 
 // One pass over every force-field item of a replica, strided over the block's threads.  The item

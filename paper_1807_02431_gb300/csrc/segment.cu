@@ -357,7 +357,11 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
         const float dx = x[0] - o.x, dy = x[1] - o.y, dz = x[2] - o.z;
         moved |= dx * dx + dy * dy + dz * dz > S.half_skin2;
       }
-    if (__syncthreads_or(moved)) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
+    if (use_list) {
+      if (__syncthreads_or(moved)) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
+    } else {
+      __syncthreads();
+    }
     if (boxes && !use_list) {
       tile_boxes<P>(S, st, boxes);
       __syncthreads();
@@ -365,7 +369,8 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
+    if (a.lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
+    else force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
     if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
     else if (S.tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
     __syncthreads();
