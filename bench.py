@@ -454,7 +454,7 @@ def main():
         peak = fp32_peak_tflops(2070.0)
         achieved = flops / (seg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "ff_segment_kernel<PathMixed,256>",
+                "traffic": None, "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems>",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
                 "kernel_ms": seg_ms, "flops_per_launch": flops, "median_sm_mhz": sm_mhz}
         # plain FP64 GPU path, same step

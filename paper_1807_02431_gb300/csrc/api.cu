@@ -300,16 +300,26 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     std::vector<double4> td;
     std::vector<float4> tf;
     std::vector<int> tsrc;
+    // Small systems (item table, idle lanes): one item per term, so that the terms of a torsion run
+    // in parallel; larger systems: one item per torsion whose terms share the geometry.
+    const bool per_term = !D.tiled;
     for (auto &key : order) {
-      dijkl.push_back(make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key)));
+      const int4 ijkl = make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key));
       const int t0 = (int)td.size();
       for (int t : groups[key]) {
         td.push_back(make_double4(d->dihedral_k[t], (double)d->dihedral_n[t], std::cos(d->dihedral_delta[t]),
                                   std::sin(d->dihedral_delta[t])));
         tf.push_back(make_float4((float)td.back().x, (float)td.back().y, (float)td.back().z, (float)td.back().w));
         tsrc.push_back(t);
+        if (per_term) {
+          dijkl.push_back(ijkl);
+          dterms.push_back(make_int2((int)td.size() - 1, (int)td.size()));
+        }
       }
-      dterms.push_back(make_int2(t0, (int)td.size()));
+      if (!per_term) {
+        dijkl.push_back(ijkl);
+        dterms.push_back(make_int2(t0, (int)td.size()));
+      }
     }
     D.n_dih = (int)dijkl.size();
     // work items: pairs, bonds, angles, dihedrals, each kind padded to a multiple of 32 entries

@@ -282,7 +282,16 @@ struct ObsAcc<PathMixed> {
 
 // ------------------------------------------------------------------------------------------------
 // One segment of replica r by the whole thread block (the block's shared memory holds its state).
-template <class P>
+// Force-field paths of the segment kernel, fixed at compile time so that each kernel carries only
+// the code of its path (a kernel with every path inlined ran 9 % slower on the 22-bead chain).
+enum : int {
+  kModeAny = -1,   // decided per launch (the batched kernel, whose runs may differ)
+  kModeItems = 0,  // explicit item table (fewer than 64 atoms)
+  kModeTiles = 1,  // 32x32 atom tiles, no cutoff
+  kModeList = 2    // Verlet lists built from the tiles (cutoff)
+};
+
+template <class P, int kMode>
 __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsigned char *smem) {
   using T = typename P::T;
   const SysDev &S = a.S;
@@ -318,7 +327,9 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   __syncthreads();
   ObsAcc<P> oacc;
   if (threadIdx.x < no) oacc.begin(acc + 4 * threadIdx.x);
-  const bool use_list = a.nbl != nullptr;
+  const bool use_list = kMode == kModeList || (kMode == kModeAny && a.nbl != nullptr);
+  const bool tiled = kMode == kModeTiles || kMode == kModeList || (kMode == kModeAny && S.tiled);
+  const bool lean = kMode != kModeItems && a.lean;
   uint32_t *list = use_list ? a.nbl + (size_t)r * a.nbl_cap : nullptr;
   float4 *qref = use_list ? a.qref + (size_t)r * n : nullptr;
   int n_list = 0;
@@ -333,51 +344,65 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
   int j = 0;  // step index inside the current noise batch
   for (int s = 0; s < a.k; ++s, ++j) {
-    if (NB > 0) {
+    int moved = 0;
+    if (kMode == kModeItems || NB > 0) {
       if (j == NB) j = 0;
       if (j == 0) {
         gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r, n);
         __syncthreads();
       }
-      for (int at = threadIdx.x; at < n; at += kThreads) st.baoa(at, xi + ((size_t)j * n + at) * 3, h, c1);
+      // one thread per coordinate; with a Verlet list, an atom is taken to have moved more than skin/2
+      // when one of its coordinates moved more than skin / (2 sqrt 3) (a sufficient test)
+      const T *xs = xi + (size_t)j * nd;
+      for (int i = threadIdx.x; i < nd; i += kThreads) {
+        st.baoa_c(i, xs[i], h, c1);
+        if (use_list) {
+          const float d = (float)st.coord(i) - (&qref[i / 3].x)[i % 3];
+          moved |= 3.f * d * d > S.half_skin2;
+        }
+      }
     } else {
       for (int at = threadIdx.x; at < n; at += kThreads) {
         T z[4];
         normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r, at), z);
         st.baoa(at, z, h, c1);
+        if (use_list) {  // Verlet list: rebuilt when some atom has moved more than skin/2
+          float x[3];
+          st.get_f32(at, x);
+          const float4 o = qref[at];
+          const float dx = x[0] - o.x, dy = x[1] - o.y, dz = x[2] - o.z;
+          moved |= dx * dx + dy * dy + dz * dz > S.half_skin2;
+        }
       }
     }
-    // Verlet list: rebuilt when some atom has moved more than skin/2 since the last build
-    int moved = 0;
-    if (use_list)
-      for (int at = threadIdx.x; at < n; at += kThreads) {
-        float x[3];
-        st.get_f32(at, x);
-        const float4 o = qref[at];
-        const float dx = x[0] - o.x, dy = x[1] - o.y, dz = x[2] - o.z;
-        moved |= dx * dx + dy * dy + dz * dz > S.half_skin2;
-      }
     if (use_list) {
       if (__syncthreads_or(moved)) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
     } else {
       __syncthreads();
     }
-    if (boxes && !use_list) {
+    if (tiled && !use_list && boxes) {
       tile_boxes<P>(S, st, boxes);
       __syncthreads();
     }
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    if (a.lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
+    if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
     else force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
     if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
-    else if (S.tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
+    else if (tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
-    for (int at = threadIdx.x; at < n; at += kThreads) {
-      const T ke = st.bk(at, fa, h);
-      if (sample) k_fix += fa.efix(ke, &err);
+    if (kMode == kModeItems || NB > 0) {
+      for (int i = threadIdx.x; i < nd; i += kThreads) {
+        const T ke = st.bk_c(i, fa, h);
+        if (sample) k_fix += fa.efix(ke, &err);
+      }
+    } else {  // the same thread owns each atom in both halves of the step
+      for (int at = threadIdx.x; at < n; at += kThreads) {
+        const T ke = st.bk(at, fa, h);
+        if (sample) k_fix += fa.efix(ke, &err);
+      }
     }
     if (sample) {
       const long long es = block_sum_ll(e_fix, red);
@@ -404,11 +429,11 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
 
 // kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
 // on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
-template <class P, int kMaxThreads, int kMinBlocks>
+template <class P, int kMaxThreads, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
   if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  segment_body<P>(a, blockIdx.x, smem);
+  segment_body<P, kMode>(a, blockIdx.x, smem);
 }
 
 // Batched segments: a persistent grid of blocks takes (run, replica) units from a queue sorted by
@@ -430,7 +455,7 @@ __global__ void __launch_bounds__(512, 1) ff_segment_batch_kernel(const SegArgs 
     int *dst = reinterpret_cast<int *>(&sa);
     for (int i = threadIdx.x; i < (int)(sizeof(SegArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    segment_body<P>(sa, (int)un.y, smem);
+    segment_body<P, kModeAny>(sa, (int)un.y, smem);
     __syncthreads();
   }
 }
@@ -533,7 +558,11 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
 template <class P>
 static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_t st) {
   if (c.threads < 32 || c.threads > 512 || c.threads % 32) return cudaErrorInvalidValue;
-  auto kern = c.threads <= 320 ? ff_segment_kernel<P, 320, 2> : ff_segment_kernel<P, 512, 1>;
+  const int mode = a.S.use_list ? kModeList : (a.S.tiled ? kModeTiles : kModeItems);
+  const bool small = c.threads <= 320;
+  auto kern = mode == kModeItems ? (small ? ff_segment_kernel<P, 320, 2, kModeItems> : ff_segment_kernel<P, 512, 1, kModeItems>)
+            : mode == kModeTiles ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles> : ff_segment_kernel<P, 512, 1, kModeTiles>)
+                                 : (small ? ff_segment_kernel<P, 320, 2, kModeList> : ff_segment_kernel<P, 512, 1, kModeList>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.n_active, c.threads, c.smem, st>>>(a);

@@ -94,6 +94,27 @@ struct State<PathF64> {
     }
     return ke;
   }
+  // the same two updates for one coordinate i = 3 atom + axis (the block spreads coordinates, not atoms)
+  __device__ __forceinline__ void baoa_c(int i, double xi, double h, double c1) {
+    const int at = i / 3;
+    const double im = atom[at].w, s = sd[at];
+    double pp = p[i] + h * f[i];
+    double qq = q[i] + h * pp * im;
+    pp = c1 * pp + s * xi;
+    qq = qq + h * pp * im;
+    p[i] = pp;
+    q[i] = qq;
+  }
+  __device__ __forceinline__ double bk_c(int i, const AccF64 &acc, double h) {
+    const double im = atom[i / 3].w;
+    const double fv = (double)acc.F[i] * kFixInv;
+    acc.F[i] = 0;
+    f[i] = fv;
+    const double pp = p[i] + h * fv;
+    p[i] = pp;
+    return 0.5 * pp * pp * im;
+  }
+  __device__ double coord(int i) const { return q[i]; }
   __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
   __device__ void get_f32(int at, float x[3]) const {
     x[0] = (float)q[3 * at]; x[1] = (float)q[3 * at + 1]; x[2] = (float)q[3 * at + 2];
@@ -197,6 +218,34 @@ struct State<PathMixed> {
     }
     return ke;
   }
+  __device__ __forceinline__ void baoa_c(int i, float xi, float h, float c1) {
+    const int at = i / 3, x = i - 3 * at;
+    const float im = atom[at].w, s = sd[at], hm = h * im;
+    float *qa = &qh[at].x, *qb = &ql[at].x;
+    ds P = {ph[i], pl[i]};
+    ds Q = {qa[x], qb[x]};
+    P = ds_add(P, h * f[i]);
+    Q = ds_add(Q, hm * P.hi);
+    P = ds_add(ds_scale(P, c1), s * xi);
+    Q = ds_add(Q, hm * P.hi);
+    ph[i] = P.hi;
+    pl[i] = P.lo;
+    qa[x] = Q.hi;
+    qb[x] = Q.lo;
+  }
+  __device__ __forceinline__ float bk_c(int i, const AccMixed &acc, float h) {
+    const float im = atom[i / 3].w;
+    const float fv = split_to_float(acc.hi[i], acc.lo[i]);
+    acc.hi[i] = 0;
+    acc.lo[i] = 0u;
+    f[i] = fv;
+    ds P = {ph[i], pl[i]};
+    P = ds_add(P, h * fv);
+    ph[i] = P.hi;
+    pl[i] = P.lo;
+    return 0.5f * P.hi * P.hi * im;
+  }
+  __device__ float coord(int i) const { return (&qh[i / 3].x)[i % 3]; }
   __device__ void get_f64(int at, double x[3]) const {
     const float4 a = qh[at], b = ql[at];
     x[0] = (double)a.x + (double)b.x; x[1] = (double)a.y + (double)b.y; x[2] = (double)a.z + (double)b.z;
