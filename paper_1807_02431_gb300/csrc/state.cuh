@@ -64,44 +64,17 @@ struct State<PathF64> {
   __device__ Params<PathF64> params(const SysDev &S) const {
     return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d};
   }
-  // B, A, O, A of BAOAB for atom `at` with the normals xi[0..2].
-  __device__ __forceinline__ void baoa(int at, const double *xi, double h, double c1) {
-    const double im = atom[at].w, s = sd[at];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      double pp = p[i] + h * f[i];
-      double qq = q[i] + h * pp * im;
-      pp = c1 * pp + s * xi[x];
-      qq = qq + h * pp * im;
-      p[i] = pp;
-      q[i] = qq;
-    }
-  }
-  // final B with the new forces (fixed point -> FP64); returns the kinetic energy of the atom.
-  __device__ __forceinline__ double bk(int at, const AccF64 &acc, double h) {
-    const double im = atom[at].w;
-    double ke = 0;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const int i = 3 * at + x;
-      const double fv = (double)acc.F[i] * kFixInv;
-      acc.F[i] = 0;
-      f[i] = fv;
-      const double pp = p[i] + h * fv;
-      p[i] = pp;
-      ke += 0.5 * pp * pp * im;
-    }
-    return ke;
-  }
-  // the same two updates for one coordinate i = 3 atom + axis (the block spreads coordinates, not atoms)
+  // B, A, O, A of BAOAB for one coordinate i = 3 atom + axis, and the final B with the new force,
+  // written with explicitly rounded operations so that no kernel leaves contraction choices to the
+  // compiler: every kernel that runs them (the segment, the adjoint's recomputation) reproduces the
+  // same trajectory bit for bit.
   __device__ __forceinline__ void baoa_c(int i, double xi, double h, double c1) {
     const int at = i / 3;
     const double im = atom[at].w, s = sd[at];
-    double pp = p[i] + h * f[i];
-    double qq = q[i] + h * pp * im;
-    pp = c1 * pp + s * xi;
-    qq = qq + h * pp * im;
+    double pp = __fma_rn(h, f[i], p[i]);
+    double qq = __fma_rn(__dmul_rn(h, pp), im, q[i]);
+    pp = __fma_rn(c1, pp, __dmul_rn(s, xi));
+    qq = __fma_rn(__dmul_rn(h, pp), im, qq);
     p[i] = pp;
     q[i] = qq;
   }
@@ -110,9 +83,20 @@ struct State<PathF64> {
     const double fv = (double)acc.F[i] * kFixInv;
     acc.F[i] = 0;
     f[i] = fv;
-    const double pp = p[i] + h * fv;
+    const double pp = __fma_rn(h, fv, p[i]);
     p[i] = pp;
-    return 0.5 * pp * pp * im;
+    return __dmul_rn(__dmul_rn(0.5, __dmul_rn(pp, pp)), im);
+  }
+  // the same for the three coordinates of atom `at` (normals xi[0..2]); returns its kinetic energy
+  __device__ __forceinline__ void baoa(int at, const double *xi, double h, double c1) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) baoa_c(3 * at + x, xi[x], h, c1);
+  }
+  __device__ __forceinline__ double bk(int at, const AccF64 &acc, double h) {
+    double ke = 0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) ke += bk_c(3 * at + x, acc, h);
+    return ke;
   }
   __device__ double coord(int i) const { return q[i]; }
   __device__ void get_f64(int at, double x[3]) const { x[0] = q[3 * at]; x[1] = q[3 * at + 1]; x[2] = q[3 * at + 2]; }
