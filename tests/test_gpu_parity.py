@@ -10,8 +10,9 @@ position perturbation of 1e-13 grows by x1e5 (median) to x2e6 (worst of 8 replic
   mixed path: FP32 forces carry ~1e-7 relative rounding every step, which the chain amplifies beyond
              any fixed tolerance after ~500 steps; so the mixed path is held to (i) the one-step local
              error (positions 1e-9, momenta 1e-6 relative), (ii) positions within 1e-4 relative after
-             200 steps, (iii) labels identical to the GPU FP64 path after a 1,000-step segment from the
-             same FP64 state for every replica whose CV is further than 2 degrees from a boundary.
+             200 steps, (iii) labels identical to the GPU FP64 path after one 500-step exit-test
+             segment from the same FP64 state for every replica whose CV is further than 2 degrees from
+             a boundary.
 Integer and index outputs (labels, exited flags, branch sources, M, k, tau) are compared exactly.
 """
 import numpy as np
@@ -337,9 +338,11 @@ def test_genparrep_loop_double_well_bit_exact(B, oracle_mod):
 
 # ----------------------------------------------------------------------------- mixed vs FP64 GPU
 def test_mixed_vs_fp64_segment_labels(B, oracle_mod, chain):
-    """Segment protocol: both paths restart from the same FP64 state and run one 1,000-step segment
-    with the same Philox stream; every replica whose FP64 CV is more than 2 degrees from a boundary
-    of the rectangle has the same label and exit flag in both paths."""
+    """Segment protocol: both paths restart from the same FP64 state and run one exit-test segment
+    (t_check = 500 steps) with the same Philox stream; every replica whose FP64 CV is more than 2 degrees
+    from a boundary of the rectangle has the same label and exit flag in both paths.  (Over 1,000 steps
+    the chain's chaos, which amplifies differences up to x2e6, once moved a replica across a boundary
+    from 2 degrees away: agreement is a per-segment property.)"""
     import torch
 
     s = chain
@@ -350,7 +353,7 @@ def test_mixed_vs_fp64_segment_labels(B, oracle_mod, chain):
     for prec in (0, 1):
         sysh = B.grp_create_system(s, prec)
         rep = B.grp_init_replicas(sysh, R, SEED, q0, p0, per_replica=True)
-        B.grp_step_k(rep, 1000, s.t_gr)
+        B.grp_step_k(rep, s.t_check, s.t_gr)
         lab = torch.zeros(R, dtype=torch.int8, device="cuda")
         ex = torch.zeros(R, dtype=torch.uint8, device="cuda")
         B.grp_check_states(rep, 1, lab, ex)
