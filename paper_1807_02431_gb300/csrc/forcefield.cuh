@@ -19,9 +19,13 @@ __device__ __forceinline__ double gsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float gsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double gatan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float gatan2(float y, float x) { return atan2f(y, x); }
-// reciprocal and quotient: IEEE in FP64, the fast hardware approximations (about 1 ulp) in FP32
+// reciprocal and quotient: IEEE in FP64, the hardware approximations (about 1 ulp) in FP32
 __device__ __forceinline__ double grcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float grcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float gdiv(float a, float b) { return __fdividef(a, b); }
 
@@ -254,10 +258,10 @@ __device__ __forceinline__ float bond_dr_ds(const Pos<PathMixed> &pos, int i, in
 // Mixed path: bonds at least this stiff (kJ/mol/nm^2) take r - r0 in double-single arithmetic.
 constexpr float kSoftBond = 1.0e4f;
 
-// Harmonic bond 1/2 k (r - r0)^2.
+// Harmonic bond 1/2 k (r - r0)^2: force on atom i (minus the force on j) and the energy.
 template <class P>
-__device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
-                                          const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
+__device__ __forceinline__ V3<typename P::T> bond_eval(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
+                                                       typename P::T &e) {
   using T = typename P::T;
   const auto kp = par.bond[b];
   V3<T> d;
@@ -276,10 +280,19 @@ __device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &pa
     dr = r - T(kp.y);
   }
   const T g = -gdiv(T(kp.x) * dr, r);
-  const V3<T> fi = {g * d.x, g * d.y, g * d.z};
+  e = T(0.5) * T(kp.x) * dr * dr;
+  return {g * d.x, g * d.y, g * d.z};
+}
+
+template <class P>
+__device__ __forceinline__ void bond_term(const Pos<P> &pos, const Params<P> &par, int b, int i, int j,
+                                          const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
+  using T = typename P::T;
+  T e;
+  const V3<T> fi = bond_eval<P>(pos, par, b, i, j, e);
   acc.add(i, fi, err);
   acc.add(j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
-  if (want_e) e_fix += acc.efix(T(0.5) * T(kp.x) * dr * dr, err);
+  if (want_e) e_fix += acc.efix(e, err);
 }
 
 // Harmonic angle 1/2 k (theta - theta0)^2 at vertex j; theta = atan2(|u x v|, u.v) with
@@ -353,24 +366,58 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   if (want_e) e_fix += acc.efix(e, err);
 }
 
-// Nonbonded pairs of a Verlet list (i | j << 16), strided over the block's threads; pairs beyond the
-// cutoff contribute nothing.  The list lives in global memory (L2): each thread loads its next four
-// entries before evaluating them, so that one load latency covers four pairs.
+// Atom-centric pass over per-atom Verlet rows (systems with a cutoff): the thread that owns atom i
+// sums the nonbonded forces on i over its row nbr[k n + i], k < count[i] (each pair appears in both
+// atoms' rows and is evaluated from both ends) and, with `bonds`, the forces of every bond of i
+// (rows atom_bonds[atom_bond_off[i] ..]), then adds the total once per component: no atomic
+// operation per pair.  Energies of pairs and bonds counted from both ends are halved.  A row is
+// screened with the high words of the positions before the low words are read.
 template <class P>
-__device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                          const uint32_t *list, int count, const typename P::Acc &acc,
-                                          bool want_e, long long &e_fix, int *err) {
+__device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
+                                            const uint16_t *nbr, const int *count, bool bonds,
+                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
   const T cut2 = (T)S.cutoff2;
-  const int bd = blockDim.x;
-  for (int t = threadIdx.x; t < count; t += 4 * bd) {
-    uint32_t pk[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) pk[u] = t + u * bd < count ? list[t + u * bd] : 0xFFFFFFFFu;  // written in this kernel: no .nc loads
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (pk[u] != 0xFFFFFFFFu)
-        pair_term<P>(pos, par, (int)(pk[u] & 0xFFFFu), (int)(pk[u] >> 16), cut2, acc, want_e, e_fix, err);
+  const int n = S.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const typename Pos<P>::At pi = pos.at(i);
+    const auto ai = par.atom[i];
+    V3<T> fi = {T(0), T(0), T(0)};
+    T en = T(0);
+    const int c = count[i];
+    uint16_t jn = c > 0 ? nbr[i] : 0;
+    for (int k = 0; k < c; ++k) {
+      const int j = jn;
+      if (k + 1 < c) jn = nbr[(size_t)(k + 1) * n + i];  // next neighbour, loaded ahead
+      const V3<T> d = Pos<P>::diff(pi, pos.at(j));
+      const T r2 = dot(d, d);
+      if (r2 < cut2) {
+        const auto aj = par.atom[j];
+        const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
+        const T inv_r2 = grcp(r2);
+        const T s2 = sig * sig * inv_r2;
+        const T s6 = s2 * s2 * s2;
+        const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+        fi.x += g * d.x;
+        fi.y += g * d.y;
+        fi.z += g * d.z;
+        if (want_e) en += T(0.5) * (T(4) * eps * (s6 * s6 - s6) + qq * inv_r2);
+      }
+    }
+    if (bonds) {
+      for (int t = S.atom_bond_off[i]; t < S.atom_bond_off[i + 1]; ++t) {
+        const int b = S.atom_bonds[t];
+        const int2 ij = S.bond_ij[b];
+        T e;
+        const V3<T> f = ij.x == i ? bond_eval<P>(pos, par, b, i, ij.y, e) : bond_eval<P>(pos, par, b, i, ij.x, e);
+        fi.x += f.x;
+        fi.y += f.y;
+        fi.z += f.z;
+        if (want_e) en += T(0.5) * e;
+      }
+    }
+    acc.add(i, fi, err);
+    if (want_e) e_fix += acc.efix(en, err);
   }
 }
 
@@ -378,9 +425,10 @@ __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, co
 // each thread loads the indices and parameters of its next two bonds before evaluating them.
 template <class P>
 __device__ __forceinline__ void bonded_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
+                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err,
+                                            bool bonds = true) {
   const int bd = blockDim.x;
-  for (int b = threadIdx.x; b < S.n_bonds; b += 2 * bd) {
+  for (int b = threadIdx.x; bonds && b < S.n_bonds; b += 2 * bd) {
     const int b2 = b + bd;
     const int2 ij0 = S.bond_ij[b];
     const int2 ij1 = b2 < S.n_bonds ? S.bond_ij[b2] : make_int2(0, 0);
