@@ -447,7 +447,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
         if (d2 < lc2) { ++cnt[i]; ++cnt[j]; }
       }
     const int mx = *std::max_element(cnt.begin(), cnt.end());
-    r->nbl_cap = std::min(n - 1, mx + mx / 2 + 32);
+    r->nbl_cap = (std::min(n - 1, mx + mx / 2 + 32) + 3) & ~3;  // whole groups of four
     AL(r->nbl, R * (size_t)r->nbl_cap * n * 2);
     AL(r->qref, R * (size_t)n * 16);
   }

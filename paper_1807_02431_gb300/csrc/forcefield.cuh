@@ -113,6 +113,25 @@ struct Params<PathMixed> {
   const float4 *term;
 };
 
+// Nonbonded parameters of an atom held in registers by the tile and row loops: sigma/2, sqrt(eps) and
+// the scaled charge q sqrt(k_e/4).  The mixed path keeps sigma/2 and sqrt(eps) in the spare fourth
+// words of the double-single position (State<PathMixed>::load), one shared-memory load fewer per pair
+// in loops that are bound by shared-memory traffic; the charge comes from the parameter table.
+template <class P>
+__device__ __forceinline__ void nb_params(const typename Pos<P>::At &pa, const Params<P> &par, int a,
+                                          typename P::T &sh, typename P::T &se, typename P::T &qc) {
+  if constexpr (P::kMixed) {
+    sh = pa.h.w;
+    se = pa.l.w;
+    qc = par.atom[a].z;
+  } else {
+    const auto p = par.atom[a];
+    sh = p.x;
+    se = p.y;
+    qc = p.z;
+  }
+}
+
 // Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j): force on i
 // (minus the force on j) and the pair energy; false beyond the cutoff.
 template <class P>
@@ -182,18 +201,21 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
     // atom i in registers (padding lanes read a valid atom and have an empty mask)
     const int ic = i < S.n ? i : S.n - 1;
     const typename Pos<P>::At pi = pos.at(ic);
-    const auto ai = par.atom[ic];
+    T ash, ase, aqc;
+    nb_params<P>(pi, par, ic, ash, ase, aqc);
 #pragma unroll 4
     for (int s = s0; s < s1; ++s) {
       const int m = (lane + s) & 31;
       const bool on = ((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16);
       if (on) {
         const int j = j0 + m;
-        const V3<T> d = Pos<P>::diff(pi, pos.at(j));
+        const typename Pos<P>::At pj = pos.at(j);
+        const V3<T> d = Pos<P>::diff(pi, pj);
         const T r2 = dot(d, d);
         if (!(cut2 > T(0) && r2 >= cut2)) {
-          const auto aj = par.atom[j];
-          const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
+          T bsh, bse, bqc;
+          nb_params<P>(pj, par, j, bsh, bse, bqc);
+          const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;
           const T inv_r2 = grcp(r2);
           const T s2 = sig * sig * inv_r2;
           const T s6 = s2 * s2 * s2;
@@ -367,7 +389,7 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
 }
 
 // Atom-centric pass over per-atom Verlet rows (systems with a cutoff): the thread that owns atom i
-// sums the nonbonded forces on i over its row nbr[k n + i], k < count[i] (each pair appears in both
+// sums the nonbonded forces on i over its row (k < count[i]; each pair appears in both
 // atoms' rows and is evaluated from both ends) and, with `bonds`, the forces of every bond of i
 // (rows atom_bonds[atom_bond_off[i] ..]), then adds the total once per component: no atomic
 // operation per pair.  Energies of pairs and bonds counted from both ends are halved.  A row is
@@ -381,19 +403,30 @@ __device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, 
   const int n = S.n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const typename Pos<P>::At pi = pos.at(i);
-    const auto ai = par.atom[i];
+    T ash, ase, aqc;
+    nb_params<P>(pi, par, i, ash, ase, aqc);
     V3<T> fi = {T(0), T(0), T(0)};
     T en = T(0);
+    uint32_t jq[4];
     const int c = count[i];
-    uint16_t jn = c > 0 ? nbr[i] : 0;
+    // rows are stored in groups of four neighbours, nbr[((k / 4) n + i) 4 + k % 4]: one 8-byte load per
+    // group, the next group loaded while this one is evaluated
+    const uint2 *rows = reinterpret_cast<const uint2 *>(nbr);
+    uint2 wn = c > 0 ? rows[i] : make_uint2(0u, 0u);
     for (int k = 0; k < c; ++k) {
-      const int j = jn;
-      if (k + 1 < c) jn = nbr[(size_t)(k + 1) * n + i];  // next neighbour, loaded ahead
-      const V3<T> d = Pos<P>::diff(pi, pos.at(j));
+      if ((k & 3) == 0) {
+        const uint2 w = wn;
+        if (k + 4 < c) wn = rows[(size_t)((k >> 2) + 1) * n + i];
+        jq[0] = w.x & 0xFFFFu; jq[1] = w.x >> 16; jq[2] = w.y & 0xFFFFu; jq[3] = w.y >> 16;
+      }
+      const int j = (int)jq[k & 3];
+      const typename Pos<P>::At pj = pos.at(j);
+      const V3<T> d = Pos<P>::diff(pi, pj);
       const T r2 = dot(d, d);
       if (r2 < cut2) {
-        const auto aj = par.atom[j];
-        const T sig = ai.x + aj.x, eps = ai.y * aj.y, qq = ai.z * aj.z;
+        T bsh, bse, bqc;
+        nb_params<P>(pj, par, j, bsh, bse, bqc);
+        const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;
         const T inv_r2 = grcp(r2);
         const T s2 = sig * sig * inv_r2;
         const T s6 = s2 * s2 * s2;

@@ -171,7 +171,8 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
 }
 
 // Verlet rows of one replica (systems with a cutoff): for every atom i, the non-excluded atoms closer
-// than cutoff + skin, nbr[k n + i] for k < count[i] (each pair in both rows), found by the tiled scan
+// than cutoff + skin, nbr[((k / 4) n + i) 4 + k % 4] for k < count[i] (each pair in both rows; groups of
+// four neighbours of an atom are contiguous), found by the tiled scan
 // over tile pairs whose bounding boxes are that close (the lane rotation of tile_pass meets each
 // unordered pair once) and appended with shared atomics on the per-atom counts; the positions at the
 // build are kept for the displacement test.  A row longer than `cap` sets kErrList and is cut.
@@ -213,8 +214,8 @@ __device__ void build_list(const SysDev &S, const State<P> &st, float *boxes, ui
         const float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
         if (dx * dx + dy * dy + dz * dz < lc2) {
           const int ki = atomicAdd(&count[i], 1), kj = atomicAdd(&count[j], 1);
-          if (ki < cap) nbr[(size_t)ki * n + i] = (uint16_t)j;
-          if (kj < cap) nbr[(size_t)kj * n + j] = (uint16_t)i;
+          if (ki < cap) nbr[((size_t)(ki >> 2) * n + i) * 4 + (ki & 3)] = (uint16_t)j;
+          if (kj < cap) nbr[((size_t)(kj >> 2) * n + j) * 4 + (kj & 3)] = (uint16_t)i;
         }
       }
     }
@@ -620,9 +621,10 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
     if constexpr (P::kMixed) {
       const ds x = ds_from_double(q[(size_t)b * nd + 3 * at]), y = ds_from_double(q[(size_t)b * nd + 3 * at + 1]),
                z = ds_from_double(q[(size_t)b * nd + 3 * at + 2]);
-      st.qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
-      st.ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
-      if (!lean) const_cast<float4 *>(st.atom)[at] = S.atom_f[at];
+      const float4 pa = S.atom_f[at];
+      st.qh[at] = make_float4(x.hi, y.hi, z.hi, pa.x);  // as State<PathMixed>::load
+      st.ql[at] = make_float4(x.lo, y.lo, z.lo, pa.y);
+      if (!lean) const_cast<float4 *>(st.atom)[at] = pa;
     } else {
       for (int x = 0; x < 3; ++x) st.q[3 * at + x] = q[(size_t)b * nd + 3 * at + x];
       if (!lean) const_cast<double4 *>(st.atom)[at] = S.atom_d[at];

@@ -108,7 +108,7 @@ struct State<PathF64> {
 
 template <>
 struct State<PathMixed> {
-  float4 *qh, *ql;   // [n] double-single positions
+  float4 *qh, *ql;   // [n] double-single positions; .w: sigma/2 (qh), sqrt(eps) (ql)
   float *ph, *pl;    // [3n] double-single momenta
   float *f, *sd;     // [3n], [n]
   const float4 *atom;  // [n] parameters: a shared-memory copy, or the global table when lean
@@ -133,9 +133,10 @@ struct State<PathMixed> {
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
       const ds x = ds_from_double(gq[3 * at]), y = ds_from_double(gq[3 * at + 1]),
                z = ds_from_double(gq[3 * at + 2]);
-      qh[at] = make_float4(x.hi, y.hi, z.hi, 0.f);
-      ql[at] = make_float4(x.lo, y.lo, z.lo, 0.f);
-      if (own_atom) const_cast<float4 *>(atom)[at] = S.atom_f[at];
+      const float4 pa = S.atom_f[at];
+      qh[at] = make_float4(x.hi, y.hi, z.hi, pa.x);  // fourth words: sigma/2 and sqrt(eps) (nb_params)
+      ql[at] = make_float4(x.lo, y.lo, z.lo, pa.y);
+      if (own_atom) const_cast<float4 *>(atom)[at] = pa;
       sd[at] = (float)sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
     }
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
