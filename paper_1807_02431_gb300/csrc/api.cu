@@ -431,8 +431,8 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   AL(r->n_branched, 4);
   AL(r->rhat, GRP_MAX_OBS * 8);
   if (D.use_list) {
-    // row capacity: 1.5 times the longest row of the first configuration (non-excluded atoms within
-    // cutoff + skin) plus 32, at most n - 1
+    // row capacity: 1.5 times the longest row of the first configuration (non-excluded pairs within
+    // cutoff + skin, each in one row) plus 32, at most n - 1
     const int n = D.n;
     const double lc2 = (double)D.list_cut2;
     std::vector<int> cnt(n, 0);
@@ -444,7 +444,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
           const double dx = h_q0[3 * i + x] - h_q0[3 * j + x];
           d2 += dx * dx;
         }
-        if (d2 < lc2) { ++cnt[i]; ++cnt[j]; }
+        if (d2 < lc2) ++cnt[((i + j) & 1) ? j : i];  // the row that takes the pair (segment kernel)
       }
     const int mx = *std::max_element(cnt.begin(), cnt.end());
     r->nbl_cap = (std::min(n - 1, mx + mx / 2 + 32) + 3) & ~3;  // whole groups of four

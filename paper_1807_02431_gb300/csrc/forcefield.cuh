@@ -388,12 +388,11 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   if (want_e) e_fix += acc.efix(e, err);
 }
 
-// Atom-centric pass over per-atom Verlet rows (systems with a cutoff): the thread that owns atom i
-// sums the nonbonded forces on i over its row (k < count[i]; each pair appears in both
-// atoms' rows and is evaluated from both ends) and, with `bonds`, the forces of every bond of i
-// (rows atom_bonds[atom_bond_off[i] ..]), then adds the total once per component: no atomic
-// operation per pair.  Energies of pairs and bonds counted from both ends are halved.  A row is
-// screened with the high words of the positions before the low words are read.
+// Atom-centric pass over per-atom Verlet rows (systems with a cutoff; each pair is in one row): the
+// thread that owns atom i sums the forces on i over its row in registers, adds the opposite force to
+// each neighbour j (fixed-point atomics) and, with `bonds`, the forces of every bond of i (rows
+// atom_bonds[atom_bond_off[i] ..], each bond evaluated from both ends, energy halved), then adds the
+// total on i once per component.
 template <class P>
 __device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                             const uint16_t *nbr, const int *count, bool bonds,
@@ -431,10 +430,12 @@ __device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, 
         const T s2 = sig * sig * inv_r2;
         const T s6 = s2 * s2 * s2;
         const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
-        fi.x += g * d.x;
-        fi.y += g * d.y;
-        fi.z += g * d.z;
-        if (want_e) en += T(0.5) * (T(4) * eps * (s6 * s6 - s6) + qq * inv_r2);
+        const V3<T> f = {g * d.x, g * d.y, g * d.z};
+        fi.x += f.x;
+        fi.y += f.y;
+        fi.z += f.z;
+        acc.add(j, V3<T>{-f.x, -f.y, -f.z}, err);
+        if (want_e) en += T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
       }
     }
     if (bonds) {

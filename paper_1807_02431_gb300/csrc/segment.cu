@@ -170,8 +170,8 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
   }
 }
 
-// Verlet rows of one replica (systems with a cutoff): for every atom i, the non-excluded atoms closer
-// than cutoff + skin, nbr[((k / 4) n + i) 4 + k % 4] for k < count[i] (each pair in both rows; groups of
+// Verlet rows of one replica (systems with a cutoff): every non-excluded pair closer than cutoff +
+// skin, in the row of one of its two atoms, nbr[((k / 4) n + i) 4 + k % 4] for k < count[i] (groups of
 // four neighbours of an atom are contiguous), found by the tiled scan
 // over tile pairs whose bounding boxes are that close (the lane rotation of tile_pass meets each
 // unordered pair once) and appended with shared atomics on the per-atom counts; the positions at the
@@ -213,9 +213,11 @@ __device__ void build_list(const SysDev &S, const State<P> &st, float *boxes, ui
         st.get_f32(j, xj);
         const float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
         if (dx * dx + dy * dy + dz * dz < lc2) {
-          const int ki = atomicAdd(&count[i], 1), kj = atomicAdd(&count[j], 1);
-          if (ki < cap) nbr[((size_t)(ki >> 2) * n + i) * 4 + (ki & 3)] = (uint16_t)j;
-          if (kj < cap) nbr[((size_t)(kj >> 2) * n + j) * 4 + (kj & 3)] = (uint16_t)i;
+          // the pair goes to one row: the larger index when i + j is odd, else the smaller one, which
+          // gives every atom about half of its neighbours whatever its place in the numbering
+          const int o = ((i + j) & 1) ? max(i, j) : min(i, j), other = i + j - o;
+          const int k = atomicAdd(&count[o], 1);
+          if (k < cap) nbr[((size_t)(k >> 2) * n + o) * 4 + (k & 3)] = (uint16_t)other;
         }
       }
     }
