@@ -72,7 +72,7 @@ struct grp_replicas {
   int *err = nullptr;
   int *n_branched = nullptr;
   double *rhat = nullptr;
-  uint16_t *nbl = nullptr;  // [R][nbl_cap][n] Verlet rows
+  uint32_t *nbl = nullptr;  // [R][nbl_cap] Verlet lists
   float4 *qref = nullptr;   // [R][n]
   int nbl_cap = 0;
   long long t_global = 0, t_phase = 0;
@@ -259,15 +259,6 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     }
     D.n_bonds = d->n_bonds;
     UP(bij.data(), bij.size(), &D.bond_ij);
-    if (D.tiled) {  // bonds of each atom, for the atom-centric pass of large systems
-      std::vector<int> off(n + 1, 0), ab(2 * (size_t)d->n_bonds);
-      for (int b = 0; b < d->n_bonds; ++b) { ++off[bij[b].x + 1]; ++off[bij[b].y + 1]; }
-      for (int i = 0; i < n; ++i) off[i + 1] += off[i];
-      std::vector<int> fill(off.begin(), off.end() - 1);
-      for (int b = 0; b < d->n_bonds; ++b) { ab[fill[bij[b].x]++] = b; ab[fill[bij[b].y]++] = b; }
-      UP(off.data(), off.size(), &D.atom_bond_off);
-      if (!ab.empty()) UP(ab.data(), ab.size(), &D.atom_bonds);
-    }
     UP(bd.data(), bd.size(), &D.bond_d);
     UP(bf.data(), bf.size(), &D.bond_f);
     // angles
@@ -385,7 +376,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
   if (e) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
-    if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet row outgrew its capacity (1.5 times the longest row of the first configuration)");
+    if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
     return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
@@ -431,11 +422,10 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   AL(r->n_branched, 4);
   AL(r->rhat, GRP_MAX_OBS * 8);
   if (D.use_list) {
-    // row capacity: 1.5 times the longest row of the first configuration (non-excluded pairs within
-    // cutoff + skin, each in one row) plus 32, at most n - 1
+    // capacity: twice the non-excluded pairs within cutoff + skin in the first configuration
     const int n = D.n;
     const double lc2 = (double)D.list_cut2;
-    std::vector<int> cnt(n, 0);
+    size_t cnt = 0;
     for (int i = 0; i < n; ++i)
       for (int j = i + 1; j < n; ++j) {
         if (s->excl[(size_t)i * n + j]) continue;
@@ -444,11 +434,11 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
           const double dx = h_q0[3 * i + x] - h_q0[3 * j + x];
           d2 += dx * dx;
         }
-        if (d2 < lc2) ++cnt[((i + j) & 1) ? j : i];  // the row that takes the pair (segment kernel)
+        cnt += d2 < lc2;
       }
-    const int mx = *std::max_element(cnt.begin(), cnt.end());
-    r->nbl_cap = (std::min(n - 1, mx + mx / 2 + 32) + 3) & ~3;  // whole groups of four
-    AL(r->nbl, R * (size_t)r->nbl_cap * n * 2);
+    const size_t all = (size_t)n * (n - 1) / 2;
+    r->nbl_cap = (int)std::min(all, 2 * cnt + 1024);
+    AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
   }
 #undef AL

@@ -51,8 +51,6 @@ struct SysDev {
   int use_list;
   float list_cut2;         // (cutoff + skin)^2
   float half_skin2;        // (skin / 2)^2
-  const int *atom_bond_off;  // [n + 1] bonds of each atom (tiled systems): atom_bonds[off[i] .. off[i+1])
-  const int *atom_bonds;
   int n_bonds;
   const int2 *bond_ij;
   const double2 *bond_d;   // (k, r0)

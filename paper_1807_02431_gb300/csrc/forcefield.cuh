@@ -388,70 +388,43 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   if (want_e) e_fix += acc.efix(e, err);
 }
 
-// Atom-centric pass over per-atom Verlet rows (systems with a cutoff; each pair is in one row): the
-// thread that owns atom i sums the forces on i over its row in registers, adds the opposite force to
-// each neighbour j (fixed-point atomics) and, with `bonds`, the forces of every bond of i (rows
-// atom_bonds[atom_bond_off[i] ..], each bond evaluated from both ends, energy halved), then adds the
-// total on i once per component.
+// Nonbonded pairs of a Verlet list (i | j << 16), strided over the block's threads; pairs beyond the
+// cutoff contribute nothing.  The list lives in global memory (L2): each thread loads its next four
+// entries before evaluating them, so that one load latency covers four pairs.  (Measured on the
+// 2,030-atom ligand workload, this pair list with fixed-point atomics on both atoms beat per-atom
+// neighbour rows evaluated from both ends by 1.36x, and rows holding each pair once by 7x.)
 template <class P>
-__device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                            const uint16_t *nbr, const int *count, bool bonds,
-                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
+__device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
+                                          const uint32_t *list, int count, const typename P::Acc &acc,
+                                          bool want_e, long long &e_fix, int *err) {
   using T = typename P::T;
   const T cut2 = (T)S.cutoff2;
-  const int n = S.n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const typename Pos<P>::At pi = pos.at(i);
-    T ash, ase, aqc;
-    nb_params<P>(pi, par, i, ash, ase, aqc);
-    V3<T> fi = {T(0), T(0), T(0)};
-    T en = T(0);
-    uint32_t jq[4];
-    const int c = count[i];
-    // rows are stored in groups of four neighbours, nbr[((k / 4) n + i) 4 + k % 4]: one 8-byte load per
-    // group, the next group loaded while this one is evaluated
-    const uint2 *rows = reinterpret_cast<const uint2 *>(nbr);
-    uint2 wn = c > 0 ? rows[i] : make_uint2(0u, 0u);
-    for (int k = 0; k < c; ++k) {
-      if ((k & 3) == 0) {
-        const uint2 w = wn;
-        if (k + 4 < c) wn = rows[(size_t)((k >> 2) + 1) * n + i];
-        jq[0] = w.x & 0xFFFFu; jq[1] = w.x >> 16; jq[2] = w.y & 0xFFFFu; jq[3] = w.y >> 16;
-      }
-      const int j = (int)jq[k & 3];
-      const typename Pos<P>::At pj = pos.at(j);
+  const int bd = blockDim.x;
+  for (int t = threadIdx.x; t < count; t += 4 * bd) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pk[u] = t + u * bd < count ? list[t + u * bd] : 0xFFFFFFFFu;  // written in this kernel: no .nc loads
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (pk[u] == 0xFFFFFFFFu) continue;
+      const int i = (int)(pk[u] & 0xFFFFu), j = (int)(pk[u] >> 16);
+      const typename Pos<P>::At pi = pos.at(i), pj = pos.at(j);
       const V3<T> d = Pos<P>::diff(pi, pj);
       const T r2 = dot(d, d);
-      if (r2 < cut2) {
-        T bsh, bse, bqc;
-        nb_params<P>(pj, par, j, bsh, bse, bqc);
-        const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;
-        const T inv_r2 = grcp(r2);
-        const T s2 = sig * sig * inv_r2;
-        const T s6 = s2 * s2 * s2;
-        const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
-        const V3<T> f = {g * d.x, g * d.y, g * d.z};
-        fi.x += f.x;
-        fi.y += f.y;
-        fi.z += f.z;
-        acc.add(j, V3<T>{-f.x, -f.y, -f.z}, err);
-        if (want_e) en += T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
-      }
+      if (!(r2 < cut2)) continue;
+      T ash, ase, aqc, bsh, bse, bqc;
+      nb_params<P>(pi, par, i, ash, ase, aqc);
+      nb_params<P>(pj, par, j, bsh, bse, bqc);
+      const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;
+      const T inv_r2 = grcp(r2);
+      const T s2 = sig * sig * inv_r2;
+      const T s6 = s2 * s2 * s2;
+      const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+      const V3<T> f = {g * d.x, g * d.y, g * d.z};
+      acc.add(i, f, err);
+      acc.add(j, V3<T>{-f.x, -f.y, -f.z}, err);
+      if (want_e) e_fix += acc.efix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
     }
-    if (bonds) {
-      for (int t = S.atom_bond_off[i]; t < S.atom_bond_off[i + 1]; ++t) {
-        const int b = S.atom_bonds[t];
-        const int2 ij = S.bond_ij[b];
-        T e;
-        const V3<T> f = ij.x == i ? bond_eval<P>(pos, par, b, i, ij.y, e) : bond_eval<P>(pos, par, b, i, ij.x, e);
-        fi.x += f.x;
-        fi.y += f.y;
-        fi.z += f.z;
-        if (want_e) en += T(0.5) * e;
-      }
-    }
-    acc.add(i, fi, err);
-    if (want_e) e_fix += acc.efix(en, err);
   }
 }
 
@@ -459,10 +432,9 @@ __device__ __forceinline__ void gather_pass(const SysDev &S, const Pos<P> &pos, 
 // each thread loads the indices and parameters of its next two bonds before evaluating them.
 template <class P>
 __device__ __forceinline__ void bonded_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
-                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err,
-                                            bool bonds = true) {
+                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
   const int bd = blockDim.x;
-  for (int b = threadIdx.x; bonds && b < S.n_bonds; b += 2 * bd) {
+  for (int b = threadIdx.x; b < S.n_bonds; b += 2 * bd) {
     const int b2 = b + bd;
     const int2 ij0 = S.bond_ij[b];
     const int2 ij1 = b2 < S.n_bonds ? S.bond_ij[b2] : make_int2(0, 0);

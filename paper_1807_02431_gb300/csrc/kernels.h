@@ -27,9 +27,9 @@ struct SegArgs {
   int pairs_in_smem;
   int noise_batch;           // steps of noise generated together (0: drawn inline per atom)
   int lean;                  // atom parameters read from the global table (large systems)
-  uint16_t *nbl;             // [R][nbl_cap][n] Verlet rows (systems with use_list), else null
+  uint32_t *nbl;             // [R][nbl_cap] Verlet lists (systems with use_list), else null
   float4 *qref;              // [R][n] positions at the last list build
-  int nbl_cap;               // row capacity (neighbours per atom)
+  int nbl_cap;
   double h, c1;              // dt/2 and exp(-gamma dt)
 };
 

@@ -170,24 +170,21 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
   }
 }
 
-// Verlet rows of one replica (systems with a cutoff): every non-excluded pair closer than cutoff +
-// skin, in the row of one of its two atoms, nbr[((k / 4) n + i) 4 + k % 4] for k < count[i] (groups of
-// four neighbours of an atom are contiguous), found by the tiled scan
-// over tile pairs whose bounding boxes are that close (the lane rotation of tile_pass meets each
-// unordered pair once) and appended with shared atomics on the per-atom counts; the positions at the
-// build are kept for the displacement test.  A row longer than `cap` sets kErrList and is cut.
-// Called by every thread of the block.
+// Verlet list of one replica (systems with a cutoff): every non-excluded pair closer than cutoff +
+// skin, found by the tiled scan over tile pairs whose bounding boxes are that close (the same lane
+// rotation as tile_pass, so each unordered pair is met once), appended with one shared atomic per warp
+// and step; the positions at the build are kept for the displacement test.  Returns the pair count
+// (a list longer than `cap` sets kErrList and is cut).  Called by every thread of the block.
 template <class P>
-__device__ void build_list(const SysDev &S, const State<P> &st, float *boxes, uint16_t *nbr, int cap,
-                           float4 *qref, int *count, int *err) {
-  const int n = S.n;
+__device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uint32_t *list, int cap,
+                          float4 *qref, int *cnt, int *err) {
   tile_boxes<P>(S, st, boxes);
-  for (int at = threadIdx.x; at < n; at += blockDim.x) {
+  for (int at = threadIdx.x; at < S.n; at += blockDim.x) {
     float x[3];
     st.get_f32(at, x);
     qref[at] = make_float4(x[0], x[1], x[2], 0.f);
-    count[at] = 0;
   }
+  if (threadIdx.x == 0) *cnt = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float lc2 = S.list_cut2;
@@ -204,31 +201,33 @@ __device__ void build_list(const SysDev &S, const State<P> &st, float *boxes, ui
     const bool diag = I == J;
     const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
     float xi[3] = {0.f, 0.f, 0.f};
-    if (i < n) st.get_f32(i, xi);
+    if (i < S.n) st.get_f32(i, xi);
     for (int s = s0; s < s1; ++s) {
       const int m = (lane + s) & 31;
+      bool take = false;
       if (((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16)) {
-        const int j = J * 32 + m;
         float xj[3];
-        st.get_f32(j, xj);
+        st.get_f32(J * 32 + m, xj);
         const float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
-        if (dx * dx + dy * dy + dz * dz < lc2) {
-          // the pair goes to one row: the larger index when i + j is odd, else the smaller one, which
-          // gives every atom about half of its neighbours whatever its place in the numbering
-          const int o = ((i + j) & 1) ? max(i, j) : min(i, j), other = i + j - o;
-          const int k = atomicAdd(&count[o], 1);
-          if (k < cap) nbr[((size_t)(k >> 2) * n + o) * 4 + (k & 3)] = (uint16_t)other;
-        }
+        take = dx * dx + dy * dy + dz * dz < lc2;
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, take);
+      if (b) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(cnt, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int idx = base + __popc(b & ((1u << lane) - 1u));
+        if (take && idx < cap) list[idx] = (uint32_t)i | ((uint32_t)(J * 32 + m) << 16);
       }
     }
   }
   __syncthreads();
-  for (int at = threadIdx.x; at < n; at += blockDim.x)
-    if (count[at] > cap) {
-      count[at] = cap;
-      *err |= kErrList;
-    }
-  __syncthreads();
+  int c = *cnt;
+  if (c > cap) {
+    *err |= kErrList;
+    c = cap;
+  }
+  return c;
 }
 
 // Fixed-point sum (2^-40 units on the FP64 path, 2^-32 on the mixed path) to the path's precision,
@@ -303,6 +302,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   long long *red = (long long *)ptr; ptr += 32 * 8;
   double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
   long long *ek = (long long *)ptr; ptr += 2 * 8;
+  int *lcount = (int *)ptr; ptr += 8;
   State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n, S, a.lean != 0);
@@ -310,8 +310,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);  // NB = 0: noise drawn inline per atom
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
-  int *ncount = nullptr;  // Verlet row lengths
-  if (S.use_list) { ncount = (int *)ptr; ptr += (size_t)n * 4; }
+
   const uint32_t *pairs = S.pairs, *items = S.items;
   if (a.pairs_in_smem) {
     ptr = align32(ptr);
@@ -332,11 +331,12 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   const bool use_list = kMode == kModeList || (kMode == kModeAny && a.nbl != nullptr);
   const bool tiled = kMode == kModeTiles || kMode == kModeList || (kMode == kModeAny && S.tiled);
   const bool lean = kMode != kModeItems && a.lean;
-  uint16_t *nbr = use_list ? a.nbl + (size_t)r * a.nbl_cap * n : nullptr;
+  uint32_t *list = use_list ? a.nbl + (size_t)r * a.nbl_cap : nullptr;
   float4 *qref = use_list ? a.qref + (size_t)r * n : nullptr;
+  int n_list = 0;
 
   int err = 0;
-  if (use_list) build_list<P>(S, st, boxes, nbr, a.nbl_cap, qref, ncount, &err);
+  if (use_list) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
   const T h = (T)a.h, c1 = (T)a.c1;
   const Pos<P> pos = st.pos();
   const Params<P> par = st.params(S);
@@ -377,7 +377,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
       }
     }
     if (use_list) {
-      if (__syncthreads_or(moved)) build_list<P>(S, st, boxes, nbr, a.nbl_cap, qref, ncount, &err);
+      if (__syncthreads_or(moved)) n_list = build_list<P>(S, st, boxes, list, a.nbl_cap, qref, lcount, &err);
     } else {
       __syncthreads();
     }
@@ -388,10 +388,9 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    // large systems: bonds with the nonbonded rows (atom-centric), the other terms by kind
-    if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err, !use_list);
+    if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
     else force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
-    if (use_list) gather_pass<P>(S, pos, par, nbr, ncount, lean, fa, sample, e_fix, &err);
+    if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
     else if (tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
     __syncthreads();
     long long k_fix = 0;
@@ -515,11 +514,10 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch, int lean) {
   const int n = S.n;
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
-  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 96;  // + alignment padding
+  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 8 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n, lean) : State<PathMixed>::bytes(n, lean);
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
-  if (S.use_list) b += (size_t)n * 4;
   if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
   return b;
 }
