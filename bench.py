@@ -330,6 +330,18 @@ def profile_case(B, case, replicas, steps, launches):
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0)
         for _ in range(launches):
             B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
+    elif case == "batch":
+        systems = W.batched_chains(n_runs=16, n_replicas=replicas)
+        keep = []
+        for k, s in enumerate(systems):
+            sysh = B.grp_create_system(s, B.GRP_MIXED)
+            q0, p0 = W.replica_states(s, replicas, seed=3000 + k, spread=0.002)
+            keep.append((sysh, B.grp_init_replicas(sysh, replicas, SEED + k, q0, p0, per_replica=True)))
+        b = B.grp_batch_create([r for _, r in keep])
+        for _ in range(launches):
+            B.grp_batch_step_k(b, steps, 10)
+        torch.cuda.synchronize()
+        del b
     elif case == "ligand":
         s = W.ligand_receptor()
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0, omega=0)
@@ -388,7 +400,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--ligand-steps", type=int, default=3)
     ap.add_argument("--gradient-reps", type=int, default=2)
-    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint"], default=None,
+    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint", "batch"], default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
     ap.add_argument("--profile-replicas", type=int, default=152)
     ap.add_argument("--profile-steps", type=int, default=100)
