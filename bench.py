@@ -431,6 +431,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1807_02431_gb300 import binding as B
     from paper_1807_02431_gb300 import build as build_mod
+    from paper_1807_02431_gb300 import ranks
 
     if rank == 0 or not os.path.exists(build_mod.LIB):
         build_mod.build()
@@ -439,7 +440,7 @@ def main():
     B.load()
     s = W.chain()
     R = s.n_replicas
-    seed = SEED + 1000 * rank
+    seed = ranks.rank_seed(SEED, rank)
     step = Step(B, s, B.GRP_MIXED, R, seed, local)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     if world > 1:
@@ -452,9 +453,7 @@ def main():
     t_total = float(np.sum(times)) / 1e3
     units_per_step = R * s.n_atoms * s.t_check
     if world > 1:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+        t_total = ranks.max_over_ranks(t_total, device="cuda")
     value = world * units_per_step * args.steps / t_total
     clocks = clk.summary()
     out = None
