@@ -218,10 +218,20 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     }
     std::vector<uint32_t> pairs;
     if (!D.tiled) {
+      // Pairs in round-robin order (the circle method: each round pairs every atom once), so that the
+      // 32 pairs of a warp touch each atom a few times at most: the fixed-point additions of a warp to
+      // the same accumulator are serialised, and the row-major order put ~20 lanes on atom i.
       pairs.reserve((size_t)n * (n - 1) / 2);
-      for (int i = 0; i < n; ++i)
-        for (int j = i + 1; j < n; ++j)
-          if (!excl[(size_t)i * n + j]) pairs.push_back((uint32_t)i | ((uint32_t)j << 16));
+      const int m = n + (n & 1);  // with a dummy atom n when n is odd
+      std::vector<int> ring(m);
+      for (int r = 0; r < m - 1; ++r) {
+        ring[0] = 0;
+        for (int k = 1; k < m; ++k) ring[k] = 1 + (k - 1 + r) % (m - 1);
+        for (int k = 0; k < m / 2; ++k) {
+          const int i = std::min(ring[k], ring[m - 1 - k]), j = std::max(ring[k], ring[m - 1 - k]);
+          if (j < n && !excl[(size_t)i * n + j]) pairs.push_back((uint32_t)i | ((uint32_t)j << 16));
+        }
+      }
     } else {
       const int nt = (n + 31) / 32;
       std::vector<uint32_t> tps, masks;
@@ -302,25 +312,27 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     std::vector<int> tsrc;
     // Small systems (item table, idle lanes): one item per term, so that the terms of a torsion run
     // in parallel; larger systems: one item per torsion whose terms share the geometry.
+    // (per term, the items run term-major -- every torsion's first term, then every second term -- so
+    // that the terms of one torsion, which add to the same four atoms, fall in different warps.)
     const bool per_term = !D.tiled;
-    for (auto &key : order) {
-      const int4 ijkl = make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key));
-      const int t0 = (int)td.size();
-      for (int t : groups[key]) {
-        td.push_back(make_double4(d->dihedral_k[t], (double)d->dihedral_n[t], std::cos(d->dihedral_delta[t]),
-                                  std::sin(d->dihedral_delta[t])));
-        tf.push_back(make_float4((float)td.back().x, (float)td.back().y, (float)td.back().z, (float)td.back().w));
-        tsrc.push_back(t);
-        if (per_term) {
-          dijkl.push_back(ijkl);
-          dterms.push_back(make_int2((int)td.size() - 1, (int)td.size()));
+    size_t max_terms = 0;
+    for (auto &key : order) max_terms = std::max(max_terms, groups[key].size());
+    for (size_t level = 0; level < (per_term ? max_terms : 1); ++level)
+      for (auto &key : order) {
+        const int4 ijkl = make_int4(std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key));
+        const std::vector<int> &g = groups[key];
+        if (per_term && level >= g.size()) continue;
+        const int t0 = (int)td.size();
+        for (size_t u = per_term ? level : 0; u < (per_term ? level + 1 : g.size()); ++u) {
+          const int t = g[u];
+          td.push_back(make_double4(d->dihedral_k[t], (double)d->dihedral_n[t], std::cos(d->dihedral_delta[t]),
+                                    std::sin(d->dihedral_delta[t])));
+          tf.push_back(make_float4((float)td.back().x, (float)td.back().y, (float)td.back().z, (float)td.back().w));
+          tsrc.push_back(t);
         }
-      }
-      if (!per_term) {
         dijkl.push_back(ijkl);
         dterms.push_back(make_int2(t0, (int)td.size()));
       }
-    }
     D.n_dih = (int)dijkl.size();
     // work items: pairs, bonds, angles, dihedrals, each kind padded to a multiple of 32 entries
     std::vector<uint32_t> items;
