@@ -335,15 +335,34 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       }
     D.n_dih = (int)dijkl.size();
     // work items: pairs, bonds, angles, dihedrals, each kind padded to a multiple of 32 entries
+    // Within a kind the items run in greedy rounds of atom-disjoint items (like the round-robin pairs),
+    // so that neighbouring lanes rarely add to the same atom's accumulator.
     std::vector<uint32_t> items;
-    auto add_kind = [&](uint32_t kind, int count) {
-      for (int i = 0; i < count; ++i) items.push_back((kind << 28) | (uint32_t)i);
+    auto add_kind = [&](uint32_t kind, int count, auto atoms_of) {
+      std::vector<int> left(count);
+      for (int i = 0; i < count; ++i) left[i] = i;
+      std::vector<int> used(n, -1);
+      for (int round = 0; !left.empty(); ++round) {
+        std::vector<int> later;
+        for (int it : left) {
+          const int4 a = atoms_of(it);
+          const int at[4] = {a.x, a.y, a.z, a.w};
+          bool free = true;
+          for (int u = 0; u < 4; ++u) free = free && (at[u] < 0 || used[at[u]] != round);
+          if (!free) { later.push_back(it); continue; }
+          for (int u = 0; u < 4; ++u) if (at[u] >= 0) used[at[u]] = round;
+          items.push_back((kind << 28) | (uint32_t)it);
+        }
+        left.swap(later);
+      }
       while (items.size() % 32) items.push_back((uint32_t)kItemNone << 28);
     };
-    add_kind(kItemPair, D.n_pairs);
-    add_kind(kItemBond, D.n_bonds);
-    add_kind(kItemAngle, D.n_angles);
-    add_kind(kItemDihedral, D.n_dih);
+    add_kind(kItemPair, D.n_pairs, [&](int t) {
+      return make_int4((int)(pairs[t] & 0xFFFFu), (int)(pairs[t] >> 16), -1, -1);
+    });
+    add_kind(kItemBond, D.n_bonds, [&](int t) { return make_int4(bij[t].x, bij[t].y, -1, -1); });
+    add_kind(kItemAngle, D.n_angles, [&](int t) { return make_int4(aijk[t].x, aijk[t].y, aijk[t].z, -1); });
+    add_kind(kItemDihedral, D.n_dih, [&](int t) { return dijkl[t]; });
     if (D.n_pairs >= (1 << 28) || items.size() >= (size_t)1 << 31) {
       grp_destroy_system(s);
       return fail(GRP_ENOTIMPL, "too many force-field items (%zu)", items.size());
