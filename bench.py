@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 from paper_1807_02431_gb300 import workloads as W  # noqa: E402
 
 WORKLOAD = "chain22_r256"
+# DRAM bytes (read + write) of one launch of the chain's segment kernel in this workload, from an ncu
+# capture of the current kernel (511,744 read, 0 written: the replicas' state is read once and stays on
+# chip); to be re-measured whenever the kernel changes.
+SEGMENT_DRAM_BYTES = 511744
 SEED = 2431
 
 
@@ -465,7 +469,7 @@ def main():
         peak = fp32_peak_tflops(2070.0)
         achieved = flops / (seg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems>",
+                "traffic": SEGMENT_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems>",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
                 "kernel_ms": seg_ms, "flops_per_launch": flops, "median_sm_mhz": sm_mhz}
         # plain FP64 GPU path, same step
