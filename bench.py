@@ -498,10 +498,11 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cores = os.cpu_count() or 1
-            cv, cwall = cpu_oracle(R, 500, cores)
+            cv, cwall = cpu_oracle(R, 10 * s.t_check, cores)
             cpu = {"value": cv, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{R} replicas x 500 BAOAB steps (one t_check segment, sampling every {s.t_gr}) "
-                             f"+ exit test, split over {cores} spawned processes; wall {cwall:.2f} s"}
+                   "sample": f"{R} replicas x {10 * s.t_check} BAOAB steps (ten t_check segments, sampling every "
+                             f"{s.t_gr}) + exit test, split over {cores} spawned processes; wall {cwall:.2f} s "
+                             f"({cwall * cores:.0f} core-seconds)"}
         out = {"metric": "replica-atom-steps/s", "value": value, "unit": "replica-atom-steps/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

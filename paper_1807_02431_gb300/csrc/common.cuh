@@ -242,4 +242,27 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *scratc
   return t;
 }
 
+// Two block-wide int64 sums in one pass (scratch >= 64 entries); the results are valid in thread 0.
+__device__ __forceinline__ void block_sum2_ll(long long &a, long long &b, long long *scratch) {
+  const int kThreads = (int)blockDim.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { scratch[warp] = a; scratch[32 + warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    const bool in = lane < (kThreads + 31) / 32;
+    a = in ? scratch[lane] : 0;
+    b = in ? scratch[32 + lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
 }  // namespace grp

@@ -299,7 +299,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   const int n = S.n, nd = 3 * n, no = S.n_obs, NB = a.noise_batch;
   unsigned char *ptr = smem;
   long long *F = (long long *)ptr; ptr += (size_t)nd * 8;
-  long long *red = (long long *)ptr; ptr += 32 * 8;
+  long long *red = (long long *)ptr; ptr += 64 * 8;
   double *acc = (double *)ptr; ptr += kMaxObs * 4 * 8;
   long long *ek = (long long *)ptr; ptr += 2 * 8;
   int *lcount = (int *)ptr; ptr += 8;
@@ -406,9 +406,8 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
       }
     }
     if (sample) {
-      const long long es = block_sum_ll(e_fix, red);
-      const long long ks = block_sum_ll(k_fix, red);
-      if (threadIdx.x == 0) { ek[0] = es; ek[1] = ks; }
+      block_sum2_ll(e_fix, k_fix, red);
+      if (threadIdx.x == 0) { ek[0] = e_fix; ek[1] = k_fix; }
       __syncthreads();
       if (threadIdx.x < no)
         oacc.add(acc + 4 * threadIdx.x,
@@ -514,7 +513,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
 static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch, int lean) {
   const int n = S.n;
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
-  size_t b = (size_t)3 * n * 8 + 32 * 8 + kMaxObs * 4 * 8 + 16 + 8 + 96;  // + alignment padding
+  size_t b = (size_t)3 * n * 8 + 64 * 8 + kMaxObs * 4 * 8 + 16 + 8 + 96;  // + alignment padding
   b += S.precision == GRP_FP64 ? State<PathF64>::bytes(n, lean) : State<PathMixed>::bytes(n, lean);
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
