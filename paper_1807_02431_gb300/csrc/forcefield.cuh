@@ -174,8 +174,9 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
 // Off-diagonal tiles take s = 0..31; a diagonal tile takes s = 1..16 (lanes 16..31 skip s = 16), which
 // meets every unordered pair once.  Per lane and tile pair the FP32 (FP64) sums are converted to fixed
 // point once, so the result does not depend on which warp takes which tile pair, or in which order.
-// With a cutoff, tile pairs whose bounding boxes are further apart than the cutoff are skipped.
-template <class P>
+// With a cutoff, tile pairs whose bounding boxes are further apart than the cutoff are skipped; kCutoff =
+// false drops the cutoff tests (the segment kernel's tile path, taken only by systems without a cutoff).
+template <class P, bool kCutoff = true>
 __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                           const typename P::Acc &acc, const float *boxes, bool want_e,
                                           long long &e_fix, int *err) {
@@ -185,16 +186,18 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
   for (int tp = warp; tp < S.n_tile_pairs; tp += nwarps) {
     const uint32_t e = S.tile_pairs[tp];
     const int I = (int)(e & 0xFFFFu), J = (int)(e >> 16);
-    if (boxes) {  // gap between the two tiles' boxes
+    if (kCutoff && boxes) {  // gap between the two tiles' boxes
       const float *a = boxes + 6 * I, *b = boxes + 6 * J;
       const float gx = fmaxf(0.f, fmaxf(a[0] - b[3], b[0] - a[3]));
       const float gy = fmaxf(0.f, fmaxf(a[1] - b[4], b[1] - a[4]));
       const float gz = fmaxf(0.f, fmaxf(a[2] - b[5], b[2] - a[5]));
       if (gx * gx + gy * gy + gz * gz >= (float)S.cutoff2) continue;
     }
-    const uint32_t mask = S.tile_masks[(size_t)tp * 32 + lane];
+    uint32_t mask = S.tile_masks[(size_t)tp * 32 + lane];
     const int i = I * 32 + lane, j0 = J * 32;
     const bool diag = I == J;
+    // on a diagonal tile, step 16 meets lane l and lane l + 16 twice: lanes 16..31 drop that pair
+    if (diag && lane >= 16) mask &= ~(1u << (lane - 16));
     const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
     V3<T> fi = {T(0), T(0), T(0)}, fj = {T(0), T(0), T(0)};
     T en = T(0);
@@ -206,13 +209,13 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
 #pragma unroll 4
     for (int s = s0; s < s1; ++s) {
       const int m = (lane + s) & 31;
-      const bool on = ((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16);
+      const bool on = (mask >> m) & 1u;
       if (on) {
         const int j = j0 + m;
         const typename Pos<P>::At pj = pos.at(j);
         const V3<T> d = Pos<P>::diff(pi, pj);
         const T r2 = dot(d, d);
-        if (!(cut2 > T(0) && r2 >= cut2)) {
+        if (!kCutoff || !(cut2 > T(0) && r2 >= cut2)) {
           T bsh, bse, bqc;
           nb_params<P>(pj, par, j, bsh, bse, bqc);
           const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;

@@ -391,7 +391,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
     else force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
     if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
-    else if (tiled) tile_pass<P>(S, pos, par, fa, boxes, sample, e_fix, &err);
+    else if (tiled) tile_pass<P, false>(S, pos, par, fa, boxes, sample, e_fix, &err);  // tiles: no cutoff
     __syncthreads();
     long long k_fix = 0;
     if (kMode == kModeItems || NB > 0) {
