@@ -11,9 +11,22 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace grp;
+
+namespace {
+// NVTX range over one host call (the phases of Fig. 1 as they appear on a profiler's timeline);
+// without a profiler attached the calls return at once.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 namespace {
 thread_local std::string g_last_error;
@@ -549,6 +562,7 @@ static grp_status run_steps(grp_replicas *r, long long k, int t_gr, int n_active
 }
 
 extern "C" grp_status grp_step_k(grp_replicas *r, int64_t k, int32_t t_gr, int32_t n_active, void *stream) {
+  const Range range("grp_step_k");
   if (!r) return fail(GRP_EINVAL, "grp_step_k: null handle");
   if (k < 0 || t_gr < 0 || n_active < 0 || n_active > r->R) return fail(GRP_EINVAL, "grp_step_k: bad k/t_gr/n_active");
   return run_steps(r, k, t_gr, n_active ? n_active : r->R, 0, 0, 0, 0, (cudaStream_t)stream);
@@ -697,6 +711,7 @@ static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, con
 }
 
 extern "C" grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, void *stream) {
+  const Range range("grp_batch_step_k");
   if (!b || k < 0 || t_gr < 0) return fail(GRP_EINVAL, "grp_batch_step_k: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   while (k > 0) {
@@ -710,6 +725,7 @@ extern "C" grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, vo
 
 extern "C" grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, int32_t t_check, int32_t t_gr,
                                          double tol, int64_t min_fv_steps, grp_fv_status *h_out, void *stream) {
+  const Range range("grp_batch_fv_check (exit test)");
   if (!b || !h_omega || !h_out || t_check < 1 || t_check > kMaxSegment || t_gr < 0)
     return fail(GRP_EINVAL, "grp_batch_fv_check: bad argument (t_check must be in [1, %lld])", kMaxSegment);
   cudaStream_t st = (cudaStream_t)stream;
@@ -864,6 +880,7 @@ static grp_status parallel_phase(grp_replicas *r, int omega, int t_check, long l
 
 extern "C" grp_status grp_run_parallel_phase(grp_replicas *r, int32_t omega, int32_t t_check, int64_t max_checks,
                                              grp_exit *h_out, void *stream) {
+  const Range range("grp_run_parallel_phase (Eq. 5)");
   if (!r || !h_out) return fail(GRP_EINVAL, "grp_run_parallel_phase: null argument");
   if (t_check < 1 || max_checks < 1) return fail(GRP_EINVAL, "grp_run_parallel_phase: t_check, max_checks >= 1");
   cudaStream_t st = (cudaStream_t)stream;
@@ -918,6 +935,7 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
 
 extern "C" grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_check, int32_t t_gr, double tol,
                                    int64_t min_fv_steps, grp_fv_status *h_out, void *stream) {
+  const Range range("grp_fv_check (convergence step)");
   if (!r || !h_out) return fail(GRP_EINVAL, "grp_fv_check: null argument");
   if (t_check < 1 || t_gr < 0) return fail(GRP_EINVAL, "grp_fv_check: need t_check >= 1, t_gr >= 0");
   return fv_check(r, omega, t_check, t_gr, tol, min_fv_steps, h_out, (cudaStream_t)stream);
@@ -926,6 +944,7 @@ extern "C" grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_che
 // ------------------------------------------------------------------------------------------------
 extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
                               int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
+  const Range range("grp_run (Fig. 1)");
   if (!r || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_run: null argument");
   if (p->t_gr < 1 || p->t_check < 1 || !(p->tol > 0)) return fail(GRP_EINVAL, "grp_run: need t_gr, t_check >= 1, tol > 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1136,6 +1155,7 @@ extern "C" grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const doubl
 extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_gr, int32_t checkpoint,
                                           const grp_loss *loss, double *h_loss, double *d_grad_theta,
                                           double *d_grad_q0, double *d_grad_p0, void *stream) {
+  const Range range("grp_adjoint_segment");
   if (!r || !loss || k < 1 || t_gr < 1 || checkpoint < 1 || k > (1 << 30))
     return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
   const grp_system *s = r->sys;
