@@ -169,8 +169,8 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
 
 // Tiled nonbonded pass: each warp takes tile pairs (I, J); lane l owns atom i = 32 I + l and, at
 // rotation step s, meets atom j = 32 J + ((l + s) mod 32).  The force on i accumulates in registers;
-// the force on j accumulates in a register that moves one lane down after every step (a warp
-// shuffle), so that it always sits in the lane currently meeting atom j and ends in a known lane.
+// the force on j accumulates in registers that move down the lanes by warp shuffles, so that they
+// always sit in the lane currently meeting atom j and end in known lanes.
 // Off-diagonal tiles take s = 0..31; a diagonal tile takes s = 1..16 (lanes 16..31 skip s = 16), which
 // meets every unordered pair once.  Per lane and tile pair the FP32 (FP64) sums are converted to fixed
 // point once, so the result does not depend on which warp takes which tile pair, or in which order.
@@ -199,18 +199,16 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
     // on a diagonal tile, step 16 meets lane l and lane l + 16 twice: lanes 16..31 drop that pair
     if (diag && lane >= 16) mask &= ~(1u << (lane - 16));
     const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
-    V3<T> fi = {T(0), T(0), T(0)}, fj = {T(0), T(0), T(0)};
+    V3<T> fi = {T(0), T(0), T(0)}, fja = {T(0), T(0), T(0)}, fjb = {T(0), T(0), T(0)};
     T en = T(0);
     // atom i in registers (padding lanes read a valid atom and have an empty mask)
     const int ic = i < S.n ? i : S.n - 1;
     const typename Pos<P>::At pi = pos.at(ic);
     T ash, ase, aqc;
     nb_params<P>(pi, par, ic, ash, ase, aqc);
-#pragma unroll 4
-    for (int s = s0; s < s1; ++s) {
+    auto meet = [&](int s, V3<T> &fj) {
       const int m = (lane + s) & 31;
-      const bool on = (mask >> m) & 1u;
-      if (on) {
+      if ((mask >> m) & 1u) {
         const int j = j0 + m;
         const typename Pos<P>::At pj = pos.at(j);
         const V3<T> d = Pos<P>::diff(pi, pj);
@@ -229,13 +227,26 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
           if (want_e) en += T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
         }
       }
-      fj.x = __shfl_sync(0xffffffffu, fj.x, (lane + 1) & 31);
-      fj.y = __shfl_sync(0xffffffffu, fj.y, (lane + 1) & 31);
-      fj.z = __shfl_sync(0xffffffffu, fj.z, (lane + 1) & 31);
+    };
+    // Steps go in pairs: the j forces of even steps ride in fja, those of odd steps in fjb, and both
+    // move two lanes down after each pair, so each register waits on one shuffle per two steps
+    // instead of one per step.  s1 - s0 is even (32, or 16 on a diagonal tile).
+#pragma unroll 2
+    for (int s = s0; s < s1; s += 2) {
+      meet(s, fja);
+      meet(s + 1, fjb);
+      fja.x = __shfl_sync(0xffffffffu, fja.x, (lane + 2) & 31);
+      fja.y = __shfl_sync(0xffffffffu, fja.y, (lane + 2) & 31);
+      fja.z = __shfl_sync(0xffffffffu, fja.z, (lane + 2) & 31);
+      fjb.x = __shfl_sync(0xffffffffu, fjb.x, (lane + 2) & 31);
+      fjb.y = __shfl_sync(0xffffffffu, fjb.y, (lane + 2) & 31);
+      fjb.z = __shfl_sync(0xffffffffu, fjb.z, (lane + 2) & 31);
     }
     if (i < S.n) acc.add(i, fi, err);
-    const int ja = j0 + ((lane + s1) & 31);
-    if (ja < S.n) acc.add(ja, fj, err);
+    // after the last pair of steps lane l holds the j forces of atoms (l + s1) and (l + s1 + 1) mod 32
+    const int ja = j0 + ((lane + s1) & 31), jb = j0 + ((lane + s1 + 1) & 31);
+    if (ja < S.n) acc.add(ja, fja, err);
+    if (jb < S.n) acc.add(jb, fjb, err);
     if (want_e) e_fix += acc.efix(en, err);
   }
 }
