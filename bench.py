@@ -121,19 +121,23 @@ def _oracle_worker(args):
     return time.time() - t, int(ex.sum())
 
 
-def cpu_oracle(n_replicas: int, steps: int, cores: int):
+def cpu_oracle(n_replicas: int, steps: int, cores: int, repeats: int = 1):
     """The FP64 oracle on the host cores: the replicas of the sample split over `cores` spawned
-    processes (each single-threaded).  Returns replica-atom-steps/s and the wall time."""
+    processes (each single-threaded), `repeats` times with one pool.  Returns a list of
+    (replica-atom-steps/s, wall time) per repeat."""
     s = W.chain()
     chunks = np.array_split(np.arange(n_replicas), cores)
     tasks = [(int(c[0]), int(c[-1]) + 1, steps, 7) for c in chunks if len(c)]
     ctx = mp.get_context("spawn")
+    out = []
     with ctx.Pool(len(tasks)) as pool:
         pool.map(_oracle_worker, [(0, 1, 1, 7)] * len(tasks))  # start-up and build outside the clock
-        t = time.time()
-        pool.map(_oracle_worker, tasks)
-        wall = time.time() - t
-    return n_replicas * steps * s.n_atoms / wall, wall
+        for _ in range(repeats):
+            t = time.time()
+            pool.map(_oracle_worker, tasks)
+            wall = time.time() - t
+            out.append((n_replicas * steps * s.n_atoms / wall, wall))
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU step
@@ -362,9 +366,17 @@ def profile_case(B, case, replicas, steps, launches):
     print(json.dumps({"profile_case": case, "replicas": replicas, "steps": steps, "launches": launches}))
 
 
+def arm_config(s: W.System, R: int, world: int) -> dict:
+    """The `config` of the benchmark line (both arms)."""
+    return {"workload": WORKLOAD, "n_atoms": s.n_atoms, "n_replicas": R, "t_check": s.t_check, "t_gr": s.t_gr,
+            "precision": "mixed (FP32 forces, int64 fixed point, double-single integration)",
+            "parallelism": f"replicas-only x{world}",
+            "l2": "flushed between timed steps (256 MB write outside the events)"}
+
+
 def run_reference(args):
     """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
-    bounded sample: the 256 replicas advanced 20 steps with sampling and the exit test."""
+    bounded sample: the 256 replicas advanced 100 steps with sampling and the exit test."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -373,18 +385,14 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count() or 1
     s = W.chain()
-    R, steps = s.n_replicas, 20
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, wall = cpu_oracle(R, steps, cores)
-        if i >= args.warmup:
-            vals.append((v, wall))
+    R, steps = s.n_replicas, 100
+    vals = cpu_oracle(R, steps, cores, args.warmup + args.steps)[args.warmup:]
     value = float(np.mean([v for v, _ in vals]))
     ms = float(np.mean([w for _, w in vals])) * 1e3
     line = {"metric": "replica-atom-steps/s", "value": value, "unit": "replica-atom-steps/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "n_replicas": R, "steps_per_sample": steps},
+            "config": arm_config(s, R, args.gpus),
             "cpu_baseline": {"value": value, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{R} replicas x {steps} BAOAB steps (sampling every {s.t_gr}) + exit test, "
                                        f"split over {cores} processes"},
@@ -498,7 +506,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cores = os.cpu_count() or 1
-            cv, cwall = cpu_oracle(R, 10 * s.t_check, cores)
+            cv, cwall = cpu_oracle(R, 10 * s.t_check, cores)[0]
             cpu = {"value": cv, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
                    "sample": f"{R} replicas x {10 * s.t_check} BAOAB steps (ten t_check segments, sampling every "
                              f"{s.t_gr}) + exit test, split over {cores} spawned processes; wall {cwall:.2f} s "
@@ -507,10 +515,7 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "n_replicas": R, "t_check": s.t_check,
-                          "t_gr": s.t_gr, "precision": "mixed (FP32 forces, int64 fixed point, double-single "
-                          "integration)", "parallelism": f"replicas-only x{world}",
-                          "l2": "flushed between timed steps (256 MB write outside the events)"},
+               "config": arm_config(s, R, world),
                "gpu_launches": step.launches_per_step * args.steps,
                "roofline": roof, "clocks": clocks,
                "fp64_path": fp64,
