@@ -5,6 +5,12 @@
 
 namespace grp {
 
+// Noise amplitude sqrt((1 - c1^2) kT m) of the O step, with explicitly rounded operations so that
+// every kernel computes the same bits (a contraction of 1 - c1^2 into an fma differs in the last bit).
+__device__ __forceinline__ double noise_scale(double c1, double kT, double m) {
+  return sqrt(__dmul_rn(__dmul_rn(__dadd_rn(1.0, -__dmul_rn(c1, c1)), kT), m));
+}
+
 __device__ __forceinline__ unsigned char *align32(unsigned char *p) {
   return (unsigned char *)(((uintptr_t)p + 31) & ~(uintptr_t)31);
 }
@@ -51,7 +57,7 @@ struct State<PathF64> {
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
       if (own_atom) const_cast<double4 *>(atom)[at] = S.atom_d[at];
-      sd[at] = sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
+      sd[at] = noise_scale(c1, S.kT, S.mass[at]);
     }
   }
   __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
@@ -137,7 +143,7 @@ struct State<PathMixed> {
       qh[at] = make_float4(x.hi, y.hi, z.hi, pa.x);  // fourth words: sigma/2 and sqrt(eps) (nb_params)
       ql[at] = make_float4(x.lo, y.lo, z.lo, pa.y);
       if (own_atom) const_cast<float4 *>(atom)[at] = pa;
-      sd[at] = (float)sqrt((1.0 - c1 * c1) * S.kT * S.mass[at]);
+      sd[at] = (float)noise_scale(c1, S.kT, S.mass[at]);
     }
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
       const ds v = ds_from_double(gp[i]);
