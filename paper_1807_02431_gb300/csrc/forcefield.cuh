@@ -422,7 +422,20 @@ __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, co
     for (int u = 0; u < 4; ++u) {
       if (pk[u] == 0xFFFFFFFFu) continue;
       const int i = (int)(pk[u] & 0xFFFFu), j = (int)(pk[u] >> 16);
-      const typename Pos<P>::At pi = pos.at(i), pj = pos.at(j);
+      typename Pos<P>::At pi, pj;
+      if constexpr (P::kMixed) {
+        // screen on the high words alone (their distance is within ~1e-6 of the double-single one):
+        // the list's pairs beyond the cutoff, about half of them, skip the low-word loads
+        pi.h = pos.qh[i];
+        pj.h = pos.qh[j];
+        const float hx = pi.h.x - pj.h.x, hy = pi.h.y - pj.h.y, hz = pi.h.z - pj.h.z;
+        if (hx * hx + hy * hy + hz * hz > cut2 * 1.0001f) continue;
+        pi.l = pos.ql[i];
+        pj.l = pos.ql[j];
+      } else {
+        pi = pos.at(i);
+        pj = pos.at(j);
+      }
       const V3<T> d = Pos<P>::diff(pi, pj);
       const T r2 = dot(d, d);
       if (!(r2 < cut2)) continue;
