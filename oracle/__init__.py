@@ -19,7 +19,7 @@ _lib = None
 MAX_OBS = 8
 MAX_GROUPS = 4
 
-EV_TRANSIENT, EV_REF_EXIT, EV_FV_CONVERGED, EV_PARALLEL_EXIT, EV_FV_ALL_EXITED = range(5)
+EV_TRANSIENT, EV_REF_EXIT, EV_FV_CONVERGED, EV_PARALLEL_EXIT, EV_FV_ALL_EXITED, EV_DECORRELATED, EV_DEPHASED = range(7)
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +77,11 @@ class OrcRunParams(C.Structure):
                 ("max_exits", C.c_int32)]
 
 
+class OrcOriginalParams(C.Structure):
+    _fields_ = [("n_rep", C.c_int32), ("seed", C.c_uint64), ("t_check", C.c_int32), ("t_corr", C.c_int64),
+                ("t_phase", C.c_int64), ("max_steps", C.c_int64), ("max_exits", C.c_int32)]
+
+
 _D = C.POINTER(C.c_double)
 _I32 = C.POINTER(C.c_int32)
 _I64 = C.POINTER(C.c_int64)
@@ -121,6 +126,9 @@ def lib():
         L.orc_parallel_phase.restype = C.c_int32
         L.orc_parallel_phase.argtypes = [C.c_void_p, C.c_int32, _D, _D, _D, C.c_uint64, C.c_int64,
                                          C.c_int32, C.c_int32, C.c_int64, C.POINTER(OrcExit)]
+        L.orc_run_original.restype = C.c_int32
+        L.orc_run_original.argtypes = [C.c_void_p, C.POINTER(OrcOriginalParams), _D, _D, C.POINTER(OrcEvent),
+                                       C.c_int32, _I64]
         L.orc_run_genparrep.restype = C.c_int32
         L.orc_run_genparrep.argtypes = [C.c_void_p, C.POINTER(OrcRunParams), _D, _D,
                                         C.POINTER(OrcEvent), C.c_int32, _I64]
@@ -279,6 +287,20 @@ class Oracle:
         ev = (OrcEvent * max_events)()
         tg = C.c_int64(0)
         n = lib().orc_run_genparrep(self.ctx, C.byref(rp), _dp(q0), _dp(p0), ev, max_events, C.byref(tg))
+        events = [{"kind": e.kind, "omega": e.omega, "label_to": e.label_to, "k": e.k, "M": e.M,
+                   "steps": e.steps, "t_sim": e.t_sim, "n_branch": e.n_branch} for e in ev[:n]]
+        return events, tg.value
+
+    def run_original(self, n_rep, seed, t_check, t_corr, t_phase, max_steps, max_exits, q0=None, p0=None,
+                     max_events=100000):
+        """The original ParRep loop (decorrelation, dephasing, parallel step); returns (events, t_global)."""
+        s = self.system
+        q0 = _c64(s.q0 if q0 is None else q0)
+        p0 = _c64(s.p0 if p0 is None else p0)
+        rp = OrcOriginalParams(n_rep, seed, t_check, t_corr, t_phase, max_steps, max_exits)
+        ev = (OrcEvent * max_events)()
+        tg = C.c_int64(0)
+        n = lib().orc_run_original(self.ctx, C.byref(rp), _dp(q0), _dp(p0), ev, max_events, C.byref(tg))
         events = [{"kind": e.kind, "omega": e.omega, "label_to": e.label_to, "k": e.k, "M": e.M,
                    "steps": e.steps, "t_sim": e.t_sim, "n_branch": e.n_branch} for e in ev[:n]]
         return events, tg.value

@@ -819,6 +819,135 @@ int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const doub
   return nev < max_events ? nev : max_events;
 }
 
+/* ---------------------------------------------------------------- original ParRep (Section 2.4.3)
+ * Transient as in Gen. ParRep; decorrelation: the reference walker alone for t_corr steps in its state
+ * (checked every t_check); dephasing: every replica r >= 1 advances until it has stayed t_phase steps in
+ * the state since its last (re)start from the decorrelated reference, the dephasing time not counted
+ * in the clock; parallel step: Eq. 5 from the dephased configurations (replica 0 keeps the
+ * decorrelated one). */
+int32_t orc_run_original(const orc_ctx *c, const orc_original_params *rp, const double *q0,
+                         const double *p0, orc_event *events, int32_t max_events, int64_t *t_global_out) {
+  const orc_system *s = &c->s;
+  int N = rp->n_rep, nd = s->n_atoms * s->dim;
+  size_t bytes = sizeof(double) * (size_t)N * nd;
+  double *q = (double *)malloc(bytes), *p = (double *)malloc(bytes), *f = (double *)malloc(bytes);
+  double *sq = (double *)malloc(bytes), *sp = (double *)malloc(bytes), *sf = (double *)malloc(bytes);
+  int64_t *stay = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+  uint8_t *done = (uint8_t *)malloc((size_t)N);
+  memcpy(q, q0, sizeof(double) * nd);
+  memcpy(p, p0, sizeof(double) * nd);
+  orc_forces(c, q, f);
+  int64_t tg = 0, tsim = 0;
+  int nev = 0, nexit = 0;
+#define LOG_EVENT(KIND, OM, TO, KK, MM, STEPS, NB)                                          \
+  do {                                                                                     \
+    if (nev < max_events) {                                                                \
+      orc_event e_ = {(KIND), (OM), (TO), (KK), (MM), (STEPS), tsim, (NB)};                \
+      events[nev] = e_;                                                                    \
+    }                                                                                      \
+    nev++;                                                                                 \
+  } while (0)
+#define COPY_REPLICA(DQ, DP, DF, DR, SQ, SP, SF, SR)                                       \
+  do {                                                                                     \
+    memcpy((DQ) + (size_t)(DR) * nd, (SQ) + (size_t)(SR) * nd, sizeof(double) * nd);       \
+    memcpy((DP) + (size_t)(DR) * nd, (SP) + (size_t)(SR) * nd, sizeof(double) * nd);       \
+    memcpy((DF) + (size_t)(DR) * nd, (SF) + (size_t)(SR) * nd, sizeof(double) * nd);       \
+  } while (0)
+
+  while (nexit < rp->max_exits && tg < rp->max_steps && nev < max_events) {
+    /* 1. transient propagation of the reference walker */
+    int64_t treach = 0;
+    int omega = orc_state_of(c, q);
+    while (omega < 0 && tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) orc_baoab_step(c, q, p, f, rp->seed, 0, tg++);
+      treach += rp->t_check;
+      omega = orc_state_of(c, q);
+    }
+    if (omega < 0) break;
+    if (treach > 0) {
+      tsim += treach;
+      LOG_EVENT(ORC_EV_TRANSIENT, -1, omega, 0, 0, treach, 0);
+    }
+    /* 2. decorrelation: the reference walker must stay t_corr steps in omega */
+    int64_t d = 0;
+    int ref_exit = 0;
+    while (d < rp->t_corr && tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) orc_baoab_step(c, q, p, f, rp->seed, 0, tg++);
+      d += rp->t_check;
+      if (orc_exited(c, q, omega)) {
+        tsim += d;
+        LOG_EVENT(ORC_EV_REF_EXIT, omega, orc_state_of(c, q), 0, 0, d, 0);
+        nexit++;
+        ref_exit = 1;
+        break;
+      }
+    }
+    if (ref_exit) continue;
+    if (d < rp->t_corr) break;
+    tsim += d;
+    LOG_EVENT(ORC_EV_DECORRELATED, omega, omega, 0, 0, d, 0);
+    /* 3. dephasing: replicas restart from the decorrelated reference until each has stayed t_phase */
+    COPY_REPLICA(sq, sp, sf, 0, q, p, f, 0);
+    for (int r = 1; r < N; ++r) COPY_REPLICA(q, p, f, r, q, p, f, 0);
+    for (int r = 0; r < N; ++r) { stay[r] = 0; done[r] = (uint8_t)(r == 0); }
+    int64_t dsteps = 0, restarts = 0;
+    int n_done = 1;
+    while (n_done < N && tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) {
+        for (int r = 0; r < N; ++r)
+          orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, rp->seed, r, tg);
+        tg++;
+      }
+      dsteps += rp->t_check;
+      for (int r = 1; r < N; ++r) {
+        if (done[r]) continue;
+        if (orc_exited(c, q + (size_t)r * nd, omega)) {
+          COPY_REPLICA(q, p, f, r, sq, sp, sf, 0);
+          stay[r] = 0;
+          restarts++;
+        } else {
+          stay[r] += rp->t_check;
+          if (stay[r] >= rp->t_phase) {
+            COPY_REPLICA(sq, sp, sf, r, q, p, f, r);
+            done[r] = 1;
+            n_done++;
+          }
+        }
+      }
+    }
+    if (n_done < N) break;
+    LOG_EVENT(ORC_EV_DEPHASED, omega, omega, 0, 0, dsteps, restarts);
+    memcpy(q, sq, bytes);
+    memcpy(p, sp, bytes);
+    memcpy(f, sf, bytes);
+    /* 4. parallel dynamics step, Eqs. 5-6 */
+    int64_t M = 0;
+    int found = -1;
+    while (tg < rp->max_steps) {
+      for (int i = 0; i < rp->t_check; ++i) {
+        for (int r = 0; r < N; ++r)
+          orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, rp->seed, r, tg);
+        tg++;
+      }
+      M++;
+      for (int r = 0; r < N; ++r)
+        if (orc_exited(c, q + (size_t)r * nd, omega)) { found = r; break; }
+      if (found >= 0) break;
+    }
+    if (found < 0) break;
+    int64_t tau = ((int64_t)N * (M - 1) + (found + 1)) * (int64_t)rp->t_check;
+    tsim += tau;
+    LOG_EVENT(ORC_EV_PARALLEL_EXIT, omega, orc_state_of(c, q + (size_t)found * nd), found + 1, M, tau, 0);
+    nexit++;
+    COPY_REPLICA(q, p, f, 0, q, p, f, found);
+  }
+#undef LOG_EVENT
+#undef COPY_REPLICA
+  if (t_global_out) *t_global_out = tg;
+  free(q); free(p); free(f); free(sq); free(sp); free(sf); free(stay); free(done);
+  return nev < max_events ? nev : max_events;
+}
+
 /* ---------------------------------------------------------------- brute-force reference dynamics */
 int32_t orc_run_bruteforce(const orc_ctx *c, uint64_t seed, int32_t t_check, const double *q0,
                            const double *p0, int64_t max_steps, int64_t *residence,

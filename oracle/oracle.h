@@ -158,7 +158,7 @@ int32_t orc_parallel_phase(const orc_ctx *c, int32_t n_rep, double *q, double *p
 
 /* Events of the whole loop of Fig. 1. */
 enum { ORC_EV_TRANSIENT = 0, ORC_EV_REF_EXIT = 1, ORC_EV_FV_CONVERGED = 2, ORC_EV_PARALLEL_EXIT = 3,
-       ORC_EV_FV_ALL_EXITED = 4 };
+       ORC_EV_FV_ALL_EXITED = 4, ORC_EV_DECORRELATED = 5, ORC_EV_DEPHASED = 6 };
 typedef struct {
   int32_t kind;
   int32_t omega;     /* state the event belongs to (-1 for a transient) */
@@ -185,6 +185,26 @@ typedef struct {
 int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const double *q0,
                           const double *p0, orc_event *events, int32_t max_events,
                           int64_t *t_global);
+
+/* The original ParRep algorithm as Section 2.4.3 contrasts it with Gen. ParRep: decorrelation (the
+ * reference walker must stay t_corr steps in its state, tested every t_check steps; leaving earlier is
+ * a reference exit, clock += elapsed), then dephasing (replicas 1..N-1 start from the decorrelated
+ * reference; each advances until it has stayed t_phase steps in the state since its last start, a
+ * replica that leaves restarts from the decorrelated reference; the dephasing time is not counted in
+ * the clock and replica 0 keeps the decorrelated configuration), then the parallel step of Eq. 5 from
+ * the dephased replicas.  Events: TRANSIENT, REF_EXIT, DECORRELATED (steps = t_corr reached),
+ * DEPHASED (steps = dephasing steps, n_branch = restarts), PARALLEL_EXIT.  All replicas advance in
+ * lockstep during dephasing (replica r draws the noise of replica r at the global step). */
+typedef struct {
+  int32_t n_rep;
+  uint64_t seed;
+  int32_t t_check;
+  int64_t t_corr, t_phase;
+  int64_t max_steps;
+  int32_t max_exits;
+} orc_original_params;
+int32_t orc_run_original(const orc_ctx *c, const orc_original_params *rp, const double *q0,
+                         const double *p0, orc_event *events, int32_t max_events, int64_t *t_global);
 
 /* Plain Langevin trajectory (replica index 0) checked every t_check steps; residence times (in
  * steps) from the check at which a state is entered to the check at which it is exited.  Returns
