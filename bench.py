@@ -223,23 +223,30 @@ def e2e_steps(B, step, K):
     return wall, 2 * nd * 8, nd * 8 + 8 * len(s.observables)
 
 
-def accelerated_speed(B, s, precision, R, seed, max_steps, max_exits=10 ** 6, unit_ns=True):
+def accelerated_speed(B, s, precision, R, seed, max_steps, max_exits=10 ** 6, unit_ns=True, original=False):
     """Simulated clock per wall time of the whole loop (Fig. 1): t_sim advances by t_reach, t_ref,
-    t_FV and tau (Eq. 6); speed = t_sim / wall as in Tables 2 and 4."""
+    t_FV and tau (Eq. 6); speed = t_sim / wall as in Tables 2 and 4.  original=True runs the original
+    ParRep loop (Section 2.4.3) with t_corr = t_phase = the minimum F-V time instead."""
     import torch
 
     sysh = B.grp_create_system(s, precision)
     rep = B.grp_init_replicas(sysh, R, seed, s.q0, s.p0)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    ev, tsim = B.grp_run(rep, s.t_gr, s.t_check, s.tol, s.min_fv_steps, max_steps, max_exits)
+    if original:
+        ev, tsim = B.grp_run_original(rep, s.t_check, s.min_fv_steps, s.min_fv_steps, max_steps, max_exits)
+    else:
+        ev, tsim = B.grp_run(rep, s.t_gr, s.t_check, s.tol, s.min_fv_steps, max_steps, max_exits)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t
     ctr = B.grp_get_state(rep)[3]
     sim = tsim * s.dt * (1e-3 if unit_ns else 1.0)
+    kinds = ((("transient", 0), ("decorrelated", 5), ("dephased", 6), ("ref_exit", 1), ("parallel_exit", 3))
+             if original else (("transient", 0), ("fv_converged", 2), ("ref_exit", 1), ("parallel_exit", 3)))
     out = {"t_sim": sim, "wall_s": wall, "global_steps": ctr["t_global"],
-           "events": {k: sum(1 for e in ev if e["kind"] == v) for k, v in
-                      (("transient", 0), ("fv_converged", 2), ("ref_exit", 1), ("parallel_exit", 3))}}
+           "events": {k: sum(1 for e in ev if e["kind"] == v) for k, v in kinds}}
+    if original:
+        out["loop"] = "original ParRep, t_corr = t_phase = %d steps" % s.min_fv_steps
     out["ns_per_day" if unit_ns else "time_units_per_day"] = sim / (wall / 86400.0)
     return out
 
@@ -503,6 +510,8 @@ def main():
             dw = W.double_well_2d()
             accel["double_well_2d"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
                                                         max_exits=8, unit_ns=False)
+            accel["double_well_2d_original"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
+                                                                 max_exits=8, unit_ns=False, original=True)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cores = os.cpu_count() or 1

@@ -137,8 +137,18 @@ typedef struct {
   int32_t max_exits;     /* stop after this many reference or parallel exits */
 } grp_run_params;
 
+/* Parameters of the original ParRep loop (Section 2.4.3): the decorrelation and dephasing times
+ * replace the Fleming-Viot convergence test. */
+typedef struct {
+  int32_t t_check;       /* exit-test period, steps */
+  int32_t max_exits;     /* stop after this many reference or parallel exits */
+  int64_t t_corr;        /* decorrelation time: the reference walker stays this long before the parallel step */
+  int64_t t_phase;       /* dephasing time: each replica's stay since its last restart */
+  int64_t max_steps;     /* bound on the global step counter */
+} grp_original_params;
+
 enum { GRP_EV_TRANSIENT = 0, GRP_EV_REF_EXIT = 1, GRP_EV_FV_CONVERGED = 2, GRP_EV_PARALLEL_EXIT = 3,
-       GRP_EV_FV_ALL_EXITED = 4 };
+       GRP_EV_FV_ALL_EXITED = 4, GRP_EV_DECORRELATED = 5, GRP_EV_DEPHASED = 6 };
 typedef struct {
   int32_t kind;
   int32_t omega;      /* state of the visit (-1 for a transient) */
@@ -249,6 +259,21 @@ grp_status grp_batch_autotune(grp_batch *b, int32_t t_gr, void *stream, int32_t 
  * events to h_events, their count to h_n_events, and the final clock to h_t_sim (optional). */
 grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
                    int32_t *h_n_events, int64_t *h_t_sim, void *stream);
+
+/* The original ParRep loop (Section 2.4.3) from the current state of replica 0.  Per visit of a
+ * state omega: transient as in grp_run; decorrelation, replica 0 alone checked every t_check until it
+ * has stayed t_corr steps (GRP_EV_DECORRELATED, counted in the clock) or left omega
+ * (GRP_EV_REF_EXIT, t_ref counted); dephasing, replicas 1..R-1 start from the decorrelated
+ * configuration, all R advance in lockstep, a replica that leaves omega restarts from that
+ * configuration and one that has stayed t_phase steps since its last start keeps that state as its
+ * sample (GRP_EV_DEPHASED: steps = the dephasing time, n_branch = the restarts; not counted in the
+ * clock); parallel step, Eq. 5 from the samples (replica 0 keeps the decorrelated one), the exit
+ * configuration becoming replica 0.  Events and the clock as for grp_run.  The dephasing keeps a
+ * second copy of q, p and F (3 R n dim doubles of device memory, allocated per call; GRP_ENOMEM
+ * when that fails).  GRP_EINVAL for t_check < 1, t_corr < 0 or t_phase < 0; t_corr and t_phase
+ * are rounded up to whole checks. */
+grp_status grp_run_original(grp_replicas *r, const grp_original_params *p, grp_event *h_events,
+                            int32_t max_events, int32_t *h_n_events, int64_t *h_t_sim, void *stream);
 
 /* Checkpoint and resume: copy positions, momenta, accumulators (each optional) and counters
  * between the replica set and host memory.  grp_set_state re-evaluates the forces. */

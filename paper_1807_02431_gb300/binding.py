@@ -22,7 +22,8 @@ GRP_EINVAL, GRP_ENOMEM, GRP_ECUDA, GRP_ENAN, GRP_EOVERFLOW, GRP_ETIMEOUT, GRP_EN
 GRP_NOEXIT = 1
 GRP_FP64, GRP_MIXED = 0, 1
 GRP_MAX_OBS, GRP_MAX_GROUPS = 8, 4
-EV_TRANSIENT, EV_REF_EXIT, EV_FV_CONVERGED, EV_PARALLEL_EXIT, EV_FV_ALL_EXITED = range(5)
+(EV_TRANSIENT, EV_REF_EXIT, EV_FV_CONVERGED, EV_PARALLEL_EXIT, EV_FV_ALL_EXITED, EV_DECORRELATED,
+ EV_DEPHASED) = range(7)
 
 _lib = None
 
@@ -73,6 +74,11 @@ class RunParams(C.Structure):
                 ("max_steps", C.c_int64), ("max_exits", C.c_int32)]
 
 
+class OriginalParams(C.Structure):
+    _fields_ = [("t_check", C.c_int32), ("max_exits", C.c_int32), ("t_corr", C.c_int64), ("t_phase", C.c_int64),
+                ("max_steps", C.c_int64)]
+
+
 class FvStatus(C.Structure):
     _fields_ = [("ref_exited", C.c_int32), ("label0", C.c_int32), ("n_branched", C.c_int32),
                 ("converged", C.c_int32), ("gr_evaluated", C.c_int32), ("pad", C.c_int32),
@@ -109,6 +115,8 @@ SIGNATURES = {
                                  C.POINTER(FvStatus), _VP]),
     "grp_run": (C.c_int32, [_VP, C.POINTER(RunParams), C.POINTER(Event), C.c_int32, _I32P,
                             C.POINTER(C.c_int64), _VP]),
+    "grp_run_original": (C.c_int32, [_VP, C.POINTER(OriginalParams), C.POINTER(Event), C.c_int32, _I32P,
+                                     C.POINTER(C.c_int64), _VP]),
     "grp_get_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
     "grp_set_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
     "grp_get_device_view": (C.c_int32, [_VP, C.POINTER(DeviceView)]),
@@ -314,6 +322,19 @@ def grp_run(r: ReplicasHandle, t_gr: int, t_check: int, tol: float, min_fv_steps
     n = C.c_int32(0)
     tsim = C.c_int64(0)
     _check(_lib.grp_run(r.handle, C.byref(p), ev, max_events, C.byref(n), C.byref(tsim), _stream(stream)))
+    events = [{"kind": e.kind, "omega": e.omega, "label_to": e.label_to, "k": e.k, "M": e.M, "steps": e.steps,
+               "t_sim": e.t_sim, "n_branch": e.n_branch} for e in ev[:n.value]]
+    return events, tsim.value
+
+
+def grp_run_original(r: ReplicasHandle, t_check: int, t_corr: int, t_phase: int, max_steps: int, max_exits: int,
+                     max_events: int = 100000, stream=None):
+    p = OriginalParams(t_check, max_exits, t_corr, t_phase, max_steps)
+    ev = (Event * max_events)()
+    n = C.c_int32(0)
+    tsim = C.c_int64(0)
+    _check(_lib.grp_run_original(r.handle, C.byref(p), ev, max_events, C.byref(n), C.byref(tsim),
+                                 _stream(stream)))
     events = [{"kind": e.kind, "omega": e.omega, "label_to": e.label_to, "k": e.k, "M": e.M, "steps": e.steps,
                "t_sim": e.t_sim, "n_branch": e.n_branch} for e in ev[:n.value]]
     return events, tsim.value

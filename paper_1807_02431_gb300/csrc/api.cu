@@ -98,6 +98,7 @@ struct grp_replicas {
     uint8_t exited0;
     int8_t pad[6];
     double rhat[GRP_MAX_OBS];
+    int dephase[2];  // replicas dephased, restarts (original ParRep)
   } *hb = nullptr;
 };
 
@@ -942,6 +943,69 @@ extern "C" grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_che
 }
 
 // ------------------------------------------------------------------------------------------------
+// Event log of a run: the host array, its capacity and the clock t_sim (Eq. 6).
+struct EventLog {
+  grp_event *h;
+  int max, n = 0;
+  long long tsim = 0;
+  void add(int kind, int omega, int to, int k, long long M, long long steps, long long nb) {
+    if (n < max) {
+      grp_event &e = h[n];
+      e.kind = kind; e.omega = omega; e.label_to = to; e.k = k; e.M = M; e.steps = steps;
+      e.t_sim = tsim; e.n_branch = nb;
+    }
+    ++n;
+  }
+};
+
+// State label of replica 0 and whether it is outside omega.
+static grp_status ref_label(grp_replicas *r, int omega, int *label, int *exited, cudaStream_t st) {
+  CU(launch_check(r->sys->dev, r->q, 1, omega, r->labels, r->exited, nullptr, 0, st));
+  CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *label = r->hb->label0;
+  *exited = r->hb->exited0;
+  return GRP_OK;
+}
+
+// Transient propagation of the reference walker until a check finds it in a state (Section 2.4.1,
+// task 1); *omega = -1 when max_steps came first.
+static grp_status transient(grp_replicas *r, int t_check, long long max_steps, EventLog &L, int *omega,
+                            cudaStream_t st) {
+  long long treach = 0;
+  int ex;
+  grp_status e = ref_label(r, 0, omega, &ex, st);
+  while (e == GRP_OK && *omega < 0 && r->t_global < max_steps) {
+    if ((e = run_steps(r, t_check, 0, 1, 0, 0, 0, 0, st)) != GRP_OK) return e;
+    treach += t_check;
+    e = ref_label(r, 0, omega, &ex, st);
+  }
+  if (e == GRP_OK && *omega >= 0 && treach > 0) {
+    L.tsim += treach;
+    L.add(GRP_EV_TRANSIENT, -1, *omega, 0, 0, treach, 0);
+  }
+  return e;
+}
+
+// Parallel dynamics step (Eq. 5) ending a visit of omega; the exit configuration becomes replica 0.
+// *found = 0 when max_steps came first.
+static grp_status parallel_step(grp_replicas *r, int omega, int t_check, long long max_steps, EventLog &L,
+                                int *found, cudaStream_t st) {
+  *found = 0;
+  const long long left = (max_steps - r->t_global + t_check - 1) / t_check;
+  if (left < 1) return GRP_OK;
+  grp_exit ex_out{};
+  grp_status e = parallel_phase(r, omega, t_check, left, &ex_out, st);
+  if (e == GRP_NOEXIT) return GRP_OK;
+  if (e != GRP_OK) return e;
+  L.tsim += ex_out.tau_steps;
+  L.add(GRP_EV_PARALLEL_EXIT, omega, ex_out.label_to, ex_out.k, ex_out.M, ex_out.tau_steps, 0);
+  if (ex_out.k != 1) CU(launch_copy_replica(r->sys->dev, r->R, r->q, r->p, r->f, r->acc, ex_out.k - 1, 0, 0, st));
+  *found = 1;
+  return GRP_OK;
+}
+
 extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events, int32_t max_events,
                               int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
   const Range range("grp_run (Fig. 1)");
@@ -950,41 +1014,14 @@ extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_even
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
   const int R = r->R;
-  int nev = 0, nexit = 0;
-  long long tsim = 0;
-  auto log = [&](int kind, int omega, int to, int k, long long M, long long steps, long long nb) {
-    if (nev < max_events) {
-      grp_event &e = h_events[nev];
-      e.kind = kind; e.omega = omega; e.label_to = to; e.k = k; e.M = M; e.steps = steps;
-      e.t_sim = tsim; e.n_branch = nb;
-    }
-    ++nev;
-  };
-  auto read_label0 = [&](int omega, int *label, int *exited) -> grp_status {
-    CU(launch_check(D, r->q, 1, omega, r->labels, r->exited, nullptr, 0, st));
-    CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    *label = r->hb->label0;
-    *exited = r->hb->exited0;
-    return GRP_OK;
-  };
+  int nexit = 0;
+  EventLog L{h_events, max_events};
   grp_status e = GRP_OK;
-  while (nexit < p->max_exits && r->t_global < p->max_steps && nev < max_events) {
+  while (nexit < p->max_exits && r->t_global < p->max_steps && L.n < max_events) {
     // 1. transient propagation of the reference walker
-    long long treach = 0;
-    int omega, ex;
-    if ((e = read_label0(0, &omega, &ex)) != GRP_OK) return e;
-    while (omega < 0 && r->t_global < p->max_steps) {
-      if ((e = run_steps(r, p->t_check, 0, 1, 0, 0, 0, 0, st)) != GRP_OK) return e;
-      treach += p->t_check;
-      if ((e = read_label0(0, &omega, &ex)) != GRP_OK) return e;
-    }
+    int omega;
+    if ((e = transient(r, p->t_check, p->max_steps, L, &omega, st)) != GRP_OK) return e;
     if (omega < 0) break;
-    if (treach > 0) {
-      tsim += treach;
-      log(GRP_EV_TRANSIENT, -1, omega, 0, 0, treach, 0);
-    }
     // 2. convergence step
     CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, 0, -1, 1, st));
     r->t_phase = 0;
@@ -995,38 +1032,156 @@ extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_even
       if ((e = fv_check(r, omega, p->t_check, p->t_gr, p->tol, p->min_fv_steps, &fs, st)) != GRP_OK) return e;
       // (a) the reference walker left omega: the F-V workers are discarded
       if (fs.ref_exited) {
-        tsim += r->t_phase;
-        log(GRP_EV_REF_EXIT, omega, fs.label0, 0, 0, r->t_phase, nbranch);
+        L.tsim += r->t_phase;
+        L.add(GRP_EV_REF_EXIT, omega, fs.label0, 0, 0, r->t_phase, nbranch);
         ++nexit;
         ref_exit = 1;
         break;
       }
       // (b) branching (done on the device)
-      if (fs.n_branched > 0 && fs.n_branched == R - 1) log(GRP_EV_FV_ALL_EXITED, omega, omega, 0, 0, r->t_phase, fs.n_branched);
+      if (fs.n_branched > 0 && fs.n_branched == R - 1)
+        L.add(GRP_EV_FV_ALL_EXITED, omega, omega, 0, 0, r->t_phase, fs.n_branched);
       nbranch += fs.n_branched;
       // (c) Gelman-Rubin test, Eq. 4
       if (fs.gr_evaluated && fs.converged) { converged = 1; break; }
     }
     if (ref_exit) continue;
     if (!converged) break;
-    tsim += r->t_phase;
-    log(GRP_EV_FV_CONVERGED, omega, omega, 0, 0, r->t_phase, nbranch);
+    L.tsim += r->t_phase;
+    L.add(GRP_EV_FV_CONVERGED, omega, omega, 0, 0, r->t_phase, nbranch);
     // 3. parallel dynamics step
-    const long long left = (p->max_steps - r->t_global + p->t_check - 1) / p->t_check;
-    if (left < 1) break;
-    grp_exit ex_out{};
-    e = parallel_phase(r, omega, p->t_check, left, &ex_out, st);
-    if (e == GRP_NOEXIT) break;
-    if (e != GRP_OK) return e;
-    tsim += ex_out.tau_steps;
-    log(GRP_EV_PARALLEL_EXIT, omega, ex_out.label_to, ex_out.k, ex_out.M, ex_out.tau_steps, 0);
+    int found;
+    if ((e = parallel_step(r, omega, p->t_check, p->max_steps, L, &found, st)) != GRP_OK) return e;
+    if (!found) break;
     ++nexit;
-    // the exit configuration becomes the reference walker
-    if (ex_out.k != 1) CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, ex_out.k - 1, 0, 0, st));
   }
-  if (h_n_events) *h_n_events = std::min(nev, max_events);
-  if (h_t_sim) *h_t_sim = tsim;
+  if (h_n_events) *h_n_events = std::min(L.n, max_events);
+  if (h_t_sim) *h_t_sim = L.tsim;
   return latch_errors(r, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Original ParRep (Section 2.4.3).  Device scratch of one call: the samples (slot 0 the decorrelated
+// reference, slot r the dephased state of replica r), each replica's stay, done flags and counters.
+struct DephaseScratch {
+  double *sq = nullptr, *sp = nullptr, *sf = nullptr;
+  long long *stay = nullptr;
+  uint8_t *done = nullptr;
+  int *cnt = nullptr;
+  ~DephaseScratch() {
+    cudaFree(sq); cudaFree(sp); cudaFree(sf); cudaFree(stay); cudaFree(done); cudaFree(cnt);
+  }
+};
+
+// Dephasing of one visit: returns in *dsteps the steps it took (all replicas in lockstep), in
+// *restarts the restarts from the decorrelated reference, *ok = 0 when max_steps came first.
+static grp_status dephase(grp_replicas *r, int omega, const grp_original_params *p, DephaseScratch &S,
+                          long long *dsteps, long long *restarts, int *ok, cudaStream_t st) {
+  const SysDev &D = r->sys->dev;
+  const int R = r->R;
+  const size_t row = (size_t)D.nd * 8;
+  CU(cudaMemcpyAsync(S.sq, r->q, row, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(S.sp, r->p, row, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(S.sf, r->f, row, cudaMemcpyDeviceToDevice, st));
+  CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, 0, -1, 1, st));
+  CU(cudaMemsetAsync(S.stay, 0, sizeof(long long) * R, st));
+  CU(cudaMemsetAsync(S.done, 0, R, st));
+  CU(cudaMemsetAsync(S.done, 1, 1, st));
+  CU(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int), st));
+  r->t_phase = 0;
+  *dsteps = 0;
+  *restarts = 0;
+  int n_done = 1;
+  while (n_done < R && r->t_global < p->max_steps) {
+    grp_status e = run_steps(r, p->t_check, 0, R, 1, omega, 0, 0, st);
+    if (e != GRP_OK) return e;
+    *dsteps += p->t_check;
+    CU(launch_dephase(D, R, r->q, r->p, r->f, S.sq, S.sp, S.sf, r->exited, S.stay, S.done, p->t_check,
+                      p->t_phase, S.cnt, st));
+    CU(cudaMemcpyAsync(r->hb->dephase, S.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&r->hb->err, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (r->hb->err) return latch_errors(r, st);
+    n_done = 1 + r->hb->dephase[0];
+    *restarts = r->hb->dephase[1];
+  }
+  *ok = n_done == R;
+  if (!*ok) return GRP_OK;
+  const size_t all = row * (size_t)R;
+  CU(cudaMemcpyAsync(r->q, S.sq, all, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(r->p, S.sp, all, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(r->f, S.sf, all, cudaMemcpyDeviceToDevice, st));
+  return GRP_OK;
+}
+
+static grp_status run_original(grp_replicas *r, const grp_original_params *p, EventLog &L, DephaseScratch &S,
+                               cudaStream_t st) {
+  int nexit = 0;
+  grp_status e = GRP_OK;
+  while (nexit < p->max_exits && r->t_global < p->max_steps && L.n < L.max) {
+    // 1. transient propagation of the reference walker
+    int omega;
+    if ((e = transient(r, p->t_check, p->max_steps, L, &omega, st)) != GRP_OK) return e;
+    if (omega < 0) break;
+    // 2. decorrelation: replica 0 alone, checked every t_check, must stay t_corr steps in omega
+    long long d = 0;
+    int ref_exit = 0;
+    while (d < p->t_corr && r->t_global < p->max_steps) {
+      if ((e = run_steps(r, p->t_check, 0, 1, 0, 0, 0, 0, st)) != GRP_OK) return e;
+      d += p->t_check;
+      int label, ex;
+      if ((e = ref_label(r, omega, &label, &ex, st)) != GRP_OK) return e;
+      if (ex) {
+        L.tsim += d;
+        L.add(GRP_EV_REF_EXIT, omega, label, 0, 0, d, 0);
+        ++nexit;
+        ref_exit = 1;
+        break;
+      }
+    }
+    if (ref_exit) continue;
+    if (d < p->t_corr) break;
+    L.tsim += d;
+    L.add(GRP_EV_DECORRELATED, omega, omega, 0, 0, d, 0);
+    // 3. dephasing (not counted in the clock)
+    long long dsteps, restarts;
+    int ok;
+    if ((e = dephase(r, omega, p, S, &dsteps, &restarts, &ok, st)) != GRP_OK) return e;
+    if (!ok) break;
+    L.add(GRP_EV_DEPHASED, omega, omega, 0, 0, dsteps, restarts);
+    // 4. parallel dynamics step
+    int found;
+    if ((e = parallel_step(r, omega, p->t_check, p->max_steps, L, &found, st)) != GRP_OK) return e;
+    if (!found) break;
+    ++nexit;
+  }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_run_original(grp_replicas *r, const grp_original_params *p, grp_event *h_events,
+                                       int32_t max_events, int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
+  const Range range("grp_run_original (Section 2.4.3)");
+  if (!r || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_run_original: null argument");
+  if (p->t_check < 1 || p->t_corr < 0 || p->t_phase < 0)
+    return fail(GRP_EINVAL, "grp_run_original: need t_check >= 1, t_corr >= 0, t_phase >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t R = (size_t)r->R, bytes = R * (size_t)r->sys->dev.nd * 8;
+  DephaseScratch S;
+  if (cudaMalloc(&S.sq, bytes) != cudaSuccess || cudaMalloc(&S.sp, bytes) != cudaSuccess ||
+      cudaMalloc(&S.sf, bytes) != cudaSuccess || cudaMalloc(&S.stay, R * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&S.done, R) != cudaSuccess || cudaMalloc(&S.cnt, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GRP_ENOMEM, "grp_run_original: cudaMalloc of the dephasing samples (%zu bytes) failed", 3 * bytes);
+  }
+  EventLog L{h_events, max_events};
+  grp_status e = run_original(r, p, L, S, st);
+  if (e == GRP_OK) {
+    if (h_n_events) *h_n_events = std::min(L.n, max_events);
+    if (h_t_sim) *h_t_sim = L.tsim;
+  }
+  cudaStreamSynchronize(st);  // the scratch is freed below: nothing may still use it
+  grp_status e2 = latch_errors(r, st);
+  return e != GRP_OK ? e : e2;
 }
 
 // ------------------------------------------------------------------------------------------------

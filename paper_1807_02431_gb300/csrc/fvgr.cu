@@ -210,4 +210,51 @@ cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p
   return cudaGetLastError();
 }
 
+// Dephasing of the original ParRep (Section 2.4.3), after each check: one block per replica r >= 1
+// not yet dephased.  A replica outside omega restarts from the decorrelated configuration (sample
+// slot 0); otherwise its stay grows by t_check and, once it reaches t_phase, its state becomes sample
+// r.  counters[0] counts the replicas dephased, counters[1] the restarts.
+__global__ void __launch_bounds__(256) dephase_kernel(int n_rep, int nd, double *q, double *p, double *f,
+                                                      double *sq, double *sp, double *sf,
+                                                      const uint8_t *exited, long long *stay, uint8_t *done,
+                                                      int t_check, long long t_phase, int *counters) {
+  const int r = blockIdx.x + 1;
+  if (r >= n_rep || done[r]) return;
+  const bool out = exited[r] != 0;
+  const long long s = out ? 0 : stay[r] + t_check;
+  __syncthreads();  // every thread has read stay[r] before thread 0 rewrites it
+  const size_t b = (size_t)r * nd;
+  if (out) {
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+      q[b + i] = sq[i];
+      p[b + i] = sp[i];
+      f[b + i] = sf[i];
+    }
+  } else if (s >= t_phase) {
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+      sq[b + i] = q[b + i];
+      sp[b + i] = p[b + i];
+      sf[b + i] = f[b + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    stay[r] = s;
+    if (out) {
+      atomicAdd(counters + 1, 1);
+    } else if (s >= t_phase) {
+      done[r] = 1;
+      atomicAdd(counters, 1);
+    }
+  }
+}
+
+cudaError_t launch_dephase(const SysDev &S, int n_rep, double *q, double *p, double *f, double *sq, double *sp,
+                           double *sf, const uint8_t *exited, long long *stay, uint8_t *done, int t_check,
+                           long long t_phase, int *counters, cudaStream_t st) {
+  if (n_rep < 2) return cudaSuccess;
+  dephase_kernel<<<n_rep - 1, 256, 0, st>>>(n_rep, S.nd, q, p, f, sq, sp, sf, exited, stay, done, t_check,
+                                            t_phase, counters);
+  return cudaGetLastError();
+}
+
 }  // namespace grp
