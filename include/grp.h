@@ -263,14 +263,14 @@ grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_event *h_events
 /* The original ParRep loop (Section 2.4.3) from the current state of replica 0.  Per visit of a
  * state omega: transient as in grp_run; decorrelation, replica 0 alone checked every t_check until it
  * has stayed t_corr steps (GRP_EV_DECORRELATED, counted in the clock) or left omega
- * (GRP_EV_REF_EXIT, t_ref counted); dephasing, replicas 1..R-1 start from the decorrelated
- * configuration, all R advance in lockstep, a replica that leaves omega restarts from that
+ * (GRP_EV_REF_EXIT, t_ref counted); dephasing, each of the R replicas starts from the decorrelated
+ * configuration, all advance in lockstep, a replica that leaves omega restarts from that
  * configuration and one that has stayed t_phase steps since its last start keeps that state as its
  * sample (GRP_EV_DEPHASED: steps = the dephasing time, n_branch = the restarts; not counted in the
- * clock); parallel step, Eq. 5 from the samples (replica 0 keeps the decorrelated one), the exit
- * configuration becoming replica 0.  Events and the clock as for grp_run.  The dephasing keeps a
- * second copy of q, p and F (3 R n dim doubles of device memory, allocated per call; GRP_ENOMEM
- * when that fails).  GRP_EINVAL for t_check < 1, t_corr < 0 or t_phase < 0; t_corr and t_phase
+ * clock); parallel step, Eq. 5 from the R samples, the exit configuration becoming replica 0.
+ * Events and the clock as for grp_run.  The dephasing keeps the samples and the reference beside
+ * the replicas (3 (R + 1) n dim doubles of device memory, allocated per call; GRP_ENOMEM when that
+ * fails).  GRP_EINVAL for t_check < 1, t_corr < 0 or t_phase < 0; t_corr and t_phase
  * are rounded up to whole checks. */
 grp_status grp_run_original(grp_replicas *r, const grp_original_params *p, grp_event *h_events,
                             int32_t max_events, int32_t *h_n_events, int64_t *h_t_sim, void *stream);

@@ -821,17 +821,19 @@ int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const doub
 
 /* ---------------------------------------------------------------- original ParRep (Section 2.4.3)
  * Transient as in Gen. ParRep; decorrelation: the reference walker alone for t_corr steps in its state
- * (checked every t_check); dephasing: every replica r >= 1 advances until it has stayed t_phase steps in
- * the state since its last (re)start from the decorrelated reference, the dephasing time not counted
- * in the clock; parallel step: Eq. 5 from the dephased configurations (replica 0 keeps the
- * decorrelated one). */
+ * (checked every t_check); dephasing: each of the N replicas starts from the decorrelated reference and
+ * advances until it has stayed t_phase steps in the state since its last (re)start, an exit restarting
+ * it from that reference; the dephasing time is not counted in the clock; parallel step: Eq. 5 from
+ * the N dephased configurations. */
 int32_t orc_run_original(const orc_ctx *c, const orc_original_params *rp, const double *q0,
                          const double *p0, orc_event *events, int32_t max_events, int64_t *t_global_out) {
   const orc_system *s = &c->s;
   int N = rp->n_rep, nd = s->n_atoms * s->dim;
   size_t bytes = sizeof(double) * (size_t)N * nd;
   double *q = (double *)malloc(bytes), *p = (double *)malloc(bytes), *f = (double *)malloc(bytes);
-  double *sq = (double *)malloc(bytes), *sp = (double *)malloc(bytes), *sf = (double *)malloc(bytes);
+  /* samples of the dephasing: slot r for replica r, slot N the decorrelated reference */
+  size_t sbytes = bytes + sizeof(double) * nd;
+  double *sq = (double *)malloc(sbytes), *sp = (double *)malloc(sbytes), *sf = (double *)malloc(sbytes);
   int64_t *stay = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
   uint8_t *done = (uint8_t *)malloc((size_t)N);
   memcpy(q, q0, sizeof(double) * nd);
@@ -887,11 +889,11 @@ int32_t orc_run_original(const orc_ctx *c, const orc_original_params *rp, const 
     tsim += d;
     LOG_EVENT(ORC_EV_DECORRELATED, omega, omega, 0, 0, d, 0);
     /* 3. dephasing: replicas restart from the decorrelated reference until each has stayed t_phase */
-    COPY_REPLICA(sq, sp, sf, 0, q, p, f, 0);
+    COPY_REPLICA(sq, sp, sf, N, q, p, f, 0);
     for (int r = 1; r < N; ++r) COPY_REPLICA(q, p, f, r, q, p, f, 0);
-    for (int r = 0; r < N; ++r) { stay[r] = 0; done[r] = (uint8_t)(r == 0); }
+    for (int r = 0; r < N; ++r) { stay[r] = 0; done[r] = 0; }
     int64_t dsteps = 0, restarts = 0;
-    int n_done = 1;
+    int n_done = 0;
     while (n_done < N && tg < rp->max_steps) {
       for (int i = 0; i < rp->t_check; ++i) {
         for (int r = 0; r < N; ++r)
@@ -899,10 +901,10 @@ int32_t orc_run_original(const orc_ctx *c, const orc_original_params *rp, const 
         tg++;
       }
       dsteps += rp->t_check;
-      for (int r = 1; r < N; ++r) {
+      for (int r = 0; r < N; ++r) {
         if (done[r]) continue;
         if (orc_exited(c, q + (size_t)r * nd, omega)) {
-          COPY_REPLICA(q, p, f, r, sq, sp, sf, 0);
+          COPY_REPLICA(q, p, f, r, sq, sp, sf, N);
           stay[r] = 0;
           restarts++;
         } else {

@@ -188,11 +188,10 @@ int32_t orc_run_genparrep(const orc_ctx *c, const orc_run_params *rp, const doub
 
 /* The original ParRep algorithm as Section 2.4.3 contrasts it with Gen. ParRep: decorrelation (the
  * reference walker must stay t_corr steps in its state, tested every t_check steps; leaving earlier is
- * a reference exit, clock += elapsed), then dephasing (replicas 1..N-1 start from the decorrelated
- * reference; each advances until it has stayed t_phase steps in the state since its last start, a
- * replica that leaves restarts from the decorrelated reference; the dephasing time is not counted in
- * the clock and replica 0 keeps the decorrelated configuration), then the parallel step of Eq. 5 from
- * the dephased replicas.  Events: TRANSIENT, REF_EXIT, DECORRELATED (steps = t_corr reached),
+ * a reference exit, clock += elapsed), then dephasing (each of the N replicas starts from the
+ * decorrelated reference and advances until it has stayed t_phase steps in the state since its last
+ * start, a replica that leaves restarting from the decorrelated reference; the dephasing time is not
+ * counted in the clock), then the parallel step of Eq. 5 from the N dephased replicas.  Events: TRANSIENT, REF_EXIT, DECORRELATED (steps = t_corr reached),
  * DEPHASED (steps = dephasing steps, n_branch = restarts), PARALLEL_EXIT.  All replicas advance in
  * lockstep during dephasing (replica r draws the noise of replica r at the global step). */
 typedef struct {

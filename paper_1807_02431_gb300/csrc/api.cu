@@ -1061,8 +1061,8 @@ extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_even
 }
 
 // ------------------------------------------------------------------------------------------------
-// Original ParRep (Section 2.4.3).  Device scratch of one call: the samples (slot 0 the decorrelated
-// reference, slot r the dephased state of replica r), each replica's stay, done flags and counters.
+// Original ParRep (Section 2.4.3).  Device scratch of one call: the samples (slot r the dephased
+// state of replica r, slot R the decorrelated reference), each replica's stay, done flags, counters.
 struct DephaseScratch {
   double *sq = nullptr, *sp = nullptr, *sf = nullptr;
   long long *stay = nullptr;
@@ -1080,18 +1080,18 @@ static grp_status dephase(grp_replicas *r, int omega, const grp_original_params 
   const SysDev &D = r->sys->dev;
   const int R = r->R;
   const size_t row = (size_t)D.nd * 8;
-  CU(cudaMemcpyAsync(S.sq, r->q, row, cudaMemcpyDeviceToDevice, st));
-  CU(cudaMemcpyAsync(S.sp, r->p, row, cudaMemcpyDeviceToDevice, st));
-  CU(cudaMemcpyAsync(S.sf, r->f, row, cudaMemcpyDeviceToDevice, st));
+  const size_t ref = row / 8 * (size_t)R;
+  CU(cudaMemcpyAsync(S.sq + ref, r->q, row, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(S.sp + ref, r->p, row, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemcpyAsync(S.sf + ref, r->f, row, cudaMemcpyDeviceToDevice, st));
   CU(launch_copy_replica(D, R, r->q, r->p, r->f, r->acc, 0, -1, 1, st));
   CU(cudaMemsetAsync(S.stay, 0, sizeof(long long) * R, st));
   CU(cudaMemsetAsync(S.done, 0, R, st));
-  CU(cudaMemsetAsync(S.done, 1, 1, st));
   CU(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int), st));
   r->t_phase = 0;
   *dsteps = 0;
   *restarts = 0;
-  int n_done = 1;
+  int n_done = 0;
   while (n_done < R && r->t_global < p->max_steps) {
     grp_status e = run_steps(r, p->t_check, 0, R, 1, omega, 0, 0, st);
     if (e != GRP_OK) return e;
@@ -1102,7 +1102,7 @@ static grp_status dephase(grp_replicas *r, int omega, const grp_original_params 
     CU(cudaMemcpyAsync(&r->hb->err, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (r->hb->err) return latch_errors(r, st);
-    n_done = 1 + r->hb->dephase[0];
+    n_done = r->hb->dephase[0];
     *restarts = r->hb->dephase[1];
   }
   *ok = n_done == R;
@@ -1165,7 +1165,7 @@ extern "C" grp_status grp_run_original(grp_replicas *r, const grp_original_param
   if (p->t_check < 1 || p->t_corr < 0 || p->t_phase < 0)
     return fail(GRP_EINVAL, "grp_run_original: need t_check >= 1, t_corr >= 0, t_phase >= 0");
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t R = (size_t)r->R, bytes = R * (size_t)r->sys->dev.nd * 8;
+  const size_t R = (size_t)r->R, bytes = (R + 1) * (size_t)r->sys->dev.nd * 8;
   DephaseScratch S;
   if (cudaMalloc(&S.sq, bytes) != cudaSuccess || cudaMalloc(&S.sp, bytes) != cudaSuccess ||
       cudaMalloc(&S.sf, bytes) != cudaSuccess || cudaMalloc(&S.stay, R * sizeof(long long)) != cudaSuccess ||

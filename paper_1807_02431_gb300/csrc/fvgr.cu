@@ -210,25 +210,25 @@ cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p
   return cudaGetLastError();
 }
 
-// Dephasing of the original ParRep (Section 2.4.3), after each check: one block per replica r >= 1
-// not yet dephased.  A replica outside omega restarts from the decorrelated configuration (sample
-// slot 0); otherwise its stay grows by t_check and, once it reaches t_phase, its state becomes sample
-// r.  counters[0] counts the replicas dephased, counters[1] the restarts.
+// Dephasing of the original ParRep (Section 2.4.3), after each check: one block per replica r not yet
+// dephased.  A replica outside omega restarts from the decorrelated reference (slot n_rep of the
+// sample arrays); otherwise its stay grows by t_check and, once it reaches t_phase, its state becomes
+// sample r.  counters[0] counts the replicas dephased, counters[1] the restarts.
 __global__ void __launch_bounds__(256) dephase_kernel(int n_rep, int nd, double *q, double *p, double *f,
                                                       double *sq, double *sp, double *sf,
                                                       const uint8_t *exited, long long *stay, uint8_t *done,
                                                       int t_check, long long t_phase, int *counters) {
-  const int r = blockIdx.x + 1;
-  if (r >= n_rep || done[r]) return;
+  const int r = blockIdx.x;
+  if (done[r]) return;
   const bool out = exited[r] != 0;
   const long long s = out ? 0 : stay[r] + t_check;
   __syncthreads();  // every thread has read stay[r] before thread 0 rewrites it
-  const size_t b = (size_t)r * nd;
+  const size_t b = (size_t)r * nd, ref = (size_t)n_rep * nd;
   if (out) {
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-      q[b + i] = sq[i];
-      p[b + i] = sp[i];
-      f[b + i] = sf[i];
+      q[b + i] = sq[ref + i];
+      p[b + i] = sp[ref + i];
+      f[b + i] = sf[ref + i];
     }
   } else if (s >= t_phase) {
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
@@ -251,9 +251,8 @@ __global__ void __launch_bounds__(256) dephase_kernel(int n_rep, int nd, double 
 cudaError_t launch_dephase(const SysDev &S, int n_rep, double *q, double *p, double *f, double *sq, double *sp,
                            double *sf, const uint8_t *exited, long long *stay, uint8_t *done, int t_check,
                            long long t_phase, int *counters, cudaStream_t st) {
-  if (n_rep < 2) return cudaSuccess;
-  dephase_kernel<<<n_rep - 1, 256, 0, st>>>(n_rep, S.nd, q, p, f, sq, sp, sf, exited, stay, done, t_check,
-                                            t_phase, counters);
+  dephase_kernel<<<n_rep, 256, 0, st>>>(n_rep, S.nd, q, p, f, sq, sp, sf, exited, stay, done, t_check, t_phase,
+                                        counters);
   return cudaGetLastError();
 }
 

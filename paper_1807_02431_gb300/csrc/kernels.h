@@ -65,8 +65,8 @@ cudaError_t launch_gelman_rubin(const SysDev &S, int n_rep, const double *acc, d
 cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                                 int src, int dst, int clear_acc, cudaStream_t st);
 
-// Dephasing step of the original ParRep after one check (replicas 1..R-1): restart exited replicas
-// from sample slot 0 of (sq, sp, sf), store those that have stayed t_phase steps as their sample.
+// Dephasing step of the original ParRep after one check: restart exited replicas from slot R of
+// (sq, sp, sf) [R + 1][nd], store those that have stayed t_phase steps as their sample (slot r).
 cudaError_t launch_dephase(const SysDev &S, int n_rep, double *q, double *p, double *f, double *sq, double *sp,
                            double *sf, const uint8_t *exited, long long *stay, uint8_t *done, int t_check,
                            long long t_phase, int *counters, cudaStream_t st);

@@ -69,24 +69,28 @@ def test_original_stops_at_max_steps(B, oracle_mod):
 
 
 def test_original_single_replica_is_brute_force(B, oracle_mod):
-    """N = 1: no dephasing, the parallel step is the walker's own trajectory, so residence times
-    equal the oracle's brute-force run step for step."""
+    """N = 1 with one check of dephasing and no restart: the walker follows the brute-force trajectory,
+    so counted time plus dephasing time per visit equals the oracle's brute-force residence times."""
     s = W.double_well_2d()
     o = oracle_mod.Oracle(s)
     sysh = B.grp_create_system(s, B.GRP_FP64)
     rep = B.grp_init_replicas(sysh, 1, SEED, s.q0, s.p0)
-    ev, tsim = B.grp_run_original(rep, s.t_check, 2000, 2000, 10 ** 9, 4)
+    ev, tsim = B.grp_run_original(rep, s.t_check, 2000, 0, 10 ** 9, 4)
     res, dec = [], None
     for e in ev:
         if e["kind"] == B.EV_DECORRELATED:
             dec = e["steps"]
+        elif e["kind"] == B.EV_DEPHASED:
+            assert e["n_branch"] == 0
+            dec += e["steps"]
         elif e["kind"] == B.EV_PARALLEL_EXIT:
             res.append(dec + e["steps"])
         elif e["kind"] == B.EV_REF_EXIT:
             res.append(e["steps"])
     bres, _ = o.run_bruteforce(SEED, s.t_check, 10 ** 9, 4)
     assert res == list(bres)
-    assert tsim == B.grp_get_state(rep)[3]["t_global"]
+    deph = sum(e["steps"] for e in ev if e["kind"] == B.EV_DEPHASED)
+    assert tsim + deph == B.grp_get_state(rep)[3]["t_global"]
 
 
 def test_original_mixed_chain_event_log_is_consistent(B):

@@ -1,8 +1,9 @@
 """Pins of the oracle's original ParRep loop (Section 2.4.3: decorrelation, dephasing, parallel step).
 
-(a) With one replica the method degenerates into plain dynamics: dephasing has nothing to do, the
-parallel step is the reference walker's own trajectory, so every residence time it reports must equal
-the brute-force run's on the same random stream, step for step, and the clock equals t_global.
+(a) With one replica the method degenerates into plain dynamics as long as the dephasing restarts
+nothing: the walker's trajectory is then the brute-force run's on the same random stream, and each
+visit's counted time plus its uncounted dephasing time equals the brute-force residence time, step for
+step; the global step counter is the clock plus the dephasing time.
 (b) With 32 replicas the residence-time distribution matches brute force (two-sample KS, the
 validation style of Section 4.1), and the event log follows the clock rules of Section 2.4.3.
 """
@@ -18,12 +19,15 @@ T_CORR = 2000
 T_PHASE = 2000
 
 
-def _visits(ev, oracle):
-    """Residence time per visit: t_ref after a reference exit, t_corr + tau after a parallel exit."""
+def _visits(ev, oracle, with_dephasing=False):
+    """Residence time per visit: t_ref after a reference exit, t_corr + tau after a parallel exit (plus
+    the dephasing steps when asked)."""
     res, frm, dec = [], [], None
     for e in ev:
         if e["kind"] == oracle.EV_DECORRELATED:
             dec = e["steps"]
+        elif e["kind"] == oracle.EV_DEPHASED and with_dephasing:
+            dec += e["steps"]
         elif e["kind"] == oracle.EV_PARALLEL_EXIT:
             res.append(dec + e["steps"])
             frm.append(e["omega"])
@@ -34,23 +38,23 @@ def _visits(ev, oracle):
     return res, frm
 
 
-def test_single_replica_reduces_to_brute_force(oracle_mod):
+@pytest.mark.parametrize("seed", [11, 12])
+def test_single_replica_reduces_to_brute_force(oracle_mod, seed):
     o = oracle_mod.Oracle(W.double_well_2d())
     s = o.system
-    for seed in (11, 12):
-        ev, tg = o.run_original(1, seed, s.t_check, T_CORR, T_PHASE, 10 ** 9, 6)
-        res, frm = _visits(ev, oracle_mod)
-        assert len(res) == 6
-        bres, bfrm = o.run_bruteforce(seed, s.t_check, 10 ** 9, 6)
-        assert list(bres) == res and list(bfrm) == frm
-        # all time is counted with one replica: the clock is the global step counter
-        assert ev[-1]["t_sim"] == tg
-        assert all(e["steps"] == 0 and e["n_branch"] == 0
-                   for e in ev if e["kind"] == oracle_mod.EV_DEPHASED)
-        # the parallel step of one replica: k = 1, tau = M t_check (Eq. 5 with N = 1)
-        for e in ev:
-            if e["kind"] == oracle_mod.EV_PARALLEL_EXIT:
-                assert e["k"] == 1 and e["steps"] == e["M"] * s.t_check
+    # one check of dephasing right after t_corr in the state: an exit there (a restart) is rare
+    ev, tg = o.run_original(1, seed, s.t_check, T_CORR, 0, 10 ** 9, 6)
+    deph = [e for e in ev if e["kind"] == oracle_mod.EV_DEPHASED]
+    assert deph and all(e["n_branch"] == 0 and e["steps"] == s.t_check for e in deph)
+    res, frm = _visits(ev, oracle_mod, with_dephasing=True)
+    assert len(res) == 6
+    bres, bfrm = o.run_bruteforce(seed, s.t_check, 10 ** 9, 6)
+    assert list(bres) == res and list(bfrm) == frm
+    assert tg == ev[-1]["t_sim"] + sum(e["steps"] for e in deph)
+    # the parallel step of one replica: k = 1, tau = M t_check (Eq. 5 with N = 1)
+    for e in ev:
+        if e["kind"] == oracle_mod.EV_PARALLEL_EXIT:
+            assert e["k"] == 1 and e["steps"] == e["M"] * s.t_check
 
 
 def _original_worker(seed, max_exits):
