@@ -250,9 +250,13 @@ class Oracle:
         return lib().orc_exited(self.ctx, _dp(_c64(q)), omega)
 
     def cv(self, q):
-        out = np.zeros(2)
+        """The state definition's collective variables: (phi, psi), (x, 0), (d, 0), or the m rotamer
+        torsions (degrees)."""
+        out = np.zeros(4)
         lib().orc_cv(self.ctx, _dp(_c64(q)), _dp(out))
-        return out
+        if self.system.cv_kind == 3:
+            return out[: int(self.system.cv_params[0])]
+        return out[:2]
 
     def observable(self, j, q, p):
         return lib().orc_observable(self.ctx, j, _dp(_c64(q)), _dp(_c64(p)))

@@ -325,9 +325,9 @@ void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t 
 }
 
 /* ---------------------------------------------------------------- states (Sections 2.2, 3.3) */
-void orc_cv(const orc_ctx *c, const double *q, double cv[2]) {
+void orc_cv(const orc_ctx *c, const double *q, double cv[4]) {
   const orc_system *s = &c->s;
-  cv[0] = cv[1] = 0.0;
+  cv[0] = cv[1] = cv[2] = cv[3] = 0.0;
   if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
     cv[0] = q[0];
   } else if (s->cv_kind == ORC_CV_DIHEDRAL_RECT) {
@@ -341,17 +341,41 @@ void orc_cv(const orc_ctx *c, const double *q, double cv[2]) {
     group_com(c, 1, q, c1);
     sub3(c0, c1, d);
     cv[0] = norm3(d);
+  } else if (s->cv_kind == ORC_CV_ROTAMERS) {
+    const int *a = s->cv_atoms, m = (int)s->cv_params[0];
+    const double deg = 180.0 / 3.14159265358979323846;
+    for (int t = 0; t < m; ++t)
+      cv[t] = deg * dihedral_angle(q + 3 * a[t], q + 3 * a[t + 1], q + 3 * a[t + 2], q + 3 * a[t + 3]);
   }
 }
 
-/* Double well: states are the cores x < -w (state 0) and x > w (state 1), w = cv_params[0];
+/* Rotamer well of a torsion phi in degrees, (-180, 180]: 0 = gauche+ [0, 120), 1 = trans
+ * [120, 180] and (-180, -120), 2 = gauche- [-120, 0). */
+static int rotamer_well(double phi) {
+  if (phi >= 0.0 && phi < 120.0) return 0;
+  if (phi >= -120.0 && phi < 0.0) return 2;
+  return 1;
+}
+
+/* Angular distance (degrees) from phi to the centre of well w (60, 180, -60). */
+static double rotamer_offset(double phi, int w) {
+  if (w == 0) return fabs(phi - 60.0);
+  if (w == 2) return fabs(phi + 60.0);
+  return 180.0 - fabs(phi);
+}
+
+/* Rotamers: m = cv_params[0] torsions along the atom path cv_atoms[0..m+2] (torsion t of atoms
+ * t..t+3); the configuration is in state sum_t well_t 3^t when every torsion lies within
+ * w = cv_params[1] degrees of its well's centre, else in no state; it has left state omega when
+ * some torsion's well differs from digit t of omega (the wells tile the circle, the cores do not).
+ * Double well: states are the cores x < -w (state 0) and x > w (state 1), w = cv_params[0];
  * the state 0 is left when x >= 0, the state 1 when x < 0.
  * Dihedral rectangle: state 0 = {phi in [p0, p1] and psi in [p2, p3]} (degrees), state 1 = the
  * complement: a two-state partition.
  * Centre-of-mass distance: state 0 = {d < cv_params[0]}, state 1 = the complement. */
 int32_t orc_state_of(const orc_ctx *c, const double *q) {
   const orc_system *s = &c->s;
-  double cv[2];
+  double cv[4];
   orc_cv(c, q, cv);
   if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
     if (cv[0] < -s->cv_params[0]) return 0;
@@ -363,6 +387,17 @@ int32_t orc_state_of(const orc_ctx *c, const double *q) {
              cv[1] <= s->cv_params[3];
     return in ? 0 : 1;
   }
+  if (s->cv_kind == ORC_CV_ROTAMERS) {
+    const int m = (int)s->cv_params[0];
+    int label = 0, scale = 1;
+    for (int t = 0; t < m; ++t) {
+      const int w = rotamer_well(cv[t]);
+      if (!(rotamer_offset(cv[t], w) < s->cv_params[1])) return -1;
+      label += w * scale;
+      scale *= 3;
+    }
+    return label;
+  }
   return cv[0] < s->cv_params[0] ? 0 : 1;
 }
 
@@ -371,6 +406,14 @@ int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega) {
   if (s->cv_kind == ORC_CV_DOUBLE_WELL) {
     double x = q[0];
     return omega == 0 ? (x >= 0.0) : (x < 0.0);
+  }
+  if (s->cv_kind == ORC_CV_ROTAMERS) {
+    double cv[4];
+    orc_cv(c, q, cv);
+    int rest = omega;
+    for (int t = 0; t < (int)s->cv_params[0]; ++t, rest /= 3)
+      if (rotamer_well(cv[t]) != rest % 3) return 1;
+    return 0;
   }
   return orc_state_of(c, q) != omega;
 }

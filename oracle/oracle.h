@@ -23,7 +23,7 @@ extern "C" {
 #endif
 
 enum { ORC_POT_DOUBLE_WELL_2D = 0, ORC_POT_FORCE_FIELD = 1 };
-enum { ORC_CV_DOUBLE_WELL = 0, ORC_CV_DIHEDRAL_RECT = 1, ORC_CV_COM_DISTANCE = 2 };
+enum { ORC_CV_DOUBLE_WELL = 0, ORC_CV_DIHEDRAL_RECT = 1, ORC_CV_COM_DISTANCE = 2, ORC_CV_ROTAMERS = 3 };
 enum {
   ORC_OBS_COORD = 0,        /* arg0 = atom, arg1 = axis */
   ORC_OBS_POTENTIAL = 1,    /* V(q) */
@@ -107,8 +107,9 @@ void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t 
  * (ii) whether q is outside the state omega. */
 int32_t orc_state_of(const orc_ctx *c, const double *q);
 int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega);
-/* Collective variables of the state definition: cv[0..1] (phi/psi in degrees, x, or distance). */
-void orc_cv(const orc_ctx *c, const double *q, double cv[2]);
+/* Collective variables of the state definition: cv[0..3] (phi/psi in degrees, x, a distance, or
+ * the rotamer torsions in degrees; unused entries 0). */
+void orc_cv(const orc_ctx *c, const double *q, double cv[4]);
 /* Observable j of Section 2.4.1 (iii). */
 double orc_observable(const orc_ctx *c, int32_t j, const double *q, const double *p);
 

@@ -11,6 +11,9 @@ Systems (stand-ins for the paper's workloads, whose force fields and structures 
     (Section 4.1): harmonic bonds and angles, periodic dihedrals, LJ + Coulomb with eps = 4r; the
     two states are the paper's (phi, psi) rectangle and its complement.
   * ``batched_chains``  - independent chains of uneven sizes for the batched path.
+  * ``alkane``          - a united-atom n-alkane whose backbone torsions have three rotamer wells:
+    3^(n-3) disjoint states (all torsions in their well cores) separated by a transient region, the
+    many-state, non-partition case of Section 2.4.1's transient propagation.
   * ``ligand_receptor`` - a packed-globule receptor with an elastic network and a short ligand chain
     in a surface pocket, shaped like the FKBP-DMSO dissociation problem (Section 4.2).
 
@@ -32,6 +35,7 @@ POT_FORCE_FIELD = 1
 CV_DOUBLE_WELL = 0
 CV_DIHEDRAL_RECT = 1
 CV_COM_DISTANCE = 2
+CV_ROTAMERS = 3
 
 OBS_COORD = 0
 OBS_POTENTIAL = 1
@@ -233,6 +237,63 @@ def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas:
                      (OBS_DIHEDRAL, (c - 2, c - 1, c, c + 1)),
                      (OBS_DIHEDRAL, (c - 1, c, c + 1, c + 2))],
         n_replicas=n_replicas, t_gr=10, t_check=500, tol=0.01, min_fv_steps=0,
+    )
+    s.q0 = x
+    s.p0 = maxwell_boltzmann(mass, kT, 3, np.random.default_rng(dyn_seed))
+    return s
+
+
+def alkane(n_atoms: int = 7, dyn_seed: int = 2431, n_replicas: int = 32, temperature: float = 300.0,
+           core_half_width: float = 35.0, torsions=None) -> System:
+    """United-atom n-alkane with rotamer states (a many-state stand-in; no dataset of the paper).
+
+    Beads of 14 amu along a chain; bonds k = 3e5 kJ/mol/nm^2, r0 = 0.154 nm; angles k = 520
+    kJ/mol/rad^2, theta0 = 114 deg; each backbone torsion V(phi) = 1/2 V1 (1 + cos phi) + 1/2 V2
+    (1 - cos 2 phi) + 1/2 V3 (1 + cos 3 phi) with (V1, V2, V3) = (5.9046, -1.1339, 13.1606) kJ/mol
+    (trans at 180 deg, gauche wells at +-60 deg, 3.6 kJ/mol above trans, barriers 10-14 kJ/mol),
+    written as terms k (1 + cos(n phi - delta)) up to a constant: (n, k, delta) = (1, V1/2, 0),
+    (2, |V2|/2, 0), (3, V3/2, 0); LJ sigma = 0.395 nm, eps = 0.382 kJ/mol between beads four or more
+    bonds apart (1-2, 1-3 and 1-4 pairs excluded); no charges, no cutoff; gamma = 1/ps, dt = 2 fs.
+    States: the rotamer wells of the n-3 torsions (gauche+ [0, 120), trans, gauche- [-120, 0)
+    degrees); a configuration is in state sum_t well_t 3^t when every torsion is within
+    `core_half_width` degrees of its well's centre, and leaves it when a torsion changes well.  The
+    initial chain is all-trans (or has the given torsions, degrees).  Observables for the
+    Gelman-Rubin test: the potential energy and the end-to-end distance."""
+    n = n_atoms
+    if not 4 <= n <= 7:
+        raise ValueError("the rotamer state index covers 1 to 4 torsions (4 to 7 beads)")
+    m = n - 3
+    mass = np.full(n, 14.0)
+    sigma = np.full(n, 0.395)
+    epsilon = np.full(n, 0.382)
+    bonds = np.array([[i, i + 1] for i in range(n - 1)], np.int32)
+    angles = np.array([[i, i + 1, i + 2] for i in range(n - 2)], np.int32)
+    v1, v2, v3 = 5.9046, -1.1339, 13.1606
+    dih, dn, dk, dd = [], [], [], []
+    for i in range(m):
+        for mult, k in ((1, v1 / 2), (2, abs(v2) / 2), (3, v3 / 2)):
+            dih.append([i, i + 1, i + 2, i + 3])
+            dn.append(mult)
+            dk.append(k)
+            dd.append(0.0)
+    excl = np.array([[i, j] for i in range(n) for j in range(i + 1, min(n, i + 4))], np.int32)
+    bond, angle = 0.154, math.radians(114.0)
+    tors = [180.0] * m if torsions is None else list(torsions)
+    x = _chain_geometry(n, bond, angle, [math.radians(t) for t in tors])
+    x -= x.mean(axis=0)
+    kT = KB_KJ_PER_MOL_K * temperature
+    s = System(
+        name=f"alkane{n}", n_atoms=n, dim=3, potential=POT_FORCE_FIELD, mass=mass,
+        kT=kT, gamma=1.0, dt=0.002, sigma=sigma, epsilon=epsilon, charge=np.zeros(n), excl=excl,
+        cutoff=0.0, coulomb_k=COULOMB_K,
+        bonds=bonds, bond_k=np.full(n - 1, 3.0e5), bond_r0=np.full(n - 1, bond),
+        angles=angles, angle_k=np.full(n - 2, 520.0), angle_theta0=np.full(n - 2, angle),
+        dihedrals=np.array(dih, np.int32).reshape(-1, 4), dihedral_n=np.array(dn, np.int32),
+        dihedral_k=np.array(dk), dihedral_delta=np.array(dd),
+        cv_kind=CV_ROTAMERS, cv_atoms=tuple(range(n)), cv_params=(float(m), float(core_half_width)),
+        groups=[[0], [n - 1]],
+        observables=[(OBS_POTENTIAL, ()), (OBS_GROUP_DISTANCE, (0, 1))],
+        n_replicas=n_replicas, t_gr=10, t_check=100, tol=0.01, min_fv_steps=1000,
     )
     s.q0 = x
     s.p0 = maxwell_boltzmann(mass, kT, 3, np.random.default_rng(dyn_seed))
