@@ -45,7 +45,7 @@ enum { GRP_FP64 = 0,  /* FP64 forces, FP64 integration, FP64 noise */
                          FP32 noise; FP64 only for state in memory, CV near boundaries, G-R */ };
 
 enum { GRP_POT_DOUBLE_WELL_2D = 0, GRP_POT_FORCE_FIELD = 1 };
-enum { GRP_CV_DOUBLE_WELL = 0, GRP_CV_DIHEDRAL_RECT = 1, GRP_CV_COM_DISTANCE = 2 };
+enum { GRP_CV_DOUBLE_WELL = 0, GRP_CV_DIHEDRAL_RECT = 1, GRP_CV_COM_DISTANCE = 2, GRP_CV_ROTAMERS = 3 };
 enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DIHEDRAL = 3,
        GRP_OBS_GROUP_DISTANCE = 4, GRP_OBS_RMS_VELOCITY = 5 };
 #define GRP_MAX_OBS 8
@@ -64,7 +64,12 @@ enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DI
  *     cv_atoms[0..3], psi of cv_atoms[1..4] (degrees, IUPAC sign); state 0 = phi in
  *     [cv_params[0], cv_params[1]] and psi in [cv_params[2], cv_params[3]], state 1 = complement.
  *     GRP_CV_COM_DISTANCE: d = |COM(group 0) - COM(group 1)|; state 0 = {d < cv_params[0]},
- *     state 1 = complement.
+ *     state 1 = complement.  GRP_CV_ROTAMERS (many disjoint states, not a partition: Section 2.4.1's
+ *     transient case): m = cv_params[0] (1..4) torsions phi_t of cv_atoms[t..t+3]; the wells of a
+ *     torsion are gauche+ [0, 120), trans [120, 180] and (-180, -120), gauche- [-120, 0) degrees
+ *     (digits 0, 1, 2); the configuration is in state sum_t well_t 3^t when every torsion lies
+ *     within w = cv_params[1] degrees (0 < w <= 60) of its well's centre (60, 180, -60), else in no
+ *     state; state omega is left when some torsion's well differs from digit t of omega.
  *   Observables: GRP_OBS_COORD (atom, axis), POTENTIAL, KINETIC, DIHEDRAL (4 atoms, radians),
  *     GROUP_DISTANCE (group a, group b), RMS_VELOCITY (group). */
 typedef struct {
@@ -250,6 +255,16 @@ grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, void *stream)
  * gives each run's state, h_out[n_runs] receives each run's status. */
 grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, int32_t t_check, int32_t t_gr, double tol,
                               int64_t min_fv_steps, grp_fv_status *h_out, void *stream);
+/* The whole loop of Fig. 1 for every run of the batch at once, each run in its own phase
+ * (transient, convergence, parallel step) and its own visits of its states: per tick one batched
+ * segment of t_check steps (replica 0 alone for a run in its transient, every replica otherwise),
+ * batched branching and Gelman-Rubin ratios for the runs in their convergence step, one readback.
+ * Each run's decisions and events are those of grp_run on that run alone (same parameters p, its
+ * own seed and state).  h_events is [n_runs][max_events] (run i's log at h_events + i max_events),
+ * h_n_events[n_runs] and h_t_sim[n_runs] (optional) receive each run's event count and clock.
+ * GRP_EINVAL for t_gr < 1, t_check outside [1, 20000] or tol <= 0. */
+grp_status grp_batch_run(grp_batch *b, const grp_run_params *p, grp_event *h_events, int32_t max_events,
+                         int32_t *h_n_events, int64_t *h_t_sim, void *stream);
 /* Pick the block size of the batched kernel by timing candidate sizes on a short segment (the
  * replicas' state and counters are restored afterwards); h_threads (optional) gets the choice. */
 grp_status grp_batch_autotune(grp_batch *b, int32_t t_gr, void *stream, int32_t *h_threads);

@@ -115,6 +115,8 @@ SIGNATURES = {
                                  C.POINTER(FvStatus), _VP]),
     "grp_run": (C.c_int32, [_VP, C.POINTER(RunParams), C.POINTER(Event), C.c_int32, _I32P,
                             C.POINTER(C.c_int64), _VP]),
+    "grp_batch_run": (C.c_int32, [_VP, C.POINTER(RunParams), C.POINTER(Event), C.c_int32, _I32P,
+                                  C.POINTER(C.c_int64), _VP]),
     "grp_run_original": (C.c_int32, [_VP, C.POINTER(OriginalParams), C.POINTER(Event), C.c_int32, _I32P,
                                      C.POINTER(C.c_int64), _VP]),
     "grp_get_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
@@ -435,6 +437,23 @@ def grp_batch_fv_check(b: BatchHandle, omegas, t_check: int, t_gr: int, tol: flo
     _check(_lib.grp_batch_fv_check(b.handle, om.ctypes.data_as(_I32P), t_check, t_gr, tol, min_fv_steps, b.status,
                                    _stream(stream)))
     return b.status
+
+
+def grp_batch_run(b: BatchHandle, t_gr: int, t_check: int, tol: float, min_fv_steps: int, max_steps: int,
+                  max_exits: int, max_events: int = 10000, stream=None):
+    """The loop of Fig. 1 for every run of the batch; returns ([events of run i], [t_sim of run i])."""
+    nr = len(b.runs)
+    p = RunParams(t_gr, t_check, tol, min_fv_steps, max_steps, max_exits)
+    ev = (Event * (max_events * nr))()
+    n = (C.c_int32 * nr)()
+    tsim = (C.c_int64 * nr)()
+    _check(_lib.grp_batch_run(b.handle, C.byref(p), ev, max_events, n, tsim, _stream(stream)))
+    out = []
+    for i in range(nr):
+        out.append([{"kind": e.kind, "omega": e.omega, "label_to": e.label_to, "k": e.k, "M": e.M,
+                     "steps": e.steps, "t_sim": e.t_sim, "n_branch": e.n_branch}
+                    for e in ev[i * max_events:i * max_events + n[i]]])
+    return out, list(tsim)
 
 
 def grp_batch_autotune(b: BatchHandle, t_gr: int = 0, stream=None) -> int:

@@ -163,6 +163,14 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       if (bad_atom(d->cv_atoms[t])) return fail(GRP_EINVAL, "cv_atoms[%d] out of range", t);
   } else if (d->cv_kind == GRP_CV_COM_DISTANCE) {
     if (d->dim != 3 || d->n_groups < 2) return fail(GRP_EINVAL, "COM-distance states need two groups");
+  } else if (d->cv_kind == GRP_CV_ROTAMERS) {
+    const double m = d->cv_params[0], w = d->cv_params[1];
+    if (d->dim != 3) return fail(GRP_EINVAL, "rotamer states need dim = 3");
+    if (!(m >= 1.0 && m <= 4.0) || m != (double)(int)m)
+      return fail(GRP_EINVAL, "rotamer states: cv_params[0] (torsions) must be an integer in [1, 4]");
+    if (!(w > 0.0 && w <= 60.0)) return fail(GRP_EINVAL, "rotamer states: core half-width cv_params[1] must be in (0, 60]");
+    for (int t = 0; t < (int)m + 3; ++t)
+      if (bad_atom(d->cv_atoms[t])) return fail(GRP_EINVAL, "cv_atoms[%d] out of range", t);
   } else {
     return fail(GRP_EINVAL, "unknown cv_kind %d", d->cv_kind);
   }
@@ -687,15 +695,25 @@ extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs
   return GRP_OK;
 }
 
-// One batched segment of k steps (k <= kMaxSegment) with or without the fused exit test.
-static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, const int32_t *omega, cudaStream_t st) {
+// What one batched segment does for one run: replicas advanced (0: none), sampling period, fused
+// exit test against omega, parallel-step check index M and early return after an earlier exit.
+struct RunTick {
+  int n_active, t_gr, do_check, omega, skip;
+  long long M;
+};
+
+// One batched segment of k steps (k <= kMaxSegment), each run as its tick says.
+static grp_status batch_launch(grp_batch *b, int k, const RunTick *ticks, cudaStream_t st) {
   const int nr = (int)b->runs.size();
   CU(cudaStreamSynchronize(st));  // the pinned argument block may still be read by a queued copy
   for (int i = 0; i < nr; ++i) {
     grp_replicas *r = b->runs[i];
-    SegArgs a = seg_args(r, k, t_gr, r->R);
-    a.do_check = do_check;
-    a.omega = omega ? omega[i] : 0;
+    const RunTick &t = ticks[i];
+    SegArgs a = seg_args(r, k, t.t_gr, t.n_active);
+    a.do_check = t.do_check;
+    a.omega = t.omega;
+    a.M = t.M;
+    a.skip_if_exit = t.skip;
     a.pairs_in_smem = r->sys->seg.pairs_in_smem;
     a.noise_batch = r->sys->seg.noise_batch;
     a.lean = r->sys->seg.lean;
@@ -704,10 +722,46 @@ static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, con
   CU(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(SegArgs) * nr, cudaMemcpyHostToDevice, st));
   CU(launch_segment_batch(b->d_args, b->d_units, b->n_units, b->d_counter, b->precision, b->threads, b->smem, st,
                           nullptr));
-  for (grp_replicas *r : b->runs) {
-    r->t_global += k;
-    r->t_phase += k;
+  for (int i = 0; i < nr; ++i) {
+    if (ticks[i].n_active <= 0) continue;
+    b->runs[i]->t_global += k;
+    b->runs[i]->t_phase += k;
   }
+  return GRP_OK;
+}
+
+// Every replica of every run, with or without the fused exit test.
+static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, const int32_t *omega, cudaStream_t st) {
+  std::vector<RunTick> ticks(b->runs.size());
+  for (size_t i = 0; i < ticks.size(); ++i)
+    ticks[i] = RunTick{b->runs[i]->R, t_gr, do_check, omega ? omega[i] : 0, 0, 0};
+  return batch_launch(b, k, ticks.data(), st);
+}
+
+// After a batched exit test: branching of the runs with branch[i], Gelman-Rubin ratios of those with
+// gr[i], and one readback of every run's status into b->h_status.
+static grp_status batch_status(grp_batch *b, const int *branch, const int *gr, cudaStream_t st) {
+  const int nr = (int)b->runs.size();
+  for (int i = 0; i < nr; ++i) {
+    grp_replicas *r = b->runs[i];
+    const SysDev &D = r->sys->dev;
+    RunArrays a;
+    a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc; a.exited = r->exited; a.labels = r->labels;
+    a.src = r->src; a.n_branched = b->d_nb + i; a.rhat = r->rhat; a.err = r->err;
+    a.nd = D.nd; a.nacc = D.n_obs * 4; a.n_rep = r->R; a.n_obs = D.n_obs;
+    a.seed = r->seed; a.t_global = r->t_global;
+    a.exit_key = r->exit_key;
+    a.branch = branch[i];
+    a.gr = gr[i];
+    b->h_arrays[i] = a;
+  }
+  CU(cudaMemcpyAsync(b->d_arrays, b->h_arrays, sizeof(RunArrays) * nr, cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(b->d_nb, 0, sizeof(int) * nr, st));
+  CU(launch_fv_branch_batch(b->d_arrays, b->d_branch_units, b->n_branch_units, st));
+  CU(launch_gelman_rubin_batch(b->d_arrays, b->d_gr_units, b->n_gr_units, st));
+  CU(launch_collect_status(b->d_arrays, nr, b->d_status, st));
+  CU(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * nr, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
   return GRP_OK;
 }
 
@@ -733,23 +787,8 @@ extern "C" grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, i
   const int nr = (int)b->runs.size();
   grp_status e = batch_segment(b, t_check, t_gr, 1, h_omega, st);
   if (e != GRP_OK) return e;
-  for (int i = 0; i < nr; ++i) {
-    grp_replicas *r = b->runs[i];
-    const SysDev &D = r->sys->dev;
-    RunArrays a;
-    a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc; a.exited = r->exited; a.labels = r->labels;
-    a.src = r->src; a.n_branched = b->d_nb + i; a.rhat = r->rhat; a.err = r->err;
-    a.nd = D.nd; a.nacc = D.n_obs * 4; a.n_rep = r->R; a.n_obs = D.n_obs;
-    a.seed = r->seed; a.t_global = r->t_global;
-    b->h_arrays[i] = a;
-  }
-  CU(cudaMemcpyAsync(b->d_arrays, b->h_arrays, sizeof(RunArrays) * nr, cudaMemcpyHostToDevice, st));
-  CU(cudaMemsetAsync(b->d_nb, 0, sizeof(int) * nr, st));
-  CU(launch_fv_branch_batch(b->d_arrays, b->d_branch_units, b->n_branch_units, st));
-  CU(launch_gelman_rubin_batch(b->d_arrays, b->d_gr_units, b->n_gr_units, st));
-  CU(launch_collect_status(b->d_arrays, nr, b->d_status, st));
-  CU(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * nr, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
+  const std::vector<int> all(nr, 1);
+  if ((e = batch_status(b, all.data(), all.data(), st)) != GRP_OK) return e;
   for (int i = 0; i < nr; ++i) {
     const grp_replicas *r = b->runs[i];
     const BatchStatus &s = b->h_status[i];
@@ -1182,6 +1221,156 @@ extern "C" grp_status grp_run_original(grp_replicas *r, const grp_original_param
   cudaStreamSynchronize(st);  // the scratch is freed below: nothing may still use it
   grp_status e2 = latch_errors(r, st);
   return e != GRP_OK ? e : e2;
+}
+
+// ------------------------------------------------------------------------------------------------
+// The loop of Fig. 1 for every run of a batch, each run in its own phase: one batched segment of
+// t_check steps per tick (replica 0 alone for a transient, every replica for a convergence or a
+// parallel step, none for a finished run), then batched branching and Gelman-Rubin ratios for the
+// runs in their convergence step and one readback of all statuses.  Each run's decisions and event
+// log are those of grp_run on that run alone.
+namespace {
+struct RunLoop {
+  enum Phase { kTransient, kFv, kParallel, kDone } phase = kTransient;
+  int omega = -1, nexit = 0;
+  long long treach = 0, nbranch = 0, M = 0, left = 0;
+  EventLog L{nullptr, 0};
+};
+}  // namespace
+
+extern "C" grp_status grp_batch_run(grp_batch *b, const grp_run_params *p, grp_event *h_events, int32_t max_events,
+                                    int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
+  const Range range("grp_batch_run (Fig. 1, every run)");
+  if (!b || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_batch_run: null argument");
+  if (p->t_gr < 1 || p->t_check < 1 || p->t_check > kMaxSegment || !(p->tol > 0))
+    return fail(GRP_EINVAL, "grp_batch_run: need t_gr >= 1, t_check in [1, %lld], tol > 0", kMaxSegment);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nr = (int)b->runs.size();
+  std::vector<RunLoop> run(nr);
+  for (int i = 0; i < nr; ++i) run[i].L = EventLog{h_events ? h_events + (size_t)i * max_events : nullptr, max_events};
+
+  auto finish = [&](int i) { run[i].phase = RunLoop::kDone; };
+  // a new visit from the current configuration of replica 0, whose state label is `label`
+  auto begin_fv = [&](int i, int omega) -> grp_status {
+    grp_replicas *r = b->runs[i];
+    CU(launch_copy_replica(r->sys->dev, r->R, r->q, r->p, r->f, r->acc, 0, -1, 1, st));
+    r->t_phase = 0;
+    run[i].omega = omega;
+    run[i].nbranch = 0;
+    run[i].phase = RunLoop::kFv;
+    return GRP_OK;
+  };
+  auto start_visit = [&](int i, int label) -> grp_status {
+    RunLoop &u = run[i];
+    const grp_replicas *r = b->runs[i];
+    if (!(u.nexit < p->max_exits && r->t_global < p->max_steps && u.L.n < max_events)) { finish(i); return GRP_OK; }
+    u.treach = 0;
+    if (label >= 0) return begin_fv(i, label);
+    u.phase = RunLoop::kTransient;
+    return GRP_OK;
+  };
+
+  // the label of every run's replica 0 before the first tick
+  for (int i = 0; i < nr; ++i) {
+    grp_replicas *r = b->runs[i];
+    CU(launch_check(r->sys->dev, r->q, 1, 0, r->labels, r->exited, nullptr, 0, st));
+    CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  grp_status e = GRP_OK;
+  for (int i = 0; i < nr && e == GRP_OK; ++i) e = start_visit(i, b->runs[i]->hb->label0);
+  if (e != GRP_OK) return e;
+
+  std::vector<RunTick> ticks(nr);
+  std::vector<int> branch(nr), gr(nr);
+  for (;;) {
+    int busy = 0;
+    for (int i = 0; i < nr; ++i) {
+      RunLoop &u = run[i];
+      grp_replicas *r = b->runs[i];
+      // the convergence step runs while t_global < max_steps (as in grp_run)
+      if (u.phase == RunLoop::kFv && r->t_global >= p->max_steps) finish(i);
+      RunTick t{0, 0, 1, 0, 0, 0};
+      branch[i] = gr[i] = 0;
+      if (u.phase == RunLoop::kTransient) {
+        t.n_active = 1;
+      } else if (u.phase == RunLoop::kFv) {
+        t = RunTick{r->R, p->t_gr, 1, u.omega, 0, 0};
+        branch[i] = 1;
+        gr[i] = (r->t_phase + p->t_check >= p->min_fv_steps && r->R > 1 && r->sys->dev.n_obs > 0) ? 1 : 0;
+      } else if (u.phase == RunLoop::kParallel) {
+        t = RunTick{r->R, 0, 1, u.omega, 1, ++u.M};
+      }
+      ticks[i] = t;
+      busy += t.n_active > 0;
+    }
+    if (!busy) break;
+    if ((e = batch_launch(b, p->t_check, ticks.data(), st)) != GRP_OK) return e;
+    if ((e = batch_status(b, branch.data(), gr.data(), st)) != GRP_OK) return e;
+    for (int i = 0; i < nr; ++i) {
+      if (b->h_status[i].err && (e = latch_errors(b->runs[i], st)) != GRP_OK) return e;
+    }
+    for (int i = 0; i < nr; ++i) {
+      RunLoop &u = run[i];
+      grp_replicas *r = b->runs[i];
+      const BatchStatus &s = b->h_status[i];
+      if (ticks[i].n_active == 0) continue;
+      if (u.phase == RunLoop::kTransient) {
+        u.treach += p->t_check;
+        if (s.label0 >= 0) {
+          if (u.treach > 0) {
+            u.L.tsim += u.treach;
+            u.L.add(GRP_EV_TRANSIENT, -1, s.label0, 0, 0, u.treach, 0);
+          }
+          if ((e = begin_fv(i, s.label0)) != GRP_OK) return e;
+        } else if (r->t_global >= p->max_steps) {
+          finish(i);
+        }
+      } else if (u.phase == RunLoop::kFv) {
+        if (s.exited0) {  // the reference walker left omega: the F-V workers are discarded
+          u.L.tsim += r->t_phase;
+          u.L.add(GRP_EV_REF_EXIT, u.omega, s.label0, 0, 0, r->t_phase, u.nbranch);
+          ++u.nexit;
+          if ((e = start_visit(i, s.label0)) != GRP_OK) return e;
+          continue;
+        }
+        if (s.n_branched > 0 && s.n_branched == r->R - 1)
+          u.L.add(GRP_EV_FV_ALL_EXITED, u.omega, u.omega, 0, 0, r->t_phase, s.n_branched);
+        u.nbranch += s.n_branched;
+        int conv = gr[i];
+        for (int j = 0; j < r->sys->dev.n_obs && conv; ++j) conv = s.rhat[j] < 1.0 + p->tol;
+        if (conv) {
+          u.L.tsim += r->t_phase;
+          u.L.add(GRP_EV_FV_CONVERGED, u.omega, u.omega, 0, 0, r->t_phase, u.nbranch);
+          u.left = (p->max_steps - r->t_global + p->t_check - 1) / p->t_check;
+          if (u.left < 1) { finish(i); continue; }
+          CU(cudaMemsetAsync(r->exit_key, 0xff, 8, st));
+          u.M = 0;
+          u.phase = RunLoop::kParallel;
+        }
+      } else if (u.phase == RunLoop::kParallel) {
+        if (s.exit_key != ~0ull) {
+          const int k0 = (int)(s.exit_key & 0xffffffffu);
+          const long long tau = ((long long)r->R * (u.M - 1) + (k0 + 1)) * (long long)p->t_check;
+          u.L.tsim += tau;
+          u.L.add(GRP_EV_PARALLEL_EXIT, u.omega, s.label_k, k0 + 1, u.M, tau, 0);
+          ++u.nexit;
+          // the exit configuration becomes the reference walker
+          if (k0 != 0) CU(launch_copy_replica(r->sys->dev, r->R, r->q, r->p, r->f, r->acc, k0, 0, 0, st));
+          if ((e = start_visit(i, s.label_k)) != GRP_OK) return e;
+        } else if (u.M >= u.left) {
+          finish(i);
+        }
+      }
+    }
+  }
+  for (int i = 0; i < nr; ++i) {
+    if (h_n_events) h_n_events[i] = std::min(run[i].L.n, max_events);
+    if (h_t_sim) h_t_sim[i] = run[i].L.tsim;
+  }
+  for (int i = 0; i < nr; ++i)
+    if ((e = latch_errors(b->runs[i], st)) != GRP_OK) return e;
+  return GRP_OK;
 }
 
 // ------------------------------------------------------------------------------------------------

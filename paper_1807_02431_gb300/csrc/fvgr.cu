@@ -84,6 +84,7 @@ cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, d
 __global__ void __launch_bounds__(256) fv_branch_batch_kernel(const RunArrays *runs, const uint2 *units) {
   const uint2 u = units[blockIdx.x];
   const RunArrays &a = runs[u.x];
+  if (!a.branch) return;
   fv_branch_one((int)u.y, a.n_rep, a.nd, a.nacc, a.q, a.p, a.f, a.acc, a.exited, a.src, a.n_branched, a.seed,
                 a.t_global);
 }
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(256) gelman_rubin_kernel(int n_rep, int n_obs,
 __global__ void __launch_bounds__(256) gelman_rubin_batch_kernel(const RunArrays *runs, const uint2 *units) {
   const uint2 u = units[blockIdx.x];
   const RunArrays &a = runs[u.x];
+  if (!a.gr) return;
   gelman_rubin_one((int)u.y, a.n_rep, a.n_obs, a.acc, a.rhat);
 }
 
@@ -170,6 +172,9 @@ __global__ void collect_status_kernel(const RunArrays *runs, int n_runs, BatchSt
   s.exited0 = a.exited[0];
   s.err = *a.err;
   for (int j = 0; j < kMaxObs; ++j) s.rhat[j] = j < a.n_obs ? a.rhat[j] : 0.0;
+  s.exit_key = a.exit_key ? *a.exit_key : ~0ull;
+  s.label_k = s.exit_key != ~0ull ? a.labels[(int)(s.exit_key & 0xffffffffu)] : -1;
+  s.pad = 0;
   out[r] = s;
 }
 

@@ -23,7 +23,7 @@ struct SegArgs {
   int n_active;
   int do_check, omega;
   long long M;               // check index written into the exit key
-  int skip_if_exit;          // return at once when *exit_key is already set
+  int skip_if_exit;          // return at once when *exit_key holds an exit of a check before M
   int pairs_in_smem;
   int noise_batch;           // steps of noise generated together (0: drawn inline per atom)
   int lean;                  // atom parameters read from the global table (large systems)
@@ -84,6 +84,9 @@ struct RunArrays {
   int nd, nacc, n_rep, n_obs;
   uint64_t seed;
   long long t_global;
+  unsigned long long *exit_key;
+  int branch;  // the run is in its convergence step: branch its exited workers
+  int gr;      // evaluate its Gelman-Rubin ratios
 };
 struct BatchStatus {
   int n_branched;
@@ -91,6 +94,9 @@ struct BatchStatus {
   int exited0;
   int err;
   double rhat[kMaxObs];
+  unsigned long long exit_key;  // (M << 32 | replica) of the first exit of a parallel step, or ~0
+  int label_k;                  // state of that replica (-1 when none)
+  int pad;
 };
 static_assert(sizeof(SegArgs) % sizeof(int) == 0, "SegArgs is copied word by word");
 

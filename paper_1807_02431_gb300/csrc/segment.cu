@@ -47,6 +47,24 @@ __device__ int state_check_f64(const SysDev &S, Get get, int omega, int *out_exi
     *out_exited = omega == 0 ? (x[0] >= 0.0) : (x[0] < 0.0);
     return x[0] < -w ? 0 : (x[0] > w ? 1 : -1);
   }
+  if (S.cv_kind == GRP_CV_ROTAMERS) {
+    // base-3 index of the torsions' wells (gauche+ [0, 120), trans, gauche- [-120, 0) degrees); in a
+    // state when every torsion is within w of its well's centre; outside omega when a well differs
+    const int *c = S.cv_atoms;
+    const int m = (int)S.cv_params[0];
+    const double w = S.cv_params[1], deg = 57.295779513082320876798154814105;
+    int label = 0, scale = 1, core = 1, ex = 0, rest = omega;
+    for (int t = 0; t < m; ++t, rest /= 3, scale *= 3) {
+      const double phi = deg * dihedral_rad_f64(get, c[t], c[t + 1], c[t + 2], c[t + 3]);
+      const int well = (phi >= 0.0 && phi < 120.0) ? 0 : ((phi >= -120.0 && phi < 0.0) ? 2 : 1);
+      const double off = well == 0 ? fabs(phi - 60.0) : (well == 2 ? fabs(phi + 60.0) : 180.0 - fabs(phi));
+      core &= off < w ? 1 : 0;
+      label += well * scale;
+      ex |= well != rest % 3 ? 1 : 0;
+    }
+    *out_exited = ex;
+    return core ? label : -1;
+  }
   int label;
   if (S.cv_kind == GRP_CV_DIHEDRAL_RECT) {
     const int *c = S.cv_atoms;
@@ -74,6 +92,13 @@ __device__ __forceinline__ void acc_add(double *acc, double v) {
   acc[1] += d;
   acc[2] += d * d;
   acc[3] += 1.0;
+}
+
+// A parallel-step segment of check M is skipped when an exit was already recorded at an earlier
+// check (segments are queued ahead of the readback); an exit at the same check M must not stop the
+// other replicas of check M, whose exits may carry a lower index k.
+__device__ __forceinline__ bool exit_seen_before(const SegArgs &a) {
+  return (*(volatile unsigned long long *)a.exit_key >> 32) < (unsigned long long)a.M;
 }
 
 __device__ __forceinline__ void record_check(const SegArgs &a, int r, int label, int ex) {
@@ -431,7 +456,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
 // on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
 template <class P, int kMaxThreads, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
-  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
+  if (a.skip_if_exit && exit_seen_before(a)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   segment_body<P, kMode>(a, blockIdx.x, smem);
 }
@@ -446,7 +471,18 @@ __global__ void __launch_bounds__(512, 1) ff_segment_batch_kernel(const SegArgs 
   __shared__ SegArgs sa;
   __shared__ int su;
   for (;;) {
-    if (threadIdx.x == 0) su = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      // units of replicas beyond a run's n_active (a transient advances replica 0 alone, a finished
+      // run none) and of runs whose parallel step saw an exit at an earlier check are passed over
+      int u = atomicAdd(counter, 1);
+      while (u < n_units) {
+        const uint2 un = units[u];
+        const SegArgs &g = runs[un.x];
+        if ((int)un.y < g.n_active && !(g.skip_if_exit && exit_seen_before(g))) break;
+        u = atomicAdd(counter, 1);
+      }
+      su = u;
+    }
     __syncthreads();
     const int u = su;
     if (u >= n_units) break;
@@ -465,7 +501,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
   const SysDev &S = a.S;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.n_active) return;
-  if (a.skip_if_exit && *(volatile unsigned long long *)a.exit_key != ~0ull) return;
+  if (a.skip_if_exit && exit_seen_before(a)) return;
   double x = a.q[2 * r], y = a.q[2 * r + 1], px = a.p[2 * r], py = a.p[2 * r + 1];
   double fx = a.f[2 * r], fy = a.f[2 * r + 1];
   const int no = S.n_obs;

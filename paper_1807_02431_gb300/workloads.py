@@ -243,7 +243,7 @@ def chain(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas:
     return s
 
 
-def alkane(n_atoms: int = 7, dyn_seed: int = 2431, n_replicas: int = 32, temperature: float = 300.0,
+def alkane(n_atoms: int = 7, dyn_seed: int = 2431, n_replicas: int = 32, temperature: float = 250.0,
            core_half_width: float = 35.0, torsions=None) -> System:
     """United-atom n-alkane with rotamer states (a many-state stand-in; no dataset of the paper).
 
@@ -258,7 +258,10 @@ def alkane(n_atoms: int = 7, dyn_seed: int = 2431, n_replicas: int = 32, tempera
     degrees); a configuration is in state sum_t well_t 3^t when every torsion is within
     `core_half_width` degrees of its well's centre, and leaves it when a torsion changes well.  The
     initial chain is all-trans (or has the given torsions, degrees).  Observables for the
-    Gelman-Rubin test: the potential energy and the end-to-end distance."""
+    Gelman-Rubin test: the potential energy and the end-to-end distance, TOL = 0.05, at least 1,000
+    F-V steps.  At 250 K a state lasts ~10^4 steps and the convergence step needs ~8 x 10^3, so
+    about 40 % of the visits end in a parallel step (at 300 K with TOL = 0.01 the reference walker
+    leaves before convergence in most visits)."""
     n = n_atoms
     if not 4 <= n <= 7:
         raise ValueError("the rotamer state index covers 1 to 4 torsions (4 to 7 beads)")
@@ -293,7 +296,7 @@ def alkane(n_atoms: int = 7, dyn_seed: int = 2431, n_replicas: int = 32, tempera
         cv_kind=CV_ROTAMERS, cv_atoms=tuple(range(n)), cv_params=(float(m), float(core_half_width)),
         groups=[[0], [n - 1]],
         observables=[(OBS_POTENTIAL, ()), (OBS_GROUP_DISTANCE, (0, 1))],
-        n_replicas=n_replicas, t_gr=10, t_check=100, tol=0.01, min_fv_steps=1000,
+        n_replicas=n_replicas, t_gr=10, t_check=100, tol=0.05, min_fv_steps=1000,
     )
     s.q0 = x
     s.p0 = maxwell_boltzmann(mass, kT, 3, np.random.default_rng(dyn_seed))

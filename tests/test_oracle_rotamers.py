@@ -75,7 +75,7 @@ def test_labels_of_each_single_torsion_well(oracle_mod):
 def test_wells_tile_the_circle(oracle_mod):
     """On configurations along a trajectory exactly one of the 81 states is not exited, and it is the
     labelled state whenever the configuration is in a core."""
-    s = W.alkane()
+    s = W.alkane(temperature=300.0)
     o = oracle_mod.Oracle(s)
     R = 4
     q = np.repeat(s.q0[None], R, 0).copy()
@@ -98,7 +98,7 @@ def test_butane_trans_gauche_occupancy(oracle_mod):
     """Occupancy ratios of the three wells against the Boltzmann weights of the torsion potential."""
     import dataclasses
 
-    s = dataclasses.replace(W.alkane(n_atoms=4), observables=[(W.OBS_DIHEDRAL, (0, 1, 2, 3))])
+    s = dataclasses.replace(W.alkane(n_atoms=4, temperature=300.0), observables=[(W.OBS_DIHEDRAL, (0, 1, 2, 3))])
     o = oracle_mod.Oracle(s)
     R, k, t_gr = 48, 200_000, 50
     q = np.repeat(s.q0[None], R, 0).copy()
