@@ -251,6 +251,40 @@ def accelerated_speed(B, s, precision, R, seed, max_steps, max_exits=10 ** 6, un
     return out
 
 
+def multistate_bench(B, max_steps, n_runs=64):
+    """The state-to-state loop at scale: n_runs independent Gen. ParRep runs of the 7-bead alkane
+    (81 rotamer states, transients between them), 32 replicas each, mixed precision, all advanced by
+    grp_batch_run until each run's step counter reaches max_steps.  Reports the summed simulated time
+    per wall time (Tables 2 and 4's speed, over all runs), the visits and the exit statistics of the
+    most visited states (mean with its 95 % chi-square interval, Section 4)."""
+    import torch
+
+    from paper_1807_02431_gb300 import analysis
+
+    s = W.alkane()
+    reps = []
+    for i in range(n_runs):
+        sysh = B.grp_create_system(s, B.GRP_MIXED)
+        reps.append((sysh, B.grp_init_replicas(sysh, s.n_replicas, 9000 + i, s.q0, s.p0)))
+    b = B.grp_batch_create([r for _, r in reps])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    evs, tsims = B.grp_batch_run(b, s.t_gr, s.t_check, s.tol, s.min_fv_steps, max_steps, 10 ** 6)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    sim_ns = sum(tsims) * s.dt * 1e-3
+    rep = analysis.state_report(evs, dt=s.dt)
+    top = sorted(rep, key=lambda k: -rep[k]["n"])[:3]
+    vis = [v for ev in evs for v in analysis.visits(ev)]
+    return {"system": f"alkane7 (81 rotamer states), {n_runs} runs x {s.n_replicas} replicas, mixed, "
+                      f"t_check {s.t_check}, TOL {s.tol}, {max_steps} steps per run",
+            "wall_s": wall, "t_sim_ns": sim_ns, "ns_per_day": sim_ns / (wall / 86400.0),
+            "visits": len(vis), "parallel_exits": sum(1 for v in vis if v[3]),
+            "states_visited": len({v[0] for v in vis}),
+            "top_states_ps": {str(k): {"n": rep[k]["n"], "mean": rep[k]["mean"], "ci95": list(rep[k]["ci"])}
+                              for k in top}}
+
+
 def batched_bench(B, steps, warmup, flush, n_runs=64, R=128):
     """64 independent runs of chains with sizes drawn uniformly in 22..400 beads, 128 replicas each,
     mixed precision, one persistent kernel per exit test (autotuned block size)."""
@@ -419,6 +453,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--ligand-steps", type=int, default=3)
     ap.add_argument("--gradient-reps", type=int, default=2)
+    ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint", "batch"], default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
     ap.add_argument("--profile-replicas", type=int, default=152)
@@ -512,6 +547,7 @@ def main():
                                                         max_exits=8, unit_ns=False)
             accel["double_well_2d_original"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
                                                                  max_exits=8, unit_ns=False, original=True)
+        multistate = multistate_bench(B, args.multistate_steps) if args.multistate_steps > 0 else None
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cores = os.cpu_count() or 1
@@ -532,6 +568,7 @@ def main():
                "ligand_receptor": ligand,
                "gradient": gradient,
                "accelerated": accel,
+               "multistate": multistate,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},
                "cpu_baseline": cpu}
