@@ -342,6 +342,60 @@ def ligand_bench(B, steps, warmup, flush, fp64_steps):
     return out
 
 
+def branch_bytes(s, n_branched):
+    """Algorithmic HBM bytes of one branching: each branched worker reads and writes q, p, F (3 n dim
+    doubles) and its observable accumulators (4 n_obs doubles)."""
+    return n_branched * 2 * 8 * (3 * s.n_atoms * s.dim + 4 * len(s.observables))
+
+
+def branch_bench(B, flush, reps=10):
+    """Fleming-Viot branching bandwidth (Section 2.4.1, task 2) on the ligand system: 1,024 replicas of
+    2,030 atoms (q, p, F of all replicas: 150 MB, more than the 129 MB L2); every odd worker exited, so
+    511 workers each copy q, p, F and accumulators from a survivor.  Kernel time by CUDA events around
+    the asynchronous calls: K launches each after an L2 flush, minus K flushes alone, so that the GPU
+    never waits for the host between the events), against the measured HBM copy bandwidth."""
+    import torch
+
+    s = W.ligand_receptor()
+    R = s.n_replicas
+    sysh = B.grp_create_system(s, B.GRP_MIXED)
+    rep = B.grp_init_replicas(sysh, R, SEED, s.q0, s.p0)
+    ex = torch.zeros(R, dtype=torch.uint8, device="cuda")
+    ex[1::2] = 1
+    src = torch.empty(R, dtype=torch.int32, device="cuda")
+    nb = B.grp_fv_branch(rep, ex, src)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(with_branch):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            flush.zero_()
+            if with_branch:
+                B.grp_fv_branch(rep, ex, src, count=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    timed(True)
+    both = [timed(True) for _ in range(3)]
+    alone = [timed(False) for _ in range(3)]
+    ms = (float(np.median(both)) - float(np.median(alone))) / reps
+    peak = measured_hbm_gbs()
+    gbs = branch_bytes(s, nb) / (ms * 1e-3) / 1e9
+    return {"workload": f"ligand_receptor{s.n_atoms}_r{R}, {nb} workers branched", "kernel_ms": ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "bytes_per_launch": branch_bytes(s, nb), "peak_basis": "measured HBM copy (MEASURED_PEAKS.json)"}}
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # the profiling recipe's fallback
+
+
 def gradient_bench(B, reps):
     """Differentiation through the dynamics (the gradient workload): 256 replicas of the 22-bead chain,
     one 1,000-step fixed-noise segment with the end-to-end distance sampled every 10 steps, forward
@@ -396,6 +450,14 @@ def profile_case(B, case, replicas, steps, launches):
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0, omega=0)
         for _ in range(launches):
             B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
+    elif case == "branch":  # every odd worker exited; `replicas` ligand replicas
+        s = W.ligand_receptor()
+        sysh = B.grp_create_system(s, B.GRP_MIXED)
+        rep = B.grp_init_replicas(sysh, replicas, SEED, s.q0, s.p0)
+        ex = torch.zeros(replicas, dtype=torch.uint8, device="cuda")
+        ex[1::2] = 1
+        for _ in range(launches):
+            B.grp_fv_branch(rep, ex)
     else:
         s = W.chain_gradient()
         q0, p0 = W.replica_states(s, replicas, seed=24, spread=0.002)
@@ -454,7 +516,8 @@ def main():
     ap.add_argument("--ligand-steps", type=int, default=3)
     ap.add_argument("--gradient-reps", type=int, default=2)
     ap.add_argument("--multistate-steps", type=int, default=40000)
-    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint", "batch"], default=None,
+    ap.add_argument("--branch-reps", type=int, default=20)
+    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint", "batch", "branch"], default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
     ap.add_argument("--profile-replicas", type=int, default=152)
     ap.add_argument("--profile-steps", type=int, default=100)
@@ -548,6 +611,7 @@ def main():
             accel["double_well_2d_original"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
                                                                  max_exits=8, unit_ns=False, original=True)
         multistate = multistate_bench(B, args.multistate_steps) if args.multistate_steps > 0 else None
+        branching = branch_bench(B, flush, args.branch_reps) if args.branch_reps > 0 else None
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cores = os.cpu_count() or 1
@@ -569,6 +633,7 @@ def main():
                "gradient": gradient,
                "accelerated": accel,
                "multistate": multistate,
+               "branching": branching,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},
                "cpu_baseline": cpu}

@@ -284,10 +284,13 @@ def grp_check_states(r: ReplicasHandle, omega: int, d_labels=None, d_exited=None
     _check(_lib.grp_check_states(r.handle, omega, _ptr(d_labels), _ptr(d_exited), _stream(stream)))
 
 
-def grp_fv_branch(r: ReplicasHandle, d_exited=None, d_src=None, stream=None) -> int:
+def grp_fv_branch(r: ReplicasHandle, d_exited=None, d_src=None, stream=None, count=True):
+    """Branch the exited workers; returns how many were branched, or None with count=False (then the
+    call does not synchronise the stream)."""
     nb = C.c_int32(0)
-    _check(_lib.grp_fv_branch(r.handle, _ptr(d_exited), _ptr(d_src), C.byref(nb), _stream(stream)))
-    return nb.value
+    _check(_lib.grp_fv_branch(r.handle, _ptr(d_exited), _ptr(d_src), C.byref(nb) if count else None,
+                              _stream(stream)))
+    return nb.value if count else None
 
 
 def grp_gelman_rubin(r: ReplicasHandle, tol: float, stream=None):

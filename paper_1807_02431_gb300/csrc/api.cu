@@ -591,7 +591,6 @@ extern "C" grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, in
   if (!r) return fail(GRP_EINVAL, "grp_fv_branch: null handle");
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
-  CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
   CU(launch_fv_branch(D, r->R, r->q, r->p, r->f, r->acc, d_exited ? d_exited : r->exited, r->src, r->n_branched,
                       r->seed, r->t_global, st));
   if (d_src) CU(cudaMemcpyAsync(d_src, r->src, (size_t)r->R * 4, cudaMemcpyDeviceToDevice, st));
@@ -945,7 +944,6 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
   const int R = r->R;
   grp_status e = run_steps(r, t_check, t_gr, R, 1, omega, 0, 0, st);
   if (e != GRP_OK) return e;
-  CU(cudaMemsetAsync(r->n_branched, 0, 4, st));
   CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
   const bool want_gr = r->t_phase >= min_fv_steps && R > 1 && D.n_obs > 0;
   if (want_gr) {

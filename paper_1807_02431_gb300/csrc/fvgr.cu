@@ -5,64 +5,126 @@
 
 namespace grp {
 
+// Copy of one replica's q, p and F rows (nd doubles each) by the whole block.  When every row starts on
+// a 16-byte boundary (nd even on the library's own 256-byte-aligned arrays; caller-owned arrays are
+// checked) the copy moves double2 words, four per thread and array in flight before the stores:
+// twelve 16-byte loads per thread keep enough bytes in flight to approach the HBM bandwidth
+// (measured: 8-byte loads one at a time reached 36 % of it).  Source and destination rows never
+// overlap, and no thread writes a source row while the kernel runs.
+__device__ __forceinline__ void copy_row3(double *__restrict__ qd, double *__restrict__ pd, double *__restrict__ fd,
+                                          const double *__restrict__ qs, const double *__restrict__ ps,
+                                          const double *__restrict__ fs, int nd) {
+  const int bd = (int)blockDim.x;
+  int i = threadIdx.x;
+  const uintptr_t any = (uintptr_t)qd | (uintptr_t)pd | (uintptr_t)fd | (uintptr_t)qs | (uintptr_t)ps | (uintptr_t)fs;
+  if ((nd & 1) == 0 && (any & 15) == 0) {
+    const int n2 = nd >> 1;
+    const double2 *q2 = reinterpret_cast<const double2 *>(qs), *p2 = reinterpret_cast<const double2 *>(ps),
+                  *f2 = reinterpret_cast<const double2 *>(fs);
+    double2 *qo = reinterpret_cast<double2 *>(qd), *po = reinterpret_cast<double2 *>(pd),
+            *fo = reinterpret_cast<double2 *>(fd);
+    for (; i + 3 * bd < n2; i += 4 * bd) {
+      double2 a[4], b[4], c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = __ldg(q2 + i + u * bd);
+        b[u] = __ldg(p2 + i + u * bd);
+        c[u] = __ldg(f2 + i + u * bd);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        qo[i + u * bd] = a[u];
+        po[i + u * bd] = b[u];
+        fo[i + u * bd] = c[u];
+      }
+    }
+    for (; i < n2; i += bd) {
+      qo[i] = __ldg(q2 + i);
+      po[i] = __ldg(p2 + i);
+      fo[i] = __ldg(f2 + i);
+    }
+    return;
+  }
+  for (; i < nd; i += bd) {
+    qd[i] = qs[i];
+    pd[i] = ps[i];
+    fd[i] = fs[i];
+  }
+}
+
 // One block per replica r.  An exited worker r >= 1 draws u from Philox stream 1 at counter
 // (t_global, replica r), picks survivor number floor(u * |S| / 2^32) in ascending index order among
 // the non-exited workers S (the reference walker when S is empty) and copies q, p, F and the
 // observable accumulators from it.  Sources are never destinations, so the copies do not race.
+// Every exited worker is branched, so the block of the reference walker (r = 0, never branched)
+// stores their number in *n_branched: no counter to clear before the launch, no atomics.
 __device__ __forceinline__ void fv_branch_one(int r, int n_rep, int nd, int nacc, double *q, double *p, double *f,
                                               double *acc, const uint8_t *exited, int32_t *src, int *n_branched,
                                               uint64_t seed, long long t_global) {
   __shared__ int s_src;
   __shared__ int s_cnt[8];
-  if (r == 0 || !exited[r]) {
+  if (r == 0) {
+    int ne = 0;
+    for (int w = 1 + threadIdx.x; w < n_rep; w += blockDim.x) ne += exited[w] ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ne += __shfl_down_sync(0xffffffffu, ne, o);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = ne;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_cnt[w];
+      *n_branched = tot;
+      if (src) src[0] = -1;
+    }
+    return;
+  }
+  if (!exited[r]) {
     if (threadIdx.x == 0 && src) src[r] = -1;
     return;
   }
+  // Survivors S = the workers 1..R-1 not exited, in ascending order.  Each thread counts those of its
+  // contiguous chunk; a block-wide scan of the counts gives |S| and the rank of each chunk's first
+  // survivor; the thread whose chunk holds rank m = floor(u |S| / 2^32) walks it to that survivor.
+  // (Three dependent rounds of loads, where a warp scanning the mask 32 workers at a time took
+  // R/32 dependent rounds.)
+  const int nt = (int)blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int chunk = (n_rep - 1 + nt - 1) / nt;
+  const int lo = 1 + threadIdx.x * chunk, hi = min(n_rep, lo + chunk);
   int cnt = 0;
-  for (int w = 1 + threadIdx.x; w < n_rep; w += blockDim.x) cnt += exited[w] ? 0 : 1;
+  for (int w = lo; w < hi; ++w) cnt += exited[w] ? 0 : 1;
+  int incl = cnt;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_cnt[warp] = incl;
+  if (threadIdx.x == 0) s_src = 0;  // no surviving worker: copy the reference walker
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int ns = lane < (int)(blockDim.x >> 5) ? s_cnt[lane] : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
-    int found = 0;  // no surviving worker: copy the reference walker
-    if (ns > 0) {
-      const uint32_t u = philox_stream(seed, t_global, 1u, r, 0).v[0];
-      int remaining = (int)(((unsigned long long)u * (unsigned long long)ns) >> 32);
-      found = -1;
-      for (int base = 1; base < n_rep && found < 0; base += 32) {
-        const int w = base + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, w < n_rep && !exited[w]);
-        const int c = __popc(m);
-        if (remaining < c) {
-          unsigned mm = m;
-          for (int i = 0; i < remaining; ++i) mm &= mm - 1;
-          found = base + __ffs(mm) - 1;
-        } else {
-          remaining -= c;
-        }
+  int ns = 0, first = incl - cnt;
+  for (int w = 0; w < (nt >> 5); ++w) {
+    const int c = s_cnt[w];
+    ns += c;
+    if (w < warp) first += c;
+  }
+  if (ns > 0) {
+    const uint32_t u = philox_stream(seed, t_global, 1u, r, 0).v[0];
+    const int m = (int)(((unsigned long long)u * (unsigned long long)ns) >> 32);
+    if (m >= first && m < first + cnt) {
+      int rem = m - first;
+      for (int w = lo; w < hi; ++w) {
+        if (exited[w]) continue;
+        if (rem == 0) { s_src = w; break; }
+        --rem;
       }
     }
-    if (lane == 0) s_src = found;
   }
   __syncthreads();
   const int s = s_src;
-  if (s < 0) return;  // unreachable: ns counts the same survivors the scan walks
   const size_t a = (size_t)s * nd, b = (size_t)r * nd;
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    q[b + i] = q[a + i];
-    p[b + i] = p[a + i];
-    f[b + i] = f[a + i];
-  }
+  copy_row3(q + b, p + b, f + b, q + a, p + a, f + a, nd);
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[(size_t)r * nacc + i] = acc[(size_t)s * nacc + i];
-  if (threadIdx.x == 0) {
-    if (src) src[r] = s;
-    atomicAdd(n_branched, 1);
-  }
+  if (threadIdx.x == 0 && src) src[r] = s;
 }
 
 __global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int nacc, double *q, double *p,
@@ -202,11 +264,7 @@ __global__ void __launch_bounds__(256) copy_replica_kernel(int n_rep, int nd, in
     for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[(size_t)r * nacc + i] = 0.0;
   if (r == src || (dst >= 0 && r != dst)) return;
   const size_t a = (size_t)src * nd, b = (size_t)r * nd;
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    q[b + i] = q[a + i];
-    p[b + i] = p[a + i];
-    f[b + i] = f[a + i];
-  }
+  copy_row3(q + b, p + b, f + b, q + a, p + a, f + a, nd);
 }
 
 cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
@@ -229,19 +287,8 @@ __global__ void __launch_bounds__(256) dephase_kernel(int n_rep, int nd, double 
   const long long s = out ? 0 : stay[r] + t_check;
   __syncthreads();  // every thread has read stay[r] before thread 0 rewrites it
   const size_t b = (size_t)r * nd, ref = (size_t)n_rep * nd;
-  if (out) {
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-      q[b + i] = sq[ref + i];
-      p[b + i] = sp[ref + i];
-      f[b + i] = sf[ref + i];
-    }
-  } else if (s >= t_phase) {
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-      sq[b + i] = q[b + i];
-      sp[b + i] = p[b + i];
-      sf[b + i] = f[b + i];
-    }
-  }
+  if (out) copy_row3(q + b, p + b, f + b, sq + ref, sp + ref, sf + ref, nd);
+  else if (s >= t_phase) copy_row3(sq + b, sp + b, sf + b, q + b, p + b, f + b, nd);
   if (threadIdx.x == 0) {
     stay[r] = s;
     if (out) {

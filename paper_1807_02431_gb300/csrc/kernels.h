@@ -52,7 +52,7 @@ cudaError_t launch_segment(const SegArgs &a, const SegConfig &cfg, cudaStream_t 
 cudaError_t launch_check(const SysDev &S, const double *q, int n_rep, int omega, int8_t *labels,
                          uint8_t *exited, unsigned long long *exit_key, long long M, cudaStream_t st);
 
-// Fleming-Viot branching of exited workers; n_branched (device int) accumulates the copies.
+// Fleming-Viot branching of exited workers; n_branched (device int) receives the number branched.
 cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                              const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
                              long long t_global, cudaStream_t st);

@@ -66,10 +66,8 @@ extern "C" grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, 
   int *src = g_scratch_ptr[dev];
   int *counter = src + kNoAllocMaxReplicas;
   cudaStream_t st = (cudaStream_t)stream;
-  // the scratch keeps the previous call's contents: the counter must start at zero
-  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
-  if (e == cudaSuccess)
-    e = grp::launch_fv_branch(D, n_rep, d_q, d_p, d_f, d_acc, d_exited, src, counter, seed, (long long)t_global, st);
+  // the kernel stores the count (the block of replica 0 writes it), so the scratch needs no clearing
+  e = grp::launch_fv_branch(D, n_rep, d_q, d_p, d_f, d_acc, d_exited, src, counter, seed, (long long)t_global, st);
   int nb = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, counter, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
