@@ -46,6 +46,12 @@ enum { GRP_FP64 = 0,  /* FP64 forces, FP64 integration, FP64 noise */
 
 enum { GRP_POT_DOUBLE_WELL_2D = 0, GRP_POT_FORCE_FIELD = 1 };
 enum { GRP_CV_DOUBLE_WELL = 0, GRP_CV_DIHEDRAL_RECT = 1, GRP_CV_COM_DISTANCE = 2, GRP_CV_ROTAMERS = 3 };
+/* Coulomb model: the dielectric eps = 4r, or the reaction field of a cutoff scheme (Section 3.2 names
+ * it among the nonbonded methods an engine should offer; the paper's MD setups use a non-periodic
+ * cutoff, which the engine it used treats by a reaction field): for r < cutoff,
+ * E = k_e q_i q_j (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3),
+ * c_rf = 1/r_c + k_rf r_c^2 (eps_r = 1); it needs cutoff > 0. */
+enum { GRP_COULOMB_EPS4R = 0, GRP_COULOMB_REACTION_FIELD = 1 };
 enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DIHEDRAL = 3,
        GRP_OBS_GROUP_DISTANCE = 4, GRP_OBS_RMS_VELOCITY = 5 };
 #define GRP_MAX_OBS 8
@@ -58,7 +64,8 @@ enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DI
  *     bonds 1/2 k (r - r0)^2, angles 1/2 k (theta - theta0)^2 (radians), dihedral terms
  *     k (1 + cos(n phi - delta)), Lennard-Jones 4 eps_ij ((s_ij/r)^12 - (s_ij/r)^6) with
  *     s_ij = (s_i + s_j)/2, eps_ij = sqrt(eps_i eps_j), and Coulomb k_e q_i q_j / (4 r^2)
- *     (dielectric 4r), over every pair not in excl, truncated at `cutoff` when cutoff > 0.
+ *     (dielectric 4r; or the reaction field, coulomb_mode), over every pair not in excl, truncated at
+ *     `cutoff` when cutoff > 0.
  *   States: GRP_CV_DOUBLE_WELL: state 0 = {x < -w}, state 1 = {x > w} (w = cv_params[0]);
  *     state 0 is left when x >= 0, state 1 when x < 0.  GRP_CV_DIHEDRAL_RECT: phi = dihedral of
  *     cv_atoms[0..3], psi of cv_atoms[1..4] (degrees, IUPAC sign); state 0 = phi in
@@ -104,6 +111,8 @@ typedef struct {
   int32_t n_obs;
   int32_t obs_kind[GRP_MAX_OBS];
   int32_t obs_arg[GRP_MAX_OBS][4];
+  int32_t coulomb_mode;         /* GRP_COULOMB_EPS4R or GRP_COULOMB_REACTION_FIELD */
+  double rf_dielectric;         /* eps_rf of the reaction field (>= 1; 0 = infinity, a conductor) */
 } grp_system_desc;
 
 typedef struct grp_system grp_system;

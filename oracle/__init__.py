@@ -59,6 +59,7 @@ class OrcSystem(C.Structure):
         ("group_atoms", C.POINTER(C.c_int32)),
         ("n_obs", C.c_int32), ("obs_kind", C.c_int32 * MAX_OBS),
         ("obs_arg", (C.c_int32 * 4) * MAX_OBS),
+        ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
     ]
 
 
@@ -171,6 +172,7 @@ class Oracle:
         st.sigma, st.epsilon, st.charge = d("sigma", ea["sigma"]), d("eps", ea["epsilon"]), d("q", ea["charge"])
         st.n_excl, st.excl = len(ea["excl"]), i("excl", ea["excl"])
         st.cutoff, st.coulomb_k = s.cutoff, s.coulomb_k
+        st.coulomb_mode, st.rf_dielectric = s.coulomb_mode, s.rf_dielectric
         st.n_bonds, st.bond_atoms = len(ea["bonds"]), i("bonds", ea["bonds"])
         st.bond_k, st.bond_r0 = d("bk", ea["bond_k"]), d("br0", ea["bond_r0"])
         st.n_angles, st.angle_atoms = len(ea["angles"]), i("angles", ea["angles"])

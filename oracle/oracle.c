@@ -67,6 +67,15 @@ static void group_com(const orc_ctx *c, int g, const double *q, double *com) {
   for (int d = 0; d < 3; ++d) com[d] = acc[d] / mt;
 }
 
+/* Reaction-field constants (eps_r = 1): k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3) and
+ * c_rf = 1/r_c + k_rf r_c^2, so that the pair energy k_e q_i q_j (1/r + k_rf r^2 - c_rf) vanishes at
+ * the cutoff r_c; eps_rf = 0 stands for a conductor (eps_rf -> infinity, k_rf = 1 / (2 r_c^3)). */
+static void rf_constants(const orc_system *s, double *krf, double *crf) {
+  const double rc = s->cutoff, er = s->rf_dielectric;
+  *krf = (er == 0.0 ? 0.5 : (er - 1.0) / (2.0 * er + 1.0)) / (rc * rc * rc);
+  *crf = 1.0 / rc + *krf * rc * rc;
+}
+
 /* ---------------------------------------------------------------- potential V(q), Eq. 1 */
 double orc_potential(const orc_ctx *c, const double *q) {
   const orc_system *s = &c->s;
@@ -108,8 +117,16 @@ double orc_potential(const orc_ctx *c, const double *q) {
       double eps = sqrt(s->epsilon[i] * s->epsilon[j]);
       double sr6 = pow(sig * sig / r2, 3);
       e += 4.0 * eps * (sr6 * sr6 - sr6);
-      /* dielectric eps(r) = 4 r: E = k_e q_i q_j / (4 r * r) */
-      e += s->coulomb_k * s->charge[i] * s->charge[j] / (4.0 * r2);
+      const double kqq = s->coulomb_k * s->charge[i] * s->charge[j];
+      if (s->coulomb_mode == 1) {
+        /* reaction field: E = k_e q_i q_j (1/r + k_rf r^2 - c_rf) */
+        double krf, crf;
+        rf_constants(s, &krf, &crf);
+        e += kqq * (1.0 / sqrt(r2) + krf * r2 - crf);
+      } else {
+        /* dielectric eps(r) = 4 r: E = k_e q_i q_j / (4 r * r) */
+        e += kqq / (4.0 * r2);
+      }
     }
   }
   return e;
@@ -199,8 +216,16 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
       double sr6 = pow(sig * sig / r2, 3);
       /* -dE_LJ/dr / r = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 */
       double g = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
-      /* -dE_C/dr / r = 2 k_e q_i q_j / (4 r^3) / r */
-      g += 2.0 * s->coulomb_k * s->charge[i] * s->charge[j] / (4.0 * r2 * r2);
+      const double kqq = s->coulomb_k * s->charge[i] * s->charge[j];
+      if (s->coulomb_mode == 1) {
+        /* reaction field: -dE_C/dr / r = k_e q_i q_j (1/r^2 - 2 k_rf r) / r */
+        double krf, crf;
+        rf_constants(s, &krf, &crf);
+        g += kqq * (1.0 / (r2 * sqrt(r2)) - 2.0 * krf);
+      } else {
+        /* -dE_C/dr / r = 2 k_e q_i q_j / (4 r^3) / r */
+        g += 2.0 * kqq / (4.0 * r2 * r2);
+      }
       for (int x = 0; x < 3; ++x) {
         f[3 * i + x] += g * d[x];
         f[3 * j + x] -= g * d[x];

@@ -72,6 +72,8 @@ typedef struct {
   int32_t n_obs;
   int32_t obs_kind[ORC_MAX_OBS];
   int32_t obs_arg[ORC_MAX_OBS][4];
+  int32_t coulomb_mode;   /* 0: dielectric eps = 4r; 1: reaction field (needs cutoff > 0) */
+  double rf_dielectric;   /* eps_rf of the reaction field; 0 = conductor (infinite) */
 } orc_system;
 
 typedef struct orc_ctx orc_ctx;

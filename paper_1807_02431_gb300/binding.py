@@ -53,6 +53,7 @@ class SystemDesc(C.Structure):
         ("n_groups", C.c_int32), ("group_offsets", C.c_int32 * (GRP_MAX_GROUPS + 1)),
         ("group_atoms", C.POINTER(C.c_int32)),
         ("n_obs", C.c_int32), ("obs_kind", C.c_int32 * GRP_MAX_OBS), ("obs_arg", (C.c_int32 * 4) * GRP_MAX_OBS),
+        ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
     ]
 
 
@@ -209,6 +210,7 @@ class SystemHandle:
         desc.sigma, desc.epsilon, desc.charge = d("sg", ea["sigma"]), d("ep", ea["epsilon"]), d("ch", ea["charge"])
         desc.n_excl, desc.excl = len(ea["excl"]), i("excl", ea["excl"])
         desc.cutoff, desc.coulomb_k = s.cutoff, s.coulomb_k
+        desc.coulomb_mode, desc.rf_dielectric = s.coulomb_mode, s.rf_dielectric
         desc.n_bonds, desc.bond_atoms = len(ea["bonds"]), i("b", ea["bonds"])
         desc.bond_k, desc.bond_r0 = d("bk", ea["bond_k"]), d("br", ea["bond_r0"])
         desc.n_angles, desc.angle_atoms = len(ea["angles"]), i("a", ea["angles"])

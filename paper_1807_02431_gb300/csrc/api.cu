@@ -227,6 +227,20 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       excl[(size_t)i * n + j] = excl[(size_t)j * n + i] = 1;
     }
     D.cutoff2 = d->cutoff > 0 ? d->cutoff * d->cutoff : 0.0;
+    if (d->coulomb_mode == GRP_COULOMB_REACTION_FIELD) {
+      if (!(d->cutoff > 0)) { grp_destroy_system(s); return fail(GRP_EINVAL, "the reaction field needs cutoff > 0"); }
+      if (!(d->rf_dielectric == 0.0 || d->rf_dielectric >= 1.0)) {
+        grp_destroy_system(s);
+        return fail(GRP_EINVAL, "rf_dielectric must be >= 1 (or 0 for a conductor)");
+      }
+      const double rc = d->cutoff, er = d->rf_dielectric;
+      D.coulomb_rf = 1;
+      D.krf = (er == 0.0 ? 0.5 : (er - 1.0) / (2.0 * er + 1.0)) / (rc * rc * rc);
+      D.crf = 1.0 / rc + D.krf * rc * rc;
+    } else if (d->coulomb_mode != GRP_COULOMB_EPS4R) {
+      grp_destroy_system(s);
+      return fail(GRP_EINVAL, "unknown coulomb_mode %d", d->coulomb_mode);
+    }
     // Small systems: an explicit list of non-excluded pairs, one thread per pair.  From 64 atoms on:
     // tiles of 32 atoms, every tile pair I <= J with per-lane interaction masks; with a cutoff, the
     // segment kernel keeps a Verlet list per replica (skin = cutoff / 6) built from the tiles.

@@ -46,6 +46,8 @@ struct SysDev {
   const uint32_t *tile_pairs;  // I | J << 16
   const uint32_t *tile_masks;  // [n_tile_pairs][32]
   double cutoff2;          // 0: no cutoff
+  int coulomb_rf;          // 1: reaction field (eps_r = 1) instead of the dielectric eps = 4r
+  double krf, crf;         // reaction-field constants k_rf, c_rf (per nm^3, per nm)
   // Verlet lists (tiled systems with a cutoff): pairs closer than cutoff + skin, rebuilt when an atom
   // has moved more than skin/2 since the last build
   int use_list;

@@ -38,6 +38,11 @@ __device__ __forceinline__ Dual grcp(Dual a) {
   const double r = 1.0 / a.v;
   return {r, -a.d * r * r};
 }
+// d (x^-1/2) = -dx / (2 x^3/2)
+__device__ __forceinline__ Dual grsqrt(Dual a) {
+  const double r = 1.0 / sqrt(a.v);
+  return {r, -0.5 * a.d * r * r * r};
+}
 __device__ __forceinline__ Dual gdiv(Dual a, Dual b) { return a / b; }
 __device__ __forceinline__ Dual gatan2(Dual y, Dual x) {
   return {atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v)};
@@ -74,6 +79,8 @@ struct Params<PathTangent> {
   const double4 *atom;
   const double2 *bond, *angle;
   const double4 *term;
+  int rf;
+  double krf, crf;
 };
 
 }  // namespace grp

@@ -26,6 +26,9 @@ __device__ __forceinline__ float grcp(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// reciprocal square root: IEEE-rounded quotient in FP64, the hardware approximation in FP32
+__device__ __forceinline__ double grsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float grsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float gdiv(float a, float b) { return __fdividef(a, b); }
 
@@ -105,13 +108,34 @@ struct Params<PathF64> {
   const double4 *atom;  // (sigma/2, sqrt(eps), q sqrt(k_e/4), 1/m), may live in shared memory
   const double2 *bond, *angle;
   const double4 *term;
+  int rf;               // Coulomb by reaction field (k_rf, c_rf) instead of eps = 4r
+  double krf, crf;
 };
 template <>
 struct Params<PathMixed> {
   const float4 *atom;
   const float2 *bond, *angle;
   const float4 *term;
+  int rf;
+  float krf, crf;
 };
+
+// Pair force factor -dE/dr / r and pair energy of Lennard-Jones (given eps_ij and (sigma_ij/r)^6) plus
+// Coulomb (qq = k_e q_i q_j / 4).  Dielectric eps = 4r: E_C = qq / r^2, -dE_C/dr / r = 2 qq / r^4.
+// Reaction field (eps_r = 1, a continuum of dielectric eps_rf beyond the cutoff r_c, as the
+// non-periodic cutoff scheme of the paper's MD setups): E_C = 4 qq (1/r + k_rf r^2 - c_rf) with
+// k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3), c_rf = 1/r_c + k_rf r_c^2 (zero at the cutoff), and
+// -dE_C/dr / r = 4 qq (1/r^3 - 2 k_rf).
+template <class T, class Par>
+__device__ __forceinline__ T pair_g(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
+  if (!par.rf) return (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+  return T(24) * eps * (T(2) * s6 * s6 - s6) * inv_r2 + T(4) * qq * (grsqrt(r2) * inv_r2 - T(2) * T(par.krf));
+}
+template <class T, class Par>
+__device__ __forceinline__ T pair_e(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
+  if (!par.rf) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * (grsqrt(r2) + T(par.krf) * r2 - T(par.crf));
+}
 
 // Nonbonded parameters of an atom held in registers by the tile and row loops: sigma/2, sqrt(eps) and
 // the scaled charge q sqrt(k_e/4).  The mixed path keeps sigma/2 and sqrt(eps) in the spare fourth
@@ -147,10 +171,10 @@ __device__ __forceinline__ bool pair_eval(const Pos<P> &pos, const Params<P> &pa
   const T inv_r2 = grcp(r2);
   const T s2 = sig * sig * inv_r2;
   const T s6 = s2 * s2 * s2;
-  // -dE/dr / r: 24 eps (2 s^12 - s^6) / r^2 + 2 k_e q_i q_j / (4 r^4)
-  const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+  // -dE/dr / r: 24 eps (2 s^12 - s^6) / r^2 + the Coulomb part (pair_g)
+  const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
   fi = {g * d.x, g * d.y, g * d.z};
-  if (want_e) e = T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  if (want_e) e = pair_e(par, eps, s6, qq, r2, inv_r2);
   return true;
 }
 
@@ -220,11 +244,11 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
           const T inv_r2 = grcp(r2);
           const T s2 = sig * sig * inv_r2;
           const T s6 = s2 * s2 * s2;
-          const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+          const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
           const V3<T> f = {g * d.x, g * d.y, g * d.z};
           fi.x += f.x; fi.y += f.y; fi.z += f.z;
           fj.x -= f.x; fj.y -= f.y; fj.z -= f.z;
-          if (want_e) en += T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+          if (want_e) en += pair_e(par, eps, s6, qq, r2, inv_r2);
         }
       }
     };
@@ -446,11 +470,11 @@ __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, co
       const T inv_r2 = grcp(r2);
       const T s2 = sig * sig * inv_r2;
       const T s6 = s2 * s2 * s2;
-      const T g = (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+      const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
       const V3<T> f = {g * d.x, g * d.y, g * d.z};
       acc.add(i, f, err);
       acc.add(j, V3<T>{-f.x, -f.y, -f.z}, err);
-      if (want_e) e_fix += acc.efix(T(4) * eps * (s6 * s6 - s6) + qq * inv_r2, err);
+      if (want_e) e_fix += acc.efix(pair_e(par, eps, s6, qq, r2, inv_r2), err);
     }
   }
 }

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
   double loss = 0.0;
   const double h = a.h, c1 = a.c1;
   const AccF64 fa{F};
-  const Params<PathTangent> tpar{S.atom_d, S.bond_d, S.angle_d, S.term_d};
+  const Params<PathTangent> tpar{S.atom_d, S.bond_d, S.angle_d, S.term_d, S.coulomb_rf, S.krf, S.crf};
 
   // the contribution of configuration q_t (see above)
   auto config = [&](const double *qt, long long t, double w) {

@@ -37,6 +37,9 @@ CV_DIHEDRAL_RECT = 1
 CV_COM_DISTANCE = 2
 CV_ROTAMERS = 3
 
+COULOMB_EPS4R = 0
+COULOMB_REACTION_FIELD = 1
+
 OBS_COORD = 0
 OBS_POTENTIAL = 1
 OBS_KINETIC = 2
@@ -63,6 +66,8 @@ class System:
     excl: np.ndarray | None = None          # [m, 2] int32
     cutoff: float = 0.0
     coulomb_k: float = 0.0
+    coulomb_mode: int = COULOMB_EPS4R       # or COULOMB_REACTION_FIELD (needs a cutoff)
+    rf_dielectric: float = 78.3             # eps_rf of the reaction field; 0 = conductor
     bonds: np.ndarray | None = None         # [nb, 2]
     bond_k: np.ndarray | None = None
     bond_r0: np.ndarray | None = None
