@@ -582,7 +582,7 @@ def main():
         peak = fp32_peak_tflops(2070.0)
         achieved = flops / (seg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": SEGMENT_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems>",
+                "traffic": SEGMENT_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu dram read + write)", "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems, 0>",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
                 "kernel_ms": seg_ms, "flops_per_launch": flops, "median_sm_mhz": sm_mhz}
         # plain FP64 GPU path, same step

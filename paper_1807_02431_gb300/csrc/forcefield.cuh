@@ -126,14 +126,18 @@ struct Params<PathMixed> {
 // non-periodic cutoff scheme of the paper's MD setups): E_C = 4 qq (1/r + k_rf r^2 - c_rf) with
 // k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3), c_rf = 1/r_c + k_rf r_c^2 (zero at the cutoff), and
 // -dE_C/dr / r = 4 qq (1/r^3 - 2 k_rf).
-template <class T, class Par>
+// kRF: 0 = eps = 4r, 1 = reaction field, -1 = as par.rf says (decided per pair; the segment kernel
+// fixes it per pass instead, keeping the branch out of its pair loops).
+template <int kRF, class T, class Par>
 __device__ __forceinline__ T pair_g(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
-  if (!par.rf) return (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+  const bool rf = kRF < 0 ? par.rf != 0 : kRF != 0;
+  if (!rf) return (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
   return T(24) * eps * (T(2) * s6 * s6 - s6) * inv_r2 + T(4) * qq * (grsqrt(r2) * inv_r2 - T(2) * T(par.krf));
 }
-template <class T, class Par>
+template <int kRF, class T, class Par>
 __device__ __forceinline__ T pair_e(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
-  if (!par.rf) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  const bool rf = kRF < 0 ? par.rf != 0 : kRF != 0;
+  if (!rf) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
   return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * (grsqrt(r2) + T(par.krf) * r2 - T(par.crf));
 }
 
@@ -158,7 +162,7 @@ __device__ __forceinline__ void nb_params(const typename Pos<P>::At &pa, const P
 
 // Lennard-Jones (Lorentz-Berthelot) + Coulomb with eps(r) = 4r for the pair (i, j): force on i
 // (minus the force on j) and the pair energy; false beyond the cutoff.
-template <class P>
+template <class P, int kRF = -1>
 __device__ __forceinline__ bool pair_eval(const Pos<P> &pos, const Params<P> &par, int i, int j,
                                           typename P::T cutoff2, V3<typename P::T> &fi, typename P::T &e,
                                           bool want_e) {
@@ -172,20 +176,20 @@ __device__ __forceinline__ bool pair_eval(const Pos<P> &pos, const Params<P> &pa
   const T s2 = sig * sig * inv_r2;
   const T s6 = s2 * s2 * s2;
   // -dE/dr / r: 24 eps (2 s^12 - s^6) / r^2 + the Coulomb part (pair_g)
-  const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
+  const T g = pair_g<kRF>(par, eps, s6, qq, r2, inv_r2);
   fi = {g * d.x, g * d.y, g * d.z};
-  if (want_e) e = pair_e(par, eps, s6, qq, r2, inv_r2);
+  if (want_e) e = pair_e<kRF>(par, eps, s6, qq, r2, inv_r2);
   return true;
 }
 
-template <class P>
+template <class P, int kRF = -1>
 __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &par, int i, int j,
                                           typename P::T cutoff2, const typename P::Acc &acc, bool want_e,
                                           long long &e_fix, int *err) {
   using T = typename P::T;
   V3<T> fi;
   T e = T(0);
-  if (!pair_eval<P>(pos, par, i, j, cutoff2, fi, e, want_e)) return;
+  if (!pair_eval<P, kRF>(pos, par, i, j, cutoff2, fi, e, want_e)) return;
   acc.add(i, fi, err);
   acc.add(j, V3<T>{-fi.x, -fi.y, -fi.z}, err);
   if (want_e) e_fix += acc.efix(e, err);
@@ -200,7 +204,7 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
 // point once, so the result does not depend on which warp takes which tile pair, or in which order.
 // With a cutoff, tile pairs whose bounding boxes are further apart than the cutoff are skipped; kCutoff =
 // false drops the cutoff tests (the segment kernel's tile path, taken only by systems without a cutoff).
-template <class P, bool kCutoff = true>
+template <class P, bool kCutoff = true, int kRF = -1>
 __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                           const typename P::Acc &acc, const float *boxes, bool want_e,
                                           long long &e_fix, int *err) {
@@ -244,11 +248,11 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
           const T inv_r2 = grcp(r2);
           const T s2 = sig * sig * inv_r2;
           const T s6 = s2 * s2 * s2;
-          const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
+          const T g = pair_g<kRF>(par, eps, s6, qq, r2, inv_r2);
           const V3<T> f = {g * d.x, g * d.y, g * d.z};
           fi.x += f.x; fi.y += f.y; fi.z += f.z;
           fj.x -= f.x; fj.y -= f.y; fj.z -= f.z;
-          if (want_e) en += pair_e(par, eps, s6, qq, r2, inv_r2);
+          if (want_e) en += pair_e<kRF>(par, eps, s6, qq, r2, inv_r2);
         }
       }
     };
@@ -431,7 +435,7 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
 // entries before evaluating them, so that one load latency covers four pairs.  (Measured on the
 // 2,030-atom ligand workload, this pair list with fixed-point atomics on both atoms beat per-atom
 // neighbour rows evaluated from both ends by 1.36x, and rows holding each pair once by 7x.)
-template <class P>
+template <class P, int kRF = -1>
 __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                           const uint32_t *list, int count, const typename P::Acc &acc,
                                           bool want_e, long long &e_fix, int *err) {
@@ -470,11 +474,11 @@ __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, co
       const T inv_r2 = grcp(r2);
       const T s2 = sig * sig * inv_r2;
       const T s6 = s2 * s2 * s2;
-      const T g = pair_g(par, eps, s6, qq, r2, inv_r2);
+      const T g = pair_g<kRF>(par, eps, s6, qq, r2, inv_r2);
       const V3<T> f = {g * d.x, g * d.y, g * d.z};
       acc.add(i, f, err);
       acc.add(j, V3<T>{-f.x, -f.y, -f.z}, err);
-      if (want_e) e_fix += acc.efix(pair_e(par, eps, s6, qq, r2, inv_r2), err);
+      if (want_e) e_fix += acc.efix(pair_e<kRF>(par, eps, s6, qq, r2, inv_r2), err);
     }
   }
 }
@@ -504,7 +508,7 @@ __device__ __forceinline__ void bonded_pass(const SysDev &S, const Pos<P> &pos, 
 // table groups pairs, bonds, angles and dihedrals, each group padded to a multiple of 32 entries, so
 // that every warp runs a single kind of item (no serialised divergent paths) and the dihedrals, the
 // longest items, land on the last warps rather than on warp 0, which also integrates atoms 0..31.
-template <class P>
+template <class P, int kRF = -1>
 __device__ __forceinline__ void force_pass(const SysDev &S, const Pos<P> &pos, const Params<P> &par,
                                            const uint32_t *items, const uint32_t *pairs,
                                            const typename P::Acc &acc, bool want_e, long long &e_fix, int *err) {
@@ -516,7 +520,7 @@ __device__ __forceinline__ void force_pass(const SysDev &S, const Pos<P> &pos, c
     const int idx = (int)(e & 0x0FFFFFFFu);
     if (kind == kItemPair) {
       const uint32_t pk = pairs[idx];
-      pair_term<P>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
+      pair_term<P, kRF>(pos, par, (int)(pk & 0xFFFFu), (int)(pk >> 16), cut2, acc, want_e, e_fix, err);
     } else if (kind == kItemBond) {
       const int2 ij = S.bond_ij[idx];
       bond_term<P>(pos, par, idx, ij.x, ij.y, acc, want_e, e_fix, err);

@@ -4,6 +4,8 @@
 // the analytic 2-D double well.
 #include <cfloat>
 
+#include <type_traits>
+
 #include "forcefield.cuh"
 #include "kernels.h"
 #include "state.cuh"
@@ -316,7 +318,10 @@ enum : int {
   kModeList = 2    // Verlet lists built from the tiles (cutoff)
 };
 
-template <class P, int kMode>
+// kRF: the Coulomb model of the force passes, 0 = eps = 4r, 1 = reaction field, -1 = per launch (the
+// batched kernel, whose runs may differ; the single-run kernels are compiled for one model, which
+// keeps one copy of the force passes in the step loop).
+template <class P, int kMode, int kRF>
 __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsigned char *smem) {
   using T = typename P::T;
   const SysDev &S = a.S;
@@ -413,10 +418,20 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
-    else force_pass<P>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
-    if (use_list) list_pass<P>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
-    else if (tiled) tile_pass<P, false>(S, pos, par, fa, boxes, sample, e_fix, &err);  // tiles: no cutoff
+    auto passes = [&](auto rf) {
+      constexpr int R = decltype(rf)::value;
+      if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
+      else force_pass<P, R>(S, pos, par, items, pairs, fa, sample, e_fix, &err);
+      if (use_list) list_pass<P, R>(S, pos, par, list, n_list, fa, sample, e_fix, &err);
+      else if (tiled) tile_pass<P, false, R>(S, pos, par, fa, boxes, sample, e_fix, &err);  // tiles: no cutoff
+    };
+    if constexpr (kRF >= 0) {
+      passes(std::integral_constant<int, kRF>{});
+    } else if (par.rf) {
+      passes(std::integral_constant<int, 1>{});
+    } else {
+      passes(std::integral_constant<int, 0>{});
+    }
     __syncthreads();
     long long k_fix = 0;
     if (kMode == kModeItems || NB > 0) {
@@ -454,11 +469,11 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
 
 // kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
 // on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
-template <class P, int kMaxThreads, int kMinBlocks, int kMode>
+template <class P, int kMaxThreads, int kMinBlocks, int kMode, int kRF>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
   if (a.skip_if_exit && exit_seen_before(a)) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  segment_body<P, kMode>(a, blockIdx.x, smem);
+  segment_body<P, kMode, kRF>(a, blockIdx.x, smem);
 }
 
 // Batched segments: a persistent grid of blocks takes (run, replica) units from a queue sorted by
@@ -491,7 +506,7 @@ __global__ void __launch_bounds__(512, 1) ff_segment_batch_kernel(const SegArgs 
     int *dst = reinterpret_cast<int *>(&sa);
     for (int i = threadIdx.x; i < (int)(sizeof(SegArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    segment_body<P, kModeAny>(sa, (int)un.y, smem);
+    segment_body<P, kModeAny, -1>(sa, (int)un.y, smem);
     __syncthreads();
   }
 }
@@ -596,9 +611,15 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
   if (c.threads < 32 || c.threads > 512 || c.threads % 32) return cudaErrorInvalidValue;
   const int mode = a.S.use_list ? kModeList : (a.S.tiled ? kModeTiles : kModeItems);
   const bool small = c.threads <= 320;
-  auto kern = mode == kModeItems ? (small ? ff_segment_kernel<P, 320, 2, kModeItems> : ff_segment_kernel<P, 512, 1, kModeItems>)
-            : mode == kModeTiles ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles> : ff_segment_kernel<P, 512, 1, kModeTiles>)
-                                 : (small ? ff_segment_kernel<P, 320, 2, kModeList> : ff_segment_kernel<P, 512, 1, kModeList>);
+  // tiles are taken only without a cutoff, so never with the reaction field
+  const bool rf = a.S.coulomb_rf != 0;
+  auto kern = mode == kModeItems
+                  ? (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 1> : ff_segment_kernel<P, 512, 1, kModeItems, 1>)
+                        : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
+            : mode == kModeTiles
+                  ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles, 0> : ff_segment_kernel<P, 512, 1, kModeTiles, 0>)
+                  : (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 1> : ff_segment_kernel<P, 512, 1, kModeList, 1>)
+                        : (small ? ff_segment_kernel<P, 320, 2, kModeList, 0> : ff_segment_kernel<P, 512, 1, kModeList, 0>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.n_active, c.threads, c.smem, st>>>(a);
