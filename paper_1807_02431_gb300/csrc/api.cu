@@ -89,6 +89,10 @@ struct grp_replicas {
   float4 *qref = nullptr;   // [R][n]
   int nbl_cap = 0;
   long long t_global = 0, t_phase = 0;
+  // one-launch status readback (branch count, reference label and exit flag, ratios, error word,
+  // first-exit key): the set's arrays for the status kernel, its output and a pinned copy
+  RunArrays *d_run = nullptr;
+  BatchStatus *d_status = nullptr, *h_status = nullptr;
   // pinned host mirror of the small per-check readback
   struct Readback {
     unsigned long long exit_key;
@@ -508,7 +512,24 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
     AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
   }
+  AL(r->d_run, sizeof(RunArrays));
+  AL(r->d_status, sizeof(BatchStatus));
 #undef AL
+  if (cudaMallocHost((void **)&r->h_status, sizeof(BatchStatus)) != cudaSuccess) {
+    grp_destroy_replicas(r);
+    return fail(GRP_ENOMEM, "cudaMallocHost failed");
+  }
+  {
+    RunArrays ra{};
+    ra.q = r->q; ra.p = r->p; ra.f = r->f; ra.acc = r->acc; ra.exited = r->exited; ra.labels = r->labels;
+    ra.src = r->src; ra.n_branched = r->n_branched; ra.rhat = r->rhat; ra.err = r->err;
+    ra.nd = D.nd; ra.nacc = D.n_obs * 4; ra.n_rep = n_replicas; ra.n_obs = D.n_obs;
+    ra.seed = seed; ra.exit_key = r->exit_key;
+    if (cudaMemcpy(r->d_run, &ra, sizeof(ra), cudaMemcpyHostToDevice) != cudaSuccess) {
+      grp_destroy_replicas(r);
+      return fail(GRP_ECUDA, "grp_init_replicas: upload failed");
+    }
+  }
   if (cudaMallocHost((void **)&r->hb, sizeof(*r->hb)) != cudaSuccess) {
     grp_destroy_replicas(r);
     return fail(GRP_ENOMEM, "cudaMallocHost failed");
@@ -541,6 +562,8 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
   cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat);
   cudaFree(r->nbl); cudaFree(r->qref);
   if (r->hb) cudaFreeHost(r->hb);
+  cudaFree(r->d_run); cudaFree(r->d_status);
+  if (r->h_status) cudaFreeHost(r->h_status);
   delete r;
 }
 
@@ -910,19 +933,19 @@ static grp_status parallel_phase(grp_replicas *r, int omega, int t_check, long l
       grp_status e = run_steps(r, t_check, 0, r->R, 1, omega, M, 1, st);
       if (e != GRP_OK) return e;
     }
-    CU(cudaMemcpyAsync(&r->hb->exit_key, r->exit_key, 8, cudaMemcpyDeviceToHost, st));
+    // the first-exit key and the label of that replica in one launch and one copy
+    CU(launch_collect_status(r->d_run, 1, r->d_status, st));
+    CU(cudaMemcpyAsync(r->h_status, r->d_status, sizeof(BatchStatus), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    const unsigned long long key = r->hb->exit_key;
+    const unsigned long long key = r->h_status->exit_key;
     if (key != ~0ull) {
       const long long Mx = (long long)(key >> 32);
       const int k0 = (int)(key & 0xffffffffu);
-      CU(cudaMemcpyAsync(&r->hb->label0, r->labels + k0, 1, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
       r->t_global = tg0 + Mx * t_check;
       r->t_phase = tp0 + Mx * t_check;
       out->M = Mx;
       out->k = k0 + 1;
-      out->label_to = r->hb->label0;
+      out->label_to = r->h_status->label_k;
       out->tau_steps = ((long long)r->R * (Mx - 1) + (k0 + 1)) * (long long)t_check;
       return GRP_OK;
     }
@@ -960,28 +983,25 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
   if (e != GRP_OK) return e;
   CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
   const bool want_gr = r->t_phase >= min_fv_steps && R > 1 && D.n_obs > 0;
-  if (want_gr) {
-    CU(launch_gelman_rubin(D, R, r->acc, tol, r->rhat, nullptr, st));
-    CU(cudaMemcpyAsync(r->hb->rhat, r->rhat, sizeof(double) * D.n_obs, cudaMemcpyDeviceToHost, st));
-  }
-  CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(&r->hb->label0, r->labels, 1, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(&r->hb->exited0, r->exited, 1, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(&r->hb->err, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (want_gr) CU(launch_gelman_rubin(D, R, r->acc, tol, r->rhat, nullptr, st));
+  // the whole status in one launch and one copy
+  CU(launch_collect_status(r->d_run, 1, r->d_status, st));
+  CU(cudaMemcpyAsync(r->h_status, r->d_status, sizeof(BatchStatus), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  out->ref_exited = r->hb->exited0;
-  out->label0 = r->hb->label0;
-  out->n_branched = r->hb->n_branched;
+  const BatchStatus &bs = *r->h_status;
+  out->ref_exited = bs.exited0;
+  out->label0 = bs.label0;
+  out->n_branched = bs.n_branched;
   out->gr_evaluated = want_gr ? 1 : 0;
   out->t_phase = r->t_phase;
   out->pad = 0;
   int conv = want_gr ? 1 : 0;
   for (int j = 0; j < GRP_MAX_OBS; ++j) {
-    out->rhat[j] = (want_gr && j < D.n_obs) ? r->hb->rhat[j] : 0.0;
-    if (want_gr && j < D.n_obs && !(r->hb->rhat[j] < 1.0 + tol)) conv = 0;
+    out->rhat[j] = (want_gr && j < D.n_obs) ? bs.rhat[j] : 0.0;
+    if (want_gr && j < D.n_obs && !(bs.rhat[j] < 1.0 + tol)) conv = 0;
   }
   out->converged = conv;
-  if (r->hb->err) return latch_errors(r, st);  // a kernel latched an error during this check
+  if (bs.err) return latch_errors(r, st);  // a kernel latched an error during this check
   return GRP_OK;
 }
 
