@@ -34,7 +34,7 @@ WORKLOAD = "chain22_r256"
 # DRAM bytes (read + write) of one launch of the chain's segment kernel in this workload, from an ncu
 # capture of the current kernel (512,000 read, 0 written: the replicas' state is read once and stays on
 # chip); to be re-measured whenever the kernel changes.
-SEGMENT_DRAM_BYTES = 512000
+SEGMENT_DRAM_BYTES = 512256  # ncu dram__bytes_read + write of one chain launch (profiles/)
 SEED = 2431
 
 
