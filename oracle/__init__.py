@@ -60,6 +60,8 @@ class OrcSystem(C.Structure):
         ("n_obs", C.c_int32), ("obs_kind", C.c_int32 * MAX_OBS),
         ("obs_arg", (C.c_int32 * 4) * MAX_OBS),
         ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
+        ("gb_radius", C.POINTER(C.c_double)), ("gb_scale", C.POINTER(C.c_double)),
+        ("gb_solute_dielectric", C.c_double), ("gb_solvent_dielectric", C.c_double),
     ]
 
 
@@ -97,6 +99,7 @@ def lib():
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(OrcSystem)]
         L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_gb_born.argtypes = [C.c_void_p, _D, _D, _D]
         L.orc_potential.restype = C.c_double
         L.orc_potential.argtypes = [C.c_void_p, _D]
         L.orc_forces.argtypes = [C.c_void_p, _D, _D]
@@ -173,6 +176,9 @@ class Oracle:
         st.n_excl, st.excl = len(ea["excl"]), i("excl", ea["excl"])
         st.cutoff, st.coulomb_k = s.cutoff, s.coulomb_k
         st.coulomb_mode, st.rf_dielectric = s.coulomb_mode, s.rf_dielectric
+        if s.gb_radius is not None:
+            st.gb_radius, st.gb_scale = d("gbr", s.gb_radius), d("gbs", s.gb_scale)
+        st.gb_solute_dielectric, st.gb_solvent_dielectric = s.gb_solute_dielectric, s.gb_solvent_dielectric
         st.n_bonds, st.bond_atoms = len(ea["bonds"]), i("bonds", ea["bonds"])
         st.bond_k, st.bond_r0 = d("bk", ea["bond_k"]), d("br0", ea["bond_r0"])
         st.n_angles, st.angle_atoms = len(ea["angles"]), i("angles", ea["angles"])
@@ -244,6 +250,13 @@ class Oracle:
         loss = lib().orc_adjoint_segment(self.ctx, q.shape[0], replica0, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr, obs,
                                          transform, center, width, _dp(gth), _dp(gq), _dp(gp))
         return loss, gth, gq, gp
+
+    def gb_born(self, q):
+        """Generalized Born radii B_i and descreening sums I_i of configuration q."""
+        n = self.system.n_atoms
+        born, integral = np.zeros(n), np.zeros(n)
+        lib().orc_gb_born(self.ctx, _dp(_c64(q)), _dp(born), _dp(integral))
+        return born, integral
 
     def state_of(self, q):
         return lib().orc_state_of(self.ctx, _dp(_c64(q)))

@@ -76,6 +76,137 @@ static void rf_constants(const orc_system *s, double *krf, double *crf) {
   *crf = 1.0 / rc + *krf * rc * rc;
 }
 
+/* ---------------------------------------------------------------- Generalized Born, OBC model II
+ * Each atom i has an offset radius a_i = rho_i - 0.009 nm.  Atom j, a sphere of radius s_j = S_j a_j
+ * at distance r, descreens atom i by h_ij = 2 x (1/4 pi) x the integral of |x|^-4 over the part of that
+ * sphere outside the sphere of radius a_i around atom i (the pairwise approximation of Hawkins, Cramer
+ * and Truhlar).  With L = max(a_i, |r - s_j|) and U = r + s_j, for a_i < U:
+ *   h = 1/L - 1/U + (r/4)(1/U^2 - 1/L^2) + (1/2r) ln(L/U) + (s_j^2/4r)(1/L^2 - 1/U^2),
+ *   plus 2 (1/a_i - 1/L) when sphere j encloses atom i's sphere (a_i < s_j - r); h = 0 otherwise.
+ * I_i = (1/2) sum_j h_ij, psi_i = a_i I_i, and the Born radius (Onufriev, Bashford and Case, model II:
+ * alpha, beta, gamma = 1, 0.8, 4.85) is 1/B_i = 1/a_i - tanh(alpha psi - beta psi^2 + gamma psi^3) / rho_i.
+ * The energy, over all pairs including bonded ones and each atom with itself, is
+ *   E = -(1/2) k_e (1/eps_in - 1/eps_out) sum_i sum_j q_i q_j / f_ij,
+ *   f_ij = sqrt(r^2 + B_i B_j exp(-r^2 / (4 B_i B_j))), f_ii = B_i. */
+static const double kGbOffset = 0.009, kGbAlpha = 1.0, kGbBeta = 0.8, kGbGamma = 4.85;
+
+/* h_ij and its derivative dh/dr (L and U depend on r). */
+static double gb_hct(double r, double ai, double sj, double *dh) {
+  const double U = r + sj;
+  if (!(ai < U)) { *dh = 0.0; return 0.0; }
+  const double diff = r - sj;
+  double L, dL;
+  if (ai > fabs(diff)) { L = ai; dL = 0.0; }
+  else { L = fabs(diff); dL = diff >= 0.0 ? 1.0 : -1.0; }
+  const double iL = 1.0 / L, iU = 1.0 / U, iL2 = iL * iL, iU2 = iU * iU, lg = log(L / U), s2 = sj * sj;
+  double h = iL - iU + 0.25 * r * (iU2 - iL2) + 0.5 / r * lg + 0.25 * s2 / r * (iL2 - iU2);
+  double d = -dL * iL2 + iU2                                  /* d(1/L - 1/U) */
+             + 0.25 * (iU2 - iL2) + 0.25 * r * (-2.0 * iU2 * iU + 2.0 * dL * iL2 * iL)
+             - 0.5 / (r * r) * lg + 0.5 / r * (dL * iL - iU)
+             - 0.25 * s2 / (r * r) * (iL2 - iU2) + 0.25 * s2 / r * (-2.0 * dL * iL2 * iL + 2.0 * iU2 * iU);
+  if (ai < sj - r) {
+    h += 2.0 * (1.0 / ai - iL);
+    d += 2.0 * dL * iL2;
+  }
+  *dh = d;
+  return h;
+}
+
+/* Born radii, their derivatives dB_i / dI_i (dbdi, optional) and the sums I_i. */
+static void gb_radii(const orc_ctx *c, const double *q, double *born, double *dbdi, double *integral) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms;
+  for (int i = 0; i < n; ++i) {
+    const double ai = s->gb_radius[i] - kGbOffset;
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3], dh;
+      sub3(q + 3 * i, q + 3 * j, d);
+      sum += gb_hct(norm3(d), ai, s->gb_scale[j] * (s->gb_radius[j] - kGbOffset), &dh);
+    }
+    const double I = 0.5 * sum, psi = ai * I;
+    const double x = kGbAlpha * psi - kGbBeta * psi * psi + kGbGamma * psi * psi * psi;
+    const double t = tanh(x);
+    const double B = 1.0 / (1.0 / ai - t / s->gb_radius[i]);
+    born[i] = B;
+    if (integral) integral[i] = I;
+    if (dbdi) dbdi[i] = B * B * (1.0 - t * t) / s->gb_radius[i] * (kGbAlpha - 2.0 * kGbBeta * psi + 3.0 * kGbGamma * psi * psi) * ai;
+  }
+}
+
+void orc_gb_born(const orc_ctx *c, const double *q, double *born, double *integral) {
+  gb_radii(c, q, born, NULL, integral);
+}
+
+static double gb_tau(const orc_system *s) {
+  return s->coulomb_k * (1.0 / s->gb_solute_dielectric - 1.0 / s->gb_solvent_dielectric);
+}
+
+static double gb_energy(const orc_ctx *c, const double *q) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms;
+  double *B = (double *)malloc(sizeof(double) * (size_t)n);
+  gb_radii(c, q, B, NULL, NULL);
+  double sum = 0.0;
+  for (int i = 0; i < n; ++i) {
+    sum += s->charge[i] * s->charge[i] / B[i];
+    for (int j = i + 1; j < n; ++j) {
+      double d[3];
+      sub3(q + 3 * i, q + 3 * j, d);
+      const double r2 = dot3(d, d), bb = B[i] * B[j];
+      sum += 2.0 * s->charge[i] * s->charge[j] / sqrt(r2 + bb * exp(-r2 / (4.0 * bb)));
+    }
+  }
+  free(B);
+  return -0.5 * gb_tau(s) * sum;
+}
+
+/* Forces -dE/dq: the pair terms at fixed Born radii, then the chain rule through B_i(I_i(r_ij)). */
+static void gb_forces(const orc_ctx *c, const double *q, double *f) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms;
+  const double tau = gb_tau(s);
+  double *B = (double *)malloc(sizeof(double) * (size_t)n), *dBdI = (double *)malloc(sizeof(double) * (size_t)n);
+  double *dEdB = (double *)calloc((size_t)n, sizeof(double));
+  gb_radii(c, q, B, dBdI, NULL);
+  for (int i = 0; i < n; ++i) dEdB[i] = 0.5 * tau * s->charge[i] * s->charge[i] / (B[i] * B[i]);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double d[3];
+      sub3(q + 3 * i, q + 3 * j, d);
+      const double r2 = dot3(d, d), r = sqrt(r2), bb = B[i] * B[j], D = r2 / (4.0 * bb), e = exp(-D);
+      const double fij = sqrt(r2 + bb * e), qq = s->charge[i] * s->charge[j];
+      /* E_pair = -tau qq / f: dE/df = tau qq / f^2 */
+      const double dEdf = tau * qq / (fij * fij);
+      const double dfdr = r * (1.0 - 0.25 * e) / fij;
+      dEdB[i] += dEdf * B[j] * e * (1.0 + D) / (2.0 * fij);
+      dEdB[j] += dEdf * B[i] * e * (1.0 + D) / (2.0 * fij);
+      const double g = dEdf * dfdr / r; /* dE/dr / r */
+      for (int x = 0; x < 3; ++x) {
+        f[3 * i + x] -= g * d[x];
+        f[3 * j + x] += g * d[x];
+      }
+    }
+  for (int i = 0; i < n; ++i) {
+    const double ai = s->gb_radius[i] - kGbOffset;
+    const double w = dEdB[i] * dBdI[i] * 0.5; /* dE/dh_ij for every j: I_i = (1/2) sum_j h_ij */
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3], dh;
+      sub3(q + 3 * i, q + 3 * j, d);
+      const double r = norm3(d);
+      gb_hct(r, ai, s->gb_scale[j] * (s->gb_radius[j] - kGbOffset), &dh);
+      const double g = w * dh / r;
+      for (int x = 0; x < 3; ++x) {
+        f[3 * i + x] -= g * d[x];
+        f[3 * j + x] += g * d[x];
+      }
+    }
+  }
+  free(B); free(dBdI); free(dEdB);
+}
+
 /* ---------------------------------------------------------------- potential V(q), Eq. 1 */
 double orc_potential(const orc_ctx *c, const double *q) {
   const orc_system *s = &c->s;
@@ -129,6 +260,7 @@ double orc_potential(const orc_ctx *c, const double *q) {
       }
     }
   }
+  if (s->gb_radius) e += gb_energy(c, q);
   return e;
 }
 
@@ -232,6 +364,7 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
       }
     }
   }
+  if (s->gb_radius) gb_forces(c, q, f);
 }
 
 /* ---------------------------------------------------------------- dV/d theta

@@ -74,6 +74,11 @@ typedef struct {
   int32_t obs_arg[ORC_MAX_OBS][4];
   int32_t coulomb_mode;   /* 0: dielectric eps = 4r; 1: reaction field (needs cutoff > 0) */
   double rf_dielectric;   /* eps_rf of the reaction field; 0 = conductor (infinite) */
+  /* Generalized Born implicit solvent, OBC model II (the solvent of the paper's protein-ligand setup,
+   * Section 4.2); off when gb_radius is NULL.  Per atom: intrinsic radius rho_i (nm) and descreening
+   * scale S_i; dielectric constants inside and outside the solute. */
+  const double *gb_radius, *gb_scale;
+  double gb_solute_dielectric, gb_solvent_dielectric;
 } orc_system;
 
 typedef struct orc_ctx orc_ctx;
@@ -109,6 +114,9 @@ void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t 
  * (ii) whether q is outside the state omega. */
 int32_t orc_state_of(const orc_ctx *c, const double *q);
 int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega);
+/* Generalized Born (OBC II) Born radii B[n] and descreening sums I[n] (nm^-1) of configuration q. */
+void orc_gb_born(const orc_ctx *c, const double *q, double *born, double *integral);
+
 /* Collective variables of the state definition: cv[0..3] (phi/psi in degrees, x, a distance, or
  * the rotamer torsions in degrees; unused entries 0). */
 void orc_cv(const orc_ctx *c, const double *q, double cv[4]);

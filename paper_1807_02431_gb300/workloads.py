@@ -68,6 +68,10 @@ class System:
     coulomb_k: float = 0.0
     coulomb_mode: int = COULOMB_EPS4R       # or COULOMB_REACTION_FIELD (needs a cutoff)
     rf_dielectric: float = 78.3             # eps_rf of the reaction field; 0 = conductor
+    gb_radius: np.ndarray | None = None     # Generalized Born (OBC II) intrinsic radii, nm; None = off
+    gb_scale: np.ndarray | None = None      # descreening scale factors S_i
+    gb_solute_dielectric: float = 1.0
+    gb_solvent_dielectric: float = 78.5
     bonds: np.ndarray | None = None         # [nb, 2]
     bond_k: np.ndarray | None = None
     bond_r0: np.ndarray | None = None
