@@ -113,6 +113,16 @@ typedef struct {
   int32_t obs_arg[GRP_MAX_OBS][4];
   int32_t coulomb_mode;         /* GRP_COULOMB_EPS4R or GRP_COULOMB_REACTION_FIELD */
   double rf_dielectric;         /* eps_rf of the reaction field (>= 1; 0 = infinity, a conductor) */
+  /* Generalized Born implicit solvent, OBC model II (the solvent of the paper's protein-ligand setup,
+   * Section 4.2), added to V when gb_radius is not NULL: per-atom intrinsic radii rho_i (nm, > 0.009)
+   * and descreening scales S_i (copied), solute and solvent dielectric constants.  With offset radii
+   * a_i = rho_i - 0.009 nm, pairwise descreening integrals give I_i, psi_i = a_i I_i, Born radii
+   * 1/B_i = 1/a_i - tanh(psi - 0.8 psi^2 + 4.85 psi^3)/rho_i, and
+   * E = -(1/2) k_e (1/eps_in - 1/eps_out) sum_i sum_j q_i q_j / sqrt(r^2 + B_i B_j exp(-r^2/(4 B_i B_j)))
+   * over all pairs and each atom with itself.  GRP_ENOTIMPL for 64 atoms or more, with a cutoff, in a
+   * batch, and for grp_adjoint_segment. */
+  const double *gb_radius, *gb_scale;
+  double gb_solute_dielectric, gb_solvent_dielectric;
 } grp_system_desc;
 
 typedef struct grp_system grp_system;

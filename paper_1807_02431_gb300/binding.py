@@ -54,6 +54,8 @@ class SystemDesc(C.Structure):
         ("group_atoms", C.POINTER(C.c_int32)),
         ("n_obs", C.c_int32), ("obs_kind", C.c_int32 * GRP_MAX_OBS), ("obs_arg", (C.c_int32 * 4) * GRP_MAX_OBS),
         ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
+        ("gb_radius", C.POINTER(C.c_double)), ("gb_scale", C.POINTER(C.c_double)),
+        ("gb_solute_dielectric", C.c_double), ("gb_solvent_dielectric", C.c_double),
     ]
 
 
@@ -211,6 +213,9 @@ class SystemHandle:
         desc.n_excl, desc.excl = len(ea["excl"]), i("excl", ea["excl"])
         desc.cutoff, desc.coulomb_k = s.cutoff, s.coulomb_k
         desc.coulomb_mode, desc.rf_dielectric = s.coulomb_mode, s.rf_dielectric
+        if s.gb_radius is not None:
+            desc.gb_radius, desc.gb_scale = d("gbr", s.gb_radius), d("gbs", s.gb_scale)
+        desc.gb_solute_dielectric, desc.gb_solvent_dielectric = s.gb_solute_dielectric, s.gb_solvent_dielectric
         desc.n_bonds, desc.bond_atoms = len(ea["bonds"]), i("b", ea["bonds"])
         desc.bond_k, desc.bond_r0 = d("bk", ea["bond_k"]), d("br", ea["bond_r0"])
         desc.n_angles, desc.angle_atoms = len(ea["angles"]), i("a", ea["angles"])

@@ -409,6 +409,47 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     }
     D.n_items = (int)items.size();
     UP(items.data(), items.size(), &D.items);
+    // Generalized Born implicit solvent (OBC II): every pair, per-atom radii and scales
+    if (d->gb_radius) {
+      if (!d->gb_scale) { grp_destroy_system(s); return fail(GRP_EINVAL, "gb_scale is null"); }
+      if (n >= 64 || d->cutoff > 0) {
+        grp_destroy_system(s);
+        return fail(GRP_ENOTIMPL, "implicit solvent is implemented for systems of fewer than 64 atoms without a cutoff");
+      }
+      if (!(d->gb_solute_dielectric > 0) || !(d->gb_solvent_dielectric > 0)) {
+        grp_destroy_system(s);
+        return fail(GRP_EINVAL, "gb dielectric constants must be positive");
+      }
+      std::vector<double4> gd(n);
+      std::vector<float4> gf(n);
+      for (int i = 0; i < n; ++i) {
+        const double a = d->gb_radius[i] - 0.009;
+        if (!(a > 0) || !(d->gb_scale[i] >= 0)) {
+          grp_destroy_system(s);
+          return fail(GRP_EINVAL, "gb atom %d: radius must exceed 0.009 nm and the scale be >= 0", i);
+        }
+        gd[i] = make_double4(a, 1.0 / d->gb_radius[i], d->gb_scale[i] * a, d->charge[i]);
+        gf[i] = make_float4((float)gd[i].x, (float)gd[i].y, (float)gd[i].z, (float)gd[i].w);
+      }
+      std::vector<uint32_t> gp;
+      gp.reserve((size_t)n * (n - 1) / 2);
+      const int m = n + (n & 1);  // round-robin order, as the nonbonded pairs
+      std::vector<int> ring(m);
+      for (int rr = 0; rr < m - 1; ++rr) {
+        ring[0] = 0;
+        for (int k = 1; k < m; ++k) ring[k] = 1 + (k - 1 + rr) % (m - 1);
+        for (int k = 0; k < m / 2; ++k) {
+          const int i = std::min(ring[k], ring[m - 1 - k]), j = std::max(ring[k], ring[m - 1 - k]);
+          if (j < n) gp.push_back((uint32_t)i | ((uint32_t)j << 16));
+        }
+      }
+      D.gb = 1;
+      D.n_gb_pairs = (int)gp.size();
+      D.gb_tau = d->coulomb_k * (1.0 / d->gb_solute_dielectric - 1.0 / d->gb_solvent_dielectric);
+      UP(gd.data(), gd.size(), &D.gb_d);
+      UP(gf.data(), gf.size(), &D.gb_f);
+      if (!gp.empty()) UP(gp.data(), gp.size(), &D.gb_pairs);
+    }
     UP(dijkl.data(), dijkl.size(), &D.dih_ijkl);
     UP(dterms.data(), dterms.size(), &D.dih_terms);
     UP(td.data(), td.size(), &D.term_d);
@@ -688,6 +729,8 @@ extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs
     if (!runs[i]) return fail(GRP_EINVAL, "grp_batch_create: run %d is null", i);
     if (runs[i]->sys->dev.potential != GRP_POT_FORCE_FIELD)
       return fail(GRP_ENOTIMPL, "grp_batch_create: batches hold force-field systems");
+    if (runs[i]->sys->dev.gb)
+      return fail(GRP_ENOTIMPL, "grp_batch_create: systems in implicit solvent run alone");
     if (runs[i]->sys->dev.precision != runs[0]->sys->dev.precision)
       return fail(GRP_EINVAL, "grp_batch_create: runs must share one precision");
   }
@@ -1536,8 +1579,8 @@ extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_
     return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
   const grp_system *s = r->sys;
   const SysDev &D = s->dev;
-  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled)
-    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms");
+  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb)
+    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms in vacuum");
   if (loss->obs < 0 || loss->obs >= D.n_obs) return fail(GRP_EINVAL, "grp_adjoint_segment: bad observable index");
   const int kind = D.obs_kind[loss->obs];
   if (kind != GRP_OBS_COORD && kind != GRP_OBS_GROUP_DISTANCE && kind != GRP_OBS_DIHEDRAL)

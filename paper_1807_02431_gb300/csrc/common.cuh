@@ -47,6 +47,12 @@ struct SysDev {
   const uint32_t *tile_masks;  // [n_tile_pairs][32]
   double cutoff2;          // 0: no cutoff
   int coulomb_rf;          // 1: reaction field (eps_r = 1) instead of the dielectric eps = 4r
+  int gb;                  // 1: Generalized Born (OBC II) implicit solvent
+  int n_gb_pairs;          // every pair i < j (i | j << 16)
+  const uint32_t *gb_pairs;
+  double gb_tau;           // k_e (1/eps_in - 1/eps_out)
+  const double4 *gb_d;     // per atom (rho - 0.009, 1/rho, S (rho - 0.009), q)
+  const float4 *gb_f;
   double krf, crf;         // reaction-field constants k_rf, c_rf (per nm^3, per nm)
   // Verlet lists (tiled systems with a cutoff): pairs closer than cutoff + skin, rebuilt when an atom
   // has moved more than skin/2 since the last build

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "forcefield.cuh"
+#include "gb.cuh"
 #include "kernels.h"
 #include "state.cuh"
 
@@ -340,6 +341,12 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);  // NB = 0: noise drawn inline per atom
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
+  GbScratch<P> gbs;  // implicit solvent (item-table systems only)
+  if (kMode == kModeItems && S.gb) {
+    ptr = align32(ptr);
+    gbs.carve(ptr, n);
+    for (int i = threadIdx.x; i < 2 * n; i += kThreads) gbs.acc.zero(i);
+  }
 
   const uint32_t *pairs = S.pairs, *items = S.items;
   if (a.pairs_in_smem) {
@@ -418,6 +425,9 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
+    if constexpr (kMode == kModeItems) {
+      if (S.gb) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
+    }
     auto passes = [&](auto rf) {
       constexpr int R = decltype(rf)::value;
       if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
@@ -569,6 +579,7 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch,
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
   if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
+  if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(n) : GbScratch<PathMixed>::bytes(n));
   return b;
 }
 
@@ -672,6 +683,12 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n, S, lean != 0);
+  GbScratch<P> gbs;
+  if (S.gb) {
+    ptr = align32(ptr);
+    gbs.carve(ptr, n);
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) gbs.acc.zero(i);
+  }
   // positions only: momenta and forces are not used
   for (int at = threadIdx.x; at < n; at += blockDim.x) {
     if constexpr (P::kMixed) {
@@ -691,6 +708,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   int err = 0;
   long long e_fix = 0;
   const typename P::Acc fa = State<P>::acc(F, n);
+  if (S.gb) gb_forces<P>(S, st.pos(), fa, gbs, energy != nullptr, e_fix, &err);
   force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, energy != nullptr, e_fix, &err);
   if (S.tiled) tile_pass<P>(S, st.pos(), st.params(S), fa, nullptr, energy != nullptr, e_fix, &err);
   __syncthreads();
@@ -726,8 +744,10 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
     return cudaGetLastError();
   }
   auto bytes = [&](bool lean) {
-    return (size_t)3 * S.n * 8 + 32 * 8 + 32 +
-           (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n, lean) : State<PathMixed>::bytes(S.n, lean));
+    size_t b = (size_t)3 * S.n * 8 + 32 * 8 + 32 +
+               (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n, lean) : State<PathMixed>::bytes(S.n, lean));
+    if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(S.n) : GbScratch<PathMixed>::bytes(S.n));
+    return b;
   };
   const int lean = bytes(false) > kMaxSmem ? 1 : 0;
   const size_t smem = bytes(lean);
