@@ -334,6 +334,15 @@ def ligand_bench(B, steps, warmup, flush, fp64_steps):
            "roofline": {"bound": "alu", "achieved": flops / (seg_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": flops / (seg_ms * 1e-3) / 1e12 / peak, "kernel_ms": seg_ms,
                         "flops_per_launch": flops}}
+    # the same system with reaction-field electrostatics (eps_rf = 78.3) instead of eps = 4r
+    import dataclasses
+
+    srf = dataclasses.replace(s, coulomb_mode=W.COULOMB_REACTION_FIELD, rf_dielectric=78.3)
+    srf.q0, srf.p0 = s.q0, s.p0
+    step_rf = Step(B, srf, B.GRP_MIXED, R, SEED, 0, omega=0)
+    t_rf = time_steps(step_rf, max(1, steps // 2), 1, flush, step_rf.stream)
+    out["reaction_field"] = {"value": units * len(t_rf) / (float(np.sum(t_rf)) / 1e3),
+                             "ms_per_step": float(np.mean(t_rf))}
     if fp64_steps > 0:
         step64 = Step(B, s, B.GRP_FP64, R, SEED, 0, omega=0)
         t64 = time_steps(step64, fp64_steps, 1, flush, step64.stream)
@@ -593,6 +602,15 @@ def main():
             fp64_value = units_per_step * len(t64) / (float(np.sum(t64)) / 1e3)
             fp64 = {"value": fp64_value, "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(t64)),
                     "speedup_of_mixed": value / world / fp64_value}
+        # the same chain in Generalized Born implicit solvent (OBC II), mixed
+        solvated = None
+        if args.fp64_steps > 0:
+            sg = W.solvated(s)
+            step_gb = Step(B, sg, B.GRP_MIXED, R, seed, local)
+            tg = time_steps(step_gb, args.fp64_steps, 1, flush, step_gb.stream)
+            solvated = {"workload": f"{sg.name}_r{R} (OBC II, all {sg.n_atoms * (sg.n_atoms - 1) // 2} pairs)",
+                        "value": units_per_step * len(tg) / (float(np.sum(tg)) / 1e3),
+                        "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tg))}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
@@ -628,6 +646,7 @@ def main():
                "gpu_launches": step.launches_per_step * args.steps,
                "roofline": roof, "clocks": clocks,
                "fp64_path": fp64,
+               "solvated_chain": solvated,
                "batched": batched,
                "ligand_receptor": ligand,
                "gradient": gradient,

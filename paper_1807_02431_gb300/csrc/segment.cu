@@ -319,10 +319,12 @@ enum : int {
   kModeList = 2    // Verlet lists built from the tiles (cutoff)
 };
 
-// kRF: the Coulomb model of the force passes, 0 = eps = 4r, 1 = reaction field, -1 = per launch (the
-// batched kernel, whose runs may differ; the single-run kernels are compiled for one model, which
-// keeps one copy of the force passes in the step loop).
-template <class P, int kMode, int kRF>
+// kFF: the nonbonded model compiled into the step loop, 0 = Coulomb with eps = 4r, 1 = reaction field,
+// 2 = eps = 4r plus Generalized Born solvent (item-table systems only), -1 = eps = 4r or reaction field
+// decided per launch (the batched kernel, whose runs may differ; implicit solvent is not batched).
+// The single-run kernels are compiled for one model, which keeps one copy of the force passes and no
+// unused solvent code in the step loop.
+template <class P, int kMode, int kFF>
 __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsigned char *smem) {
   using T = typename P::T;
   const SysDev &S = a.S;
@@ -341,8 +343,10 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);  // NB = 0: noise drawn inline per atom
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
+  constexpr bool kGB = kMode == kModeItems && kFF == 2;
+  constexpr int kRF = kFF == 2 ? 0 : kFF;
   GbScratch<P> gbs;  // implicit solvent (item-table systems only)
-  if (kMode == kModeItems && S.gb) {
+  if constexpr (kGB) {
     ptr = align32(ptr);
     gbs.carve(ptr, n);
     for (int i = threadIdx.x; i < 2 * n; i += kThreads) gbs.acc.zero(i);
@@ -425,9 +429,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     const bool sample = --until == 0;
     if (sample) until = a.t_gr;
     long long e_fix = 0;
-    if constexpr (kMode == kModeItems) {
-      if (S.gb) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
-    }
+    if constexpr (kGB) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
     auto passes = [&](auto rf) {
       constexpr int R = decltype(rf)::value;
       if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
@@ -479,11 +481,11 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
 
 // kMaxThreads/kMinBlocks: blocks of up to 320 threads keep two resident per SM (256 replica blocks
 // on 152 SMs then run in one wave); larger systems use up to 512 threads, one block per SM.
-template <class P, int kMaxThreads, int kMinBlocks, int kMode, int kRF>
+template <class P, int kMaxThreads, int kMinBlocks, int kMode, int kFF>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(const SegArgs a) {
   if (a.skip_if_exit && exit_seen_before(a)) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  segment_body<P, kMode, kRF>(a, blockIdx.x, smem);
+  segment_body<P, kMode, kFF>(a, blockIdx.x, smem);
 }
 
 // Batched segments: a persistent grid of blocks takes (run, replica) units from a queue sorted by
@@ -622,11 +624,13 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
   if (c.threads < 32 || c.threads > 512 || c.threads % 32) return cudaErrorInvalidValue;
   const int mode = a.S.use_list ? kModeList : (a.S.tiled ? kModeTiles : kModeItems);
   const bool small = c.threads <= 320;
-  // tiles are taken only without a cutoff, so never with the reaction field
-  const bool rf = a.S.coulomb_rf != 0;
+  // tiles are taken only without a cutoff, so never with the reaction field; implicit solvent only on
+  // the item table (and never with a cutoff)
+  const bool rf = a.S.coulomb_rf != 0, gb = a.S.gb != 0;
   auto kern = mode == kModeItems
-                  ? (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 1> : ff_segment_kernel<P, 512, 1, kModeItems, 1>)
-                        : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
+                  ? (gb   ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 2> : ff_segment_kernel<P, 512, 1, kModeItems, 2>)
+                     : rf ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 1> : ff_segment_kernel<P, 512, 1, kModeItems, 1>)
+                          : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
             : mode == kModeTiles
                   ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles, 0> : ff_segment_kernel<P, 512, 1, kModeTiles, 0>)
                   : (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 1> : ff_segment_kernel<P, 512, 1, kModeList, 1>)
