@@ -278,12 +278,16 @@ grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, int32_t t_ch
  * (transient, convergence, parallel step) and its own visits of its states: per tick one batched
  * segment of t_check steps (replica 0 alone for a run in its transient, every replica otherwise),
  * batched branching and Gelman-Rubin ratios for the runs in their convergence step, one readback.
+ * After the first tick the tick's launches and copies are replayed as one captured CUDA graph.
  * Each run's decisions and events are those of grp_run on that run alone (same parameters p, its
  * own seed and state).  h_events is [n_runs][max_events] (run i's log at h_events + i max_events),
  * h_n_events[n_runs] and h_t_sim[n_runs] (optional) receive each run's event count and clock.
  * GRP_EINVAL for t_gr < 1, t_check outside [1, 20000] or tol <= 0. */
 grp_status grp_batch_run(grp_batch *b, const grp_run_params *p, grp_event *h_events, int32_t max_events,
                          int32_t *h_n_events, int64_t *h_t_sim, void *stream);
+/* Ticks of the last grp_batch_run, and how many of them were replayed as a captured CUDA graph (all
+ * but the first, unless the capture was unavailable and every tick was launched node by node). */
+grp_status grp_batch_stats(const grp_batch *b, int64_t *h_ticks, int64_t *h_graph_ticks);
 /* Pick the block size of the batched kernel by timing candidate sizes on a short segment (the
  * replicas' state and counters are restored afterwards); h_threads (optional) gets the choice. */
 grp_status grp_batch_autotune(grp_batch *b, int32_t t_gr, void *stream, int32_t *h_threads);

@@ -120,6 +120,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int64), _VP]),
     "grp_batch_run": (C.c_int32, [_VP, C.POINTER(RunParams), C.POINTER(Event), C.c_int32, _I32P,
                                   C.POINTER(C.c_int64), _VP]),
+    "grp_batch_stats": (C.c_int32, [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "grp_run_original": (C.c_int32, [_VP, C.POINTER(OriginalParams), C.POINTER(Event), C.c_int32, _I32P,
                                      C.POINTER(C.c_int64), _VP]),
     "grp_get_state": (C.c_int32, [_VP, _D, _D, _D, C.POINTER(Counters), _VP]),
@@ -464,6 +465,13 @@ def grp_batch_run(b: BatchHandle, t_gr: int, t_check: int, tol: float, min_fv_st
                      "steps": e.steps, "t_sim": e.t_sim, "n_branch": e.n_branch}
                     for e in ev[i * max_events:i * max_events + n[i]]])
     return out, list(tsim)
+
+
+def grp_batch_stats(b: BatchHandle):
+    """(ticks, ticks replayed as a CUDA graph) of the last grp_batch_run."""
+    t, g = C.c_int64(0), C.c_int64(0)
+    _check(_lib.grp_batch_stats(b.handle, C.byref(t), C.byref(g)))
+    return t.value, g.value
 
 
 def grp_batch_autotune(b: BatchHandle, t_gr: int = 0, stream=None) -> int:

@@ -712,6 +712,7 @@ struct grp_batch {
   uint2 *d_units = nullptr, *d_branch_units = nullptr, *d_gr_units = nullptr;
   int *d_counter = nullptr, *d_nb = nullptr;
   BatchStatus *d_status = nullptr, *h_status = nullptr;  // h_ pinned
+  long long ticks = 0, graph_ticks = 0;                  // of the last grp_batch_run
 };
 
 extern "C" void grp_batch_destroy(grp_batch *b) {
@@ -784,9 +785,10 @@ struct RunTick {
 };
 
 // One batched segment of k steps (k <= kMaxSegment), each run as its tick says.
-static grp_status batch_launch(grp_batch *b, int k, const RunTick *ticks, cudaStream_t st) {
+// Host half of a batched segment: the argument block of every run (pinned memory, read by the copy
+// that enqueue_segment queues) and the runs' step counters.
+static void fill_args(grp_batch *b, int k, const RunTick *ticks) {
   const int nr = (int)b->runs.size();
-  CU(cudaStreamSynchronize(st));  // the pinned argument block may still be read by a queued copy
   for (int i = 0; i < nr; ++i) {
     grp_replicas *r = b->runs[i];
     const RunTick &t = ticks[i];
@@ -800,15 +802,25 @@ static grp_status batch_launch(grp_batch *b, int k, const RunTick *ticks, cudaSt
     a.lean = r->sys->seg.lean;
     b->h_args[i] = a;
   }
-  CU(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(SegArgs) * nr, cudaMemcpyHostToDevice, st));
-  CU(launch_segment_batch(b->d_args, b->d_units, b->n_units, b->d_counter, b->precision, b->threads, b->smem, st,
-                          nullptr));
   for (int i = 0; i < nr; ++i) {
     if (ticks[i].n_active <= 0) continue;
     b->runs[i]->t_global += k;
     b->runs[i]->t_phase += k;
   }
+}
+
+static grp_status enqueue_segment(grp_batch *b, cudaStream_t st) {
+  CU(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(SegArgs) * b->runs.size(), cudaMemcpyHostToDevice, st));
+  CU(launch_segment_batch(b->d_args, b->d_units, b->n_units, b->d_counter, b->precision, b->threads, b->smem, st,
+                          nullptr));
   return GRP_OK;
+}
+
+// One batched segment of k steps (k <= kMaxSegment), each run as its tick says.
+static grp_status batch_launch(grp_batch *b, int k, const RunTick *ticks, cudaStream_t st) {
+  CU(cudaStreamSynchronize(st));  // the pinned argument block may still be read by a queued copy
+  fill_args(b, k, ticks);
+  return enqueue_segment(b, st);
 }
 
 // Every replica of every run, with or without the fused exit test.
@@ -819,9 +831,8 @@ static grp_status batch_segment(grp_batch *b, int k, int t_gr, int do_check, con
   return batch_launch(b, k, ticks.data(), st);
 }
 
-// After a batched exit test: branching of the runs with branch[i], Gelman-Rubin ratios of those with
-// gr[i], and one readback of every run's status into b->h_status.
-static grp_status batch_status(grp_batch *b, const int *branch, const int *gr, cudaStream_t st) {
+// Host half of a batched status: the runs' arrays with their branching and Gelman-Rubin flags.
+static void fill_arrays(grp_batch *b, const int *branch, const int *gr) {
   const int nr = (int)b->runs.size();
   for (int i = 0; i < nr; ++i) {
     grp_replicas *r = b->runs[i];
@@ -836,15 +847,57 @@ static grp_status batch_status(grp_batch *b, const int *branch, const int *gr, c
     a.gr = gr[i];
     b->h_arrays[i] = a;
   }
+}
+
+static grp_status enqueue_status(grp_batch *b, cudaStream_t st) {
+  const int nr = (int)b->runs.size();
   CU(cudaMemcpyAsync(b->d_arrays, b->h_arrays, sizeof(RunArrays) * nr, cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(b->d_nb, 0, sizeof(int) * nr, st));
   CU(launch_fv_branch_batch(b->d_arrays, b->d_branch_units, b->n_branch_units, st));
   CU(launch_gelman_rubin_batch(b->d_arrays, b->d_gr_units, b->n_gr_units, st));
   CU(launch_collect_status(b->d_arrays, nr, b->d_status, st));
   CU(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * nr, cudaMemcpyDeviceToHost, st));
+  return GRP_OK;
+}
+
+// After a batched exit test: branching of the runs with branch[i], Gelman-Rubin ratios of those with
+// gr[i], and one readback of every run's status into b->h_status.
+static grp_status batch_status(grp_batch *b, const int *branch, const int *gr, cudaStream_t st) {
+  fill_arrays(b, branch, gr);
+  grp_status e = enqueue_status(b, st);
+  if (e != GRP_OK) return e;
   CU(cudaStreamSynchronize(st));
   return GRP_OK;
 }
+
+// One tick of the batched loop as a CUDA graph: the segment, branching, Gelman-Rubin ratios and the
+// status readback, captured once per grp_batch_run call.  Every node reads fixed buffers (the pinned
+// argument blocks are refilled before each launch), so the graph is replayed as captured.
+struct TickGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~TickGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  // false (and no graph) when capture is unavailable; the caller then launches the nodes one by one
+  bool capture(grp_batch *b) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return false; }
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const bool queued = ok && enqueue_segment(b, cs) == GRP_OK && enqueue_status(b, cs) == GRP_OK;
+    if (ok) ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && queued;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cudaStreamDestroy(cs);
+    if (!ok) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      graph = nullptr;
+      exec = nullptr;
+    }
+    return ok;
+  }
+};
 
 extern "C" grp_status grp_batch_step_k(grp_batch *b, int64_t k, int32_t t_gr, void *stream) {
   const Range range("grp_batch_step_k");
@@ -895,6 +948,13 @@ extern "C" grp_status grp_batch_fv_check(grp_batch *b, const int32_t *h_omega, i
       if (e != GRP_OK) return e;
     }
   }
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_batch_stats(const grp_batch *b, int64_t *h_ticks, int64_t *h_graph_ticks) {
+  if (!b) return fail(GRP_EINVAL, "grp_batch_stats: null batch");
+  if (h_ticks) *h_ticks = b->ticks;
+  if (h_graph_ticks) *h_graph_ticks = b->graph_ticks;
   return GRP_OK;
 }
 
@@ -1360,6 +1420,10 @@ extern "C" grp_status grp_batch_run(grp_batch *b, const grp_run_params *p, grp_e
 
   std::vector<RunTick> ticks(nr);
   std::vector<int> branch(nr), gr(nr);
+  TickGraph tick;
+  bool graphs = true;
+  long long n_ticks = 0;
+  b->ticks = b->graph_ticks = 0;
   for (;;) {
     int busy = 0;
     for (int i = 0; i < nr; ++i) {
@@ -1382,8 +1446,21 @@ extern "C" grp_status grp_batch_run(grp_batch *b, const grp_run_params *p, grp_e
       busy += t.n_active > 0;
     }
     if (!busy) break;
-    if ((e = batch_launch(b, p->t_check, ticks.data(), st)) != GRP_OK) return e;
-    if ((e = batch_status(b, branch.data(), gr.data(), st)) != GRP_OK) return e;
+    // the first tick runs node by node (it also sets the kernels' attributes); the graph is captured
+    // before the second and replayed from then on
+    if (graphs && n_ticks == 1 && !tick.capture(b)) graphs = false;
+    fill_args(b, p->t_check, ticks.data());
+    fill_arrays(b, branch.data(), gr.data());
+    if (graphs && tick.exec) {
+      CU(cudaGraphLaunch(tick.exec, st));
+      ++b->graph_ticks;
+    } else {
+      if ((e = enqueue_segment(b, st)) != GRP_OK) return e;
+      if ((e = enqueue_status(b, st)) != GRP_OK) return e;
+    }
+    CU(cudaStreamSynchronize(st));
+    ++n_ticks;
+    ++b->ticks;
     for (int i = 0; i < nr; ++i) {
       if (b->h_status[i].err && (e = latch_errors(b->runs[i], st)) != GRP_OK) return e;
     }

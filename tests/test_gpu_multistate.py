@@ -80,6 +80,8 @@ def test_batch_run_matches_single_runs(B, prec):
     batch_reps = _runs(B, P, specs)
     b = B.grp_batch_create([r for _, r in batch_reps])
     evs, tsims = B.grp_batch_run(b, *args)
+    ticks, graph_ticks = B.grp_batch_stats(b)
+    assert ticks > 10 and graph_ticks == ticks - 1  # every tick after the first replayed as a CUDA graph
     kinds = set()
     for i, (s, seed) in enumerate(specs):
         sysh, rep = _runs(B, P, [(s, seed)])[0]
