@@ -62,6 +62,9 @@ class OrcSystem(C.Structure):
         ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
         ("gb_radius", C.POINTER(C.c_double)), ("gb_scale", C.POINTER(C.c_double)),
         ("gb_solute_dielectric", C.c_double), ("gb_solvent_dielectric", C.c_double),
+        ("n_constraints", C.c_int32), ("constraint_atoms", C.POINTER(C.c_int32)),
+        ("constraint_length", C.POINTER(C.c_double)), ("constraint_tol", C.c_double),
+        ("constraint_max_iter", C.c_int32),
     ]
 
 
@@ -179,6 +182,11 @@ class Oracle:
         if s.gb_radius is not None:
             st.gb_radius, st.gb_scale = d("gbr", s.gb_radius), d("gbs", s.gb_scale)
         st.gb_solute_dielectric, st.gb_solvent_dielectric = s.gb_solute_dielectric, s.gb_solvent_dielectric
+        if s.constraints is not None and len(s.constraints):
+            st.n_constraints = len(s.constraints)
+            st.constraint_atoms = i("con", s.constraints)
+            st.constraint_length = d("conl", s.constraint_length)
+        st.constraint_tol, st.constraint_max_iter = s.constraint_tol, s.constraint_max_iter
         st.n_bonds, st.bond_atoms = len(ea["bonds"]), i("bonds", ea["bonds"])
         st.bond_k, st.bond_r0 = d("bk", ea["bond_k"]), d("br0", ea["bond_r0"])
         st.n_angles, st.angle_atoms = len(ea["angles"]), i("angles", ea["angles"])

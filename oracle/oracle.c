@@ -459,9 +459,99 @@ uint32_t orc_branch_word(uint64_t seed, int64_t step, int32_t replica) {
 /* ---------------------------------------------------------------- BAOAB step of Eq. 1
  * B: p += dt/2 F; A: q += dt/2 M^-1 p; O: p = c1 p + sqrt((1 - c1^2) m kT) xi with c1 = exp(-gamma dt)
  * (gamma read as a collision rate); A: q += dt/2 M^-1 p; F = F(q); B: p += dt/2 F. */
+/* ---------------------------------------------------------------- bond constraints
+ * RATTLE projection of the momenta: Gauss-Seidel sweeps over the constraints, each removing the
+ * relative velocity of its two atoms along their bond, until a sweep changes nothing beyond the
+ * tolerance |r . v| <= tol d^2 / dt (or the iteration bound). */
+static void rattle_momenta(const orc_ctx *c, const double *q, double *p) {
+  const orc_system *s = &c->s;
+  for (int it = 0; it < s->constraint_max_iter; ++it) {
+    int moved = 0;
+    for (int k = 0; k < s->n_constraints; ++k) {
+      const int i = s->constraint_atoms[2 * k], j = s->constraint_atoms[2 * k + 1];
+      const double d = s->constraint_length[k], wi = 1.0 / s->mass[i], wj = 1.0 / s->mass[j];
+      double r[3], v[3];
+      sub3(q + 3 * i, q + 3 * j, r);
+      for (int x = 0; x < 3; ++x) v[x] = p[3 * i + x] * wi - p[3 * j + x] * wj;
+      const double rv = dot3(r, v);
+      if (fabs(rv) <= s->constraint_tol * d * d / s->dt) continue;
+      const double mu = rv / ((wi + wj) * dot3(r, r));
+      for (int x = 0; x < 3; ++x) {
+        p[3 * i + x] -= mu * r[x];
+        p[3 * j + x] += mu * r[x];
+      }
+      moved = 1;
+    }
+    if (!moved) return;
+  }
+}
+
+/* SHAKE after an A step: q holds the unconstrained update of q_old; Gauss-Seidel sweeps move each
+ * constrained pair along its bond vector at q_old until | |r|^2 - d^2 | <= tol d^2, adding the
+ * matching impulse (the displacement times m / h) to the momenta. */
+static void shake_positions(const orc_ctx *c, double *q, const double *q_old, double *p, double h) {
+  const orc_system *s = &c->s;
+  for (int it = 0; it < s->constraint_max_iter; ++it) {
+    int moved = 0;
+    for (int k = 0; k < s->n_constraints; ++k) {
+      const int i = s->constraint_atoms[2 * k], j = s->constraint_atoms[2 * k + 1];
+      const double d = s->constraint_length[k], wi = 1.0 / s->mass[i], wj = 1.0 / s->mass[j];
+      double r[3], so[3];
+      sub3(q + 3 * i, q + 3 * j, r);
+      const double diff = d * d - dot3(r, r);
+      if (fabs(diff) <= s->constraint_tol * d * d) continue;
+      sub3(q_old + 3 * i, q_old + 3 * j, so);
+      const double g = diff / (2.0 * (wi + wj) * dot3(so, r));
+      for (int x = 0; x < 3; ++x) {
+        q[3 * i + x] += g * wi * so[x];
+        q[3 * j + x] -= g * wj * so[x];
+        p[3 * i + x] += g / h * so[x];
+        p[3 * j + x] -= g / h * so[x];
+      }
+      moved = 1;
+    }
+    if (!moved) return;
+  }
+}
+
+/* BAOAB with constraints: every sub-step of the unconstrained step, in the same order per
+ * coordinate, then its projection. */
+static void baoab_constrained(const orc_ctx *c, double *q, double *p, double *f, uint64_t seed, int32_t replica,
+                              int64_t step) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms, nd = 3 * n;
+  const double h = 0.5 * s->dt, c1 = exp(-s->gamma * s->dt);
+  double *q_old = (double *)malloc(sizeof(double) * (size_t)nd);
+  for (int i = 0; i < nd; ++i) p[i] += h * f[i];                                 /* B */
+  rattle_momenta(c, q, p);
+  memcpy(q_old, q, sizeof(double) * (size_t)nd);                                /* A */
+  for (int i = 0; i < nd; ++i) q[i] += h * p[i] / s->mass[i / 3];
+  shake_positions(c, q, q_old, p, h);
+  rattle_momenta(c, q, p);
+  for (int a = 0; a < n; ++a) {                                                 /* O */
+    const double m = s->mass[a], sd = sqrt((1.0 - c1 * c1) * m * s->kT);
+    double xi[4];
+    orc_normals(seed, step, replica, a, xi);
+    for (int x = 0; x < 3; ++x) p[3 * a + x] = c1 * p[3 * a + x] + sd * xi[x];
+  }
+  rattle_momenta(c, q, p);
+  memcpy(q_old, q, sizeof(double) * (size_t)nd);                                /* A */
+  for (int i = 0; i < nd; ++i) q[i] += h * p[i] / s->mass[i / 3];
+  shake_positions(c, q, q_old, p, h);
+  rattle_momenta(c, q, p);
+  orc_forces(c, q, f);                                                          /* B */
+  for (int i = 0; i < nd; ++i) p[i] += h * f[i];
+  rattle_momenta(c, q, p);
+  free(q_old);
+}
+
 void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t seed,
                     int32_t replica, int64_t step) {
   const orc_system *s = &c->s;
+  if (s->n_constraints > 0) {
+    baoab_constrained(c, q, p, f, seed, replica, step);
+    return;
+  }
   int n = s->n_atoms, dim = s->dim;
   double h = 0.5 * s->dt;
   double c1 = exp(-s->gamma * s->dt);

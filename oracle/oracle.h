@@ -79,6 +79,13 @@ typedef struct {
    * scale S_i; dielectric constants inside and outside the solute. */
   const double *gb_radius, *gb_scale;
   double gb_solute_dielectric, gb_solvent_dielectric;
+  /* Holonomic bond constraints |q_i - q_j| = d (the paper's setups constrain the bonds of hydrogens):
+   * [n_constraints][2] atoms, lengths; relative tolerance of the iterations and their bound. */
+  int32_t n_constraints;
+  const int32_t *constraint_atoms;
+  const double *constraint_length;
+  double constraint_tol;
+  int32_t constraint_max_iter;
 } orc_system;
 
 typedef struct orc_ctx orc_ctx;
@@ -106,7 +113,9 @@ void orc_normals(uint64_t seed, int64_t step, int32_t replica, int32_t atom, dou
 /* First Philox word of stream 1 for (seed, step, replica): the Fleming-Viot branching draw. */
 uint32_t orc_branch_word(uint64_t seed, int64_t step, int32_t replica);
 
-/* One BAOAB step of Eq. 1 for one replica; f holds F(q) on entry and on exit. */
+/* One BAOAB step of Eq. 1 for one replica; f holds F(q) on entry and on exit.  With constraints each
+ * sub-step is followed by its projection: positions by SHAKE along the bond vectors before the A step,
+ * momenta by RATTLE onto the tangent space (relative velocity along each bond zero). */
 void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t seed,
                     int32_t replica, int64_t step);
 

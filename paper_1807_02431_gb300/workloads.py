@@ -72,6 +72,10 @@ class System:
     gb_scale: np.ndarray | None = None      # descreening scale factors S_i
     gb_solute_dielectric: float = 1.0
     gb_solvent_dielectric: float = 78.5
+    constraints: np.ndarray | None = None   # [m, 2] atom pairs of fixed bond length
+    constraint_length: np.ndarray | None = None
+    constraint_tol: float = 1e-10           # relative tolerance of SHAKE / RATTLE
+    constraint_max_iter: int = 1000
     bonds: np.ndarray | None = None         # [nb, 2]
     bond_k: np.ndarray | None = None
     bond_r0: np.ndarray | None = None
@@ -323,6 +327,51 @@ def solvated(s: System, seed: int = 77) -> System:
                               gb_solvent_dielectric=78.5)
     out.q0, out.p0 = s.q0, s.p0
     return out
+
+
+def chain_h(n_heavy: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas: int = 256) -> System:
+    """The peptide-like chain with one hydrogen (1.008 amu) on every bead, its bond of 0.109 nm held
+    fixed by a constraint (as the paper's setups constrain the bonds of hydrogens, Section 4): 2 x 22
+    atoms.  Each hydrogen carries 0.1 e taken from its bead's charge, LJ sigma 0.25 nm and eps 0.1
+    kJ/mol, angles H-C-C of k = 300 kJ/mol/rad^2 and 109.5 deg with each neighbour of its bead; 1-2 and
+    1-3 pairs through the hydrogens excluded.  Hydrogens are placed opposite the bisector of their
+    bead's neighbours.  States, observables and the Gen. ParRep parameters are the chain's."""
+    base = chain(n_atoms=n_heavy, seed=seed, dyn_seed=dyn_seed, n_replicas=n_replicas)
+    nh = n_heavy
+    x = base.q0
+    hpos = np.zeros((nh, 3))
+    for i in range(nh):
+        nb = [k for k in (i - 1, i + 1) if 0 <= k < nh]
+        u = sum((x[i] - x[k]) / np.linalg.norm(x[i] - x[k]) for k in nb)
+        if np.linalg.norm(u) < 1e-6:
+            u = np.cross(x[nb[0]] - x[i], [0.0, 0.0, 1.0])
+        hpos[i] = x[i] + 0.109 * u / np.linalg.norm(u)
+    n = 2 * nh
+    mass = np.concatenate([base.mass, np.full(nh, 1.008)])
+    charge = np.concatenate([base.charge - 0.1, np.full(nh, 0.1)])
+    sigma = np.concatenate([base.sigma, np.full(nh, 0.25)])
+    epsilon = np.concatenate([base.epsilon, np.full(nh, 0.1)])
+    angles = [list(a) for a in base.angles]
+    angle_k = list(base.angle_k)
+    angle_t0 = list(base.angle_theta0)
+    excl = {tuple(e) for e in base.excl.tolist()}
+    for i in range(nh):
+        h = nh + i
+        excl.add((i, h))
+        for k in (i - 1, i + 1):
+            if 0 <= k < nh:
+                angles.append([h, i, k])
+                angle_k.append(300.0)
+                angle_t0.append(math.radians(109.5))
+                excl.add((min(k, h), max(k, h)))
+    excl = np.array(sorted(excl), np.int32)
+    s = dataclasses.replace(
+        base, name=f"chain{nh}h", n_atoms=n, mass=mass, charge=charge, sigma=sigma, epsilon=epsilon,
+        excl=excl, angles=np.array(angles, np.int32), angle_k=np.array(angle_k), angle_theta0=np.array(angle_t0),
+        constraints=np.array([[i, nh + i] for i in range(nh)], np.int32), constraint_length=np.full(nh, 0.109))
+    s.q0 = np.concatenate([x, hpos])
+    s.p0 = maxwell_boltzmann(mass, s.kT, 3, np.random.default_rng(dyn_seed))
+    return s
 
 
 def _kd_order(x, leaf=32):
