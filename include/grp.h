@@ -123,6 +123,18 @@ typedef struct {
    * batch, and for grp_adjoint_segment. */
   const double *gb_radius, *gb_scale;
   double gb_solute_dielectric, gb_solvent_dielectric;
+  /* Bond constraints |q_i - q_j| = d (the paper's MD setups hold the bonds of hydrogens fixed): each
+   * sub-step of BAOAB is followed by its projection, positions by SHAKE along the bond vectors, momenta
+   * by RATTLE (no relative velocity along any bond), Gauss-Seidel sweeps until |r^2 - d^2| <= tol d^2
+   * and |r . v| <= tol d^2 / dt; GRP_ETIMEOUT (latched) when constraint_max_iter sweeps do not reach
+   * that.  A constrained pair should be excluded from the nonbonded terms and carry no bond term.
+   * GRP_ENOTIMPL for 64 atoms or more, with the reaction field or implicit solvent, for groups of
+   * coupled constraints larger than 16 constraints or atoms, in a batch, and for grp_adjoint_segment. */
+  int32_t n_constraints;
+  const int32_t *constraint_atoms;  /* [n_constraints][2] */
+  const double *constraint_length;  /* [n_constraints] */
+  double constraint_tol;            /* relative, e.g. 1e-10 */
+  int32_t constraint_max_iter;
 } grp_system_desc;
 
 typedef struct grp_system grp_system;

@@ -56,6 +56,9 @@ class SystemDesc(C.Structure):
         ("coulomb_mode", C.c_int32), ("rf_dielectric", C.c_double),
         ("gb_radius", C.POINTER(C.c_double)), ("gb_scale", C.POINTER(C.c_double)),
         ("gb_solute_dielectric", C.c_double), ("gb_solvent_dielectric", C.c_double),
+        ("n_constraints", C.c_int32), ("constraint_atoms", C.POINTER(C.c_int32)),
+        ("constraint_length", C.POINTER(C.c_double)), ("constraint_tol", C.c_double),
+        ("constraint_max_iter", C.c_int32),
     ]
 
 
@@ -217,6 +220,11 @@ class SystemHandle:
         if s.gb_radius is not None:
             desc.gb_radius, desc.gb_scale = d("gbr", s.gb_radius), d("gbs", s.gb_scale)
         desc.gb_solute_dielectric, desc.gb_solvent_dielectric = s.gb_solute_dielectric, s.gb_solvent_dielectric
+        if s.constraints is not None and len(s.constraints):
+            desc.n_constraints = len(s.constraints)
+            desc.constraint_atoms = i("con", s.constraints)
+            desc.constraint_length = d("conl", s.constraint_length)
+        desc.constraint_tol, desc.constraint_max_iter = s.constraint_tol, s.constraint_max_iter
         desc.n_bonds, desc.bond_atoms = len(ea["bonds"]), i("b", ea["bonds"])
         desc.bond_k, desc.bond_r0 = d("bk", ea["bond_k"]), d("br", ea["bond_r0"])
         desc.n_angles, desc.angle_atoms = len(ea["angles"]), i("a", ea["angles"])

@@ -452,6 +452,67 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       UP(gf.data(), gf.size(), &D.gb_f);
       if (!gp.empty()) UP(gp.data(), gp.size(), &D.gb_pairs);
     }
+    // bond constraints: independent groups (connected components of the constraint graph)
+    if (d->n_constraints > 0) {
+      if (!d->constraint_atoms || !d->constraint_length) { grp_destroy_system(s); return fail(GRP_EINVAL, "constraint arrays null"); }
+      if (D.tiled || D.coulomb_rf || D.gb) {
+        grp_destroy_system(s);
+        return fail(GRP_ENOTIMPL, "bond constraints are implemented for systems of fewer than 64 atoms with the eps = 4r "
+                                  "Coulomb model and no implicit solvent");
+      }
+      if (!(d->constraint_tol > 0) || d->constraint_max_iter < 1) {
+        grp_destroy_system(s);
+        return fail(GRP_EINVAL, "constraint_tol must be > 0 and constraint_max_iter >= 1");
+      }
+      const int nc = d->n_constraints;
+      std::vector<int> parent(n);
+      for (int i = 0; i < n; ++i) parent[i] = i;
+      auto root = [&](int x) { while (parent[x] != x) x = parent[x] = parent[parent[x]]; return x; };
+      std::vector<int2> cij(nc);
+      std::vector<unsigned char> flag(n, 0);
+      for (int k = 0; k < nc; ++k) {
+        const int i = d->constraint_atoms[2 * k], j = d->constraint_atoms[2 * k + 1];
+        if (bad_atom(i) || bad_atom(j) || i == j || !(d->constraint_length[k] > 0)) {
+          grp_destroy_system(s);
+          return fail(GRP_EINVAL, "constraint %d invalid", k);
+        }
+        cij[k] = make_int2(i, j);
+        flag[i] = flag[j] = 1;
+        parent[root(i)] = root(j);
+      }
+      std::map<int, int> gid;  // root -> group, numbered by first constraint
+      std::vector<std::vector<int>> gcons, gatoms;
+      for (int k = 0; k < nc; ++k) {
+        const int rk = root(cij[k].x);
+        if (!gid.count(rk)) { gid[rk] = (int)gcons.size(); gcons.emplace_back(); gatoms.emplace_back(); }
+        const int g = gid[rk];
+        gcons[g].push_back(k);
+        for (int a : {cij[k].x, cij[k].y})
+          if (std::find(gatoms[g].begin(), gatoms[g].end(), a) == gatoms[g].end()) gatoms[g].push_back(a);
+      }
+      std::vector<int> off{0}, cons, aoff{0}, atoms;
+      for (size_t g = 0; g < gcons.size(); ++g) {
+        if (gcons[g].size() > 16 || gatoms[g].size() > 16) {
+          grp_destroy_system(s);
+          return fail(GRP_ENOTIMPL, "a group of coupled constraints holds more than 16 constraints or atoms");
+        }
+        cons.insert(cons.end(), gcons[g].begin(), gcons[g].end());
+        off.push_back((int)cons.size());
+        atoms.insert(atoms.end(), gatoms[g].begin(), gatoms[g].end());
+        aoff.push_back((int)atoms.size());
+      }
+      D.n_cons = nc;
+      D.con_tol = d->constraint_tol;
+      D.con_max_iter = d->constraint_max_iter;
+      D.n_cgroups = (int)gcons.size();
+      UP(cij.data(), cij.size(), &D.con_ij);
+      UP(d->constraint_length, (size_t)nc, &D.con_len);
+      UP(flag.data(), flag.size(), &D.con_atom);
+      UP(off.data(), off.size(), &D.cgroup_off);
+      UP(cons.data(), cons.size(), &D.cgroup_cons);
+      UP(aoff.data(), aoff.size(), &D.cgroup_aoff);
+      UP(atoms.data(), atoms.size(), &D.cgroup_atoms);
+    }
     UP(dijkl.data(), dijkl.size(), &D.dih_ijkl);
     UP(dterms.data(), dterms.size(), &D.dih_terms);
     UP(td.data(), td.size(), &D.term_d);
@@ -491,6 +552,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
     if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
+    if (e & kErrConstraint) return fail(GRP_ETIMEOUT, "SHAKE or RATTLE did not converge within constraint_max_iter sweeps");
     return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
@@ -732,8 +794,8 @@ extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs
     if (!runs[i]) return fail(GRP_EINVAL, "grp_batch_create: run %d is null", i);
     if (runs[i]->sys->dev.potential != GRP_POT_FORCE_FIELD)
       return fail(GRP_ENOTIMPL, "grp_batch_create: batches hold force-field systems");
-    if (runs[i]->sys->dev.gb)
-      return fail(GRP_ENOTIMPL, "grp_batch_create: systems in implicit solvent run alone");
+    if (runs[i]->sys->dev.gb || runs[i]->sys->dev.n_cons)
+      return fail(GRP_ENOTIMPL, "grp_batch_create: systems in implicit solvent or with constraints run alone");
     if (runs[i]->sys->dev.precision != runs[0]->sys->dev.precision)
       return fail(GRP_EINVAL, "grp_batch_create: runs must share one precision");
   }
@@ -1658,7 +1720,7 @@ extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_
     return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
   const grp_system *s = r->sys;
   const SysDev &D = s->dev;
-  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb)
+  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb || D.n_cons)
     return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms in vacuum");
   if (loss->obs < 0 || loss->obs >= D.n_obs) return fail(GRP_EINVAL, "grp_adjoint_segment: bad observable index");
   const int kind = D.obs_kind[loss->obs];

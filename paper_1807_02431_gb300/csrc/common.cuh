@@ -12,7 +12,7 @@ constexpr int kMaxObs = GRP_MAX_OBS;
 constexpr int kMaxGroups = GRP_MAX_GROUPS;
 
 // Error bits latched by kernels into the replica set's error word.
-enum : int { kErrNaN = 1, kErrOverflow = 2, kErrList = 4 };
+enum : int { kErrNaN = 1, kErrOverflow = 2, kErrList = 4, kErrConstraint = 8 };
 
 // Kinds of force-field work items.
 enum : uint32_t { kItemPair = 0, kItemBond = 1, kItemAngle = 2, kItemDihedral = 3, kItemNone = 15 };
@@ -48,6 +48,17 @@ struct SysDev {
   double cutoff2;          // 0: no cutoff
   int coulomb_rf;          // 1: reaction field (eps_r = 1) instead of the dielectric eps = 4r
   int gb;                  // 1: Generalized Born (OBC II) implicit solvent
+  int n_cons;              // bond constraints, in the description's order
+  const int2 *con_ij;
+  const double *con_len;
+  double con_tol;          // relative tolerance of SHAKE / RATTLE
+  int con_max_iter;
+  const unsigned char *con_atom;  // [n] 1 for atoms of a constraint
+  int n_cgroups;           // connected groups of constraints (independent of each other)
+  const int *cgroup_off;   // [n_cgroups + 1] into cgroup_cons and cgroup_atoms_off
+  const int *cgroup_cons;  // constraint indices of each group, ascending
+  const int *cgroup_aoff;  // [n_cgroups + 1] into cgroup_atoms
+  const int *cgroup_atoms; // atoms of each group
   int n_gb_pairs;          // every pair i < j (i | j << 16)
   const uint32_t *gb_pairs;
   double gb_tau;           // k_e (1/eps_in - 1/eps_out)

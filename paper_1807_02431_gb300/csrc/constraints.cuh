@@ -1,0 +1,204 @@
+// Bond constraints in the BAOAB step (the paper's MD setups hold the bonds of hydrogens fixed,
+// Section 4): every sub-step of the unconstrained step is followed by its projection -- positions by
+// SHAKE along the bond vectors before the A step, momenta by RATTLE onto the tangent space (no relative
+// velocity along any bond).  The constraints form independent groups (connected components); one thread
+// integrates a whole group in FP64 (both precision paths), with Gauss-Seidel sweeps over the group's
+// constraints in their order until a sweep moves nothing beyond the tolerance, so that the result is
+// that of sweeping over every constraint of the system.  Item-table systems only.
+#pragma once
+#include "state.cuh"
+
+namespace grp {
+
+constexpr int kMaxGroupAtoms = 16;
+constexpr int kMaxGroupCons = 16;
+
+// One group in registers and local memory, positions, momenta, forces in FP64.
+struct ConGroup {
+  int na, nc;
+  int atom[kMaxGroupAtoms];
+  int ci[kMaxGroupCons], cj[kMaxGroupCons];  // local atom indices of each constraint
+  double d[kMaxGroupCons];
+  double w[kMaxGroupAtoms];                  // 1 / m
+  double q[kMaxGroupAtoms][3], p[kMaxGroupAtoms][3];
+};
+
+// FP64 views of a replica's shared-memory state, per coordinate i = 3 atom + axis.
+__device__ __forceinline__ double st_q(const State<PathF64> &st, int i) { return st.q[i]; }
+__device__ __forceinline__ double st_p(const State<PathF64> &st, int i) { return st.p[i]; }
+__device__ __forceinline__ double st_f(const State<PathF64> &st, int i) { return st.f[i]; }
+__device__ __forceinline__ void st_set_q(State<PathF64> &st, int i, double v) { st.q[i] = v; }
+__device__ __forceinline__ void st_set_p(State<PathF64> &st, int i, double v) { st.p[i] = v; }
+__device__ __forceinline__ double st_q(const State<PathMixed> &st, int i) {
+  return (double)(&st.qh[i / 3].x)[i % 3] + (double)(&st.ql[i / 3].x)[i % 3];
+}
+__device__ __forceinline__ double st_p(const State<PathMixed> &st, int i) {
+  return (double)st.ph[i] + (double)st.pl[i];
+}
+__device__ __forceinline__ double st_f(const State<PathMixed> &st, int i) { return (double)st.f[i]; }
+__device__ __forceinline__ void st_set_q(State<PathMixed> &st, int i, double v) {
+  const ds x = ds_from_double(v);
+  (&st.qh[i / 3].x)[i % 3] = x.hi;
+  (&st.ql[i / 3].x)[i % 3] = x.lo;
+}
+__device__ __forceinline__ void st_set_p(State<PathMixed> &st, int i, double v) {
+  const ds x = ds_from_double(v);
+  st.ph[i] = x.hi;
+  st.pl[i] = x.lo;
+}
+
+__device__ __forceinline__ int local_atom(const ConGroup &G, int a) {
+  for (int u = 0; u < G.na; ++u)
+    if (G.atom[u] == a) return u;
+  return 0;  // unreachable: the group lists every atom of its constraints
+}
+
+template <class P>
+__device__ void con_load(const SysDev &S, const State<P> &st, int g, ConGroup &G) {
+  const int a0 = S.cgroup_aoff[g], a1 = S.cgroup_aoff[g + 1], k0 = S.cgroup_off[g], k1 = S.cgroup_off[g + 1];
+  G.na = a1 - a0;
+  G.nc = k1 - k0;
+  for (int u = 0; u < G.na; ++u) {
+    const int a = S.cgroup_atoms[a0 + u];
+    G.atom[u] = a;
+    G.w[u] = 1.0 / S.mass[a];
+    for (int x = 0; x < 3; ++x) {
+      G.q[u][x] = st_q(st, 3 * a + x);
+      G.p[u][x] = st_p(st, 3 * a + x);
+    }
+  }
+  for (int c = 0; c < G.nc; ++c) {
+    const int k = S.cgroup_cons[k0 + c];
+    const int2 ij = S.con_ij[k];
+    G.ci[c] = local_atom(G, ij.x);
+    G.cj[c] = local_atom(G, ij.y);
+    G.d[c] = S.con_len[k];
+  }
+}
+
+// RATTLE: remove each bond's relative velocity until |r . v| <= tol d^2 / dt for all; false when the
+// sweeps ran out.
+__device__ bool con_rattle(const SysDev &S, ConGroup &G) {
+  for (int it = 0; it < S.con_max_iter; ++it) {
+    bool moved = false;
+    for (int c = 0; c < G.nc; ++c) {
+      const int i = G.ci[c], j = G.cj[c];
+      const double wi = G.w[i], wj = G.w[j], d = G.d[c];
+      const double r[3] = {G.q[i][0] - G.q[j][0], G.q[i][1] - G.q[j][1], G.q[i][2] - G.q[j][2]};
+      double rv = 0.0, rr = 0.0;
+      for (int x = 0; x < 3; ++x) {
+        rv += r[x] * (G.p[i][x] * wi - G.p[j][x] * wj);
+        rr += r[x] * r[x];
+      }
+      if (fabs(rv) <= S.con_tol * d * d / S.dt) continue;
+      const double mu = rv / ((wi + wj) * rr);
+      for (int x = 0; x < 3; ++x) {
+        G.p[i][x] -= mu * r[x];
+        G.p[j][x] += mu * r[x];
+      }
+      moved = true;
+    }
+    if (!moved) return true;
+  }
+  return false;
+}
+
+// SHAKE after an A step from q_old: move each pair along its bond vector at q_old until
+// | |r|^2 - d^2 | <= tol d^2, adding the matching impulses (displacement times m / h) to the momenta.
+__device__ bool con_shake(const SysDev &S, ConGroup &G, const double (*q_old)[3], double h) {
+  for (int it = 0; it < S.con_max_iter; ++it) {
+    bool moved = false;
+    for (int c = 0; c < G.nc; ++c) {
+      const int i = G.ci[c], j = G.cj[c];
+      const double wi = G.w[i], wj = G.w[j], d = G.d[c];
+      double rr = 0.0, sr = 0.0, so[3];
+      for (int x = 0; x < 3; ++x) {
+        const double r = G.q[i][x] - G.q[j][x];
+        so[x] = q_old[i][x] - q_old[j][x];
+        rr += r * r;
+        sr += so[x] * r;
+      }
+      const double diff = d * d - rr;
+      if (fabs(diff) <= S.con_tol * d * d) continue;
+      const double gam = diff / (2.0 * (wi + wj) * sr);
+      for (int x = 0; x < 3; ++x) {
+        G.q[i][x] += gam * wi * so[x];
+        G.q[j][x] -= gam * wj * so[x];
+        G.p[i][x] += gam / h * so[x];
+        G.p[j][x] -= gam / h * so[x];
+      }
+      moved = true;
+    }
+    if (!moved) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void con_a_step(const SysDev &S, ConGroup &G, double h, int *err) {
+  double q_old[kMaxGroupAtoms][3];
+  for (int u = 0; u < G.na; ++u)
+    for (int x = 0; x < 3; ++x) {
+      q_old[u][x] = G.q[u][x];
+      G.q[u][x] += h * G.p[u][x] * G.w[u];
+    }
+  if (!con_shake(S, G, q_old, h)) *err |= kErrConstraint;
+  if (!con_rattle(S, G)) *err |= kErrConstraint;
+}
+
+// B, A, O, A of one constrained group (the force of the previous step in the state's f, the noise of
+// this step in xs[3 atom + axis]).
+template <class P>
+__device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P::T *xs, double h, double c1,
+                         int *err) {
+  ConGroup G;
+  con_load<P>(S, st, g, G);
+  for (int u = 0; u < G.na; ++u)
+    for (int x = 0; x < 3; ++x) G.p[u][x] += h * st_f(st, 3 * G.atom[u] + x);
+  if (!con_rattle(S, G)) *err |= kErrConstraint;
+  con_a_step(S, G, h, err);
+  for (int u = 0; u < G.na; ++u) {
+    const double sd = noise_scale(c1, S.kT, S.mass[G.atom[u]]);
+    for (int x = 0; x < 3; ++x) G.p[u][x] = c1 * G.p[u][x] + sd * (double)xs[3 * G.atom[u] + x];
+  }
+  if (!con_rattle(S, G)) *err |= kErrConstraint;
+  con_a_step(S, G, h, err);
+  for (int u = 0; u < G.na; ++u)
+    for (int x = 0; x < 3; ++x) {
+      st_set_q(st, 3 * G.atom[u] + x, G.q[u][x]);
+      st_set_p(st, 3 * G.atom[u] + x, G.p[u][x]);
+    }
+}
+
+// The closing B of a constrained group with the new forces (taken from the fixed-point accumulators,
+// which are cleared, and kept in the state's f), then RATTLE; returns the group's kinetic energy.
+__device__ __forceinline__ double con_take_force(State<PathF64> &st, const AccF64 &fa, int i) {
+  const double v = (double)fa.F[i] * kFixInv;
+  fa.F[i] = 0;
+  st.f[i] = v;
+  return v;
+}
+__device__ __forceinline__ double con_take_force(State<PathMixed> &st, const AccMixed &fa, int i) {
+  const float v = split_to_float(fa.hi[i], fa.lo[i]);
+  fa.hi[i] = 0;
+  fa.lo[i] = 0u;
+  st.f[i] = v;
+  return (double)v;
+}
+
+template <class P>
+__device__ double con_b(const SysDev &S, State<P> &st, const typename P::Acc &fa, int g, double h, int *err) {
+  ConGroup G;
+  con_load<P>(S, st, g, G);
+  for (int u = 0; u < G.na; ++u)
+    for (int x = 0; x < 3; ++x) G.p[u][x] += h * con_take_force(st, fa, 3 * G.atom[u] + x);
+  if (!con_rattle(S, G)) *err |= kErrConstraint;
+  double ke = 0.0;
+  for (int u = 0; u < G.na; ++u)
+    for (int x = 0; x < 3; ++x) {
+      st_set_p(st, 3 * G.atom[u] + x, G.p[u][x]);
+      ke += 0.5 * G.p[u][x] * G.p[u][x] * G.w[u];
+    }
+  return ke;
+}
+
+}  // namespace grp

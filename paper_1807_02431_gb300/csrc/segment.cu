@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "forcefield.cuh"
+#include "constraints.cuh"
 #include "gb.cuh"
 #include "kernels.h"
 #include "state.cuh"
@@ -320,7 +321,8 @@ enum : int {
 };
 
 // kFF: the nonbonded model compiled into the step loop, 0 = Coulomb with eps = 4r, 1 = reaction field,
-// 2 = eps = 4r plus Generalized Born solvent (item-table systems only), -1 = eps = 4r or reaction field
+// 2 = eps = 4r plus Generalized Born solvent, 3 = eps = 4r with bond constraints (2 and 3 on the item
+// table only), -1 = eps = 4r or reaction field
 // decided per launch (the batched kernel, whose runs may differ; implicit solvent is not batched).
 // The single-run kernels are compiled for one model, which keeps one copy of the force passes and no
 // unused solvent code in the step loop.
@@ -344,7 +346,8 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
   constexpr bool kGB = kMode == kModeItems && kFF == 2;
-  constexpr int kRF = kFF == 2 ? 0 : kFF;
+  constexpr bool kCon = kMode == kModeItems && kFF == 3;
+  constexpr int kRF = kFF >= 2 ? 0 : kFF;
   GbScratch<P> gbs;  // implicit solvent (item-table systems only)
   if constexpr (kGB) {
     ptr = align32(ptr);
@@ -397,12 +400,17 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
       // when one of its coordinates moved more than skin / (2 sqrt 3) (a sufficient test)
       const T *xs = xi + (size_t)j * nd;
       for (int i = threadIdx.x; i < nd; i += kThreads) {
+        if constexpr (kCon) {
+          if (S.con_atom[i / 3]) continue;  // integrated with its constraint group below
+        }
         st.baoa_c(i, xs[i], h, c1);
         if (use_list) {
           const float d = (float)st.coord(i) - (&qref[i / 3].x)[i % 3];
           moved |= 3.f * d * d > S.half_skin2;
         }
       }
+      if constexpr (kCon)
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) con_baoa<P>(S, st, g, xs, a.h, a.c1, &err);
     } else {
       for (int at = threadIdx.x; at < n; at += kThreads) {
         T z[4];
@@ -448,9 +456,17 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     long long k_fix = 0;
     if (kMode == kModeItems || NB > 0) {
       for (int i = threadIdx.x; i < nd; i += kThreads) {
+        if constexpr (kCon) {
+          if (S.con_atom[i / 3]) continue;
+        }
         const T ke = st.bk_c(i, fa, h);
         if (sample) k_fix += fa.efix(ke, &err);
       }
+      if constexpr (kCon)
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) {
+          const double ke = con_b<P>(S, st, fa, g, a.h, &err);
+          if (sample) k_fix += fa.efix((T)ke, &err);
+        }
     } else {  // the same thread owns each atom in both halves of the step
       for (int at = threadIdx.x; at < n; at += kThreads) {
         const T ke = st.bk(at, fa, h);
@@ -626,9 +642,10 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
   const bool small = c.threads <= 320;
   // tiles are taken only without a cutoff, so never with the reaction field; implicit solvent only on
   // the item table (and never with a cutoff)
-  const bool rf = a.S.coulomb_rf != 0, gb = a.S.gb != 0;
+  const bool rf = a.S.coulomb_rf != 0, gb = a.S.gb != 0, con = a.S.n_cons > 0;
   auto kern = mode == kModeItems
-                  ? (gb   ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 2> : ff_segment_kernel<P, 512, 1, kModeItems, 2>)
+                  ? (con  ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 3> : ff_segment_kernel<P, 512, 1, kModeItems, 3>)
+                     : gb ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 2> : ff_segment_kernel<P, 512, 1, kModeItems, 2>)
                      : rf ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 1> : ff_segment_kernel<P, 512, 1, kModeItems, 1>)
                           : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
             : mode == kModeTiles

@@ -342,9 +342,14 @@ def chain_h(n_heavy: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replica
     hpos = np.zeros((nh, 3))
     for i in range(nh):
         nb = [k for k in (i - 1, i + 1) if 0 <= k < nh]
-        u = sum((x[i] - x[k]) / np.linalg.norm(x[i] - x[k]) for k in nb)
-        if np.linalg.norm(u) < 1e-6:
-            u = np.cross(x[nb[0]] - x[i], [0.0, 0.0, 1.0])
+        if len(nb) == 2:  # opposite the bisector of the two bonds
+            u = sum((x[i] - x[k]) / np.linalg.norm(x[i] - x[k]) for k in nb)
+        else:  # an end bead: 109.5 deg from its one bond, in the plane of the next bond
+            b = (x[nb[0]] - x[i]) / np.linalg.norm(x[nb[0]] - x[i])
+            other = x[nb[0] + (1 if nb[0] > i else -1)] - x[nb[0]]
+            perp = other - np.dot(other, b) * b
+            perp /= np.linalg.norm(perp)
+            u = math.cos(math.radians(109.5)) * b - math.sin(math.radians(109.5)) * perp
         hpos[i] = x[i] + 0.109 * u / np.linalg.norm(u)
     n = 2 * nh
     mass = np.concatenate([base.mass, np.full(nh, 1.008)])
