@@ -153,7 +153,7 @@ class Step:
         self.q0, self.p0 = q0, p0
         self.stream = torch.cuda.current_stream()
         self.rep = B.grp_init_replicas(self.sysh, R, seed, q0, p0, per_replica=True, stream=self.stream)
-        self.launches_per_step = 3  # segment, branching, Gelman-Rubin
+        self.launches_per_step = 4  # segment, branching, Gelman-Rubin, status
         self.status = B.FvStatus()
 
     def __call__(self):
@@ -611,6 +611,15 @@ def main():
             solvated = {"workload": f"{sg.name}_r{R} (OBC II, all {sg.n_atoms * (sg.n_atoms - 1) // 2} pairs)",
                         "value": units_per_step * len(tg) / (float(np.sum(tg)) / 1e3),
                         "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tg))}
+        # the chain with one constrained hydrogen per bead (SHAKE / RATTLE), mixed
+        constrained = None
+        if args.fp64_steps > 0:
+            sh = W.chain_h(n_replicas=R)
+            step_h = Step(B, sh, B.GRP_MIXED, R, seed, local)
+            th = time_steps(step_h, args.fp64_steps, 1, flush, step_h.stream)
+            constrained = {"workload": f"{sh.name}_r{R} ({sh.n_atoms} atoms, {len(sh.constraints)} constraints)",
+                           "value": R * sh.n_atoms * sh.t_check * len(th) / (float(np.sum(th)) / 1e3),
+                           "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(th))}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
@@ -647,6 +656,7 @@ def main():
                "roofline": roof, "clocks": clocks,
                "fp64_path": fp64,
                "solvated_chain": solvated,
+               "constrained_chain": constrained,
                "batched": batched,
                "ligand_receptor": ligand,
                "gradient": gradient,

@@ -145,11 +145,111 @@ __device__ __forceinline__ void con_a_step(const SysDev &S, ConGroup &G, double 
   if (!con_rattle(S, G)) *err |= kErrConstraint;
 }
 
+// The same for a group of one constraint (two atoms: the common case of one hydrogen on a heavy
+// atom), in registers: the same sweeps, tests and updates as the general group code, without its
+// local arrays and atom lookups.
+struct ConPair {
+  int a, b;
+  double wa, wb, d, tq, tv;  // 1/m, length, SHAKE and RATTLE thresholds (tol d^2, tol d^2 / dt)
+  double q[2][3], p[2][3];
+};
+
+__device__ __forceinline__ bool pair_rattle(const SysDev &S, ConPair &C) {
+  for (int it = 0; it < S.con_max_iter; ++it) {
+    const double r[3] = {C.q[0][0] - C.q[1][0], C.q[0][1] - C.q[1][1], C.q[0][2] - C.q[1][2]};
+    double rv = 0.0, rr = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      rv += r[x] * (C.p[0][x] * C.wa - C.p[1][x] * C.wb);
+      rr += r[x] * r[x];
+    }
+    if (fabs(rv) <= C.tv) return true;
+    const double mu = rv / ((C.wa + C.wb) * rr);
+    for (int x = 0; x < 3; ++x) {
+      C.p[0][x] -= mu * r[x];
+      C.p[1][x] += mu * r[x];
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void pair_a_step(const SysDev &S, ConPair &C, double h, double ih, int *err) {
+  double so[3];
+  for (int x = 0; x < 3; ++x) {
+    so[x] = C.q[0][x] - C.q[1][x];
+    C.q[0][x] += h * C.p[0][x] * C.wa;
+    C.q[1][x] += h * C.p[1][x] * C.wb;
+  }
+  bool ok = false;
+  for (int it = 0; it < S.con_max_iter && !ok; ++it) {
+    double rr = 0.0, sr = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      const double r = C.q[0][x] - C.q[1][x];
+      rr += r * r;
+      sr += so[x] * r;
+    }
+    const double diff = C.d * C.d - rr;
+    if (fabs(diff) <= C.tq) { ok = true; break; }
+    const double gam = diff / (2.0 * (C.wa + C.wb) * sr);
+    for (int x = 0; x < 3; ++x) {
+      C.q[0][x] += gam * C.wa * so[x];
+      C.q[1][x] -= gam * C.wb * so[x];
+      C.p[0][x] += gam * ih * so[x];
+      C.p[1][x] -= gam * ih * so[x];
+    }
+  }
+  if (!ok) *err |= kErrConstraint;
+  if (!pair_rattle(S, C)) *err |= kErrConstraint;
+}
+
+template <class P>
+__device__ __forceinline__ void pair_load(const SysDev &S, const State<P> &st, int g, ConPair &C) {
+  const int k = S.cgroup_cons[S.cgroup_off[g]];
+  const int2 ij = S.con_ij[k];
+  C.a = ij.x;
+  C.b = ij.y;
+  C.wa = 1.0 / S.mass[C.a];
+  C.wb = 1.0 / S.mass[C.b];
+  C.d = S.con_len[k];
+  C.tq = S.con_tol * C.d * C.d;
+  C.tv = C.tq / S.dt;
+  for (int x = 0; x < 3; ++x) {
+    C.q[0][x] = st_q(st, 3 * C.a + x);
+    C.q[1][x] = st_q(st, 3 * C.b + x);
+    C.p[0][x] = st_p(st, 3 * C.a + x);
+    C.p[1][x] = st_p(st, 3 * C.b + x);
+  }
+}
+
 // B, A, O, A of one constrained group (the force of the previous step in the state's f, the noise of
 // this step in xs[3 atom + axis]).
 template <class P>
 __device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P::T *xs, double h, double c1,
                          int *err) {
+  if (S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {  // one constraint, two atoms
+    ConPair C;
+    pair_load<P>(S, st, g, C);
+    const double ih = 1.0 / h;
+    for (int x = 0; x < 3; ++x) {
+      C.p[0][x] += h * st_f(st, 3 * C.a + x);
+      C.p[1][x] += h * st_f(st, 3 * C.b + x);
+    }
+    if (!pair_rattle(S, C)) *err |= kErrConstraint;
+    pair_a_step(S, C, h, ih, err);
+    const double sa = noise_scale(c1, S.kT, S.mass[C.a]), sb = noise_scale(c1, S.kT, S.mass[C.b]);
+    for (int x = 0; x < 3; ++x) {
+      C.p[0][x] = c1 * C.p[0][x] + sa * (double)xs[3 * C.a + x];
+      C.p[1][x] = c1 * C.p[1][x] + sb * (double)xs[3 * C.b + x];
+    }
+    if (!pair_rattle(S, C)) *err |= kErrConstraint;
+    pair_a_step(S, C, h, ih, err);
+    for (int x = 0; x < 3; ++x) {
+      st_set_q(st, 3 * C.a + x, C.q[0][x]);
+      st_set_q(st, 3 * C.b + x, C.q[1][x]);
+      st_set_p(st, 3 * C.a + x, C.p[0][x]);
+      st_set_p(st, 3 * C.b + x, C.p[1][x]);
+    }
+    return;
+  }
   ConGroup G;
   con_load<P>(S, st, g, G);
   for (int u = 0; u < G.na; ++u)
@@ -187,6 +287,22 @@ __device__ __forceinline__ double con_take_force(State<PathMixed> &st, const Acc
 
 template <class P>
 __device__ double con_b(const SysDev &S, State<P> &st, const typename P::Acc &fa, int g, double h, int *err) {
+  if (S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {
+    ConPair C;
+    pair_load<P>(S, st, g, C);
+    for (int x = 0; x < 3; ++x) {
+      C.p[0][x] += h * con_take_force(st, fa, 3 * C.a + x);
+      C.p[1][x] += h * con_take_force(st, fa, 3 * C.b + x);
+    }
+    if (!pair_rattle(S, C)) *err |= kErrConstraint;
+    double ke = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      st_set_p(st, 3 * C.a + x, C.p[0][x]);
+      st_set_p(st, 3 * C.b + x, C.p[1][x]);
+      ke += 0.5 * (C.p[0][x] * C.p[0][x] * C.wa + C.p[1][x] * C.p[1][x] * C.wb);
+    }
+    return ke;
+  }
   ConGroup G;
   con_load<P>(S, st, g, G);
   for (int u = 0; u < G.na; ++u)
