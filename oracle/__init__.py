@@ -65,6 +65,8 @@ class OrcSystem(C.Structure):
         ("n_constraints", C.c_int32), ("constraint_atoms", C.POINTER(C.c_int32)),
         ("constraint_length", C.POINTER(C.c_double)), ("constraint_tol", C.c_double),
         ("constraint_max_iter", C.c_int32),
+        ("box", C.c_double * 3), ("ewald_beta", C.c_double), ("pme_grid", C.c_int32 * 3),
+        ("pme_order", C.c_int32), ("ewald_kmax", C.c_int32),
     ]
 
 
@@ -103,6 +105,7 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(OrcSystem)]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_gb_born.argtypes = [C.c_void_p, _D, _D, _D]
+        L.orc_ewald_parts.argtypes = [C.c_void_p, _D, _D]
         L.orc_potential.restype = C.c_double
         L.orc_potential.argtypes = [C.c_void_p, _D]
         L.orc_forces.argtypes = [C.c_void_p, _D, _D]
@@ -187,6 +190,10 @@ class Oracle:
             st.constraint_atoms = i("con", s.constraints)
             st.constraint_length = d("conl", s.constraint_length)
         st.constraint_tol, st.constraint_max_iter = s.constraint_tol, s.constraint_max_iter
+        if s.box is not None:
+            for x in range(3):
+                st.box[x], st.pme_grid[x] = s.box[x], s.pme_grid[x]
+        st.ewald_beta, st.pme_order, st.ewald_kmax = s.ewald_beta, s.pme_order, s.ewald_kmax
         st.n_bonds, st.bond_atoms = len(ea["bonds"]), i("bonds", ea["bonds"])
         st.bond_k, st.bond_r0 = d("bk", ea["bond_k"]), d("br0", ea["bond_r0"])
         st.n_angles, st.angle_atoms = len(ea["angles"]), i("angles", ea["angles"])
@@ -258,6 +265,13 @@ class Oracle:
         loss = lib().orc_adjoint_segment(self.ctx, q.shape[0], replica0, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr, obs,
                                          transform, center, width, _dp(gth), _dp(gq), _dp(gp))
         return loss, gth, gq, gp
+
+    def ewald_parts(self, q):
+        """The five parts of the periodic Coulomb energy (real space, excluded pairs, self,
+        reciprocal, background) of one configuration."""
+        out = np.zeros(5)
+        lib().orc_ewald_parts(self.ctx, _dp(_c64(q)), _dp(out))
+        return out
 
     def gb_born(self, q):
         """Generalized Born radii B_i and descreening sums I_i of configuration q."""

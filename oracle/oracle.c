@@ -207,6 +207,249 @@ static void gb_forces(const orc_ctx *c, const double *q, double *f) {
   free(B); free(dBdI); free(dEdB);
 }
 
+/* ---------------------------------------------------------------- periodic electrostatics
+ * Ewald's splitting of the lattice sum of k_e q_i q_j / r over all periodic images, the sum that the
+ * particle mesh Ewald method (cited in Section 3.2 among the optimisations an engine should offer)
+ * approximates.  With beta the splitting parameter, V the box volume and Q the net charge:
+ *   E = sum_{i<j, not excluded, r_ij < r_c} k_e q_i q_j erfc(beta r_ij) / r_ij       (minimum image)
+ *     - sum_{excluded i<j} k_e q_i q_j erf(beta r_ij) / r_ij                          (minimum image)
+ *     - k_e beta / sqrt(pi) sum_i q_i^2
+ *     + k_e / (2 pi V) sum_{m != 0} exp(-pi^2 |m|^2 / beta^2) / |m|^2 |S(m)|^2
+ *     - k_e pi Q^2 / (2 V beta^2),
+ * S(m) = sum_j q_j exp(2 pi i m.r_j), m = (k_0/L_0, k_1/L_1, k_2/L_2) over integer k != 0.  The
+ * excluded pairs' erf term removes what the reciprocal sum adds for the nearest image of a pair that
+ * has no Coulomb interaction; their other images keep theirs. */
+static const double kPi = 3.14159265358979323846;
+
+static int periodic(const orc_system *s) { return s->coulomb_mode == 2 || s->coulomb_mode == 3; }
+
+/* q_i - q_j, at the nearest image in a periodic system */
+static void pair_vec(const orc_system *s, const double *q, int i, int j, double *d) {
+  sub3(q + 3 * i, q + 3 * j, d);
+  if (periodic(s))
+    for (int x = 0; x < 3; ++x) d[x] -= s->box[x] * nearbyint(d[x] / s->box[x]);
+}
+
+static double box_volume(const orc_system *s) { return s->box[0] * s->box[1] * s->box[2]; }
+
+/* Excluded pairs, the self term and the background: energy, and their forces added to f (if not
+ * NULL).  parts[1], parts[2], parts[4] as in orc_ewald_parts. */
+static void ewald_corrections(const orc_ctx *c, const double *q, double *f, double parts[5]) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms;
+  const double b = s->ewald_beta, ke = s->coulomb_k;
+  double ex = 0.0, q2 = 0.0, qt = 0.0;
+  for (int i = 0; i < n; ++i) {
+    q2 += s->charge[i] * s->charge[i];
+    qt += s->charge[i];
+    for (int j = i + 1; j < n; ++j) {
+      if (!c->excluded[(size_t)i * n + j]) continue;
+      double d[3];
+      pair_vec(s, q, i, j, d);
+      const double r2 = dot3(d, d), r = sqrt(r2), kqq = ke * s->charge[i] * s->charge[j];
+      ex -= kqq * erf(b * r) / r;
+      if (f) {
+        /* E = -kqq erf(b r)/r: -dE/dr / r = kqq (2 b/sqrt(pi) exp(-b^2 r^2) - erf(b r)/r) / r^2 */
+        const double g = kqq * (2.0 * b / sqrt(kPi) * exp(-b * b * r2) - erf(b * r) / r) / r2;
+        for (int x = 0; x < 3; ++x) {
+          f[3 * i + x] += g * d[x];
+          f[3 * j + x] -= g * d[x];
+        }
+      }
+    }
+  }
+  parts[1] = ex;
+  parts[2] = -ke * b / sqrt(kPi) * q2;
+  parts[4] = -ke * kPi * qt * qt / (2.0 * box_volume(s) * b * b);
+}
+
+/* Reciprocal sum of the plain Ewald method over |k_d| <= ewald_kmax; forces added to f (if not
+ * NULL): F_i = (2 k_e q_i / V) sum_m g(m) m (C(m) sin(2 pi m.r_i) - S(m) cos(2 pi m.r_i)) with
+ * S(m) = C(m) + i S(m) split into its real and imaginary parts and g = exp(-pi^2 m^2/beta^2)/m^2. */
+static double ewald_reciprocal(const orc_ctx *c, const double *q, double *f) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms, K = s->ewald_kmax;
+  const double V = box_volume(s), b = s->ewald_beta, ke = s->coulomb_k;
+  double e = 0.0;
+  for (int k0 = -K; k0 <= K; ++k0)
+    for (int k1 = -K; k1 <= K; ++k1)
+      for (int k2 = -K; k2 <= K; ++k2) {
+        if (k0 == 0 && k1 == 0 && k2 == 0) continue;
+        const double m[3] = {k0 / s->box[0], k1 / s->box[1], k2 / s->box[2]};
+        const double m2 = dot3(m, m), g = exp(-kPi * kPi * m2 / (b * b)) / m2;
+        double sc = 0.0, ss = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double th = 2.0 * kPi * dot3(m, q + 3 * j);
+          sc += s->charge[j] * cos(th);
+          ss += s->charge[j] * sin(th);
+        }
+        e += g * (sc * sc + ss * ss);
+        if (f)
+          for (int i = 0; i < n; ++i) {
+            const double th = 2.0 * kPi * dot3(m, q + 3 * i);
+            const double w = 2.0 * ke * s->charge[i] / V * g * (sc * sin(th) - ss * cos(th));
+            for (int x = 0; x < 3; ++x) f[3 * i + x] += w * m[x];
+          }
+      }
+  return ke * e / (2.0 * kPi * V);
+}
+
+/* Cardinal B-spline M_p (Essmann et al. 1995): M_2(x) = 1 - |x - 1| on [0, 2], and
+ * M_p(x) = (x M_{p-1}(x) + (p - x) M_{p-1}(x - 1)) / (p - 1), supported on (0, p). */
+static double bspline(int p, double x) {
+  if (x <= 0.0 || x >= (double)p) return 0.0;
+  if (p == 2) return 1.0 - fabs(x - 1.0);
+  return (x * bspline(p - 1, x) + ((double)p - x) * bspline(p - 1, x - 1.0)) / (double)(p - 1);
+}
+/* dM_p/dx = M_{p-1}(x) - M_{p-1}(x - 1) */
+static double bspline_d(int p, double x) { return bspline(p - 1, x) - bspline(p - 1, x - 1.0); }
+
+/* Interpolation weights of one coordinate on a periodic axis of K points: u = K r / L taken into
+ * [0, K); w[k] = sum over images n of M_p(u - k - n K), dw[k] its derivative in u. */
+static void spline_weights(int p, int K, double L, double r, double *w, double *dw) {
+  double u = (double)K * (r / L - floor(r / L));
+  for (int k = 0; k < K; ++k) {
+    w[k] = dw[k] = 0.0;
+    for (int img = -2; img <= 2; ++img) {
+      const double x = u - k - (double)img * K;
+      w[k] += bspline(p, x);
+      dw[k] += bspline_d(p, x);
+    }
+  }
+}
+
+/* One-dimensional discrete Fourier transform of every line along axis ax of a complex grid
+ * [K0][K1][K2]: X(m) = sum_k x(k) exp(sign 2 pi i m k / K_ax), in place. */
+static void dft_lines(double *re, double *im, const int *K, int ax, int sign) {
+  const int stride[3] = {K[1] * K[2], K[2], 1};
+  const int Ka = K[ax], oa = (ax + 1) % 3, ob = (ax + 2) % 3;
+  double *tr = (double *)malloc(sizeof(double) * Ka), *ti = (double *)malloc(sizeof(double) * Ka);
+  for (int a = 0; a < K[oa]; ++a)
+    for (int c2 = 0; c2 < K[ob]; ++c2) {
+      const size_t base = (size_t)a * stride[oa] + (size_t)c2 * stride[ob];
+      for (int m = 0; m < Ka; ++m) {
+        double xr = 0.0, xi = 0.0;
+        for (int k = 0; k < Ka; ++k) {
+          const double th = sign * 2.0 * kPi * (double)m * (double)k / (double)Ka;
+          const double vr = re[base + (size_t)k * stride[ax]], vi = im[base + (size_t)k * stride[ax]];
+          xr += vr * cos(th) - vi * sin(th);
+          xi += vr * sin(th) + vi * cos(th);
+        }
+        tr[m] = xr;
+        ti[m] = xi;
+      }
+      for (int m = 0; m < Ka; ++m) {
+        re[base + (size_t)m * stride[ax]] = tr[m];
+        im[base + (size_t)m * stride[ax]] = ti[m];
+      }
+    }
+  free(tr);
+  free(ti);
+}
+
+/* Smooth particle mesh Ewald reciprocal sum (Essmann et al. 1995, Section 3 and Eq. 4.7):
+ *   Q(k) = sum_i q_i w_0i(k_0) w_1i(k_1) w_2i(k_2)   (the charges spread by B-splines of order p),
+ *   F(m) = sum_k Q(k) exp(2 pi i sum_d m_d k_d / K_d),
+ *   E = (k_e/2) sum_m G(m) |F(m)|^2,  G(m) = B(m) exp(-pi^2 |m'|^2 / beta^2) / (pi V |m'|^2), G(0) = 0,
+ * with m'_d = m_d / L_d for m_d <= K_d/2, (m_d - K_d) / L_d otherwise, and the Euler exponential
+ * spline factor B(m) = prod_d |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m_d k / K_d)|^-2.  Forces:
+ * phi(k) = sum_m G(m) F(m) exp(-2 pi i m.k/K) is dE/dQ(k) / k_e, and F_i = -k_e sum_k dQ(k)/dr_i phi(k). */
+static double pme_reciprocal(const orc_ctx *c, const double *q, double *f) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms, p = s->pme_order;
+  const int *K = s->pme_grid;
+  const size_t ng = (size_t)K[0] * K[1] * K[2];
+  const double V = box_volume(s), b = s->ewald_beta, ke = s->coulomb_k;
+  double *w[3], *dw[3];
+  for (int d = 0; d < 3; ++d) {
+    w[d] = (double *)malloc(sizeof(double) * (size_t)n * K[d]);
+    dw[d] = (double *)malloc(sizeof(double) * (size_t)n * K[d]);
+    for (int i = 0; i < n; ++i)
+      spline_weights(p, K[d], s->box[d], q[3 * i + d], w[d] + (size_t)i * K[d], dw[d] + (size_t)i * K[d]);
+  }
+  double *re = (double *)calloc(ng, sizeof(double)), *im = (double *)calloc(ng, sizeof(double));
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < K[0]; ++a)
+      for (int bb = 0; bb < K[1]; ++bb)
+        for (int cc = 0; cc < K[2]; ++cc)
+          re[((size_t)a * K[1] + bb) * K[2] + cc] +=
+              s->charge[i] * w[0][(size_t)i * K[0] + a] * w[1][(size_t)i * K[1] + bb] * w[2][(size_t)i * K[2] + cc];
+  for (int d = 0; d < 3; ++d) dft_lines(re, im, K, d, +1);
+  /* B(m) per axis */
+  double *bmod[3];
+  for (int d = 0; d < 3; ++d) {
+    bmod[d] = (double *)malloc(sizeof(double) * K[d]);
+    for (int m = 0; m < K[d]; ++m) {
+      double dr = 0.0, di = 0.0;
+      for (int k = 0; k <= p - 2; ++k) {
+        const double th = 2.0 * kPi * (double)m * (double)k / (double)K[d];
+        dr += bspline(p, k + 1.0) * cos(th);
+        di += bspline(p, k + 1.0) * sin(th);
+      }
+      bmod[d][m] = 1.0 / (dr * dr + di * di);
+    }
+  }
+  double e = 0.0;
+  for (int a = 0; a < K[0]; ++a)
+    for (int bb = 0; bb < K[1]; ++bb)
+      for (int cc = 0; cc < K[2]; ++cc) {
+        const size_t t = ((size_t)a * K[1] + bb) * K[2] + cc;
+        const int mi[3] = {a, bb, cc};
+        double m2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double md = (mi[d] <= K[d] / 2 ? mi[d] : mi[d] - K[d]) / s->box[d];
+          m2 += md * md;
+        }
+        double G = 0.0;
+        if (m2 > 0.0) G = bmod[0][a] * bmod[1][bb] * bmod[2][cc] * exp(-kPi * kPi * m2 / (b * b)) / (kPi * V * m2);
+        e += 0.5 * ke * G * (re[t] * re[t] + im[t] * im[t]);
+        re[t] *= G;
+        im[t] *= G;
+      }
+  if (f) {
+    for (int d = 0; d < 3; ++d) dft_lines(re, im, K, d, -1); /* re = phi */
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < K[0]; ++a)
+        for (int bb = 0; bb < K[1]; ++bb)
+          for (int cc = 0; cc < K[2]; ++cc) {
+            const double ph = re[((size_t)a * K[1] + bb) * K[2] + cc];
+            const double w0 = w[0][(size_t)i * K[0] + a], w1 = w[1][(size_t)i * K[1] + bb], w2 = w[2][(size_t)i * K[2] + cc];
+            const double d0 = dw[0][(size_t)i * K[0] + a], d1 = dw[1][(size_t)i * K[1] + bb], d2 = dw[2][(size_t)i * K[2] + cc];
+            const double kq = -ke * s->charge[i] * ph;
+            f[3 * i + 0] += kq * K[0] / s->box[0] * d0 * w1 * w2;
+            f[3 * i + 1] += kq * K[1] / s->box[1] * w0 * d1 * w2;
+            f[3 * i + 2] += kq * K[2] / s->box[2] * w0 * w1 * d2;
+          }
+  }
+  for (int d = 0; d < 3; ++d) { free(w[d]); free(dw[d]); free(bmod[d]); }
+  free(re);
+  free(im);
+  return e;
+}
+
+static double periodic_reciprocal(const orc_ctx *c, const double *q, double *f) {
+  return c->s.coulomb_mode == 2 ? pme_reciprocal(c, q, f) : ewald_reciprocal(c, q, f);
+}
+
+void orc_ewald_parts(const orc_ctx *c, const double *q, double parts[5]) {
+  const orc_system *s = &c->s;
+  const int n = s->n_atoms;
+  double dir = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      if (c->excluded[(size_t)i * n + j]) continue;
+      double d[3];
+      pair_vec(s, q, i, j, d);
+      const double r2 = dot3(d, d);
+      if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
+      const double r = sqrt(r2);
+      dir += s->coulomb_k * s->charge[i] * s->charge[j] * erfc(s->ewald_beta * r) / r;
+    }
+  ewald_corrections(c, q, NULL, parts);
+  parts[0] = dir;
+  parts[3] = periodic_reciprocal(c, q, NULL);
+}
+
 /* ---------------------------------------------------------------- potential V(q), Eq. 1 */
 double orc_potential(const orc_ctx *c, const double *q) {
   const orc_system *s = &c->s;
@@ -241,7 +484,7 @@ double orc_potential(const orc_ctx *c, const double *q) {
     for (int j = i + 1; j < n; ++j) {
       if (c->excluded[(size_t)i * n + j]) continue;
       double d[3];
-      sub3(q + 3 * i, q + 3 * j, d);
+      pair_vec(s, q, i, j, d);
       double r2 = dot3(d, d);
       if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
       double sig = 0.5 * (s->sigma[i] + s->sigma[j]);
@@ -249,7 +492,11 @@ double orc_potential(const orc_ctx *c, const double *q) {
       double sr6 = pow(sig * sig / r2, 3);
       e += 4.0 * eps * (sr6 * sr6 - sr6);
       const double kqq = s->coulomb_k * s->charge[i] * s->charge[j];
-      if (s->coulomb_mode == 1) {
+      if (periodic(s)) {
+        /* real-space part of the Ewald sum */
+        const double r = sqrt(r2);
+        e += kqq * erfc(s->ewald_beta * r) / r;
+      } else if (s->coulomb_mode == 1) {
         /* reaction field: E = k_e q_i q_j (1/r + k_rf r^2 - c_rf) */
         double krf, crf;
         rf_constants(s, &krf, &crf);
@@ -261,6 +508,11 @@ double orc_potential(const orc_ctx *c, const double *q) {
     }
   }
   if (s->gb_radius) e += gb_energy(c, q);
+  if (periodic(s)) {
+    double parts[5];
+    ewald_corrections(c, q, NULL, parts);
+    e += parts[1] + parts[2] + parts[4] + periodic_reciprocal(c, q, NULL);
+  }
   return e;
 }
 
@@ -340,7 +592,7 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
     for (int j = i + 1; j < n; ++j) {
       if (c->excluded[(size_t)i * n + j]) continue;
       double d[3];
-      sub3(q + 3 * i, q + 3 * j, d);
+      pair_vec(s, q, i, j, d);
       double r2 = dot3(d, d);
       if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
       double sig = 0.5 * (s->sigma[i] + s->sigma[j]);
@@ -349,7 +601,11 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
       /* -dE_LJ/dr / r = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 */
       double g = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
       const double kqq = s->coulomb_k * s->charge[i] * s->charge[j];
-      if (s->coulomb_mode == 1) {
+      if (periodic(s)) {
+        /* E = kqq erfc(b r)/r: -dE/dr / r = kqq (erfc(b r)/r + 2 b/sqrt(pi) exp(-b^2 r^2)) / r^2 */
+        const double r = sqrt(r2), b = s->ewald_beta;
+        g += kqq * (erfc(b * r) / r + 2.0 * b / sqrt(kPi) * exp(-b * b * r2)) / r2;
+      } else if (s->coulomb_mode == 1) {
         /* reaction field: -dE_C/dr / r = k_e q_i q_j (1/r^2 - 2 k_rf r) / r */
         double krf, crf;
         rf_constants(s, &krf, &crf);
@@ -365,6 +621,11 @@ void orc_forces(const orc_ctx *c, const double *q, double *f) {
     }
   }
   if (s->gb_radius) gb_forces(c, q, f);
+  if (periodic(s)) {
+    double parts[5];
+    ewald_corrections(c, q, f, parts);
+    periodic_reciprocal(c, q, f);
+  }
 }
 
 /* ---------------------------------------------------------------- dV/d theta
@@ -382,7 +643,7 @@ void orc_param_grad(const orc_ctx *c, const double *q, double *g) {
     for (int j = i + 1; j < n; ++j) {
       if (c->excluded[(size_t)i * n + j]) continue;
       double d[3];
-      sub3(q + 3 * i, q + 3 * j, d);
+      pair_vec(s, q, i, j, d);
       double r2 = dot3(d, d);
       if (s->cutoff > 0 && r2 >= s->cutoff * s->cutoff) continue;
       double sig = 0.5 * (s->sigma[i] + s->sigma[j]);

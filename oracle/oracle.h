@@ -41,7 +41,7 @@ typedef struct {
   int32_t potential;  /* ORC_POT_* */
   const double *mass; /* [n_atoms] */
   double dw_a, dw_b;  /* V(x,y) = dw_a (x^2-1)^2 + dw_b y^2 */
-  /* nonbonded: Lennard-Jones (Lorentz-Berthelot) + Coulomb with distance-dependent dielectric 4r */
+  /* nonbonded: Lennard-Jones (Lorentz-Berthelot) + Coulomb (coulomb_mode below) */
   const double *sigma, *epsilon, *charge; /* [n_atoms] */
   int32_t n_excl;
   const int32_t *excl; /* [n_excl][2] excluded nonbonded pairs */
@@ -72,7 +72,8 @@ typedef struct {
   int32_t n_obs;
   int32_t obs_kind[ORC_MAX_OBS];
   int32_t obs_arg[ORC_MAX_OBS][4];
-  int32_t coulomb_mode;   /* 0: dielectric eps = 4r; 1: reaction field (needs cutoff > 0) */
+  int32_t coulomb_mode;   /* 0: dielectric eps = 4r; 1: reaction field (needs cutoff > 0);
+                             2: periodic, particle mesh Ewald; 3: periodic, plain Ewald sum */
   double rf_dielectric;   /* eps_rf of the reaction field; 0 = conductor (infinite) */
   /* Generalized Born implicit solvent, OBC model II (the solvent of the paper's protein-ligand setup,
    * Section 4.2); off when gb_radius is NULL.  Per atom: intrinsic radius rho_i (nm) and descreening
@@ -86,6 +87,20 @@ typedef struct {
   const double *constraint_length;
   double constraint_tol;
   int32_t constraint_max_iter;
+  /* Periodic electrostatics (coulomb_mode 2 and 3), the Ewald sums that the particle mesh Ewald
+   * method cited among the engine's expected optimisations (Section 3.2) approximates.  Orthorhombic
+   * box of edges box[0..2] (nm); splitting parameter beta (nm^-1): each Coulomb pair is split into
+   * k_e q_i q_j erfc(beta r)/r, summed over minimum images within the cutoff (at most half the
+   * shortest edge), and a smooth remainder summed in reciprocal space.  Mode 2 evaluates the
+   * reciprocal sum by smooth particle mesh Ewald (Essmann et al. 1995: B-splines of order pme_order
+   * on a pme_grid[0] x pme_grid[1] x pme_grid[2] grid); mode 3 sums it directly over the
+   * reciprocal vectors (k_0/L_0, k_1/L_1, k_2/L_2), 0 < max |k_d| <= ewald_kmax.  Lennard-Jones takes
+   * the same minimum image and cutoff. */
+  double box[3];
+  double ewald_beta;
+  int32_t pme_grid[3];
+  int32_t pme_order;
+  int32_t ewald_kmax;
 } orc_system;
 
 typedef struct orc_ctx orc_ctx;
@@ -125,6 +140,11 @@ int32_t orc_state_of(const orc_ctx *c, const double *q);
 int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega);
 /* Generalized Born (OBC II) Born radii B[n] and descreening sums I[n] (nm^-1) of configuration q. */
 void orc_gb_born(const orc_ctx *c, const double *q, double *born, double *integral);
+/* The parts of the periodic Coulomb energy (coulomb_mode 2 or 3) of configuration q: parts[0] the
+ * real-space sum over non-excluded pairs, [1] minus the smooth part of the excluded pairs,
+ * [2] the self term -k_e beta/sqrt(pi) sum q_i^2, [3] the reciprocal sum, [4] the neutralising
+ * background -k_e pi Q^2 / (2 V beta^2) of a net charge Q.  Their sum is the Coulomb part of V. */
+void orc_ewald_parts(const orc_ctx *c, const double *q, double parts[5]);
 
 /* Collective variables of the state definition: cv[0..3] (phi/psi in degrees, x, a distance, or
  * the rotamer torsions in degrees; unused entries 0). */

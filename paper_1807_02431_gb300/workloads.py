@@ -14,6 +14,8 @@ Systems (stand-ins for the paper's workloads, whose force fields and structures 
   * ``alkane``          - a united-atom n-alkane whose backbone torsions have three rotamer wells:
     3^(n-3) disjoint states (all torsions in their well cores) separated by a transient region, the
     many-state, non-partition case of Section 2.4.1's transient propagation.
+  * ``chain_ions``      - the chain with ion pairs in a periodic box, electrostatics by particle
+    mesh Ewald.
   * ``ligand_receptor`` - a packed-globule receptor with an elastic network and a short ligand chain
     in a surface pocket, shaped like the FKBP-DMSO dissociation problem (Section 4.2).
 
@@ -39,6 +41,8 @@ CV_ROTAMERS = 3
 
 COULOMB_EPS4R = 0
 COULOMB_REACTION_FIELD = 1
+COULOMB_PME = 2     # periodic box, smooth particle mesh Ewald
+COULOMB_EWALD = 3   # periodic box, plain Ewald sum over reciprocal vectors (oracle only)
 
 OBS_COORD = 0
 OBS_POTENTIAL = 1
@@ -76,6 +80,11 @@ class System:
     constraint_length: np.ndarray | None = None
     constraint_tol: float = 1e-10           # relative tolerance of SHAKE / RATTLE
     constraint_max_iter: int = 1000
+    box: tuple | None = None                # periodic box edges (nm) of the Ewald modes
+    ewald_beta: float = 0.0                 # splitting parameter, nm^-1
+    pme_grid: tuple = (16, 16, 16)          # PME grid points per axis
+    pme_order: int = 4                      # B-spline order
+    ewald_kmax: int = 8                     # plain Ewald: |k_d| <= kmax
     bonds: np.ndarray | None = None         # [nb, 2]
     bond_k: np.ndarray | None = None
     bond_r0: np.ndarray | None = None
@@ -377,6 +386,55 @@ def chain_h(n_heavy: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replica
     s.q0 = np.concatenate([x, hpos])
     s.p0 = maxwell_boltzmann(mass, s.kT, 3, np.random.default_rng(dyn_seed))
     return s
+
+
+def chain_ions(n_pairs: int = 20, edge=2.6, seed: int = 1807, dyn_seed: int = 2431,
+               n_replicas: int = 256, grid=16, order: int = 4, ewald_rtol: float = 1e-5) -> System:
+    """The 22-bead chain with `n_pairs` ion pairs in a periodic box of edge `edge` nm (or edges), its
+    electrostatics summed over all periodic images by particle mesh Ewald (an optimisation the paper
+    expects of an MD engine, Section 3.2): 62 atoms for 20 pairs.  Ions of 20 amu, LJ sigma 0.3 nm and
+    eps 0.5 kJ/mol, charges +-0.3 e, placed uniformly at least 0.3 nm from every atom placed before;
+    plain Coulomb (eps = 1) with real-space cutoff 1.2 nm, beta such that erfc(beta r_c) = ewald_rtol
+    (2.6 nm^-1 for 1e-5, the usual MD setting), a grid x grid x grid mesh (0.16 nm spacing for 16) and
+    B-splines of order `order`; Lennard-Jones cut at the same distance over minimum images.  States,
+    observables and the Gen. ParRep parameters are the chain's."""
+    base = chain(seed=seed, dyn_seed=dyn_seed, n_replicas=n_replicas)
+    rng = np.random.default_rng(seed + 7)
+    box = np.broadcast_to(np.asarray(edge, float), 3)
+    grid = tuple(int(g) for g in np.broadcast_to(grid, 3))
+    x = [v for v in base.q0]
+    ions = []
+    while len(ions) < 2 * n_pairs:
+        cand = rng.uniform(-0.5 * box, 0.5 * box)
+        d = np.asarray(x) - cand
+        d -= box * np.round(d / box)
+        if np.min(np.linalg.norm(d, axis=1)) >= 0.3:
+            x.append(cand)
+            ions.append(cand)
+    n = base.n_atoms + 2 * n_pairs
+    ni = 2 * n_pairs
+    cutoff = 1.2
+    beta = _erfc_inverse(ewald_rtol) / cutoff
+    mass = np.concatenate([base.mass, np.full(ni, 20.0)])
+    s = dataclasses.replace(
+        base, name=f"chain{base.n_atoms}_ions{ni}", n_atoms=n, mass=mass,
+        charge=np.concatenate([base.charge, np.tile([0.3, -0.3], n_pairs)]),
+        sigma=np.concatenate([base.sigma, np.full(ni, 0.3)]),
+        epsilon=np.concatenate([base.epsilon, np.full(ni, 0.5)]),
+        cutoff=cutoff, coulomb_mode=COULOMB_PME, box=tuple(float(b) for b in box), ewald_beta=beta,
+        pme_grid=grid, pme_order=order, ewald_kmax=int(math.ceil(3.5 * beta * box.max() / math.pi)))
+    s.q0 = np.asarray(x)
+    s.p0 = maxwell_boltzmann(mass, s.kT, 3, np.random.default_rng(dyn_seed))
+    return s
+
+
+def _erfc_inverse(y: float) -> float:
+    """x with erfc(x) = y (bisection; 0 < y < 1)."""
+    lo, hi = 0.0, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if math.erfc(mid) > y else (lo, mid)
+    return 0.5 * (lo + hi)
 
 
 def _kd_order(x, leaf=32):
