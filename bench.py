@@ -437,8 +437,8 @@ def profile_case(B, case, replicas, steps, launches):
     """A small fixed case for ncu captures: `launches` launches of the case's main kernel."""
     import torch
 
-    if case == "chain":
-        s = W.chain()
+    if case in ("chain", "pme"):
+        s = W.chain() if case == "chain" else W.chain_ions()
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0)
         for _ in range(launches):
             B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
@@ -526,7 +526,7 @@ def main():
     ap.add_argument("--gradient-reps", type=int, default=2)
     ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--branch-reps", type=int, default=20)
-    ap.add_argument("--profile-case", choices=["chain", "ligand", "adjoint", "batch", "branch"], default=None,
+    ap.add_argument("--profile-case", choices=["chain", "pme", "ligand", "adjoint", "batch", "branch"], default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
     ap.add_argument("--profile-replicas", type=int, default=152)
     ap.add_argument("--profile-steps", type=int, default=100)
@@ -620,6 +620,16 @@ def main():
             constrained = {"workload": f"{sh.name}_r{R} ({sh.n_atoms} atoms, {len(sh.constraints)} constraints)",
                            "value": R * sh.n_atoms * sh.t_check * len(th) / (float(np.sum(th)) / 1e3),
                            "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(th))}
+        # the chain with 20 ion pairs in a periodic box, particle mesh Ewald, mixed
+        periodic = None
+        if args.fp64_steps > 0:
+            sp = W.chain_ions(n_replicas=R)
+            step_p = Step(B, sp, B.GRP_MIXED, R, seed, local)
+            tp = time_steps(step_p, args.fp64_steps, 1, flush, step_p.stream)
+            periodic = {"workload": f"{sp.name}_r{R} ({sp.n_atoms} atoms, box {sp.box[0]} nm, grid "
+                                    f"{'x'.join(str(k) for k in sp.pme_grid)}, order {sp.pme_order}, cutoff {sp.cutoff} nm)",
+                        "value": R * sp.n_atoms * sp.t_check * len(tp) / (float(np.sum(tp)) / 1e3),
+                        "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tp))}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)
@@ -657,6 +667,7 @@ def main():
                "fp64_path": fp64,
                "solvated_chain": solvated,
                "constrained_chain": constrained,
+               "periodic_pme": periodic,
                "batched": batched,
                "ligand_receptor": ligand,
                "gradient": gradient,

@@ -51,7 +51,7 @@ enum { GRP_CV_DOUBLE_WELL = 0, GRP_CV_DIHEDRAL_RECT = 1, GRP_CV_COM_DISTANCE = 2
  * cutoff, which the engine it used treats by a reaction field): for r < cutoff,
  * E = k_e q_i q_j (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3),
  * c_rf = 1/r_c + k_rf r_c^2 (eps_r = 1); it needs cutoff > 0. */
-enum { GRP_COULOMB_EPS4R = 0, GRP_COULOMB_REACTION_FIELD = 1 };
+enum { GRP_COULOMB_EPS4R = 0, GRP_COULOMB_REACTION_FIELD = 1, GRP_COULOMB_PME = 2 };
 enum { GRP_OBS_COORD = 0, GRP_OBS_POTENTIAL = 1, GRP_OBS_KINETIC = 2, GRP_OBS_DIHEDRAL = 3,
        GRP_OBS_GROUP_DISTANCE = 4, GRP_OBS_RMS_VELOCITY = 5 };
 #define GRP_MAX_OBS 8
@@ -111,7 +111,7 @@ typedef struct {
   int32_t n_obs;
   int32_t obs_kind[GRP_MAX_OBS];
   int32_t obs_arg[GRP_MAX_OBS][4];
-  int32_t coulomb_mode;         /* GRP_COULOMB_EPS4R or GRP_COULOMB_REACTION_FIELD */
+  int32_t coulomb_mode;         /* GRP_COULOMB_EPS4R, GRP_COULOMB_REACTION_FIELD or GRP_COULOMB_PME */
   double rf_dielectric;         /* eps_rf of the reaction field (>= 1; 0 = infinity, a conductor) */
   /* Generalized Born implicit solvent, OBC model II (the solvent of the paper's protein-ligand setup,
    * Section 4.2), added to V when gb_radius is not NULL: per-atom intrinsic radii rho_i (nm, > 0.009)
@@ -135,6 +135,22 @@ typedef struct {
   const double *constraint_length;  /* [n_constraints] */
   double constraint_tol;            /* relative, e.g. 1e-10 */
   int32_t constraint_max_iter;
+  /* Periodic electrostatics, coulomb_mode GRP_COULOMB_PME (particle mesh Ewald, one of the nonbonded
+   * methods Section 3.2 expects of an engine): an orthorhombic box of edges box[0..2] (nm), plain
+   * Coulomb (eps = 1) summed over all periodic images by Ewald's splitting with parameter ewald_beta
+   * (nm^-1).  Real space: k_e q_i q_j erfc(beta r)/r over the minimum images of non-excluded pairs
+   * within `cutoff` (required, at most half the shortest edge); excluded pairs: -k_e q_i q_j erf(beta r)/r;
+   * self: -k_e beta/sqrt(pi) sum q_i^2; background of a net charge Q: -k_e pi Q^2 / (2 V beta^2);
+   * reciprocal space by smooth particle mesh Ewald (Essmann et al. 1995) with cardinal B-splines of
+   * order pme_order on a pme_grid[0] x pme_grid[1] x pme_grid[2] grid.  Lennard-Jones takes the same
+   * minimum images and cutoff; bonded terms use the positions as they are (molecules are never
+   * wrapped).  Positions may leave the box.  GRP_EINVAL for a non-positive edge or beta, a missing or
+   * too long cutoff; GRP_ENOTIMPL for 64 atoms or more, grid sizes other than 8 or 16, an order other
+   * than 4, with implicit solvent or constraints, in a batch, and for grp_adjoint_segment. */
+  double box[3];
+  double ewald_beta;
+  int32_t pme_grid[3];
+  int32_t pme_order;
 } grp_system_desc;
 
 typedef struct grp_system grp_system;

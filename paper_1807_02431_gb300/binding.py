@@ -59,6 +59,8 @@ class SystemDesc(C.Structure):
         ("n_constraints", C.c_int32), ("constraint_atoms", C.POINTER(C.c_int32)),
         ("constraint_length", C.POINTER(C.c_double)), ("constraint_tol", C.c_double),
         ("constraint_max_iter", C.c_int32),
+        ("box", C.c_double * 3), ("ewald_beta", C.c_double), ("pme_grid", C.c_int32 * 3),
+        ("pme_order", C.c_int32),
     ]
 
 
@@ -225,6 +227,10 @@ class SystemHandle:
             desc.constraint_atoms = i("con", s.constraints)
             desc.constraint_length = d("conl", s.constraint_length)
         desc.constraint_tol, desc.constraint_max_iter = s.constraint_tol, s.constraint_max_iter
+        if s.box is not None:
+            for x in range(3):
+                desc.box[x], desc.pme_grid[x] = s.box[x], s.pme_grid[x]
+        desc.ewald_beta, desc.pme_order = s.ewald_beta, s.pme_order
         desc.n_bonds, desc.bond_atoms = len(ea["bonds"]), i("b", ea["bonds"])
         desc.bond_k, desc.bond_r0 = d("bk", ea["bond_k"]), d("br", ea["bond_r0"])
         desc.n_angles, desc.angle_atoms = len(ea["angles"]), i("a", ea["angles"])

@@ -113,6 +113,88 @@ grp::SysDev grp_system_device_view(const grp_system *s) { return s->dev; }
 void grp_set_last_error(const char *msg) { g_last_error = msg; }
 
 // ------------------------------------------------------------------------------------------------
+// Periodic electrostatics by smooth particle mesh Ewald: validation and the device tables (box,
+// excluded pairs, the self and background energies, the influence function on the grid).
+static double host_bspline(int p, double x) {  // cardinal B-spline M_p, support (0, p)
+  if (x <= 0.0 || x >= p) return 0.0;
+  if (p == 2) return 1.0 - std::fabs(x - 1.0);
+  return (x * host_bspline(p - 1, x) + (p - x) * host_bspline(p - 1, x - 1.0)) / (p - 1);
+}
+
+static grp_status setup_pme(const grp_system_desc *d, const std::vector<uint8_t> &excl, grp_system *s) {
+  SysDev &D = s->dev;
+  const int n = d->n_atoms;
+  const double pi = 3.14159265358979323846;
+  if (n >= 64) return fail(GRP_ENOTIMPL, "particle mesh Ewald is implemented for systems of fewer than 64 atoms");
+  for (int x = 0; x < 3; ++x)
+    if (!(d->box[x] > 0) || !std::isfinite(d->box[x])) return fail(GRP_EINVAL, "box edge %d must be positive", x);
+  if (!(d->ewald_beta > 0) || !std::isfinite(d->ewald_beta)) return fail(GRP_EINVAL, "ewald_beta must be positive");
+  const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2]));
+  if (!(d->cutoff > 0) || d->cutoff > 0.5 * lmin)
+    return fail(GRP_EINVAL, "particle mesh Ewald needs 0 < cutoff <= half the shortest box edge");
+  for (int x = 0; x < 3; ++x)
+    if (d->pme_grid[x] != 8 && d->pme_grid[x] != 16)
+      return fail(GRP_ENOTIMPL, "particle mesh Ewald grids of 8 or 16 points per axis (axis %d: %d)", x, d->pme_grid[x]);
+  if (d->pme_order != 4) return fail(GRP_ENOTIMPL, "particle mesh Ewald with B-splines of order 4 (got %d)", d->pme_order);
+  if (d->gb_radius || d->n_constraints > 0)
+    return fail(GRP_ENOTIMPL, "particle mesh Ewald without implicit solvent or constraints");
+  D.coulomb_rf = 2;
+  D.ewald_beta = d->ewald_beta;
+  for (int x = 0; x < 3; ++x) {
+    D.box[x] = d->box[x];
+    D.ibox[x] = 1.0 / d->box[x];
+    D.pme_K[x] = d->pme_grid[x];
+  }
+  const double V = d->box[0] * d->box[1] * d->box[2], b = d->ewald_beta, ke = d->coulomb_k;
+  double q2 = 0.0, qt = 0.0;
+  for (int i = 0; i < n; ++i) {
+    q2 += d->charge[i] * d->charge[i];
+    qt += d->charge[i];
+  }
+  D.pme_e_const = -ke * b / std::sqrt(pi) * q2 - ke * pi * qt * qt / (2.0 * V * b * b);
+  std::vector<uint32_t> ex;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (excl[(size_t)i * n + j]) ex.push_back((uint32_t)i | ((uint32_t)j << 16));
+  D.n_excl_pairs = (int)ex.size();
+  grp_status st = GRP_OK;
+  if (!ex.empty() && (st = upload(s->owned, ex.data(), ex.size(), &D.excl_pairs)) != GRP_OK) return st;
+  // influence function times 4 (charges enter the grid scaled by sqrt(k_e/4)):
+  // 4 B(m) exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2), B(m) = prod_d |sum_{k<p-1} M_p(k+1) e^{2 pi i m_d k/K_d}|^-2
+  const int p = d->pme_order, *K = d->pme_grid;
+  std::vector<double> bmod[3];
+  for (int x = 0; x < 3; ++x) {
+    bmod[x].resize(K[x]);
+    for (int m = 0; m < K[x]; ++m) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k + 1 < p; ++k) {
+        const double a = 2.0 * pi * m * k / K[x], w = host_bspline(p, k + 1.0);
+        re += w * std::cos(a);
+        im += w * std::sin(a);
+      }
+      bmod[x][m] = 1.0 / (re * re + im * im);
+    }
+  }
+  const size_t G = (size_t)K[0] * K[1] * K[2];
+  std::vector<double> gd(G);
+  std::vector<float> gf(G);
+  for (int a = 0; a < K[0]; ++a)
+    for (int c = 0; c < K[1]; ++c)
+      for (int e = 0; e < K[2]; ++e) {
+        const int mi[3] = {a, c, e};
+        double m2 = 0.0;
+        for (int x = 0; x < 3; ++x) {
+          const double mx = (mi[x] <= K[x] / 2 ? mi[x] : mi[x] - K[x]) / d->box[x];
+          m2 += mx * mx;
+        }
+        const size_t t = ((size_t)a * K[1] + c) * K[2] + e;
+        gd[t] = m2 > 0.0 ? 4.0 * bmod[0][a] * bmod[1][c] * bmod[2][e] * std::exp(-pi * pi * m2 / (b * b)) / (pi * V * m2) : 0.0;
+        gf[t] = (float)gd[t];
+      }
+  if ((st = upload(s->owned, gd.data(), G, &D.pme_g_d)) != GRP_OK) return st;
+  return upload(s->owned, gf.data(), G, &D.pme_g_f);
+}
+
 extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **out) {
   if (!d || !out) return fail(GRP_EINVAL, "grp_create_system: null argument");
   *out = nullptr;
@@ -241,6 +323,9 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       D.coulomb_rf = 1;
       D.krf = (er == 0.0 ? 0.5 : (er - 1.0) / (2.0 * er + 1.0)) / (rc * rc * rc);
       D.crf = 1.0 / rc + D.krf * rc * rc;
+    } else if (d->coulomb_mode == GRP_COULOMB_PME) {
+      const grp_status ps = setup_pme(d, excl, s);
+      if (ps != GRP_OK) { grp_destroy_system(s); return ps; }
     } else if (d->coulomb_mode != GRP_COULOMB_EPS4R) {
       grp_destroy_system(s);
       return fail(GRP_EINVAL, "unknown coulomb_mode %d", d->coulomb_mode);
@@ -794,8 +879,8 @@ extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs
     if (!runs[i]) return fail(GRP_EINVAL, "grp_batch_create: run %d is null", i);
     if (runs[i]->sys->dev.potential != GRP_POT_FORCE_FIELD)
       return fail(GRP_ENOTIMPL, "grp_batch_create: batches hold force-field systems");
-    if (runs[i]->sys->dev.gb || runs[i]->sys->dev.n_cons)
-      return fail(GRP_ENOTIMPL, "grp_batch_create: systems in implicit solvent or with constraints run alone");
+    if (runs[i]->sys->dev.gb || runs[i]->sys->dev.n_cons || runs[i]->sys->dev.coulomb_rf == 2)
+      return fail(GRP_ENOTIMPL, "grp_batch_create: systems in implicit solvent, with constraints or periodic run alone");
     if (runs[i]->sys->dev.precision != runs[0]->sys->dev.precision)
       return fail(GRP_EINVAL, "grp_batch_create: runs must share one precision");
   }
@@ -1683,6 +1768,7 @@ extern "C" grp_status grp_energy_grad(grp_system *s, int32_t n_conf, const doubl
   if (!s || !d_q || n_conf < 0) return fail(GRP_EINVAL, "grp_energy_grad: bad argument");
   if (d_grad_theta && s->dev.potential != GRP_POT_FORCE_FIELD)
     return fail(GRP_EINVAL, "grp_energy_grad: no force-field parameters to differentiate");
+  if (s->dev.coulomb_rf == 2) return fail(GRP_ENOTIMPL, "grp_energy_grad: periodic systems are not differentiated");
   cudaStream_t st = (cudaStream_t)stream;
   const int nt = 2 * s->dev.n + s->n_terms;
   if (d_grad_theta && (size_t)nt * 8 > kMaxSmem)
@@ -1720,7 +1806,8 @@ extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_
     return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
   const grp_system *s = r->sys;
   const SysDev &D = s->dev;
-  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb || D.n_cons)
+  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb || D.n_cons ||
+      D.coulomb_rf == 2)
     return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms in vacuum");
   if (loss->obs < 0 || loss->obs >= D.n_obs) return fail(GRP_EINVAL, "grp_adjoint_segment: bad observable index");
   const int kind = D.obs_kind[loss->obs];

@@ -46,7 +46,8 @@ struct SysDev {
   const uint32_t *tile_pairs;  // I | J << 16
   const uint32_t *tile_masks;  // [n_tile_pairs][32]
   double cutoff2;          // 0: no cutoff
-  int coulomb_rf;          // 1: reaction field (eps_r = 1) instead of the dielectric eps = 4r
+  int coulomb_rf;          // Coulomb model: 0 dielectric eps = 4r, 1 reaction field (eps_r = 1),
+                           // 2 periodic: Ewald real space on pairs plus particle mesh Ewald
   int gb;                  // 1: Generalized Born (OBC II) implicit solvent
   int n_cons;              // bond constraints, in the description's order
   const int2 *con_ij;
@@ -65,6 +66,15 @@ struct SysDev {
   const double4 *gb_d;     // per atom (rho - 0.009, 1/rho, S (rho - 0.009), q)
   const float4 *gb_f;
   double krf, crf;         // reaction-field constants k_rf, c_rf (per nm^3, per nm)
+  // Periodic electrostatics by smooth particle mesh Ewald (coulomb_rf = 2, item-table systems)
+  double box[3], ibox[3];  // orthorhombic box edges (nm) and their inverses
+  double ewald_beta;       // splitting parameter (per nm)
+  int pme_K[3];            // grid points per axis (8 or 16)
+  double pme_e_const;      // self and neutralising-background energy
+  int n_excl_pairs;        // excluded pairs (i | j << 16): minus the smooth part of their Coulomb
+  const uint32_t *excl_pairs;
+  const double *pme_g_d;   // [K0][K1][K2] 4 B(m) exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2), 0 at m = 0
+  const float *pme_g_f;
   // Verlet lists (tiled systems with a cutoff): pairs closer than cutoff + skin, rebuilt when an atom
   // has moved more than skin/2 since the last build
   int use_list;

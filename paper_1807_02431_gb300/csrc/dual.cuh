@@ -81,6 +81,7 @@ struct Params<PathTangent> {
   const double4 *term;
   int rf;
   double krf, crf;
+  double box[3], ibox[3], beta;
 };
 
 }  // namespace grp

@@ -3,6 +3,8 @@
 #pragma once
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace grp {
 
 template <class T>
@@ -17,6 +19,8 @@ __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
 }
 __device__ __forceinline__ double gsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float gsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double gexp(double x) { return exp(x); }
+__device__ __forceinline__ float gexp(float x) { return expf(x); }
 __device__ __forceinline__ double gatan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float gatan2(float y, float x) { return atan2f(y, x); }
 // reciprocal and quotient: IEEE in FP64, the hardware approximations (about 1 ulp) in FP32
@@ -108,8 +112,9 @@ struct Params<PathF64> {
   const double4 *atom;  // (sigma/2, sqrt(eps), q sqrt(k_e/4), 1/m), may live in shared memory
   const double2 *bond, *angle;
   const double4 *term;
-  int rf;               // Coulomb by reaction field (k_rf, c_rf) instead of eps = 4r
+  int rf;               // Coulomb model: 0 eps = 4r, 1 reaction field (k_rf, c_rf), 2 Ewald real space
   double krf, crf;
+  double box[3], ibox[3], beta;  // periodic box edges, their inverses, Ewald splitting parameter
 };
 template <>
 struct Params<PathMixed> {
@@ -118,6 +123,7 @@ struct Params<PathMixed> {
   const float4 *term;
   int rf;
   float krf, crf;
+  float box[3], ibox[3], beta;
 };
 
 // Pair force factor -dE/dr / r and pair energy of Lennard-Jones (given eps_ij and (sigma_ij/r)^6) plus
@@ -125,20 +131,57 @@ struct Params<PathMixed> {
 // Reaction field (eps_r = 1, a continuum of dielectric eps_rf beyond the cutoff r_c, as the
 // non-periodic cutoff scheme of the paper's MD setups): E_C = 4 qq (1/r + k_rf r^2 - c_rf) with
 // k_rf = (eps_rf - 1) / ((2 eps_rf + 1) r_c^3), c_rf = 1/r_c + k_rf r_c^2 (zero at the cutoff), and
-// -dE_C/dr / r = 4 qq (1/r^3 - 2 k_rf).
-// kRF: 0 = eps = 4r, 1 = reaction field, -1 = as par.rf says (decided per pair; the segment kernel
-// fixes it per pass instead, keeping the branch out of its pair loops).
+// -dE_C/dr / r = 4 qq (1/r^3 - 2 k_rf).  Ewald real space (a periodic box, the rest of the lattice
+// sum on the particle mesh): E_C = 4 qq erfc(beta r) / r and
+// -dE_C/dr / r = 4 qq (erfc(beta r) / r + 2 beta / sqrt(pi) exp(-beta^2 r^2)) / r^2.
+// kRF: 0 = eps = 4r, 1 = reaction field, 2 = Ewald real space, -1 = as par.rf says (decided per pair;
+// the segment kernel fixes it per pass instead, keeping the branch out of its pair loops).
+constexpr double kTwoOverSqrtPi = 1.1283791670955126;  // 2 / sqrt(pi)
+__device__ __forceinline__ double gerfc(double x) { return erfc(x); }
+__device__ __forceinline__ float gerfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double gerf(double x) { return erf(x); }
+__device__ __forceinline__ float gerf(float x) { return erff(x); }
+__device__ __forceinline__ double gnearest(double x) { return rint(x); }
+__device__ __forceinline__ float gnearest(float x) { return rintf(x); }
+
 template <int kRF, class T, class Par>
 __device__ __forceinline__ T pair_g(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
-  const bool rf = kRF < 0 ? par.rf != 0 : kRF != 0;
-  if (!rf) return (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
-  return T(24) * eps * (T(2) * s6 * s6 - s6) * inv_r2 + T(4) * qq * (grsqrt(r2) * inv_r2 - T(2) * T(par.krf));
+  const int mode = kRF < 0 ? par.rf : kRF;
+  if (mode == 0) return (T(24) * eps * (T(2) * s6 * s6 - s6) + T(2) * qq * inv_r2) * inv_r2;
+  const T lj = T(24) * eps * (T(2) * s6 * s6 - s6) * inv_r2;
+  if constexpr (std::is_floating_point<T>::value) {  // the tangent path never sees a periodic system
+    if (mode == 2) {
+      const T b = T(par.beta), ir = grsqrt(r2);
+      return lj + T(4) * qq * (gerfc(b * r2 * ir) * ir + T(kTwoOverSqrtPi) * b * gexp(-b * b * r2)) * inv_r2;
+    }
+  }
+  return lj + T(4) * qq * (grsqrt(r2) * inv_r2 - T(2) * T(par.krf));
 }
 template <int kRF, class T, class Par>
 __device__ __forceinline__ T pair_e(const Par &par, T eps, T s6, T qq, T r2, T inv_r2) {
-  const bool rf = kRF < 0 ? par.rf != 0 : kRF != 0;
-  if (!rf) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  const int mode = kRF < 0 ? par.rf : kRF;
+  if (mode == 0) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
+  if constexpr (std::is_floating_point<T>::value) {
+    if (mode == 2) {
+      const T ir = grsqrt(r2);
+      return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * gerfc(T(par.beta) * r2 * ir) * ir;
+    }
+  }
   return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * (grsqrt(r2) + T(par.krf) * r2 - T(par.crf));
+}
+
+// The nearest periodic image of a pair difference (Ewald real space; a no-op otherwise).
+template <int kRF, class T, class Par>
+__device__ __forceinline__ V3<T> pair_image(const Par &par, V3<T> d) {
+  if constexpr (std::is_floating_point<T>::value) {
+    const int mode = kRF < 0 ? par.rf : kRF;
+    if (mode == 2) {
+      d.x -= T(par.box[0]) * gnearest(d.x * T(par.ibox[0]));
+      d.y -= T(par.box[1]) * gnearest(d.y * T(par.ibox[1]));
+      d.z -= T(par.box[2]) * gnearest(d.z * T(par.ibox[2]));
+    }
+  }
+  return d;
 }
 
 // Nonbonded parameters of an atom held in registers by the tile and row loops: sigma/2, sqrt(eps) and
@@ -167,7 +210,7 @@ __device__ __forceinline__ bool pair_eval(const Pos<P> &pos, const Params<P> &pa
                                           typename P::T cutoff2, V3<typename P::T> &fi, typename P::T &e,
                                           bool want_e) {
   using T = typename P::T;
-  const V3<T> d = pos.diff(i, j);
+  const V3<T> d = pair_image<kRF>(par, pos.diff(i, j));
   const T r2 = dot(d, d);
   if (cutoff2 > T(0) && r2 >= cutoff2) return false;
   const auto ai = par.atom[i], aj = par.atom[j];
@@ -532,5 +575,38 @@ __device__ __forceinline__ void force_pass(const SysDev &S, const Pos<P> &pos, c
     }
   }
 }
+
+// Scalar fixed-point accumulators of a path: [m] values (the FP64 path's 2^-40 int64, the mixed
+// path's split words).
+template <class P>
+struct ScalarAcc;
+template <>
+struct ScalarAcc<PathF64> {
+  long long *v;
+  static size_t bytes(int m) { return (size_t)m * 8; }
+  __device__ void carve(unsigned char *&ptr, int m) { v = (long long *)ptr; ptr += (size_t)m * 8; }
+  __device__ __forceinline__ void add(int i, double x, int *err) const { fix_add(&v[i], to_fix(x, err)); }
+  __device__ __forceinline__ double get(int i) const { return (double)v[i] * kFixInv; }
+  __device__ __forceinline__ void zero(int i) const { v[i] = 0; }
+  __device__ __forceinline__ void set(int i, double x, int *err) const { v[i] = to_fix(x, err); }
+};
+template <>
+struct ScalarAcc<PathMixed> {
+  int *hi;
+  unsigned int *lo;
+  static size_t bytes(int m) { return (size_t)m * 8; }
+  __device__ void carve(unsigned char *&ptr, int m) {
+    hi = (int *)ptr; ptr += (size_t)m * 4;
+    lo = (unsigned int *)ptr; ptr += (size_t)m * 4;
+  }
+  __device__ __forceinline__ void add(int i, float x, int *err) const { split_add(hi, lo, i, to_split(x, err)); }
+  __device__ __forceinline__ float get(int i) const { return split_to_float(hi[i], lo[i]); }
+  __device__ __forceinline__ void zero(int i) const { hi[i] = 0; lo[i] = 0u; }
+  __device__ __forceinline__ void set(int i, float x, int *err) const {
+    const Split s = to_split(x, err);
+    hi[i] = s.hi;
+    lo[i] = s.lo;
+  }
+};
 
 }  // namespace grp

@@ -16,47 +16,14 @@
 
 namespace grp {
 
-// Scalar fixed-point accumulators of a path: [m] values (the FP64 path's 2^-40 int64, the mixed
-// path's split words).
-template <class P>
-struct GbAcc;
-template <>
-struct GbAcc<PathF64> {
-  long long *v;
-  static size_t bytes(int m) { return (size_t)m * 8; }
-  __device__ void carve(unsigned char *&ptr, int m) { v = (long long *)ptr; ptr += (size_t)m * 8; }
-  __device__ __forceinline__ void add(int i, double x, int *err) const { fix_add(&v[i], to_fix(x, err)); }
-  __device__ __forceinline__ double get(int i) const { return (double)v[i] * kFixInv; }
-  __device__ __forceinline__ void zero(int i) const { v[i] = 0; }
-  __device__ __forceinline__ void set(int i, double x, int *err) const { v[i] = to_fix(x, err); }
-};
-template <>
-struct GbAcc<PathMixed> {
-  int *hi;
-  unsigned int *lo;
-  static size_t bytes(int m) { return (size_t)m * 8; }
-  __device__ void carve(unsigned char *&ptr, int m) {
-    hi = (int *)ptr; ptr += (size_t)m * 4;
-    lo = (unsigned int *)ptr; ptr += (size_t)m * 4;
-  }
-  __device__ __forceinline__ void add(int i, float x, int *err) const { split_add(hi, lo, i, to_split(x, err)); }
-  __device__ __forceinline__ float get(int i) const { return split_to_float(hi[i], lo[i]); }
-  __device__ __forceinline__ void zero(int i) const { hi[i] = 0; lo[i] = 0u; }
-  __device__ __forceinline__ void set(int i, float x, int *err) const {
-    const Split s = to_split(x, err);
-    hi[i] = s.hi;
-    lo[i] = s.lo;
-  }
-};
-
 // Shared-memory scratch of the solvent term: accumulators of I_i and dE/dB_i, Born radii and the
 // per-atom chain-rule weights.
 template <class P>
 struct GbScratch {
   using T = typename P::T;
-  GbAcc<P> acc;  // [0, n): sum_j h_ij;  [n, 2n): dE/dB_i
+  ScalarAcc<P> acc;  // [0, n): sum_j h_ij;  [n, 2n): dE/dB_i
   T *born, *w;   // [n]
-  static size_t bytes(int n) { return GbAcc<P>::bytes(2 * n) + (size_t)2 * n * sizeof(T) + 32; }
+  static size_t bytes(int n) { return ScalarAcc<P>::bytes(2 * n) + (size_t)2 * n * sizeof(T) + 32; }
   __device__ void carve(unsigned char *&ptr, int n) {
     acc.carve(ptr, 2 * n);
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
@@ -69,8 +36,6 @@ __device__ __forceinline__ double glog(double x) { return log(x); }
 __device__ __forceinline__ float glog(float x) { return logf(x); }
 __device__ __forceinline__ double gtanh(double x) { return tanh(x); }
 __device__ __forceinline__ float gtanh(float x) { return tanhf(x); }
-__device__ __forceinline__ double gexp(double x) { return exp(x); }
-__device__ __forceinline__ float gexp(float x) { return expf(x); }
 
 // h_ij and dh/dr for atom i (offset radius ai) descreened by a sphere of radius sj at distance r.
 template <class T>

@@ -1,0 +1,381 @@
+// Smooth particle mesh Ewald (Essmann et al. 1995; the particle mesh Ewald method is among the
+// optimisations the paper expects of an MD engine, Section 3.2) for one replica of an item-table system
+// (fewer than 64 atoms) in an orthorhombic periodic box.
+//
+// The pair loop evaluates the real-space part k_e q_i q_j erfc(beta r)/r over minimum images within
+// the cutoff.  This file adds the rest of the Ewald sum:
+//   * excluded pairs: -k_e q_i q_j erf(beta r)/r (minimum image), removing what the reciprocal sum
+//     gives the nearest image of a pair without Coulomb interaction;
+//   * the reciprocal sum on a K0 x K1 x K2 grid.  Each charge is spread by cubic cardinal B-splines
+//     (order 4) of its scaled fractional coordinates u_d = K_d frac(r_d / L_d): the weight of grid
+//     point (floor(u) - t) mod K is M_4(u - floor(u) + t), t = 0..3.  The grid Q is transformed, each
+//     coefficient multiplied by the influence function G(m) = B(m) exp(-pi^2 |m|^2/beta^2)/(pi V |m|^2)
+//     (B the Euler exponential spline factor, G(0) = 0) and transformed back, which gives the
+//     potential phi on the grid; E = 1/2 sum_k Q(k) phi(k), and F_i = -q_i sum_k grad W_i(k) phi(k);
+//   * the self and neutralising-background energies, constants of the system.
+// Charges enter scaled by sqrt(k_e / 4) (the atom table's third word), so the table holds 4 G.
+//
+// The grid is summed in fixed point (order-independent, like the force accumulators), then copied
+// into a complex array in shared memory whose rows along the third axis are padded by one element (so
+// that a warp's threads, each transforming one row, fall on different banks).  One thread transforms
+// one line of K = 8 or 16 points in registers (radix-2, decimation in time).  The third axis runs
+// last forward and first backward in one pass that applies G in between.
+#pragma once
+#include "forcefield.cuh"
+
+namespace grp {
+
+template <class P>
+struct PmeCplx;
+template <>
+struct PmeCplx<PathF64> {
+  using type = double2;
+};
+template <>
+struct PmeCplx<PathMixed> {
+  using type = float2;
+};
+
+// Shared-memory scratch of the mesh: the charge grid's fixed-point accumulators, the complex grid, and
+// per atom and axis the grid cell floor(u) and the offset u - floor(u) in it.
+template <class P>
+struct PmeScratch {
+  using T = typename P::T;
+  using C2 = typename PmeCplx<P>::type;
+  ScalarAcc<P> acc;  // [K0 K1 K2]
+  C2 *c;             // [K0][K1][K2 + 1]
+  int *cell;         // [3n]
+  T *frac;           // [3n]
+  static size_t bytes(const SysDev &S) {
+    const size_t g = (size_t)S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
+    const size_t gc = (size_t)S.pme_K[0] * S.pme_K[1] * (S.pme_K[2] + 1);
+    return ScalarAcc<P>::bytes((int)g) + 32 + gc * sizeof(C2) + (size_t)3 * S.n * (4 + sizeof(T)) + 32;
+  }
+  __device__ void carve(unsigned char *&ptr, const SysDev &S) {
+    const int g = S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
+    acc.carve(ptr, g);
+    ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
+    c = (C2 *)ptr;
+    ptr += (size_t)S.pme_K[0] * S.pme_K[1] * (S.pme_K[2] + 1) * sizeof(C2);
+    frac = (T *)ptr;
+    ptr += (size_t)3 * S.n * sizeof(T);
+    cell = (int *)ptr;
+    ptr += (size_t)3 * S.n * 4;
+    ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
+  }
+  __device__ void zero(const SysDev &S) const {
+    const int g = S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
+    for (int i = threadIdx.x; i < g; i += blockDim.x) acc.zero(i);
+  }
+};
+
+// Coordinate x of atom i in FP64 (the mixed path's double-single pair summed).
+template <class P>
+__device__ __forceinline__ double pme_coord(const Pos<P> &pos, int i, int x) {
+  if constexpr (P::kMixed) return (double)(&pos.qh[i].x)[x] + (double)(&pos.ql[i].x)[x];
+  else return pos.q[3 * i + x];
+}
+
+// Cubic B-spline weights m[t] = M_4(w + t) and derivatives d[t] = M_4'(w + t), t = 0..3, for an offset
+// w in [0, 1), built up from M_2 by the recursion M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) /
+// (n - 1), and M_4'(x) = M_3(x) - M_3(x - 1).
+template <class T>
+__device__ __forceinline__ void bspline4(T w, T (&m)[4], T (&d)[4]) {
+  m[0] = w;  // order 2: M_2(w), M_2(w + 1)
+  m[1] = T(1) - w;
+  m[2] = T(0.5) * (T(1) - w) * m[1];  // order 3, from the top index down
+  m[1] = T(0.5) * ((w + T(1)) * m[1] + (T(2) - w) * m[0]);
+  m[0] = T(0.5) * w * m[0];
+  d[0] = m[0];
+  d[1] = m[1] - m[0];
+  d[2] = m[2] - m[1];
+  d[3] = -m[2];
+  const T c = T(1) / T(3);  // order 4
+  m[3] = c * (T(1) - w) * m[2];
+  m[2] = c * ((w + T(2)) * m[2] + (T(2) - w) * m[1]);
+  m[1] = c * ((w + T(1)) * m[1] + (T(3) - w) * m[0]);
+  m[0] = c * w * m[0];
+}
+
+// m[t] for a run-time t in 0..3, by selects (an indexed local array would live in local memory)
+template <class T>
+__device__ __forceinline__ T pick4(const T (&m)[4], int t) {
+  return t == 0 ? m[0] : t == 1 ? m[1] : t == 2 ? m[2] : m[3];
+}
+
+// exp(2 pi i j / 16), j = 0..7: cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2.
+__host__ __device__ constexpr double tw16_re(int j) {
+  return j == 0 ? 1.0 : j == 1 ? 0.92387953251128674 : j == 2 ? 0.70710678118654752 : j == 3 ? 0.38268343236508977
+       : j == 4 ? 0.0 : j == 5 ? -0.38268343236508977 : j == 6 ? -0.70710678118654752 : -0.92387953251128674;
+}
+__host__ __device__ constexpr double tw16_im(int j) {
+  return j == 0 ? 0.0 : j == 1 ? 0.38268343236508977 : j == 2 ? 0.70710678118654752 : j == 3 ? 0.92387953251128674
+       : j == 4 ? 1.0 : j == 5 ? 0.92387953251128674 : j == 6 ? 0.70710678118654752 : 0.38268343236508977;
+}
+// the low `bits` (3 or 4) bits of i reversed
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  return bits == 4 ? ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)
+                   : ((i & 1) << 2) | (i & 2) | ((i & 4) >> 2);
+}
+template <int K>
+struct Log2;
+template <>
+struct Log2<8> {
+  static constexpr int value = 3;
+};
+template <>
+struct Log2<16> {
+  static constexpr int value = 4;
+};
+
+// In-register discrete Fourier transforms of K = 8 or 16 points, X(m) = sum_k x(k) exp(s 2 pi i m k / K),
+// unnormalised, radix 2.  The forward transform (s = +1) decimates in time: it takes its input in
+// bit-reversed order (x(bitrev(e)) in register e) and leaves X in natural order.  The backward one
+// (s = -1) decimates in frequency: natural order in, bit-reversed order out.  The callers load and
+// store at bit-reversed addresses, so no permutation happens in registers.
+template <class T>
+__device__ __forceinline__ void twiddle(T &re, T &im, int idx16, int sign) {
+  const T wr = T(tw16_re(idx16)), wi = T(sign * tw16_im(idx16));
+  const T r = re * wr - im * wi;
+  im = re * wi + im * wr;
+  re = r;
+}
+// One stage of butterflies of length kLen (decimation in time: twiddle, then sum and difference;
+// in frequency: sum and difference, then twiddle), unrolled at compile time.
+template <int K, int kLen, class T>
+__device__ __forceinline__ void dit_stage(T (&re)[K], T (&im)[K]) {
+  constexpr int kHalf = kLen / 2, kStep = 16 / kLen;
+#pragma unroll
+  for (int i = 0; i < K; i += kLen) {
+#pragma unroll
+    for (int j = 0; j < kHalf; ++j) {
+      const int a = i + j, b = a + kHalf;
+      T vr = re[b], vi = im[b];
+      if (j > 0) twiddle(vr, vi, j * kStep, 1);
+      re[b] = re[a] - vr;
+      im[b] = im[a] - vi;
+      re[a] += vr;
+      im[a] += vi;
+    }
+  }
+}
+template <int K, int kLen, class T>
+__device__ __forceinline__ void dif_stage(T (&re)[K], T (&im)[K]) {
+  constexpr int kHalf = kLen / 2, kStep = 16 / kLen;
+#pragma unroll
+  for (int i = 0; i < K; i += kLen) {
+#pragma unroll
+    for (int j = 0; j < kHalf; ++j) {
+      const int a = i + j, b = a + kHalf;
+      const T ur = re[a], ui = im[a];
+      re[a] = ur + re[b];
+      im[a] = ui + im[b];
+      T dr = ur - re[b], di = ui - im[b];
+      if (j > 0) twiddle(dr, di, j * kStep, -1);
+      re[b] = dr;
+      im[b] = di;
+    }
+  }
+}
+template <int K, class T>
+__device__ __forceinline__ void fft_fwd(T (&re)[K], T (&im)[K]) {
+  dit_stage<K, 2>(re, im);
+  dit_stage<K, 4>(re, im);
+  dit_stage<K, 8>(re, im);
+  if constexpr (K == 16) dit_stage<K, 16>(re, im);
+}
+template <int K, class T>
+__device__ __forceinline__ void fft_bwd(T (&re)[K], T (&im)[K]) {
+  if constexpr (K == 16) dif_stage<K, 16>(re, im);
+  dif_stage<K, 8>(re, im);
+  dif_stage<K, 4>(re, im);
+  dif_stage<K, 2>(re, im);
+}
+
+// Transform every line of the complex grid along axis kAxis (0 or 1): forward (kSign = 1) or backward.
+template <int K, int kAxis, int kSign, class C2, class T>
+__device__ __forceinline__ void fft_lines(C2 *c, int K0, int K1, int K2) {
+  constexpr int kBits = Log2<K>::value;
+  const int rz = K2 + 1;  // padded row length along the third axis
+  const int n_lines = (kAxis == 0 ? K1 : K0) * K2;
+  const int stride = kAxis == 0 ? K1 * rz : rz;
+  for (int l = threadIdx.x; l < n_lines; l += blockDim.x) {
+    const int a = l / K2, k2 = l - a * K2;
+    const int base = (kAxis == 0 ? a * rz : a * K1 * rz) + k2;
+    T re[K], im[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      const C2 v = c[base + (kSign > 0 ? bitrev(e, kBits) : e) * stride];
+      re[e] = v.x;
+      im[e] = v.y;
+    }
+    if (kSign > 0) fft_fwd<K>(re, im);
+    else fft_bwd<K>(re, im);
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      C2 v;
+      v.x = re[e];
+      v.y = im[e];
+      c[base + (kSign > 0 ? e : bitrev(e, kBits)) * stride] = v;
+    }
+  }
+}
+template <int kAxis, int kSign, class C2, class T>
+__device__ __forceinline__ void fft_axis(C2 *c, const int *K) {
+  if (K[kAxis] == 16) fft_lines<16, kAxis, kSign, C2, T>(c, K[0], K[1], K[2]);
+  else fft_lines<8, kAxis, kSign, C2, T>(c, K[0], K[1], K[2]);
+}
+
+// The third axis: forward transform, multiplication by the influence table (and its energy
+// 1/2 sum G |F|^2), backward transform.
+template <int K, class C2, class T>
+__device__ __forceinline__ T fft_third(C2 *c, const T *gtab, int K0, int K1, bool want_e) {
+  constexpr int kBits = Log2<K>::value;
+  const int rz = K + 1;
+  T e = T(0);
+  for (int l = threadIdx.x; l < K0 * K1; l += blockDim.x) {
+    const int base = l * rz;
+    T re[K], im[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      const C2 v = c[base + bitrev(m, kBits)];
+      re[m] = v.x;
+      im[m] = v.y;
+    }
+    fft_fwd<K>(re, im);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      const T g = __ldg(gtab + l * K + m);
+      if (want_e) e += T(0.5) * g * (re[m] * re[m] + im[m] * im[m]);
+      re[m] *= g;
+      im[m] *= g;
+    }
+    fft_bwd<K>(re, im);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      C2 v;
+      v.x = re[m];
+      v.y = im[m];
+      c[base + bitrev(m, kBits)] = v;
+    }
+  }
+  return e;
+}
+
+// The mesh part of the periodic electrostatics of one replica (everything but the real-space pairs),
+// added to the force accumulators, and its energy when want_e; called by every thread of the block
+// with the positions final.  The grid accumulators are zero on entry and left zero; returns after the
+// gather (the caller's barrier before reading the forces covers it).
+template <class P>
+__device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &par, const typename P::Acc &fa,
+                           const PmeScratch<P> &g, bool want_e, long long &e_fix, int *err) {
+  using T = typename P::T;
+  using C2 = typename PmeCplx<P>::type;
+  const int n = S.n, bd = blockDim.x;
+  const int K0 = S.pme_K[0], K1 = S.pme_K[1], K2 = S.pme_K[2];
+  // 1. grid cell and offset of every coordinate (FP64: unwrapped positions may lie many boxes out)
+  for (int i = threadIdx.x; i < 3 * n; i += bd) {
+    const int at = i / 3, x = i - 3 * at;
+    const double t = pme_coord<P>(pos, at, x) * S.ibox[x];
+    const double u = (t - floor(t)) * (double)S.pme_K[x];
+    const double fl = floor(u);
+    int k = (int)fl;
+    if (k >= S.pme_K[x]) k -= S.pme_K[x];
+    g.cell[i] = k;
+    g.frac[i] = (T)(u - fl);
+  }
+  // excluded pairs: E = -4 qq erf(b r)/r, -dE/dr / r = 4 qq (2 b/sqrt(pi) exp(-b^2 r^2) - erf(b r)/r) / r^2
+  const T b = T(par.beta);
+  for (int e = threadIdx.x; e < S.n_excl_pairs; e += bd) {
+    const uint32_t pk = S.excl_pairs[e];
+    const int i = (int)(pk & 0xFFFFu), j = (int)(pk >> 16);
+    const V3<T> d = pair_image<2>(par, pos.diff(i, j));
+    const T r2 = dot(d, d), ir = grsqrt(r2), qq = T(par.atom[i].z) * T(par.atom[j].z);
+    const T erfr = gerf(b * r2 * ir) * ir;
+    const T gr = T(4) * qq * (T(kTwoOverSqrtPi) * b * gexp(-b * b * r2) - erfr) * ir * ir;
+    fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
+    fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
+    if (want_e) e_fix += fa.efix(T(-4) * qq * erfr, err);
+  }
+  if (want_e && threadIdx.x == 0) e_fix += fa.efix((T)S.pme_e_const, err);
+  __syncthreads();
+  // 2. spread: one thread per (atom, t0, t1), four grid points along the third axis each
+  for (int it = threadIdx.x; it < 16 * n; it += bd) {
+    const int at = it >> 4, t0 = (it >> 2) & 3, t1 = it & 3;
+    T m0[4], m1[4], m2[4], dd[4];
+    bspline4(g.frac[3 * at], m0, dd);
+    bspline4(g.frac[3 * at + 1], m1, dd);
+    bspline4(g.frac[3 * at + 2], m2, dd);
+    int k0 = g.cell[3 * at] - t0, k1 = g.cell[3 * at + 1] - t1;
+    k0 += k0 < 0 ? K0 : 0;
+    k1 += k1 < 0 ? K1 : 0;
+    const T w = T(par.atom[at].z) * pick4(m0, t0) * pick4(m1, t1);
+    const int row = (k0 * K1 + k1) * K2, c2 = g.cell[3 * at + 2];
+#pragma unroll
+    for (int t2 = 0; t2 < 4; ++t2) {
+      const int k2 = c2 - t2 + (c2 - t2 < 0 ? K2 : 0);
+      g.acc.add(row + k2, w * m2[t2], err);
+    }
+  }
+  __syncthreads();
+  // 3. the charge grid into the complex array (accumulators back to zero)
+  for (int t = threadIdx.x; t < K0 * K1 * K2; t += bd) {
+    const int row = t / K2, k2 = t - row * K2;
+    C2 v;
+    v.x = g.acc.get(t);
+    v.y = T(0);
+    g.c[row * (K2 + 1) + k2] = v;
+    g.acc.zero(t);
+  }
+  __syncthreads();
+  // 4. transforms: axes 0 and 1 forward, axis 2 forward-G-backward, axes 1 and 0 backward
+  fft_axis<0, 1, C2, T>(g.c, S.pme_K);
+  __syncthreads();
+  fft_axis<1, 1, C2, T>(g.c, S.pme_K);
+  __syncthreads();
+  const T *gtab;
+  if constexpr (P::kMixed) gtab = S.pme_g_f;
+  else gtab = S.pme_g_d;
+  const T erec = K2 == 16 ? fft_third<16, C2, T>(g.c, gtab, K0, K1, want_e) : fft_third<8, C2, T>(g.c, gtab, K0, K1, want_e);
+  if (want_e) e_fix += fa.efix(erec, err);
+  __syncthreads();
+  fft_axis<1, -1, C2, T>(g.c, S.pme_K);
+  __syncthreads();
+  fft_axis<0, -1, C2, T>(g.c, S.pme_K);
+  __syncthreads();
+  // 5. gather: one thread per (atom, t0); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d
+  for (int it = threadIdx.x; it < 4 * n; it += bd) {
+    const int at = it >> 2, t0 = it & 3;
+    T m0[4], m1[4], m2[4], d0[4], d1[4], d2[4];
+    bspline4(g.frac[3 * at], m0, d0);
+    bspline4(g.frac[3 * at + 1], m1, d1);
+    bspline4(g.frac[3 * at + 2], m2, d2);
+    int k0 = g.cell[3 * at] - t0;
+    k0 += k0 < 0 ? K0 : 0;
+    const int c1 = g.cell[3 * at + 1], c2 = g.cell[3 * at + 2];
+    T sx = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+    for (int t1 = 0; t1 < 4; ++t1) {
+      const int k1 = c1 - t1 + (c1 - t1 < 0 ? K1 : 0);
+      const int row = (k0 * K1 + k1) * (K2 + 1);
+      T px = T(0), pz = T(0);  // sum over t2 of phi m2 and phi d2
+#pragma unroll
+      for (int t2 = 0; t2 < 4; ++t2) {
+        const int k2 = c2 - t2 + (c2 - t2 < 0 ? K2 : 0);
+        const T ph = g.c[row + k2].x;
+        px += ph * m2[t2];
+        pz += ph * d2[t2];
+      }
+      sx += m1[t1] * px;
+      sy += d1[t1] * px;
+      sz += m1[t1] * pz;
+    }
+    const T qi = T(par.atom[at].z);
+    const T w0 = pick4(m0, t0), dw0 = pick4(d0, t0);
+    const V3<T> f{-qi * dw0 * sx * T(K0 * par.ibox[0]), -qi * w0 * sy * T(K1 * par.ibox[1]),
+                  -qi * w0 * sz * T(K2 * par.ibox[2])};
+    fa.add(at, f, err);
+  }
+}
+
+}  // namespace grp

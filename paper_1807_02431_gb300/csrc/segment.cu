@@ -9,6 +9,7 @@
 #include "forcefield.cuh"
 #include "constraints.cuh"
 #include "gb.cuh"
+#include "pme.cuh"
 #include "kernels.h"
 #include "state.cuh"
 
@@ -321,8 +322,8 @@ enum : int {
 };
 
 // kFF: the nonbonded model compiled into the step loop, 0 = Coulomb with eps = 4r, 1 = reaction field,
-// 2 = eps = 4r plus Generalized Born solvent, 3 = eps = 4r with bond constraints (2 and 3 on the item
-// table only), -1 = eps = 4r or reaction field
+// 2 = eps = 4r plus Generalized Born solvent, 3 = eps = 4r with bond constraints, 4 = periodic box with
+// particle mesh Ewald (2, 3 and 4 on the item table only), -1 = eps = 4r or reaction field
 // decided per launch (the batched kernel, whose runs may differ; implicit solvent is not batched).
 // The single-run kernels are compiled for one model, which keeps one copy of the force passes and no
 // unused solvent code in the step loop.
@@ -347,12 +348,19 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
   constexpr bool kGB = kMode == kModeItems && kFF == 2;
   constexpr bool kCon = kMode == kModeItems && kFF == 3;
-  constexpr int kRF = kFF >= 2 ? 0 : kFF;
+  constexpr bool kPME = kMode == kModeItems && kFF == 4;
+  constexpr int kRF = kFF == 4 ? 2 : (kFF >= 2 ? 0 : kFF);
   GbScratch<P> gbs;  // implicit solvent (item-table systems only)
   if constexpr (kGB) {
     ptr = align32(ptr);
     gbs.carve(ptr, n);
     for (int i = threadIdx.x; i < 2 * n; i += kThreads) gbs.acc.zero(i);
+  }
+  PmeScratch<P> pms;  // particle mesh (item-table systems only)
+  if constexpr (kPME) {
+    ptr = align32(ptr);
+    pms.carve(ptr, S);
+    pms.zero(S);
   }
 
   const uint32_t *pairs = S.pairs, *items = S.items;
@@ -438,6 +446,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if (sample) until = a.t_gr;
     long long e_fix = 0;
     if constexpr (kGB) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
+    if constexpr (kPME) pme_forces<P>(S, pos, par, fa, pms, sample, e_fix, &err);
     auto passes = [&](auto rf) {
       constexpr int R = decltype(rf)::value;
       if (lean) bonded_pass<P>(S, pos, par, fa, sample, e_fix, &err);
@@ -598,6 +607,8 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch,
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
   if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
   if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(n) : GbScratch<PathMixed>::bytes(n));
+  if (S.coulomb_rf == 2)
+    b += 32 + (S.precision == GRP_FP64 ? PmeScratch<PathF64>::bytes(S) : PmeScratch<PathMixed>::bytes(S));
   return b;
 }
 
@@ -617,6 +628,9 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
     if (S.tiled && 32 * S.n_tile_pairs > t) t = 32 * S.n_tile_pairs;
   }
   t = t < 64 ? 64 : (t > 512 ? 512 : ((t + 31) / 32) * 32);
+  // the mixed path's particle mesh: 320 threads, two replicas per SM (its 256 lines per transform pass
+  // take one round of the block; the FP64 transforms need the registers of the 512-thread variant)
+  if (S.coulomb_rf == 2 && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320) t = 320;
   c.threads = t;
   // noise for up to 16 steps at a time, within 32 KB
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
@@ -642,9 +656,10 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
   const bool small = c.threads <= 320;
   // tiles are taken only without a cutoff, so never with the reaction field; implicit solvent only on
   // the item table (and never with a cutoff)
-  const bool rf = a.S.coulomb_rf != 0, gb = a.S.gb != 0, con = a.S.n_cons > 0;
+  const bool rf = a.S.coulomb_rf == 1, gb = a.S.gb != 0, con = a.S.n_cons > 0, pme = a.S.coulomb_rf == 2;
   auto kern = mode == kModeItems
-                  ? (con  ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 3> : ff_segment_kernel<P, 512, 1, kModeItems, 3>)
+                  ? (pme  ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 4> : ff_segment_kernel<P, 512, 1, kModeItems, 4>)
+                     : con ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 3> : ff_segment_kernel<P, 512, 1, kModeItems, 3>)
                      : gb ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 2> : ff_segment_kernel<P, 512, 1, kModeItems, 2>)
                      : rf ? (small ? ff_segment_kernel<P, 320, 2, kModeItems, 1> : ff_segment_kernel<P, 512, 1, kModeItems, 1>)
                           : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
@@ -710,6 +725,12 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
     gbs.carve(ptr, n);
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) gbs.acc.zero(i);
   }
+  PmeScratch<P> pms;
+  if (S.coulomb_rf == 2) {
+    ptr = align32(ptr);
+    pms.carve(ptr, S);
+    pms.zero(S);
+  }
   // positions only: momenta and forces are not used
   for (int at = threadIdx.x; at < n; at += blockDim.x) {
     if constexpr (P::kMixed) {
@@ -730,6 +751,7 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   long long e_fix = 0;
   const typename P::Acc fa = State<P>::acc(F, n);
   if (S.gb) gb_forces<P>(S, st.pos(), fa, gbs, energy != nullptr, e_fix, &err);
+  if (S.coulomb_rf == 2) pme_forces<P>(S, st.pos(), st.params(S), fa, pms, energy != nullptr, e_fix, &err);
   force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, energy != nullptr, e_fix, &err);
   if (S.tiled) tile_pass<P>(S, st.pos(), st.params(S), fa, nullptr, energy != nullptr, e_fix, &err);
   __syncthreads();
@@ -768,6 +790,8 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
     size_t b = (size_t)3 * S.n * 8 + 32 * 8 + 32 +
                (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n, lean) : State<PathMixed>::bytes(S.n, lean));
     if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(S.n) : GbScratch<PathMixed>::bytes(S.n));
+    if (S.coulomb_rf == 2)
+      b += 32 + (S.precision == GRP_FP64 ? PmeScratch<PathF64>::bytes(S) : PmeScratch<PathMixed>::bytes(S));
     return b;
   };
   const int lean = bytes(false) > kMaxSmem ? 1 : 0;

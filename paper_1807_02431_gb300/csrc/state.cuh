@@ -68,7 +68,8 @@ struct State<PathF64> {
   }
   __device__ Pos<PathF64> pos() const { return Pos<PathF64>{q}; }
   __device__ Params<PathF64> params(const SysDev &S) const {
-    return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d, S.coulomb_rf, S.krf, S.crf};
+    return Params<PathF64>{atom, S.bond_d, S.angle_d, S.term_d, S.coulomb_rf, S.krf, S.crf,
+                           {S.box[0], S.box[1], S.box[2]}, {S.ibox[0], S.ibox[1], S.ibox[2]}, S.ewald_beta};
   }
   // B, A, O, A of BAOAB for one coordinate i = 3 atom + axis, and the final B with the new force,
   // written with explicitly rounded operations so that no kernel leaves contraction choices to the
@@ -168,7 +169,9 @@ struct State<PathMixed> {
   }
   __device__ Pos<PathMixed> pos() const { return Pos<PathMixed>{qh, ql}; }
   __device__ Params<PathMixed> params(const SysDev &S) const {
-    return Params<PathMixed>{atom, S.bond_f, S.angle_f, S.term_f, S.coulomb_rf, (float)S.krf, (float)S.crf};
+    return Params<PathMixed>{atom, S.bond_f, S.angle_f, S.term_f, S.coulomb_rf, (float)S.krf, (float)S.crf,
+                             {(float)S.box[0], (float)S.box[1], (float)S.box[2]},
+                             {(float)S.ibox[0], (float)S.ibox[1], (float)S.ibox[2]}, (float)S.ewald_beta};
   }
   __device__ __forceinline__ void baoa(int at, const float *xi, float h, float c1) {
     const float im = atom[at].w, s = sd[at], hm = h * im;
