@@ -55,6 +55,26 @@ def algorithmic_flops_per_replica_step(s: W.System) -> float:
     return 40.0 * n_pairs + 15.0 * len(s.bonds) + 40.0 * len(s.angles) + 33.3 * len(s.dihedral_k)
 
 
+def pme_flops_per_replica_step(s: W.System) -> float:
+    """FP32 flops per replica-step of the periodic force kernel (particle mesh Ewald): 46 per
+    non-excluded pair within the cutoff over minimum images in the initial configuration (the pair
+    count of `algorithmic_flops_per_replica_step` plus 6 for the image; erfc and exp counted as one
+    each), 20 per excluded pair, the bonded terms as there; on the mesh of G points with K_d per axis,
+    six transform passes of 5 K log2 K per line (10 G sum_d log2 K_d), 2 G for the influence function,
+    188 per atom for spreading (3 B-spline evaluations of 20 and 64 multiply-adds) and 512 per atom for
+    the gather (64 points x 8)."""
+    n, box = s.n_atoms, np.asarray(s.box)
+    d = s.q0[:, None] - s.q0[None]
+    d -= box * np.round(d / box)
+    within = np.triu(np.linalg.norm(d, axis=-1) < s.cutoff, 1)
+    within[s.excl[:, 0], s.excl[:, 1]] = False
+    within[s.excl[:, 1], s.excl[:, 0]] = False
+    G = int(np.prod(s.pme_grid))
+    mesh = 10.0 * G * sum(np.log2(k) for k in s.pme_grid) + 2.0 * G + n * (188.0 + 512.0)
+    bonded = 15.0 * len(s.bonds) + 40.0 * len(s.angles) + 33.3 * len(s.dihedral_k)
+    return 46.0 * int(within.sum()) + 20.0 * len(s.excl) + bonded + mesh
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     """152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -626,10 +646,16 @@ def main():
             sp = W.chain_ions(n_replicas=R)
             step_p = Step(B, sp, B.GRP_MIXED, R, seed, local)
             tp = time_steps(step_p, args.fp64_steps, 1, flush, step_p.stream)
+            pk_ms = segment_kernel_ms(B, step_p, 3)
+            pflops = pme_flops_per_replica_step(sp) * R * sp.t_check
+            pach = pflops / (pk_ms * 1e-3) / 1e12
             periodic = {"workload": f"{sp.name}_r{R} ({sp.n_atoms} atoms, box {sp.box[0]} nm, grid "
                                     f"{'x'.join(str(k) for k in sp.pme_grid)}, order {sp.pme_order}, cutoff {sp.cutoff} nm)",
                         "value": R * sp.n_atoms * sp.t_check * len(tp) / (float(np.sum(tp)) / 1e3),
-                        "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tp))}
+                        "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tp)),
+                        "roofline": {"bound": "alu", "achieved": pach, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": pach / peak, "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems, 4>",
+                                     "kernel_ms": pk_ms, "flops_per_launch": pflops}}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)

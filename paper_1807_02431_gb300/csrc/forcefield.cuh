@@ -137,8 +137,18 @@ struct Params<PathMixed> {
 // kRF: 0 = eps = 4r, 1 = reaction field, 2 = Ewald real space, -1 = as par.rf says (decided per pair;
 // the segment kernel fixes it per pass instead, keeping the branch out of its pair loops).
 constexpr double kTwoOverSqrtPi = 1.1283791670955126;  // 2 / sqrt(pi)
-__device__ __forceinline__ double gerfc(double x) { return erfc(x); }
-__device__ __forceinline__ float gerfc(float x) { return erfcf(x); }
+// erfc(x) for x >= 0 given e = exp(-x^2): the library function in FP64; in FP32 the rational
+// approximation of Abramowitz and Stegun (Handbook of Mathematical Functions, 1964, formula 7.1.26),
+// erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x), absolute error below
+// 1.5e-7 (the FP32 rounding of the pair terms is ~6e-8 relative), which reuses the exponential the
+// force needs anyway.
+__device__ __forceinline__ double gerfc_e(double x, double) { return erfc(x); }
+__device__ __forceinline__ float gerfc_e(float x, float e) {
+  const float t = grcp(fmaf(0.3275911f, x, 1.0f));
+  const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                              0.254829592f);
+  return poly * e;
+}
 __device__ __forceinline__ double gerf(double x) { return erf(x); }
 __device__ __forceinline__ float gerf(float x) { return erff(x); }
 __device__ __forceinline__ double gnearest(double x) { return rint(x); }
@@ -151,8 +161,8 @@ __device__ __forceinline__ T pair_g(const Par &par, T eps, T s6, T qq, T r2, T i
   const T lj = T(24) * eps * (T(2) * s6 * s6 - s6) * inv_r2;
   if constexpr (std::is_floating_point<T>::value) {  // the tangent path never sees a periodic system
     if (mode == 2) {
-      const T b = T(par.beta), ir = grsqrt(r2);
-      return lj + T(4) * qq * (gerfc(b * r2 * ir) * ir + T(kTwoOverSqrtPi) * b * gexp(-b * b * r2)) * inv_r2;
+      const T b = T(par.beta), ir = grsqrt(r2), e = gexp(-b * b * r2);
+      return lj + T(4) * qq * (gerfc_e(b * r2 * ir, e) * ir + T(kTwoOverSqrtPi) * b * e) * inv_r2;
     }
   }
   return lj + T(4) * qq * (grsqrt(r2) * inv_r2 - T(2) * T(par.krf));
@@ -163,8 +173,8 @@ __device__ __forceinline__ T pair_e(const Par &par, T eps, T s6, T qq, T r2, T i
   if (mode == 0) return T(4) * eps * (s6 * s6 - s6) + qq * inv_r2;
   if constexpr (std::is_floating_point<T>::value) {
     if (mode == 2) {
-      const T ir = grsqrt(r2);
-      return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * gerfc(T(par.beta) * r2 * ir) * ir;
+      const T b = T(par.beta), ir = grsqrt(r2);
+      return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * gerfc_e(b * r2 * ir, gexp(-b * b * r2)) * ir;
     }
   }
   return T(4) * eps * (s6 * s6 - s6) + T(4) * qq * (grsqrt(r2) + T(par.krf) * r2 - T(par.crf));

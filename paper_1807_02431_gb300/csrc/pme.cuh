@@ -15,9 +15,9 @@
 //   * the self and neutralising-background energies, constants of the system.
 // Charges enter scaled by sqrt(k_e / 4) (the atom table's third word), so the table holds 4 G.
 //
-// The grid is summed in fixed point (order-independent, like the force accumulators), then copied
-// into a complex array in shared memory whose rows along the third axis are padded by one element (so
-// that a warp's threads, each transforming one row, fall on different banks).  One thread transforms
+// The grid is summed in fixed point (order-independent, like the force accumulators); the first
+// transform pass reads it into a complex array in shared memory whose rows along the third axis are
+// padded by one element (so that a warp's threads, each transforming one row, fall on different banks).  One thread transforms
 // one line of K = 8 or 16 points in registers (radix-2, decimation in time).  The third axis runs
 // last forward and first backward in one pass that applies G in between.
 #pragma once
@@ -37,19 +37,19 @@ struct PmeCplx<PathMixed> {
 };
 
 // Shared-memory scratch of the mesh: the charge grid's fixed-point accumulators, the complex grid, and
-// per atom and axis the grid cell floor(u) and the offset u - floor(u) in it.
+// per atom and axis the grid cell floor(u) and the B-spline weights and derivatives at u.
 template <class P>
 struct PmeScratch {
   using T = typename P::T;
   using C2 = typename PmeCplx<P>::type;
   ScalarAcc<P> acc;  // [K0 K1 K2]
   C2 *c;             // [K0][K1][K2 + 1]
+  T *wm, *wd;        // [3n][4]: M_4(w + t), M_4'(w + t)
   int *cell;         // [3n]
-  T *frac;           // [3n]
   static size_t bytes(const SysDev &S) {
     const size_t g = (size_t)S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
     const size_t gc = (size_t)S.pme_K[0] * S.pme_K[1] * (S.pme_K[2] + 1);
-    return ScalarAcc<P>::bytes((int)g) + 32 + gc * sizeof(C2) + (size_t)3 * S.n * (4 + sizeof(T)) + 32;
+    return ScalarAcc<P>::bytes((int)g) + 32 + gc * sizeof(C2) + (size_t)3 * S.n * (4 + 8 * sizeof(T)) + 32;
   }
   __device__ void carve(unsigned char *&ptr, const SysDev &S) {
     const int g = S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
@@ -57,8 +57,10 @@ struct PmeScratch {
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
     c = (C2 *)ptr;
     ptr += (size_t)S.pme_K[0] * S.pme_K[1] * (S.pme_K[2] + 1) * sizeof(C2);
-    frac = (T *)ptr;
-    ptr += (size_t)3 * S.n * sizeof(T);
+    wm = (T *)ptr;
+    ptr += (size_t)12 * S.n * sizeof(T);
+    wd = (T *)ptr;
+    ptr += (size_t)12 * S.n * sizeof(T);
     cell = (int *)ptr;
     ptr += (size_t)3 * S.n * 4;
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
@@ -97,12 +99,6 @@ __device__ __forceinline__ void bspline4(T w, T (&m)[4], T (&d)[4]) {
   m[0] = c * w * m[0];
 }
 
-// m[t] for a run-time t in 0..3, by selects (an indexed local array would live in local memory)
-template <class T>
-__device__ __forceinline__ T pick4(const T (&m)[4], int t) {
-  return t == 0 ? m[0] : t == 1 ? m[1] : t == 2 ? m[2] : m[3];
-}
-
 // exp(2 pi i j / 16), j = 0..7: cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2.
 __host__ __device__ constexpr double tw16_re(int j) {
   return j == 0 ? 1.0 : j == 1 ? 0.92387953251128674 : j == 2 ? 0.70710678118654752 : j == 3 ? 0.38268343236508977
@@ -135,6 +131,12 @@ struct Log2<16> {
 // store at bit-reversed addresses, so no permutation happens in registers.
 template <class T>
 __device__ __forceinline__ void twiddle(T &re, T &im, int idx16, int sign) {
+  if (idx16 == 4) {  // exp(+-i pi/2) = +-i: a swap and a sign, exact
+    const T r = re;
+    re = sign > 0 ? -im : im;
+    im = sign > 0 ? r : -r;
+    return;
+  }
   const T wr = T(tw16_re(idx16)), wi = T(sign * tw16_im(idx16));
   const T r = re * wr - im * wi;
   im = re * wi + im * wr;
@@ -220,6 +222,32 @@ __device__ __forceinline__ void fft_lines(C2 *c, int K0, int K1, int K2) {
     }
   }
 }
+// The first pass: lines along axis 0 read from the fixed-point charge grid (which they zero), forward.
+template <int K, class P, class C2, class T>
+__device__ __forceinline__ void fft_first(const ScalarAcc<P> &acc, C2 *c, int K1, int K2) {
+  constexpr int kBits = Log2<K>::value;
+  const int rz = K2 + 1;
+  for (int l = threadIdx.x; l < K1 * K2; l += blockDim.x) {
+    const int k1 = l / K2, k2 = l - k1 * K2;
+    T re[K], im[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      const int g = (bitrev(e, kBits) * K1 + k1) * K2 + k2;
+      re[e] = acc.get(g);
+      im[e] = T(0);
+      acc.zero(g);
+    }
+    fft_fwd<K>(re, im);
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      C2 v;
+      v.x = re[e];
+      v.y = im[e];
+      c[(e * K1 + k1) * rz + k2] = v;
+    }
+  }
+}
+
 template <int kAxis, int kSign, class C2, class T>
 __device__ __forceinline__ void fft_axis(C2 *c, const int *K) {
   if (K[kAxis] == 16) fft_lines<16, kAxis, kSign, C2, T>(c, K[0], K[1], K[2]);
@@ -273,7 +301,8 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   using C2 = typename PmeCplx<P>::type;
   const int n = S.n, bd = blockDim.x;
   const int K0 = S.pme_K[0], K1 = S.pme_K[1], K2 = S.pme_K[2];
-  // 1. grid cell and offset of every coordinate (FP64: unwrapped positions may lie many boxes out)
+  // 1. grid cell and B-spline weights of every coordinate (u in FP64: unwrapped positions may lie many
+  // boxes out)
   for (int i = threadIdx.x; i < 3 * n; i += bd) {
     const int at = i / 3, x = i - 3 * at;
     const double t = pme_coord<P>(pos, at, x) * S.ibox[x];
@@ -282,7 +311,13 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
     int k = (int)fl;
     if (k >= S.pme_K[x]) k -= S.pme_K[x];
     g.cell[i] = k;
-    g.frac[i] = (T)(u - fl);
+    T m[4], d[4];
+    bspline4((T)(u - fl), m, d);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      g.wm[4 * i + t] = m[t];
+      g.wd[4 * i + t] = d[t];
+    }
   }
   // excluded pairs: E = -4 qq erf(b r)/r, -dE/dr / r = 4 qq (2 b/sqrt(pi) exp(-b^2 r^2) - erf(b r)/r) / r^2
   const T b = T(par.beta);
@@ -302,14 +337,11 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   // 2. spread: one thread per (atom, t0, t1), four grid points along the third axis each
   for (int it = threadIdx.x; it < 16 * n; it += bd) {
     const int at = it >> 4, t0 = (it >> 2) & 3, t1 = it & 3;
-    T m0[4], m1[4], m2[4], dd[4];
-    bspline4(g.frac[3 * at], m0, dd);
-    bspline4(g.frac[3 * at + 1], m1, dd);
-    bspline4(g.frac[3 * at + 2], m2, dd);
     int k0 = g.cell[3 * at] - t0, k1 = g.cell[3 * at + 1] - t1;
     k0 += k0 < 0 ? K0 : 0;
     k1 += k1 < 0 ? K1 : 0;
-    const T w = T(par.atom[at].z) * pick4(m0, t0) * pick4(m1, t1);
+    const T w = T(par.atom[at].z) * g.wm[12 * at + t0] * g.wm[12 * at + 4 + t1];
+    const T *m2 = g.wm + 12 * at + 8;
     const int row = (k0 * K1 + k1) * K2, c2 = g.cell[3 * at + 2];
 #pragma unroll
     for (int t2 = 0; t2 < 4; ++t2) {
@@ -318,18 +350,10 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
     }
   }
   __syncthreads();
-  // 3. the charge grid into the complex array (accumulators back to zero)
-  for (int t = threadIdx.x; t < K0 * K1 * K2; t += bd) {
-    const int row = t / K2, k2 = t - row * K2;
-    C2 v;
-    v.x = g.acc.get(t);
-    v.y = T(0);
-    g.c[row * (K2 + 1) + k2] = v;
-    g.acc.zero(t);
-  }
-  __syncthreads();
-  // 4. transforms: axes 0 and 1 forward, axis 2 forward-G-backward, axes 1 and 0 backward
-  fft_axis<0, 1, C2, T>(g.c, S.pme_K);
+  // 3. transforms: axis 0 forward from the fixed-point grid (left zero), axis 1 forward, axis 2
+  // forward-G-backward, axes 1 and 0 backward
+  if (K0 == 16) fft_first<16, P, C2, T>(g.acc, g.c, K1, K2);
+  else fft_first<8, P, C2, T>(g.acc, g.c, K1, K2);
   __syncthreads();
   fft_axis<1, 1, C2, T>(g.c, S.pme_K);
   __syncthreads();
@@ -343,13 +367,10 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   __syncthreads();
   fft_axis<0, -1, C2, T>(g.c, S.pme_K);
   __syncthreads();
-  // 5. gather: one thread per (atom, t0); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d
+  // 4. gather: one thread per (atom, t0); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d
   for (int it = threadIdx.x; it < 4 * n; it += bd) {
     const int at = it >> 2, t0 = it & 3;
-    T m0[4], m1[4], m2[4], d0[4], d1[4], d2[4];
-    bspline4(g.frac[3 * at], m0, d0);
-    bspline4(g.frac[3 * at + 1], m1, d1);
-    bspline4(g.frac[3 * at + 2], m2, d2);
+    const T *m1 = g.wm + 12 * at + 4, *m2 = g.wm + 12 * at + 8, *d1 = g.wd + 12 * at + 4, *d2 = g.wd + 12 * at + 8;
     int k0 = g.cell[3 * at] - t0;
     k0 += k0 < 0 ? K0 : 0;
     const int c1 = g.cell[3 * at + 1], c2 = g.cell[3 * at + 2];
@@ -371,7 +392,7 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
       sz += m1[t1] * pz;
     }
     const T qi = T(par.atom[at].z);
-    const T w0 = pick4(m0, t0), dw0 = pick4(d0, t0);
+    const T w0 = g.wm[12 * at + t0], dw0 = g.wd[12 * at + t0];
     const V3<T> f{-qi * dw0 * sx * T(K0 * par.ibox[0]), -qi * w0 * sy * T(K1 * par.ibox[1]),
                   -qi * w0 * sz * T(K2 * par.ibox[2])};
     fa.add(at, f, err);
