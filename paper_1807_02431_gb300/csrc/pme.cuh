@@ -194,7 +194,8 @@ __device__ __forceinline__ void fft_bwd(T (&re)[K], T (&im)[K]) {
   dif_stage<K, 2>(re, im);
 }
 
-// Transform every line of the complex grid along axis kAxis (0 or 1): forward (kSign = 1) or backward.
+// Transform every line of the complex grid along axis kAxis (0 or 1) in the first K0 planes of axis 0:
+// forward (kSign = 1) or backward.
 template <int K, int kAxis, int kSign, class C2, class T>
 __device__ __forceinline__ void fft_lines(C2 *c, int K0, int K1, int K2) {
   constexpr int kBits = Log2<K>::value;
@@ -222,47 +223,99 @@ __device__ __forceinline__ void fft_lines(C2 *c, int K0, int K1, int K2) {
     }
   }
 }
-// The first pass: lines along axis 0 read from the fixed-point charge grid (which they zero), forward.
+// The first pass, real to complex: the lines (k1, k2) and (k1, k2 + K2/2) along axis 0 of the real
+// fixed-point charge grid (which they zero) are transformed together as z = a + i b; the spectra of the
+// real lines follow from Z(m) and Z(K - m): A(m) = (Z(m) + conj Z(K-m)) / 2, B(m) = (Z(m) - conj Z(K-m)) / 2i.
+// Only m = 0..K/2 is kept (A(K - m) = conj A(m)): planes 0..K0/2 of the complex grid.
 template <int K, class P, class C2, class T>
-__device__ __forceinline__ void fft_first(const ScalarAcc<P> &acc, C2 *c, int K1, int K2) {
+__device__ __forceinline__ void fft_first_r2c(const ScalarAcc<P> &acc, C2 *c, int K1, int K2) {
   constexpr int kBits = Log2<K>::value;
-  const int rz = K2 + 1;
-  for (int l = threadIdx.x; l < K1 * K2; l += blockDim.x) {
-    const int k1 = l / K2, k2 = l - k1 * K2;
+  const int rz = K2 + 1, h2 = K2 >> 1;
+  for (int l = threadIdx.x; l < K1 * h2; l += blockDim.x) {
+    const int k1 = l / h2, k2 = l - k1 * h2;
     T re[K], im[K];
 #pragma unroll
     for (int e = 0; e < K; ++e) {
       const int g = (bitrev(e, kBits) * K1 + k1) * K2 + k2;
       re[e] = acc.get(g);
-      im[e] = T(0);
+      im[e] = acc.get(g + h2);
       acc.zero(g);
+      acc.zero(g + h2);
     }
     fft_fwd<K>(re, im);
 #pragma unroll
-    for (int e = 0; e < K; ++e) {
-      C2 v;
-      v.x = re[e];
-      v.y = im[e];
-      c[(e * K1 + k1) * rz + k2] = v;
+    for (int m = 0; m <= K / 2; ++m) {
+      const int mk = (K - m) & (K - 1);
+      const T xr = re[m], xi = im[m], yr = re[mk], yi = im[mk];
+      C2 a, b;
+      a.x = T(0.5) * (xr + yr);
+      a.y = T(0.5) * (xi - yi);
+      b.x = T(0.5) * (xi + yi);
+      b.y = T(0.5) * (yr - xr);
+      c[(m * K1 + k1) * rz + k2] = a;
+      c[(m * K1 + k1) * rz + k2 + h2] = b;
     }
   }
 }
 
-template <int kAxis, int kSign, class C2, class T>
-__device__ __forceinline__ void fft_axis(C2 *c, const int *K) {
-  if (K[kAxis] == 16) fft_lines<16, kAxis, kSign, C2, T>(c, K[0], K[1], K[2]);
-  else fft_lines<8, kAxis, kSign, C2, T>(c, K[0], K[1], K[2]);
+// The last pass, complex to real: the half spectra A, B (planes 0..K0/2) of the lines (k1, k2) and
+// (k1, k2 + K2/2) are extended by A(K - m) = conj A(m) and transformed back together as A + i B, whose
+// real and imaginary parts are the two real lines; they are stored in the real parts of the grid.
+template <int K, class C2, class T>
+__device__ __forceinline__ void fft_last_c2r(C2 *c, int K1, int K2) {
+  constexpr int kBits = Log2<K>::value;
+  const int rz = K2 + 1, h2 = K2 >> 1;
+  for (int l = threadIdx.x; l < K1 * h2; l += blockDim.x) {
+    const int k1 = l / h2, k2 = l - k1 * h2;
+    T ar[K / 2 + 1], ai[K / 2 + 1], br[K / 2 + 1], bi[K / 2 + 1];
+#pragma unroll
+    for (int m = 0; m <= K / 2; ++m) {
+      const C2 a = c[(m * K1 + k1) * rz + k2], b = c[(m * K1 + k1) * rz + k2 + h2];
+      ar[m] = a.x;
+      ai[m] = a.y;
+      br[m] = b.x;
+      bi[m] = b.y;
+    }
+    T re[K], im[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      if (m <= K / 2) {
+        re[m] = ar[m] - bi[m];
+        im[m] = ai[m] + br[m];
+      } else {
+        const int mk = K - m;
+        re[m] = ar[mk] + bi[mk];
+        im[m] = br[mk] - ai[mk];
+      }
+    }
+    fft_bwd<K>(re, im);
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      const int k0 = bitrev(e, kBits);
+      c[(k0 * K1 + k1) * rz + k2].x = re[e];
+      c[(k0 * K1 + k1) * rz + k2 + h2].x = im[e];
+    }
+  }
 }
 
-// The third axis: forward transform, multiplication by the influence table (and its energy
-// 1/2 sum G |F|^2), backward transform.
+// Lines along axis 1 in planes 0..n0-1 of axis 0.
+template <int kSign, class C2, class T>
+__device__ __forceinline__ void fft_axis1(C2 *c, int n0, const int *K) {
+  if (K[1] == 16) fft_lines<16, 1, kSign, C2, T>(c, n0, K[1], K[2]);
+  else fft_lines<8, 1, kSign, C2, T>(c, n0, K[1], K[2]);
+}
+
+// The third axis in planes 0..K0/2 of axis 0: forward transform, multiplication by the influence table
+// (and its energy 1/2 sum G |F|^2, planes 0 < m0 < K0/2 counted twice for their conjugates
+// K0 - m0), backward transform.
 template <int K, class C2, class T>
 __device__ __forceinline__ T fft_third(C2 *c, const T *gtab, int K0, int K1, bool want_e) {
   constexpr int kBits = Log2<K>::value;
   const int rz = K + 1;
   T e = T(0);
-  for (int l = threadIdx.x; l < K0 * K1; l += blockDim.x) {
-    const int base = l * rz;
+  for (int l = threadIdx.x; l < (K0 / 2 + 1) * K1; l += blockDim.x) {
+    const int base = l * rz, m0 = l / K1;
+    const T wplane = (m0 == 0 || 2 * m0 == K0) ? T(0.5) : T(1);
     T re[K], im[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) {
@@ -274,7 +327,7 @@ __device__ __forceinline__ T fft_third(C2 *c, const T *gtab, int K0, int K1, boo
 #pragma unroll
     for (int m = 0; m < K; ++m) {
       const T g = __ldg(gtab + l * K + m);
-      if (want_e) e += T(0.5) * g * (re[m] * re[m] + im[m] * im[m]);
+      if (want_e) e += wplane * g * (re[m] * re[m] + im[m] * im[m]);
       re[m] *= g;
       im[m] *= g;
     }
@@ -352,10 +405,11 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   __syncthreads();
   // 3. transforms: axis 0 forward from the fixed-point grid (left zero), axis 1 forward, axis 2
   // forward-G-backward, axes 1 and 0 backward
-  if (K0 == 16) fft_first<16, P, C2, T>(g.acc, g.c, K1, K2);
-  else fft_first<8, P, C2, T>(g.acc, g.c, K1, K2);
+  const int n0 = K0 / 2 + 1;  // planes of axis 0 that the middle passes need (the grid is real)
+  if (K0 == 16) fft_first_r2c<16, P, C2, T>(g.acc, g.c, K1, K2);
+  else fft_first_r2c<8, P, C2, T>(g.acc, g.c, K1, K2);
   __syncthreads();
-  fft_axis<1, 1, C2, T>(g.c, S.pme_K);
+  fft_axis1<1, C2, T>(g.c, n0, S.pme_K);
   __syncthreads();
   const T *gtab;
   if constexpr (P::kMixed) gtab = S.pme_g_f;
@@ -363,9 +417,10 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   const T erec = K2 == 16 ? fft_third<16, C2, T>(g.c, gtab, K0, K1, want_e) : fft_third<8, C2, T>(g.c, gtab, K0, K1, want_e);
   if (want_e) e_fix += fa.efix(erec, err);
   __syncthreads();
-  fft_axis<1, -1, C2, T>(g.c, S.pme_K);
+  fft_axis1<-1, C2, T>(g.c, n0, S.pme_K);
   __syncthreads();
-  fft_axis<0, -1, C2, T>(g.c, S.pme_K);
+  if (K0 == 16) fft_last_c2r<16, C2, T>(g.c, K1, K2);
+  else fft_last_c2r<8, C2, T>(g.c, K1, K2);
   __syncthreads();
   // 4. gather: one thread per (atom, t0); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d
   for (int it = threadIdx.x; it < 4 * n; it += bd) {
