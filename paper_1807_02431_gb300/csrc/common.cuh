@@ -253,6 +253,30 @@ __device__ __forceinline__ ds ds_scale(ds x, float c) {
   return r;
 }
 
+// x + y and x - y of two double-single numbers (TwoSum of the high words, the low words added to the
+// error, renormalised by Fast2Sum; about 2^-46 relative), and x * y (Dekker's product of the high words
+// by an fma, the cross terms in FP32).
+__device__ __forceinline__ ds ds_add2(ds x, ds y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bp = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bp)), __fsub_rn(y.hi, bp));
+  const float lo = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+  ds r;
+  r.hi = __fadd_rn(s, lo);
+  r.lo = __fsub_rn(lo, __fsub_rn(r.hi, s));
+  return r;
+}
+__device__ __forceinline__ ds ds_sub2(ds x, ds y) { return ds_add2(x, ds{-y.hi, -y.lo}); }
+__device__ __forceinline__ ds ds_mul2(ds x, ds y) {
+  const float ph = __fmul_rn(x.hi, y.hi);
+  const float pl = __fmaf_rn(x.hi, y.hi, -ph);
+  const float lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, pl));
+  ds r;
+  r.hi = __fadd_rn(ph, lo);
+  r.lo = __fsub_rn(lo, __fsub_rn(r.hi, ph));
+  return r;
+}
+
 // Block-wide sum of int64 values (every thread contributes; result valid in thread 0).
 __device__ __forceinline__ long long block_sum_ll(long long v, long long *scratch /* >= 32 */) {
   const int kThreads = (int)blockDim.x;

@@ -2,7 +2,8 @@
 // Section 4): every sub-step of the unconstrained step is followed by its projection -- positions by
 // SHAKE along the bond vectors before the A step, momenta by RATTLE onto the tangent space (no relative
 // velocity along any bond).  The constraints form independent groups (connected components); one thread
-// integrates a whole group in FP64 (both precision paths), with Gauss-Seidel sweeps over the group's
+// integrates a whole group in FP64 (the mixed path's single-bond groups in double-single, below), with
+// Gauss-Seidel sweeps over the group's
 // constraints in their order until a sweep moves nothing beyond the tolerance, so that the result is
 // that of sweeping over every constraint of the system.  Item-table systems only.
 #pragma once
@@ -220,11 +221,161 @@ __device__ __forceinline__ void pair_load(const SysDev &S, const State<P> &st, i
   }
 }
 
+// The mixed path's groups of one constraint in double-single arithmetic (FP32 instructions: each FP64
+// warp instruction costs GB300 ~64 cycles, and one warp carries every group of the block).  Positions,
+// momenta, inverse masses and d^2 are double-single; the SHAKE residual d^2 - |r|^2 and the RATTLE
+// residual r . (v_a - v_b) are evaluated in double-single, so the tolerances are those of the FP64 code;
+// the drift h p / m is double-single too; the corrections (a Newton step on each residual) are computed in
+// FP32 and added in double-single, so a sweep may take one more iteration.  Per-group constants, computed once per launch in FP64, sit in
+// shared memory: PairDsConst.
+struct PairDsConst {
+  ds wa, wb, ha, hb, d2;  // 1/m, h/m (h half a step), d^2
+  float tq, tv, sa, sb;   // SHAKE and RATTLE thresholds, noise amplitudes sqrt((1 - c1^2) kT m)
+};
+__device__ __forceinline__ void pair_ds_const(const SysDev &S, int g, double h, double c1, PairDsConst &K) {
+  const int k = S.cgroup_cons[S.cgroup_off[g]];
+  const int2 ij = S.con_ij[k];
+  const double d = S.con_len[k];
+  K.wa = ds_from_double(1.0 / S.mass[ij.x]);
+  K.wb = ds_from_double(1.0 / S.mass[ij.y]);
+  K.ha = ds_from_double(h / S.mass[ij.x]);
+  K.hb = ds_from_double(h / S.mass[ij.y]);
+  K.d2 = ds_from_double(d * d);
+  K.tq = (float)(S.con_tol * d * d);
+  K.tv = (float)(S.con_tol * d * d / S.dt);
+  K.sa = (float)noise_scale(c1, S.kT, S.mass[ij.x]);
+  K.sb = (float)noise_scale(c1, S.kT, S.mass[ij.y]);
+}
+
+struct ConPairDs {
+  int a, b;
+  ds q[2][3], p[2][3];
+};
+
+__device__ __forceinline__ void pair_load_ds(const SysDev &S, const State<PathMixed> &st, int g, ConPairDs &C) {
+  const int2 ij = S.con_ij[S.cgroup_cons[S.cgroup_off[g]]];
+  C.a = ij.x;
+  C.b = ij.y;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    C.q[0][x] = ds{(&st.qh[C.a].x)[x], (&st.ql[C.a].x)[x]};
+    C.q[1][x] = ds{(&st.qh[C.b].x)[x], (&st.ql[C.b].x)[x]};
+    C.p[0][x] = ds{st.ph[3 * C.a + x], st.pl[3 * C.a + x]};
+    C.p[1][x] = ds{st.ph[3 * C.b + x], st.pl[3 * C.b + x]};
+  }
+}
+__device__ __forceinline__ void pair_store_ds(State<PathMixed> &st, const ConPairDs &C, bool positions) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    if (positions) {
+      (&st.qh[C.a].x)[x] = C.q[0][x].hi;
+      (&st.ql[C.a].x)[x] = C.q[0][x].lo;
+      (&st.qh[C.b].x)[x] = C.q[1][x].hi;
+      (&st.ql[C.b].x)[x] = C.q[1][x].lo;
+    }
+    st.ph[3 * C.a + x] = C.p[0][x].hi;
+    st.pl[3 * C.a + x] = C.p[0][x].lo;
+    st.ph[3 * C.b + x] = C.p[1][x].hi;
+    st.pl[3 * C.b + x] = C.p[1][x].lo;
+  }
+}
+
+// RATTLE for one bond: until |r . (p_a w_a - p_b w_b)| <= tv, p_a -= mu r, p_b += mu r with
+// mu = r . v / ((w_a + w_b) |r|^2).
+__device__ __forceinline__ bool pair_rattle_ds(const SysDev &S, const PairDsConst &K, ConPairDs &C) {
+  float r[3];
+  ds rd[3];
+  float rr = 0.f;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    rd[x] = ds_sub2(C.q[0][x], C.q[1][x]);
+    r[x] = rd[x].hi;
+    rr = fmaf(r[x], r[x], rr);
+  }
+  const float den = (K.wa.hi + K.wb.hi) * rr;
+  for (int it = 0; it < S.con_max_iter; ++it) {
+    ds rv{0.f, 0.f};
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+      rv = ds_add2(rv, ds_mul2(rd[x], ds_sub2(ds_mul2(C.p[0][x], K.wa), ds_mul2(C.p[1][x], K.wb))));
+    if (fabsf(rv.hi) <= K.tv) return true;
+    const float mu = rv.hi / den;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      C.p[0][x] = ds_add(C.p[0][x], -mu * r[x]);
+      C.p[1][x] = ds_add(C.p[1][x], mu * r[x]);
+    }
+  }
+  return false;
+}
+
+// A (half a step of drift) then SHAKE along the bond vector s_o before the drift: until
+// |d^2 - |r|^2| <= tq, q_a += g w_a s_o, q_b -= g w_b s_o with g = (d^2 - |r|^2) / (2 (w_a + w_b) s_o . r),
+// and the momenta by the matching impulse g s_o / h; then RATTLE.
+__device__ __forceinline__ void pair_a_step_ds(const SysDev &S, const PairDsConst &K, ConPairDs &C, float ih,
+                                               int *err) {
+  float so[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {  // the drift h p / m in double-single (a hydrogen's is large)
+    so[x] = ds_sub2(C.q[0][x], C.q[1][x]).hi;
+    C.q[0][x] = ds_add2(C.q[0][x], ds_mul2(C.p[0][x], K.ha));
+    C.q[1][x] = ds_add2(C.q[1][x], ds_mul2(C.p[1][x], K.hb));
+  }
+  bool ok = false;
+  for (int it = 0; it < S.con_max_iter && !ok; ++it) {
+    ds rr{0.f, 0.f};
+    float sr = 0.f;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const ds r = ds_sub2(C.q[0][x], C.q[1][x]);
+      rr = ds_add2(rr, ds_mul2(r, r));
+      sr = fmaf(so[x], r.hi, sr);
+    }
+    const float diff = ds_sub2(K.d2, rr).hi;
+    if (fabsf(diff) <= K.tq) { ok = true; break; }
+    const float gam = diff / (2.f * (K.wa.hi + K.wb.hi) * sr);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const float gs = gam * so[x];
+      C.q[0][x] = ds_add(C.q[0][x], gs * K.wa.hi);
+      C.q[1][x] = ds_add(C.q[1][x], -gs * K.wb.hi);
+      C.p[0][x] = ds_add(C.p[0][x], gs * ih);
+      C.p[1][x] = ds_add(C.p[1][x], -gs * ih);
+    }
+  }
+  if (!ok) *err |= kErrConstraint;
+  if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
+}
+
 // B, A, O, A of one constrained group (the force of the previous step in the state's f, the noise of
 // this step in xs[3 atom + axis]).
 template <class P>
 __device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P::T *xs, double h, double c1,
-                         int *err) {
+                         int *err, const PairDsConst *kds = nullptr) {
+  if constexpr (P::kMixed) {
+    if (kds && S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {  // one bond, double-single
+      const PairDsConst &K = kds[g];
+      ConPairDs C;
+      pair_load_ds(S, st, g, C);
+      const float hf = (float)h, ih = (float)(1.0 / h), c1f = (float)c1;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        C.p[0][x] = ds_add(C.p[0][x], hf * st.f[3 * C.a + x]);
+        C.p[1][x] = ds_add(C.p[1][x], hf * st.f[3 * C.b + x]);
+      }
+      if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
+      pair_a_step_ds(S, K, C, ih, err);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        C.p[0][x] = ds_add(ds_scale(C.p[0][x], c1f), K.sa * xs[3 * C.a + x]);
+        C.p[1][x] = ds_add(ds_scale(C.p[1][x], c1f), K.sb * xs[3 * C.b + x]);
+      }
+      if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
+      pair_a_step_ds(S, K, C, ih, err);
+      pair_store_ds(st, C, true);
+      return;
+    }
+  }
   if (S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {  // one constraint, two atoms
     ConPair C;
     pair_load<P>(S, st, g, C);
@@ -286,7 +437,28 @@ __device__ __forceinline__ double con_take_force(State<PathMixed> &st, const Acc
 }
 
 template <class P>
-__device__ double con_b(const SysDev &S, State<P> &st, const typename P::Acc &fa, int g, double h, int *err) {
+__device__ double con_b(const SysDev &S, State<P> &st, const typename P::Acc &fa, int g, double h, int *err,
+                        const PairDsConst *kds = nullptr) {
+  if constexpr (P::kMixed) {
+    if (kds && S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {
+      const PairDsConst &K = kds[g];
+      ConPairDs C;
+      pair_load_ds(S, st, g, C);
+      const float hf = (float)h;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        C.p[0][x] = ds_add(C.p[0][x], hf * (float)con_take_force(st, fa, 3 * C.a + x));
+        C.p[1][x] = ds_add(C.p[1][x], hf * (float)con_take_force(st, fa, 3 * C.b + x));
+      }
+      if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
+      pair_store_ds(st, C, false);
+      float ke = 0.f;
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+        ke += 0.5f * (C.p[0][x].hi * C.p[0][x].hi * K.wa.hi + C.p[1][x].hi * C.p[1][x].hi * K.wb.hi);
+      return (double)ke;
+    }
+  }
   if (S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {
     ConPair C;
     pair_load<P>(S, st, g, C);

@@ -362,6 +362,14 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     pms.carve(ptr, S);
     pms.zero(S);
   }
+  PairDsConst *kds = nullptr;  // the mixed path's single-bond constraint groups: constants per group
+  if constexpr (kCon && P::kMixed) {
+    ptr = align32(ptr);
+    kds = (PairDsConst *)ptr;
+    ptr += (size_t)S.n_cgroups * sizeof(PairDsConst);
+    for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads)
+      if (S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) pair_ds_const(S, g, a.h, a.c1, kds[g]);
+  }
 
   const uint32_t *pairs = S.pairs, *items = S.items;
   if (a.pairs_in_smem) {
@@ -418,7 +426,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
         }
       }
       if constexpr (kCon)
-        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) con_baoa<P>(S, st, g, xs, a.h, a.c1, &err);
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) con_baoa<P>(S, st, g, xs, a.h, a.c1, &err, kds);
     } else {
       for (int at = threadIdx.x; at < n; at += kThreads) {
         T z[4];
@@ -473,7 +481,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
       }
       if constexpr (kCon)
         for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) {
-          const double ke = con_b<P>(S, st, fa, g, a.h, &err);
+          const double ke = con_b<P>(S, st, fa, g, a.h, &err, kds);
           if (sample) k_fix += fa.efix((T)ke, &err);
         }
     } else {  // the same thread owns each atom in both halves of the step
@@ -609,6 +617,7 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch,
   if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(n) : GbScratch<PathMixed>::bytes(n));
   if (S.coulomb_rf == 2)
     b += 32 + (S.precision == GRP_FP64 ? PmeScratch<PathF64>::bytes(S) : PmeScratch<PathMixed>::bytes(S));
+  if (S.n_cons > 0 && S.precision != GRP_FP64) b += 32 + (size_t)S.n_cgroups * sizeof(PairDsConst);
   return b;
 }
 
