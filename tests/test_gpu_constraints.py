@@ -128,3 +128,58 @@ def test_declined_combinations(B, ch):
     with pytest.raises(B.GrpError) as e:
         B.grp_adjoint_segment(rep, 10, 10, 5, obs=0)
     assert e.value.status == B.GRP_ENOTIMPL
+
+
+def _with_second_hydrogens(s, beads=(3, 7, 11, 15)):
+    """The hydrogenated chain with a second constrained hydrogen on some beads: their two C-H bonds
+    form one group of two coupled constraints (the FP64 group code on both paths), next to the
+    single-bond groups (double-single on the mixed path).  The new hydrogen sits 0.109 nm from its bead
+    along the normal of the plane of the bead and its two neighbours (90 degrees from the first
+    hydrogen and from both C-C bonds); it is excluded from its bead, the bead's neighbours and the first
+    hydrogen, and carries no angle term."""
+    nh = len(s.constraints)
+    q0 = [v for v in s.q0]
+    extra, excl, cons = [], [tuple(e) for e in s.excl.tolist()], [tuple(c) for c in s.constraints.tolist()]
+    for b in beads:
+        h1 = nh + b
+        nrm = np.cross(s.q0[b + 1] - s.q0[b], s.q0[b - 1] - s.q0[b])
+        k = len(q0)
+        q0.append(s.q0[b] + 0.109 * nrm / np.linalg.norm(nrm))
+        extra.append(k)
+        cons.append((b, k))
+        for j in (b - 1, b, b + 1, h1):
+            excl.append((min(j, k), max(j, k)))
+    n = len(q0)
+    ne = len(extra)
+    s2 = dataclasses.replace(
+        s, name=s.name + "h2", n_atoms=n, mass=np.concatenate([s.mass, np.full(ne, 1.008)]),
+        charge=np.concatenate([s.charge, np.zeros(ne)]), sigma=np.concatenate([s.sigma, np.full(ne, 0.25)]),
+        epsilon=np.concatenate([s.epsilon, np.full(ne, 0.1)]), excl=np.array(sorted(set(excl)), np.int32),
+        constraints=np.array(cons, np.int32), constraint_length=np.full(len(cons), 0.109))
+    s2.q0 = np.asarray(q0)
+    s2.p0 = W.maxwell_boltzmann(s2.mass, s2.kT, 3, np.random.default_rng(5))
+    return s2
+
+
+@pytest.mark.parametrize("prec,steps,tq,tp", [(0, 200, 1e-9, 1e-8), (1, 1, 1e-8, 1e-6)])
+def test_coupled_and_single_groups(B, oracle_mod, ch, prec, steps, tq, tp):
+    """Groups of two coupled bonds (FP64 sweeps) beside single bonds (double-single on the mixed path)
+    in one system: the FP64 path over 200 steps and the mixed path over one step against the oracle,
+    with every bond at its length after 200 mixed steps.  The mixed bound on positions is that of its
+    FP32 forces moving a hydrogen: 2e-6 of the largest force (1,880 kJ/mol/nm here) over one step of
+    two half-kicks and two half-drifts, 2 h^2 dF / m_H ~ 7e-9 nm (measured 1.4e-9 nm)."""
+    s = _with_second_hydrogens(ch)
+    o = oracle_mod.Oracle(s)
+    q0, p0 = _states(s, 4, 6)
+    q, p = _oracle_run(o, q0, p0, steps)
+    sysh = B.grp_create_system(s, prec)
+    rep = B.grp_init_replicas(sysh, 4, SEED, q0, p0, per_replica=True)
+    B.grp_step_k(rep, steps, 0)
+    qg, pg, _, _ = B.grp_get_state(rep)
+    assert np.abs(qg - q).max() < tq * np.abs(q).max()
+    assert np.abs(pg - p).max() < tp * np.abs(p).max()
+    if prec == 1:
+        B.grp_step_k(rep, 199, 0)
+        qg = B.grp_get_state(rep)[0]
+        i, j = s.constraints[:, 0], s.constraints[:, 1]
+        assert np.abs(np.linalg.norm(qg[:, i] - qg[:, j], axis=-1) - 0.109).max() < 1e-9 * 0.109
