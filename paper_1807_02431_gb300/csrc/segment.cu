@@ -637,9 +637,11 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
     if (S.tiled && 32 * S.n_tile_pairs > t) t = 32 * S.n_tile_pairs;
   }
   t = t < 64 ? 64 : (t > 512 ? 512 : ((t + 31) / 32) * 32);
-  // the mixed path's particle mesh: 320 threads, two replicas per SM (its 256 lines per transform pass
-  // take one round of the block; the FP64 transforms need the registers of the 512-thread variant)
-  if (S.coulomb_rf == 2 && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320) t = 320;
+  // the mixed path's particle mesh and constraints: 320 threads, two replicas per SM (the mesh's 256
+  // lines per transform pass take one round of the block; the constraint groups run on one warp, and
+  // two blocks per SM run two such warps at once and 256 replicas in one wave); the FP64 transforms and
+  // groups need the registers of the 512-thread variant
+  if ((S.coulomb_rf == 2 || S.n_cons > 0) && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320) t = 320;
   c.threads = t;
   // noise for up to 16 steps at a time, within 32 KB
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
