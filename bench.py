@@ -59,10 +59,10 @@ def pme_flops_per_replica_step(s: W.System) -> float:
     """FP32 flops per replica-step of the periodic force kernel (particle mesh Ewald): 46 per
     non-excluded pair within the cutoff over minimum images in the initial configuration (the pair
     count of `algorithmic_flops_per_replica_step` plus 6 for the image; erfc and exp counted as one
-    each), 20 per excluded pair, the bonded terms as there; on the mesh of G points with K_d per axis,
-    six transform passes of 5 K log2 K per line (10 G sum_d log2 K_d), 2 G for the influence function,
-    188 per atom for spreading (3 B-spline evaluations of 20 and 64 multiply-adds) and 512 per atom for
-    the gather (64 points x 8)."""
+    each), 20 per excluded pair, the bonded terms as there; on the mesh of G points, a real-data 3-D
+    transform forward and back at 2.5 G log2 G each (half the complex transform's 5 G log2 G: the
+    grid is real), 2 G for the influence function, 188 per atom for spreading (3 B-spline evaluations
+    of 20 and 64 multiply-adds) and 512 per atom for the gather (64 points x 8)."""
     n, box = s.n_atoms, np.asarray(s.box)
     d = s.q0[:, None] - s.q0[None]
     d -= box * np.round(d / box)
@@ -70,7 +70,7 @@ def pme_flops_per_replica_step(s: W.System) -> float:
     within[s.excl[:, 0], s.excl[:, 1]] = False
     within[s.excl[:, 1], s.excl[:, 0]] = False
     G = int(np.prod(s.pme_grid))
-    mesh = 10.0 * G * sum(np.log2(k) for k in s.pme_grid) + 2.0 * G + n * (188.0 + 512.0)
+    mesh = 5.0 * G * np.log2(G) + 2.0 * G + n * (188.0 + 512.0)
     bonded = 15.0 * len(s.bonds) + 40.0 * len(s.angles) + 33.3 * len(s.dihedral_k)
     return 46.0 * int(within.sum()) + 20.0 * len(s.excl) + bonded + mesh
 
