@@ -9,7 +9,8 @@
 // I_i = (1/2) sum_j h_ij, psi = a_i I_i, 1/B_i = 1/a_i - tanh(psi - 0.8 psi^2 + 4.85 psi^3) / rho_i, and
 //   E = -(tau/2) sum_i sum_j q_i q_j / f_ij,  f_ij = sqrt(r^2 + B_i B_j exp(-r^2 / 4 B_i B_j)), f_ii = B_i,
 // tau = k_e (1/eps_in - 1/eps_out), over all pairs (bonded ones included).  Forces: the pair terms at
-// fixed Born radii, then the chain rule through B_i(I_i(r_ij)).  Three passes over the pairs, separated
+// fixed Born radii, then the chain rule through B_i(I_i(r_ij)) with the derivatives dh/dr that the first
+// pass keeps per pair in shared memory.  Three passes over the pairs, separated
 // by block barriers; sums go to fixed-point accumulators, so the result does not depend on the order.
 #pragma once
 #include "forcefield.cuh"
@@ -23,12 +24,16 @@ struct GbScratch {
   using T = typename P::T;
   ScalarAcc<P> acc;  // [0, n): sum_j h_ij;  [n, 2n): dE/dB_i
   T *born, *w;   // [n]
-  static size_t bytes(int n) { return ScalarAcc<P>::bytes(2 * n) + (size_t)2 * n * sizeof(T) + 32; }
+  T *dh;         // [2 n (n - 1) / 2]: dh_ij/dr and dh_ji/dr of every pair, from the first pass
+  static size_t bytes(int n) {
+    return ScalarAcc<P>::bytes(2 * n) + (size_t)2 * n * sizeof(T) + (size_t)n * (n - 1) * sizeof(T) + 32;
+  }
   __device__ void carve(unsigned char *&ptr, int n) {
     acc.carve(ptr, 2 * n);
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
     born = (T *)ptr; ptr += (size_t)n * sizeof(T);
     w = (T *)ptr; ptr += (size_t)n * sizeof(T);
+    dh = (T *)ptr; ptr += (size_t)n * (n - 1) * sizeof(T);
   }
 };
 
@@ -85,9 +90,11 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
     const V3<T> d = pos.diff(i, j);
     const T r = gsqrt(dot(d, d));
     const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
-    T dh;
-    g.acc.add(i, gb_hct<T>(r, (T)pi.x, (T)pj.z, dh), err);
-    g.acc.add(j, gb_hct<T>(r, (T)pj.x, (T)pi.z, dh), err);
+    T dhij, dhji;
+    g.acc.add(i, gb_hct<T>(r, (T)pi.x, (T)pj.z, dhij), err);
+    g.acc.add(j, gb_hct<T>(r, (T)pj.x, (T)pi.z, dhji), err);
+    g.dh[2 * t] = dhij;  // kept for the chain rule (pass 5)
+    g.dh[2 * t + 1] = dhji;
   }
   __syncthreads();
   // 2. Born radii, dB/dI, the self terms of E and dE/dB
@@ -134,11 +141,7 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
     const int i = (int)(pk & 0xFFFFu), j = (int)(pk >> 16);
     const V3<T> d = pos.diff(i, j);
     const T r = gsqrt(dot(d, d));
-    const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
-    T dhij, dhji;
-    gb_hct<T>(r, (T)pi.x, (T)pj.z, dhij);
-    gb_hct<T>(r, (T)pj.x, (T)pi.z, dhji);
-    const T gr = -(g.w[i] * dhij + g.w[j] * dhji) / r;
+    const T gr = -(g.w[i] * g.dh[2 * t] + g.w[j] * g.dh[2 * t + 1]) / r;
     fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
     fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
   }
