@@ -106,6 +106,8 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_gb_born.argtypes = [C.c_void_p, _D, _D, _D]
         L.orc_ewald_parts.argtypes = [C.c_void_p, _D, _D]
+        L.orc_unconverged.restype = C.c_int64
+        L.orc_unconverged.argtypes = [C.c_void_p]
         L.orc_potential.restype = C.c_double
         L.orc_potential.argtypes = [C.c_void_p, _D]
         L.orc_forces.argtypes = [C.c_void_p, _D, _D]
@@ -265,6 +267,10 @@ class Oracle:
         loss = lib().orc_adjoint_segment(self.ctx, q.shape[0], replica0, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr, obs,
                                          transform, center, width, _dp(gth), _dp(gq), _dp(gp))
         return loss, gth, gq, gp
+
+    def unconverged(self):
+        """Constraint projections so far whose sweeps ran out before the tolerance."""
+        return lib().orc_unconverged(self.ctx)
 
     def ewald_parts(self, q):
         """The five parts of the periodic Coulomb energy (real space, excluded pairs, self,

@@ -13,6 +13,7 @@
 struct orc_ctx {
   orc_system s;
   uint8_t *excluded; /* [n][n] 1 when the nonbonded pair is excluded */
+  int64_t unconverged; /* SHAKE or RATTLE projections that ran out of sweeps (the state goes on) */
 };
 
 orc_ctx *orc_create(const orc_system *sys) {
@@ -29,6 +30,8 @@ orc_ctx *orc_create(const orc_system *sys) {
   }
   return c;
 }
+
+int64_t orc_unconverged(const orc_ctx *c) { return c->unconverged; }
 
 void orc_destroy(orc_ctx *c) {
   if (!c) return;
@@ -745,6 +748,7 @@ static void rattle_momenta(const orc_ctx *c, const double *q, double *p) {
     }
     if (!moved) return;
   }
+  ((orc_ctx *)c)->unconverged++;
 }
 
 /* SHAKE after an A step: q holds the unconstrained update of q_old; Gauss-Seidel sweeps move each
@@ -773,6 +777,7 @@ static void shake_positions(const orc_ctx *c, double *q, const double *q_old, do
     }
     if (!moved) return;
   }
+  ((orc_ctx *)c)->unconverged++;
 }
 
 /* BAOAB with constraints: every sub-step of the unconstrained step, in the same order per

@@ -138,6 +138,9 @@ void orc_baoab_step(const orc_ctx *c, double *q, double *p, double *f, uint64_t 
  * (ii) whether q is outside the state omega. */
 int32_t orc_state_of(const orc_ctx *c, const double *q);
 int32_t orc_exited(const orc_ctx *c, const double *q, int32_t omega);
+/* Number of SHAKE or RATTLE projections (all steps so far) whose sweeps reached constraint_max_iter
+ * without meeting the tolerance; the dynamics carries on from the last sweep. */
+int64_t orc_unconverged(const orc_ctx *c);
 /* Generalized Born (OBC II) Born radii B[n] and descreening sums I[n] (nm^-1) of configuration q. */
 void orc_gb_born(const orc_ctx *c, const double *q, double *born, double *integral);
 /* The parts of the periodic Coulomb energy (coulomb_mode 2 or 3) of configuration q: parts[0] the

@@ -23,6 +23,23 @@ def test_constraints_hold_along_trajectories(oracle_mod):
     assert np.abs(np.linalg.norm(r, axis=-1) - s.constraint_length).max() < 1e-9 * 0.109
     v = p[:, i] / s.mass[i][:, None] - p[:, j] / s.mass[j][:, None]
     assert np.abs((r * v).sum(-1)).max() < 1e-9 * 0.109 ** 2 / s.dt
+    assert o.unconverged() == 0
+
+
+def test_unconverged_projections_are_counted(oracle_mod):
+    """One sweep cannot meet a 1e-14 tolerance from a thermal start, so projections that ran out of
+    sweeps are counted; with the default tolerance and bound the same steps count none."""
+    s = dataclasses.replace(W.chain_h(), constraint_max_iter=1, constraint_tol=1e-14)
+    o = oracle_mod.Oracle(s)
+    q = s.q0[None].copy()
+    p = W.maxwell_boltzmann(s.mass, s.kT, 3, np.random.default_rng(0))[None]
+    f = np.stack([o.forces(x) for x in q])
+    o.step_k(q, p, f, 3, 0, 0, 5, 0)
+    assert o.unconverged() > 0
+    o2 = oracle_mod.Oracle(W.chain_h())
+    q2, p2 = W.chain_h().q0[None].copy(), p.copy()
+    o2.step_k(q2, p2, np.stack([o2.forces(x) for x in q2]), 3, 0, 0, 5, 0)
+    assert o2.unconverged() == 0
 
 
 def test_free_rigid_rotor(oracle_mod):
