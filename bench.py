@@ -457,8 +457,9 @@ def profile_case(B, case, replicas, steps, launches):
     """A small fixed case for ncu captures: `launches` launches of the case's main kernel."""
     import torch
 
-    if case in ("chain", "pme", "constrained"):
-        s = {"chain": W.chain, "pme": W.chain_ions, "constrained": W.chain_h}[case]()
+    if case in ("chain", "pme", "constrained", "solvated"):
+        s = {"chain": W.chain, "pme": W.chain_ions, "constrained": W.chain_h,
+             "solvated": lambda: W.solvated(W.chain())}[case]()
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0)
         for _ in range(launches):
             B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
@@ -546,7 +547,8 @@ def main():
     ap.add_argument("--gradient-reps", type=int, default=2)
     ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--branch-reps", type=int, default=20)
-    ap.add_argument("--profile-case", choices=["chain", "pme", "constrained", "ligand", "adjoint", "batch", "branch"],
+    ap.add_argument("--profile-case", choices=["chain", "pme", "constrained", "solvated", "ligand", "adjoint", "batch",
+                                                     "branch"],
                     default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")
     ap.add_argument("--profile-replicas", type=int, default=152)
