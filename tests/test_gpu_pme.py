@@ -50,7 +50,8 @@ def _configs(s, k, seed, spread=0.01):
     return np.stack([s.q0 + spread * rng.standard_normal(s.q0.shape) for _ in range(k)])
 
 
-SHAPES = {"cube": {}, "ortho": dict(edge=(2.6, 2.9, 2.45), grid=(16, 8, 16))}
+# grids of 8 points on the first and third axes take the 8-point real-to-complex and fused passes
+SHAPES = {"cube": {}, "ortho": dict(edge=(2.6, 2.9, 2.45), grid=(16, 8, 16)), "coarse": dict(grid=(8, 16, 8))}
 
 
 @pytest.mark.parametrize("shape", list(SHAPES))
