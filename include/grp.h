@@ -128,8 +128,10 @@ typedef struct {
    * by RATTLE (no relative velocity along any bond), Gauss-Seidel sweeps until |r^2 - d^2| <= tol d^2
    * and |r . v| <= tol d^2 / dt; GRP_ETIMEOUT (latched) when constraint_max_iter sweeps do not reach
    * that.  A constrained pair should be excluded from the nonbonded terms and carry no bond term.
-   * GRP_ENOTIMPL for 64 atoms or more, with the reaction field or implicit solvent, for groups of
-   * coupled constraints larger than 16 constraints or atoms, in a batch, and for grp_adjoint_segment. */
+   * GRP_ENOTIMPL for 64 atoms or more, with the reaction field, particle mesh Ewald or implicit
+   * solvent, for groups of coupled constraints larger than 16 constraints or atoms, in a batch, and for
+   * grp_adjoint_segment.  On the mixed path a group of one constraint is integrated in double-single
+   * arithmetic, a larger group in FP64; both meet the same tolerances. */
   int32_t n_constraints;
   const int32_t *constraint_atoms;  /* [n_constraints][2] */
   const double *constraint_length;  /* [n_constraints] */
