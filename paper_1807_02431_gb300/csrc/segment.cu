@@ -643,10 +643,13 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
   // groups need the registers of the 512-thread variant
   if ((S.coulomb_rf == 2 || S.n_cons > 0) && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320) t = 320;
   c.threads = t;
-  // noise for up to 16 steps at a time, within 32 KB
+  // noise for up to 64 steps at a time (one barrier per batch), within 32 KB; beyond 16 steps only where
+  // the block keeps to half an SM's shared memory, so that a larger batch costs no occupancy (the
+  // counter-based noise is the same whatever the batch)
   const size_t real = S.precision == GRP_FP64 ? 8 : 4;
-  int nb = 16;
+  int nb = 64;
   while (nb > 1 && (size_t)nb * 3 * S.n * real > 32 * 1024) nb /= 2;
+  while (nb > 16 && ff_smem_bytes(S, 1, nb, 0) > 113 * 1024) nb /= 2;
   c.noise_batch = nb;
   c.lean = 0;
   // large systems: atom parameters read from the global table and noise drawn inline, so that the
