@@ -173,3 +173,20 @@ def test_lennard_jones_through_a_face(oracle_mod):
     f = o.forces(pos)
     g = 24 * eps * (2 * sr6 * sr6 - sr6) / 0.2  # repulsive: atom 0 moves away from atom 1's image at x = -1.1
     assert f[0, 0] == pytest.approx(g, rel=1e-10) and f[1, 0] == pytest.approx(-g, rel=1e-10)
+
+
+@pytest.mark.parametrize("shape", [{}, ORTHO])
+def test_chain_ions_recipe(shape):
+    """The periodic workload as documented: neutral, every ion at least 0.3 nm (minimum image) from
+    every other atom, erfc(beta r_c) = 1e-5, the cutoff within half the shortest edge."""
+    s = W.chain_ions(**shape)
+    box = np.asarray(s.box)
+    assert abs(s.charge.sum()) < 1e-12
+    assert math.erfc(s.ewald_beta * s.cutoff) == pytest.approx(1e-5, rel=1e-9)
+    assert s.cutoff <= 0.5 * box.min()
+    n_chain = 22
+    d = s.q0[n_chain:, None] - s.q0[None]
+    d -= box * np.round(d / box)
+    r = np.linalg.norm(d, axis=-1)
+    r[np.arange(s.n_atoms - n_chain), n_chain + np.arange(s.n_atoms - n_chain)] = np.inf  # self
+    assert r.min() >= 0.3 - 1e-12
