@@ -423,8 +423,10 @@ grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_gr, int32_t
  *   receives the number of copies.  Synchronises `stream` before returning.
  * Scratch: one source index per replica plus a counter in a static device array that every GPU which
  * loads the library holds until exit (256 KB); n_rep above 65,536 is rejected with GRP_EINVAL.  The
- * counter is cleared at each call; calls that overlap on the GPU share the array and race.  The first
- * call on each device looks the array's address up (cudaGetSymbolAddress) with that device current. */
+ * kernel stores the count itself, so nothing needs clearing between calls; calls that overlap on the
+ * GPU share the array and race.  The device that was current when `s` was created must be current
+ * (else GRP_EINVAL, before anything is launched).  The first call on each device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current. */
 grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, double *d_q, double *d_p, double *d_f,
                                  double *d_acc, const uint8_t *d_exited, uint64_t seed, int64_t t_global,
                                  int32_t *h_n_branched, void *stream);

@@ -110,6 +110,7 @@ extern "C" const char *grp_last_error(void) { return g_last_error.c_str(); }
 
 // Shared with noalloc.cu.
 grp::SysDev grp_system_device_view(const grp_system *s) { return s->dev; }
+int grp_system_device_index(const grp_system *s) { return s->device; }
 void grp_set_last_error(const char *msg) { g_last_error = msg; }
 
 // ------------------------------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 // grp_fv_branch_noalloc serves them: its only scratch (one source index per replica and a branch
 // counter) lives in a file-scope device array of fixed size that every GPU loading the library keeps
 // until the process exits.  It launches the same branching kernel as grp_fv_branch.
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -20,13 +21,32 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) int g_fv_scratch[kNoAllocMaxReplicas + 64];
 
 // Device address of g_fv_scratch, looked up once per device.  In host code the symbol is only a
-// host-side stand-in, so kernels must be given the address cudaGetSymbolAddress returns.
-int *g_scratch_ptr[kMaxDevices] = {nullptr};
+// host-side stand-in, so kernels must be given the address cudaGetSymbolAddress returns.  Two host
+// threads making their first call on one device at once both look it up and store the same value;
+// the atomics make that well defined.
+std::atomic<int *> g_scratch_ptr[kMaxDevices];
 }  // namespace
 
 // Implemented in api.cu.
 grp::SysDev grp_system_device_view(const grp_system *s);
+int grp_system_device_index(const grp_system *s);
 void grp_set_last_error(const char *msg);
+
+// Host-only part of the entry point's device check: the system's parameter tables live on the
+// device that was current when it was created, and the scratch address is per device, so a call
+// made with another device current is refused before anything is launched.  Returns GRP_OK or
+// GRP_EINVAL (with the message set).  Exported without a header declaration so that the tests can
+// check it on a machine without a GPU.
+extern "C" grp_status grp_noalloc_check_device(int32_t system_device, int32_t current_device) {
+  if (system_device == current_device) return GRP_OK;
+  char msg[200];
+  snprintf(msg, sizeof msg,
+           "grp_fv_branch_noalloc: the current device is %d but the system was created on device %d; "
+           "make that device current before the call",
+           (int)current_device, (int)system_device);
+  grp_set_last_error(msg);
+  return GRP_EINVAL;
+}
 
 extern "C" grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, double *d_q, double *d_p,
                                             double *d_f, double *d_acc, const uint8_t *d_exited, uint64_t seed,
@@ -53,7 +73,9 @@ extern "C" grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, 
     grp_set_last_error("grp_fv_branch_noalloc: no usable current device");
     return GRP_ECUDA;
   }
-  if (!g_scratch_ptr[dev]) {  // first call on this device: look the scratch address up
+  if (grp_noalloc_check_device(grp_system_device_index(s), dev) != GRP_OK) return GRP_EINVAL;
+  int *src = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!src) {  // first call on this device: look the scratch address up
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_fv_scratch);
     if (e != cudaSuccess) {
@@ -61,9 +83,9 @@ extern "C" grp_status grp_fv_branch_noalloc(const grp_system *s, int32_t n_rep, 
       grp_set_last_error(msg);
       return GRP_ECUDA;
     }
-    g_scratch_ptr[dev] = (int *)p;
+    src = (int *)p;
+    g_scratch_ptr[dev].store(src, std::memory_order_release);
   }
-  int *src = g_scratch_ptr[dev];
   int *counter = src + kNoAllocMaxReplicas;
   cudaStream_t st = (cudaStream_t)stream;
   // the kernel stores the count (the block of replica 0 writes it), so the scratch needs no clearing

@@ -43,3 +43,21 @@ def test_binding_fails_loudly_without_library(tmp_path):
             binding.load(str(tmp_path / "missing.so"))
     finally:
         binding._lib = saved
+
+
+def test_noalloc_device_check_host_side():
+    """The allocation-free branching entry point refuses a call made with a device current other
+    than the one its system was created on (its tables and the per-device scratch address would
+    belong to different GPUs); the check runs on the host before any launch."""
+    from paper_1807_02431_gb300 import binding, build
+
+    lib = ctypes.CDLL(build.build())
+    f = lib.grp_noalloc_check_device
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.grp_last_error.restype = ctypes.c_char_p
+    assert f(0, 0) == binding.GRP_OK and f(3, 3) == binding.GRP_OK
+    assert f(1, 0) == binding.GRP_EINVAL
+    msg = lib.grp_last_error().decode()
+    assert "device is 0" in msg and "device 1" in msg
+    assert f(0, 5) == binding.GRP_EINVAL

@@ -297,28 +297,36 @@ def test_parallel_phase_double_well_bit_exact(B, oracle_mod):
     assert _rel(q, qo) < 1e-9
 
 
-def test_parallel_phase_chain_fp64_bit_exact(B, oracle_mod, chain):
-    """Eq. 5 on the chain (FP64 path): replicas started near the rectangle's edge so that exits
-    come within a few checks; M, k, tau and the exit state are exact."""
+@pytest.mark.parametrize("order", [(0, 1, 2, 3, 4, 5, 6, 7), (5, 6, 7, 0, 1, 2, 3, 4)])
+def test_parallel_phase_chain_fp64_bit_exact(B, oracle_mod, chain, order):
+    """Eq. 5 on the chain (FP64 path): eight replicas in state 1 (outside the rectangle), several of
+    them a few degrees from its edge, so that an exit comes within 40 checks of 50 steps (the oracle
+    finds one at the third check; in the second ordering the first exit is replica k = 7, so the
+    tie-break over indices is exercised).  An exit must be found; M, k, tau, the label entered and
+    the positions at the exit check are those of the oracle."""
     s = chain
     o = oracle_mod.Oracle(s)
     R, tc = 16, 50
     q0, p0 = _spread_states(s, R, seed=31)
-    # keep the replicas inside state 1 (the complement) so that the exit is entering the rectangle
     keep = [r for r in range(R) if o.state_of(q0[r]) == 1]
+    assert len(keep) >= 8
     q0, p0 = q0[keep][:8], p0[keep][:8]
+    q0, p0 = q0[list(order)].copy(), p0[list(order)].copy()
     R = len(q0)
     qo, po = q0.copy(), p0.copy()
     fo = np.stack([o.forces(qo[r]) for r in range(R)])
     found, exo = o.parallel_phase(qo, po, fo, SEED, 0, 1, tc, 40)
+    assert found, "the starts were chosen so that the oracle sees an exit within 40 checks"
     sysh = B.grp_create_system(s, B.GRP_FP64)
     rep = B.grp_init_replicas(sysh, R, SEED, q0, p0, per_replica=True)
     ex = B.grp_run_parallel_phase(rep, 1, tc, 40)
     print(ex, exo)
-    if not found:
-        assert ex is None
-    else:
-        assert (ex["M"], ex["k"], ex["tau_steps"], ex["label_to"]) == (exo["M"], exo["k"], exo["tau_steps"], exo["label_to"])
+    assert ex is not None
+    assert (ex["M"], ex["k"], ex["tau_steps"], ex["label_to"]) == (exo["M"], exo["k"], exo["tau_steps"], exo["label_to"])
+    assert exo["tau_steps"] == (R * (exo["M"] - 1) + exo["k"]) * tc
+    q, _, _, ctr = B.grp_get_state(rep)
+    assert ctr["t_global"] == ex["M"] * tc
+    assert _rel(q, qo) < 1e-9
 
 
 def test_genparrep_loop_double_well_bit_exact(B, oracle_mod):
@@ -393,8 +401,12 @@ def test_deterministic(B, chain):
 def test_full_size_chain_sampled_replicas(B, oracle_mod, chain):
     """256 replicas of the 22-bead chain in the benchmark's launch configuration (mixed path, one
     exit test of the convergence step = 500-step segment with sampling, exit test, branching and
-    Gelman-Rubin): sampled replicas advanced alone by the oracle agree after 200 steps (1e-4); after
-    the full segment the exit flags of replicas far from a boundary agree with the oracle."""
+    Gelman-Rubin).  (i) Sampled replicas advanced alone by the oracle agree after 200 steps (1e-4
+    relative).  (ii) After the full 500-step segment, 32 sampled replicas spread over both states
+    are advanced alone by the oracle: every one whose oracle CV ends more than 2 degrees from a
+    boundary of the rectangle has the oracle's label and exit flag (the margin of the mixed-path
+    segment protocol).  (iii) The number of branched workers is the oracle's Fleming-Viot count for
+    the device's exit mask."""
     s = chain
     o = oracle_mod.Oracle(s)
     R = s.n_replicas
@@ -407,11 +419,35 @@ def test_full_size_chain_sampled_replicas(B, oracle_mod, chain):
     qo, _, _, _ = _oracle_step(o, q0[sample], p0[sample], 0, 0, 200, 0, replicas=sample)
     for row, r in enumerate(sample):
         assert _rel(q[r], qo[row]) < 1e-4
+
+    q0, p0 = _spread_states(s, R, seed=13)
+    omega = 1
     B.grp_set_state(rep, q0, p0, np.zeros((R, len(s.observables), 4)), {"t_global": 0, "t_phase": 0})
-    st = B.grp_fv_check(rep, 1, s.t_check, s.t_gr, s.tol, 0)
+    st = B.grp_fv_check(rep, omega, s.t_check, s.t_gr, s.tol, 0)
+    view = B.device_tensors(rep)
+    lab = view["labels"].cpu().numpy().astype(np.int64)
+    exm = view["exited"].cpu().numpy()
     assert st.t_phase == s.t_check and st.gr_evaluated == 1
     assert all(np.isfinite(st.rhat[j]) and st.rhat[j] >= 1.0 for j in range(len(s.observables)))
-    assert 0 <= st.n_branched < R
+    assert st.ref_exited == exm[0] and st.label0 == lab[0]
+    nbo, _ = oracle_mod.fv_branch(SEED, s.t_check, np.concatenate([[0], exm[1:]]).astype(np.uint8))
+    assert st.n_branched == nbo and 0 <= st.n_branched < R
+
+    sample = list(range(0, R, 8))
+    qo, _, _, _ = _oracle_step(o, q0[sample], p0[sample], 0, 0, s.t_check, 0, replicas=sample)
+    lo, hi = np.array(s.cv_params[0:2]), np.array(s.cv_params[2:4])
+    far, labo = [], []
+    for row in range(len(sample)):
+        phi, psi = o.cv(qo[row])
+        far.append(min(abs(phi - lo[0]), abs(phi - lo[1]), abs(psi - hi[0]), abs(psi - hi[1])) > 2.0)
+        labo.append(o.state_of(qo[row]))
+    far, labo = np.array(far), np.array(labo)
+    got = lab[sample]
+    print(f"sampled {len(sample)}, far {far.sum()}, oracle labels {np.bincount(labo, minlength=2)}")
+    assert far.sum() >= len(sample) // 2
+    assert len(set(labo[far].tolist())) == 2, "the sample covers both states"
+    assert np.array_equal(got[far], labo[far])
+    assert np.array_equal(exm[sample][far], (labo[far] != omega).astype(np.uint8))
 
 
 # ----------------------------------------------------------------------------- edge cases
