@@ -509,7 +509,8 @@ def arm_config(s: W.System, R: int, world: int) -> dict:
 
 def run_reference(args):
     """The oracle (FP64 C, as it stands) on the host cores, same workload and metric; each step is a
-    bounded sample: the 256 replicas advanced 100 steps with sampling and the exit test."""
+    bounded sample, the same as the GPU arm's cpu_baseline leg: the 256 replicas advanced ten t_check
+    segments (5,000 steps) with sampling and the exit test."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -518,7 +519,7 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count() or 1
     s = W.chain()
-    R, steps = s.n_replicas, 100
+    R, steps = s.n_replicas, 10 * s.t_check
     vals = cpu_oracle(R, steps, cores, args.warmup + args.steps)[args.warmup:]
     value = float(np.mean([v for v, _ in vals]))
     ms = float(np.mean([w for _, w in vals])) * 1e3
@@ -527,8 +528,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": arm_config(s, R, args.gpus),
             "cpu_baseline": {"value": value, "unit": "replica-atom-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{R} replicas x {steps} BAOAB steps (sampling every {s.t_gr}) + exit test, "
-                                       f"split over {cores} processes"},
+                             "sample": f"{R} replicas x {steps} BAOAB steps (ten t_check segments, sampling every "
+                                       f"{s.t_gr}) + exit test, split over {cores} spawned processes"},
             "e2e": {"value": value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -290,6 +290,52 @@ typedef struct {
 grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_check, int32_t t_gr, double tol,
                         int64_t min_fv_steps, grp_fv_status *h_out, void *stream);
 
+/* ---- Runs sharded over several processes, one GPU each.  Section 3.1 distributes the replicas of a
+ * run over processes and names the exchanges (the F-V copies between processes, the Gelman-Rubin sums,
+ * the first exit of the parallel step); Section 5 names GPUs as the next target.  A shard is a replica
+ * set holding the global replicas [first, first + R) of a run of n_global replicas; the shard with
+ * first = 0 holds the reference walker.  The caller moves the small per-check data between processes
+ * with its own communicator (exit flags, sources, the sums below, packed rows); these calls do each
+ * shard's part on its GPU.  grp_fv_branch, grp_gelman_rubin, grp_fv_check, grp_run_parallel_phase,
+ * grp_run, grp_run_original and grp_batch_create treat a set as a whole run and refuse a shard
+ * (GRP_EINVAL). */
+
+/* Make r the shard [first, first + R) of a run of n_global replicas (GRP_EINVAL unless 0 <= first and
+ * first + R <= n_global).  The noise of local replica i is that of global replica first + i, so the
+ * shards of a run draw exactly the noise of one unsharded set of n_global replicas. */
+grp_status grp_set_shard(grp_replicas *r, int32_t first, int32_t n_global);
+
+/* Fleming-Viot sources (Section 2.4.1, task 2) of the shard's replicas from the exit flags of all
+ * n_global replicas (d_exited_global: device u8 [n_global]; the flag of the reference walker is not
+ * read): d_src[i] (device int32 [R]) = the global index of the survivor that global replica
+ * g = first + i copies, drawn as grp_fv_branch draws it (Philox stream 1, counter (t_global, g), the
+ * survivors being the workers 1..n_global-1 not exited, or the reference walker when none survives),
+ * or -1 when g is the reference walker or did not exit.  Changes no state. */
+grp_status grp_fv_plan(grp_replicas *r, const uint8_t *d_exited_global, int32_t *d_src, void *stream);
+
+/* Rows for copies between shards (Section 3.1: a branched replica receives positions, momenta and the
+ * observable history of its source): row i = q, p, F of local replica d_idx[i] (3 n dim doubles each,
+ * layout as the state) followed by its 4 n_obs accumulator words.  grp_pack_rows writes the rows to
+ * d_buf (device [n][3 n dim + 4 n_obs] FP64); grp_unpack_rows writes them into the replicas.  d_idx:
+ * device int32 [n]; an index outside [0, R) is skipped and reported (GRP_EINVAL) by the next
+ * synchronising call. */
+grp_status grp_pack_rows(grp_replicas *r, int32_t n, const int32_t *d_idx, double *d_buf, void *stream);
+grp_status grp_unpack_rows(grp_replicas *r, int32_t n, const int32_t *d_idx, const double *d_buf, void *stream);
+
+/* Gelman-Rubin sums of Eq. 3 over the shard's F-V workers (global index >= 1), from the accumulators.
+ * pass 1: h_out[3 j + 0..2] = (sum over workers of the sample mean O^k_j, workers with samples, workers
+ * without samples).  pass 2, with h_sums1 = the pass-1 sums added over every shard: h_out[2 j + 0..1] =
+ * (sum of (O^k_j - O_j)^2 with O_j the mean over all workers, sum of the within-worker variances).
+ * Synchronises `stream`. */
+grp_status grp_gr_partials(grp_replicas *r, int32_t pass, const double *h_sums1, double *h_out, void *stream);
+
+/* Ratios of Eq. 3 from the pass-1 and pass-2 sums added over every shard: R_j = 1 + B_j / W_j with B_j
+ * and W_j the sums of pass 2 divided by the number of workers (+inf when a worker has no sample, there
+ * is none or W_j <= 0), as grp_gelman_rubin gives on one unsharded set; h_converged = every R_j < 1 +
+ * tol (Eq. 4).  Host arithmetic only; either output may be NULL. */
+grp_status grp_gr_combine(int32_t n_obs, const double *h_sums1, const double *h_sums2, double tol, double *h_rhat,
+                          int32_t *h_converged);
+
 /* Batched runs: several independent Gen. ParRep runs (replica sets, of the same or of different
  * systems, all of one precision) advanced by one persistent kernel that takes (run, replica) units
  * from a queue sorted by decreasing system size; branching, Gelman-Rubin and the status readback are

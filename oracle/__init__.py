@@ -135,6 +135,9 @@ def lib():
         L.orc_step_k.restype = C.c_int32
         L.orc_step_k.argtypes = [C.c_void_p, C.c_int32, _D, _D, _D, C.c_uint64, C.c_int64, C.c_int64,
                                  C.c_int64, C.c_int32, _D, C.c_int32]
+        L.orc_step_k_from.restype = C.c_int32
+        L.orc_step_k_from.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _D, _D, _D, C.c_uint64, C.c_int64,
+                                      C.c_int64, C.c_int64, C.c_int32, _D, C.c_int32]
         L.orc_parallel_phase.restype = C.c_int32
         L.orc_parallel_phase.argtypes = [C.c_void_p, C.c_int32, _D, _D, _D, C.c_uint64, C.c_int64,
                                          C.c_int32, C.c_int32, C.c_int64, C.POINTER(OrcExit)]
@@ -317,6 +320,15 @@ class Oracle:
         samples = np.zeros((R, max(cap, 1), max(no, 1)))
         ns = lib().orc_step_k(self.ctx, R, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr,
                               _dp(samples), cap)
+        return samples[:, :min(ns, cap), :no]
+
+    def step_k_from(self, q, p, f, seed, replica0, t0, tp0, k, t_gr, cap=0):
+        """step_k for rows that are the replicas replica0.. of a larger set (their noise indices)."""
+        R = q.shape[0]
+        no = len(self.system.observables)
+        samples = np.zeros((R, max(cap, 1), max(no, 1)))
+        ns = lib().orc_step_k_from(self.ctx, R, replica0, _dp(q), _dp(p), _dp(f), seed, t0, tp0, k, t_gr,
+                                   _dp(samples), cap)
         return samples[:, :min(ns, cap), :no]
 
     def parallel_phase(self, q, p, f, seed, t0, omega, t_check, max_checks):

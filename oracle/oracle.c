@@ -1027,15 +1027,15 @@ int32_t orc_fv_branch(uint64_t seed, int64_t step, int32_t n_rep, const uint8_t 
 }
 
 /* ---------------------------------------------------------------- k steps with sampling */
-int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
-                   uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
-                   double *samples, int32_t cap) {
+int32_t orc_step_k_from(const orc_ctx *c, int32_t n_rep, int32_t replica0, double *q, double *p, double *f,
+                        uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
+                        double *samples, int32_t cap) {
   const orc_system *s = &c->s;
   int nd = s->n_atoms * s->dim, no = s->n_obs;
   int ns = 0;
   for (int64_t i = 0; i < k; ++i) {
     for (int r = 0; r < n_rep; ++r)
-      orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, seed, r, t0 + i);
+      orc_baoab_step(c, q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd, seed, replica0 + r, t0 + i);
     if (t_gr > 0 && (tp0 + i + 1) % t_gr == 0) {
       if (samples && ns < cap)
         for (int r = 0; r < n_rep; ++r)
@@ -1046,6 +1046,12 @@ int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double
     }
   }
   return ns;
+}
+
+int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
+                   uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
+                   double *samples, int32_t cap) {
+  return orc_step_k_from(c, n_rep, 0, q, p, f, seed, t0, tp0, k, t_gr, samples, cap);
 }
 
 /* ---------------------------------------------------------------- adjoint of a segment

@@ -173,6 +173,11 @@ int32_t orc_fv_branch(uint64_t seed, int64_t step, int32_t n_rep, const uint8_t 
 int32_t orc_step_k(const orc_ctx *c, int32_t n_rep, double *q, double *p, double *f,
                    uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
                    double *samples, int32_t cap);
+/* The same for rows that are the replicas replica0 .. replica0 + n_rep - 1 of a larger set: row r
+ * draws the noise of replica replica0 + r (a shard of a run spread over several processes). */
+int32_t orc_step_k_from(const orc_ctx *c, int32_t n_rep, int32_t replica0, double *q, double *p, double *f,
+                        uint64_t seed, int64_t t0, int64_t tp0, int64_t k, int32_t t_gr,
+                        double *samples, int32_t cap);
 
 /* Adjoint of k BAOAB steps with the noise fixed (differentiation through the dynamics, not part of
  * the paper): advances (q, p, f) [n_rep][n][dim] like orc_step_k, row r drawing the noise of replica

@@ -146,6 +146,12 @@ SIGNATURES = {
     "grp_batch_fv_check": (C.c_int32, [_VP, _I32P, C.c_int32, C.c_int32, C.c_double, C.c_int64,
                                        C.POINTER(FvStatus), _VP]),
     "grp_batch_autotune": (C.c_int32, [_VP, C.c_int32, _VP, _I32P]),
+    "grp_set_shard": (C.c_int32, [_VP, C.c_int32, C.c_int32]),
+    "grp_fv_plan": (C.c_int32, [_VP, _VP, _VP, _VP]),
+    "grp_pack_rows": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP]),
+    "grp_unpack_rows": (C.c_int32, [_VP, C.c_int32, _VP, _VP, _VP]),
+    "grp_gr_partials": (C.c_int32, [_VP, C.c_int32, _D, _D, _VP]),
+    "grp_gr_combine": (C.c_int32, [C.c_int32, _D, _D, C.c_double, _D, _I32P]),
 }
 
 
@@ -501,6 +507,50 @@ def grp_fv_branch_noalloc(sysh: SystemHandle, n_rep: int, d_q, d_p, d_f, d_acc, 
     _check(_lib.grp_fv_branch_noalloc(sysh.handle, n_rep, _ptr(d_q), _ptr(d_p), _ptr(d_f), _ptr(d_acc),
                                       _ptr(d_exited), seed, t_global, C.byref(nb), _stream(stream)))
     return nb.value
+
+
+def grp_set_shard(r: ReplicasHandle, first: int, n_global: int):
+    """Make r the shard [first, first + R) of a run of n_global replicas."""
+    _check(_lib.grp_set_shard(r.handle, first, n_global))
+
+
+def grp_fv_plan(r: ReplicasHandle, d_exited_global, d_src, stream=None):
+    """Fleming-Viot sources (global indices, -1 = kept) of the shard's replicas."""
+    _check(_lib.grp_fv_plan(r.handle, _ptr(d_exited_global), _ptr(d_src), _stream(stream)))
+
+
+def row_len(r: ReplicasHandle) -> int:
+    """Doubles per packed row: q, p, F (n dim each) and 4 n_obs accumulator words."""
+    R, n, dim = r.shape
+    return 3 * n * dim + 4 * r.n_obs
+
+
+def grp_pack_rows(r: ReplicasHandle, n: int, d_idx, d_buf, stream=None):
+    _check(_lib.grp_pack_rows(r.handle, n, _ptr(d_idx), _ptr(d_buf), _stream(stream)))
+
+
+def grp_unpack_rows(r: ReplicasHandle, n: int, d_idx, d_buf, stream=None):
+    _check(_lib.grp_unpack_rows(r.handle, n, _ptr(d_idx), _ptr(d_buf), _stream(stream)))
+
+
+def grp_gr_partials(r: ReplicasHandle, pass_: int, sums1=None, stream=None) -> np.ndarray:
+    """Gelman-Rubin sums of the shard's workers: pass 1 -> [n_obs][3], pass 2 (sums1 = the pass-1
+    sums of all shards) -> [n_obs][2]."""
+    out = np.zeros((r.n_obs, 3 if pass_ == 1 else 2))
+    s1 = None if sums1 is None else np.ascontiguousarray(sums1, dtype=np.float64)
+    _check(_lib.grp_gr_partials(r.handle, pass_, None if s1 is None else _dp(s1), _dp(out), _stream(stream)))
+    return out
+
+
+def grp_gr_combine(sums1, sums2, tol: float):
+    """Ratios of Eq. 3 and the convergence flag of Eq. 4 from the sums added over every shard."""
+    s1 = np.ascontiguousarray(sums1, dtype=np.float64)
+    s2 = np.ascontiguousarray(sums2, dtype=np.float64)
+    n_obs = s1.shape[0]
+    rhat = np.zeros(n_obs)
+    conv = C.c_int32(0)
+    _check(_lib.grp_gr_combine(n_obs, _dp(s1), _dp(s2), tol, _dp(rhat), C.byref(conv)))
+    return rhat, bool(conv.value)
 
 
 class _CudaArray:

@@ -89,6 +89,10 @@ struct grp_replicas {
   float4 *qref = nullptr;   // [R][n]
   int nbl_cap = 0;
   long long t_global = 0, t_phase = 0;
+  // shard of a run sharded over processes: global index of replica 0 and the run's replica count
+  // (rep0 = 0, n_global = R for a set that is the whole run)
+  int rep0 = 0, n_global = 0;
+  double *d_gr = nullptr;  // [3 GRP_MAX_OBS] Gelman-Rubin sums of the shard
   // one-launch status readback (branch count, reference label and exit flag, ratios, error word,
   // first-exit key): the set's arrays for the status kernel, its output and a pinned copy
   RunArrays *d_run = nullptr;
@@ -639,10 +643,20 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
     if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
     if (e & kErrConstraint) return fail(GRP_ETIMEOUT, "SHAKE or RATTLE did not converge within constraint_max_iter sweeps");
+    if (e & kErrIndex) return fail(GRP_EINVAL, "a row index outside the replica set");
     return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
 }
+
+// The calls that treat the set as a whole run (its replica 0 the reference walker, its replicas all
+// the workers) refuse a shard of a larger run.
+static bool sharded(const grp_replicas *r) { return r->rep0 != 0 || r->n_global != r->R; }
+#define NOT_SHARDED(r, name)                                                                          \
+  do {                                                                                                \
+    if (sharded(r)) return fail(GRP_EINVAL, "%s: the replica set is a shard of a larger run (use the " \
+                                            "shard calls)", name);                                    \
+  } while (0)
 
 static grp_status compute_forces(grp_replicas *r, cudaStream_t st) {
   CU(launch_energy_forces(r->sys->dev, r->R, r->q, nullptr, r->f, r->err, st));
@@ -658,6 +672,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   grp_replicas *r = new grp_replicas();
   r->sys = s;
   r->R = n_replicas;
+  r->n_global = n_replicas;
   r->seed = seed;
   const SysDev &D = s->dev;
   const size_t nd = (size_t)D.nd, R = (size_t)n_replicas, nacc = (size_t)D.n_obs * 4;
@@ -683,6 +698,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   AL(r->err, 4);
   AL(r->n_branched, 4);
   AL(r->rhat, GRP_MAX_OBS * 8);
+  AL(r->d_gr, 3 * GRP_MAX_OBS * 8);
   if (D.use_list) {
     // capacity: twice the non-excluded pairs within cutoff + skin in the first configuration
     const int n = D.n;
@@ -750,7 +766,7 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
   if (!r) return;
   cudaFree(r->q); cudaFree(r->p); cudaFree(r->f); cudaFree(r->acc);
   cudaFree(r->labels); cudaFree(r->exited); cudaFree(r->src); cudaFree(r->exit_key);
-  cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat);
+  cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat); cudaFree(r->d_gr);
   cudaFree(r->nbl); cudaFree(r->qref);
   if (r->hb) cudaFreeHost(r->hb);
   cudaFree(r->d_run); cudaFree(r->d_status);
@@ -762,6 +778,7 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
 static SegArgs seg_args(grp_replicas *r, int k, int t_gr, int n_active) {
   SegArgs a{};
   a.S = r->sys->dev;
+  a.rep0 = r->rep0;
   a.q = r->q; a.p = r->p; a.f = r->f; a.acc = r->acc;
   a.labels = r->labels; a.exited = r->exited; a.exit_key = r->exit_key; a.err = r->err;
   a.nbl = r->nbl;
@@ -817,6 +834,7 @@ extern "C" grp_status grp_check_states(grp_replicas *r, int32_t omega, int8_t *d
 extern "C" grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, int32_t *d_src, int32_t *h_n_branched,
                                     void *stream) {
   if (!r) return fail(GRP_EINVAL, "grp_fv_branch: null handle");
+  NOT_SHARDED(r, "grp_fv_branch");
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
   CU(launch_fv_branch(D, r->R, r->q, r->p, r->f, r->acc, d_exited ? d_exited : r->exited, r->src, r->n_branched,
@@ -832,6 +850,7 @@ extern "C" grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, in
 
 extern "C" grp_status grp_gelman_rubin(grp_replicas *r, double tol, double *h_rhat, int32_t *h_converged, void *stream) {
   if (!r) return fail(GRP_EINVAL, "grp_gelman_rubin: null handle");
+  NOT_SHARDED(r, "grp_gelman_rubin");
   if (r->R < 2) return fail(GRP_EINVAL, "grp_gelman_rubin: needs at least one F-V worker (R >= 2)");
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
@@ -878,6 +897,7 @@ extern "C" grp_status grp_batch_create(grp_replicas *const *runs, int32_t n_runs
   *out = nullptr;
   for (int i = 0; i < n_runs; ++i) {
     if (!runs[i]) return fail(GRP_EINVAL, "grp_batch_create: run %d is null", i);
+    if (sharded(runs[i])) return fail(GRP_EINVAL, "grp_batch_create: run %d is a shard of a larger run", i);
     if (runs[i]->sys->dev.potential != GRP_POT_FORCE_FIELD)
       return fail(GRP_ENOTIMPL, "grp_batch_create: batches hold force-field systems");
     if (runs[i]->sys->dev.gb || runs[i]->sys->dev.n_cons || runs[i]->sys->dev.coulomb_rf == 2)
@@ -1211,6 +1231,7 @@ extern "C" grp_status grp_run_parallel_phase(grp_replicas *r, int32_t omega, int
                                              grp_exit *h_out, void *stream) {
   const Range range("grp_run_parallel_phase (Eq. 5)");
   if (!r || !h_out) return fail(GRP_EINVAL, "grp_run_parallel_phase: null argument");
+  NOT_SHARDED(r, "grp_run_parallel_phase");
   if (t_check < 1 || max_checks < 1) return fail(GRP_EINVAL, "grp_run_parallel_phase: t_check, max_checks >= 1");
   cudaStream_t st = (cudaStream_t)stream;
   grp_status e = parallel_phase(r, omega, t_check, max_checks, h_out, st);
@@ -1262,6 +1283,7 @@ extern "C" grp_status grp_fv_check(grp_replicas *r, int32_t omega, int32_t t_che
                                    int64_t min_fv_steps, grp_fv_status *h_out, void *stream) {
   const Range range("grp_fv_check (convergence step)");
   if (!r || !h_out) return fail(GRP_EINVAL, "grp_fv_check: null argument");
+  NOT_SHARDED(r, "grp_fv_check");
   if (t_check < 1 || t_gr < 0) return fail(GRP_EINVAL, "grp_fv_check: need t_check >= 1, t_gr >= 0");
   return fv_check(r, omega, t_check, t_gr, tol, min_fv_steps, h_out, (cudaStream_t)stream);
 }
@@ -1334,6 +1356,7 @@ extern "C" grp_status grp_run(grp_replicas *r, const grp_run_params *p, grp_even
                               int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
   const Range range("grp_run (Fig. 1)");
   if (!r || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_run: null argument");
+  NOT_SHARDED(r, "grp_run");
   if (p->t_gr < 1 || p->t_check < 1 || !(p->tol > 0)) return fail(GRP_EINVAL, "grp_run: need t_gr, t_check >= 1, tol > 0");
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
@@ -1486,6 +1509,7 @@ extern "C" grp_status grp_run_original(grp_replicas *r, const grp_original_param
                                        int32_t max_events, int32_t *h_n_events, int64_t *h_t_sim, void *stream) {
   const Range range("grp_run_original (Section 2.4.3)");
   if (!r || !p || (max_events > 0 && !h_events)) return fail(GRP_EINVAL, "grp_run_original: null argument");
+  NOT_SHARDED(r, "grp_run_original");
   if (p->t_check < 1 || p->t_corr < 0 || p->t_phase < 0)
     return fail(GRP_EINVAL, "grp_run_original: need t_check >= 1, t_corr >= 0, t_phase >= 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1706,6 +1730,75 @@ extern "C" grp_status grp_set_state(grp_replicas *r, const double *h_q, const do
     if (e != GRP_OK) return e;
   }
   return latch_errors(r, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Runs sharded over several processes (Section 3.1 distributes the replicas over processes).
+extern "C" grp_status grp_set_shard(grp_replicas *r, int32_t first, int32_t n_global) {
+  if (!r) return fail(GRP_EINVAL, "grp_set_shard: null handle");
+  if (first < 0 || n_global < 1 || (long long)first + r->R > n_global)
+    return fail(GRP_EINVAL, "grp_set_shard: need 0 <= first and first + R <= n_global (first %d, R %d, n_global %d)",
+                first, r->R, n_global);
+  r->rep0 = first;
+  r->n_global = n_global;
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_fv_plan(grp_replicas *r, const uint8_t *d_exited_global, int32_t *d_src, void *stream) {
+  if (!r || !d_exited_global || !d_src) return fail(GRP_EINVAL, "grp_fv_plan: null argument");
+  CU(launch_fv_plan(r->R, r->rep0, r->n_global, d_exited_global, d_src, r->seed, r->t_global, (cudaStream_t)stream));
+  return GRP_OK;
+}
+
+static grp_status pack_rows(grp_replicas *r, int32_t n, const int32_t *d_idx, double *d_buf, int unpack,
+                            const char *name, cudaStream_t st) {
+  if (!r || n < 0 || (n > 0 && (!d_idx || !d_buf))) return fail(GRP_EINVAL, "%s: bad argument", name);
+  CU(launch_pack_rows(r->sys->dev, r->R, r->q, r->p, r->f, r->acc, n, d_idx, d_buf, unpack, r->err, st));
+  return GRP_OK;
+}
+
+extern "C" grp_status grp_pack_rows(grp_replicas *r, int32_t n, const int32_t *d_idx, double *d_buf, void *stream) {
+  return pack_rows(r, n, d_idx, d_buf, 0, "grp_pack_rows", (cudaStream_t)stream);
+}
+
+extern "C" grp_status grp_unpack_rows(grp_replicas *r, int32_t n, const int32_t *d_idx, const double *d_buf,
+                                      void *stream) {
+  return pack_rows(r, n, d_idx, const_cast<double *>(d_buf), 1, "grp_unpack_rows", (cudaStream_t)stream);
+}
+
+extern "C" grp_status grp_gr_partials(grp_replicas *r, int32_t pass, const double *h_sums1, double *h_out,
+                                      void *stream) {
+  if (!r || !h_out || (pass != 1 && pass != 2) || (pass == 2 && !h_sums1))
+    return fail(GRP_EINVAL, "grp_gr_partials: need pass 1, or pass 2 with the summed pass-1 sums, and h_out");
+  cudaStream_t st = (cudaStream_t)stream;
+  const SysDev &D = r->sys->dev;
+  GrGrand g{};
+  if (pass == 2)
+    for (int j = 0; j < D.n_obs; ++j) {
+      const double nw = h_sums1[3 * j + 1] + h_sums1[3 * j + 2];
+      g.v[j] = nw > 0 ? h_sums1[3 * j] / nw : 0.0;
+    }
+  CU(launch_gr_partials(D, r->R, r->rep0, r->acc, pass, g, r->d_gr, st));
+  const size_t bytes = sizeof(double) * (size_t)D.n_obs * (pass == 1 ? 3 : 2);
+  if (bytes) CU(cudaMemcpyAsync(h_out, r->d_gr, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return latch_errors(r, st);
+}
+
+extern "C" grp_status grp_gr_combine(int32_t n_obs, const double *h_sums1, const double *h_sums2, double tol,
+                                     double *h_rhat, int32_t *h_converged) {
+  if (n_obs < 0 || n_obs > GRP_MAX_OBS || (n_obs > 0 && (!h_sums1 || !h_sums2)))
+    return fail(GRP_EINVAL, "grp_gr_combine: bad argument");
+  int conv = n_obs > 0 ? 1 : 0;
+  for (int j = 0; j < n_obs; ++j) {
+    const double good = h_sums1[3 * j + 1], bad = h_sums1[3 * j + 2], nw = good + bad;
+    const double B = h_sums2[2 * j] / nw, W = h_sums2[2 * j + 1] / nw;
+    const double R = (nw < 1 || bad > 0 || !(W > 0)) ? INFINITY : 1.0 + B / W;
+    if (h_rhat) h_rhat[j] = R;
+    if (!(R < 1.0 + tol)) conv = 0;
+  }
+  if (h_converged) *h_converged = conv;
+  return GRP_OK;
 }
 
 extern "C" grp_status grp_get_device_view(grp_replicas *r, grp_device_view *out) {

@@ -1,92 +1,74 @@
 // Fleming-Viot branching (Section 2.4.1, task 2; copies of Section 3.1), Gelman-Rubin reduction
 // (Eqs. 2-4) and replica broadcast/copy kernels.  All of them are HBM- or latency-bound copies and
 // reductions over replicas; none needs the tensor cores.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace grp {
 
-// Copy of one replica's q, p and F rows (nd doubles each) by the whole block.  When every row starts on
-// a 16-byte boundary (nd even on the library's own 256-byte-aligned arrays; caller-owned arrays are
-// checked) the copy moves double2 words, four per thread and array in flight before the stores:
-// twelve 16-byte loads per thread keep enough bytes in flight to approach the HBM bandwidth
-// (measured: 8-byte loads one at a time reached 36 % of it).  Source and destination rows never
-// overlap, and no thread writes a source row while the kernel runs.
+// Copy of part `part` of `parts` equal slices of one replica's q, p and F rows (nd doubles each) by
+// the whole block.  When every row starts on a 16-byte boundary (nd even on the library's own
+// 256-byte-aligned arrays; caller-owned arrays are checked) the copy moves double2 words, issuing
+// up to four loads per thread and array (twelve 16-byte loads in flight) before the stores: enough
+// bytes in flight to approach the HBM bandwidth (measured: 8-byte loads one at a time reached 36 %
+// of it).  Source and destination rows never overlap, and no thread writes a source row while the
+// kernel runs.
 __device__ __forceinline__ void copy_row3(double *__restrict__ qd, double *__restrict__ pd, double *__restrict__ fd,
                                           const double *__restrict__ qs, const double *__restrict__ ps,
-                                          const double *__restrict__ fs, int nd) {
+                                          const double *__restrict__ fs, int nd, int part = 0, int parts = 1) {
   const int bd = (int)blockDim.x;
-  int i = threadIdx.x;
   const uintptr_t any = (uintptr_t)qd | (uintptr_t)pd | (uintptr_t)fd | (uintptr_t)qs | (uintptr_t)ps | (uintptr_t)fs;
   if ((nd & 1) == 0 && (any & 15) == 0) {
-    const int n2 = nd >> 1;
+    const int n2 = nd >> 1, per = (n2 + parts - 1) / parts;
+    const int lo = part * per, hi = min(n2, lo + per);
     const double2 *q2 = reinterpret_cast<const double2 *>(qs), *p2 = reinterpret_cast<const double2 *>(ps),
                   *f2 = reinterpret_cast<const double2 *>(fs);
     double2 *qo = reinterpret_cast<double2 *>(qd), *po = reinterpret_cast<double2 *>(pd),
             *fo = reinterpret_cast<double2 *>(fd);
-    for (; i + 3 * bd < n2; i += 4 * bd) {
+    for (int base = lo + (int)threadIdx.x; base < hi; base += 4 * bd) {
       double2 a[4], b[4], c[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        a[u] = __ldg(q2 + i + u * bd);
-        b[u] = __ldg(p2 + i + u * bd);
-        c[u] = __ldg(f2 + i + u * bd);
+        const int i = base + u * bd;
+        if (i < hi) {
+          a[u] = __ldg(q2 + i);
+          b[u] = __ldg(p2 + i);
+          c[u] = __ldg(f2 + i);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        qo[i + u * bd] = a[u];
-        po[i + u * bd] = b[u];
-        fo[i + u * bd] = c[u];
+        const int i = base + u * bd;
+        if (i < hi) {
+          qo[i] = a[u];
+          po[i] = b[u];
+          fo[i] = c[u];
+        }
       }
-    }
-    for (; i < n2; i += bd) {
-      qo[i] = __ldg(q2 + i);
-      po[i] = __ldg(p2 + i);
-      fo[i] = __ldg(f2 + i);
     }
     return;
   }
-  for (; i < nd; i += bd) {
+  const int per = (nd + parts - 1) / parts;
+  const int lo = part * per, hi = min(nd, lo + per);
+  for (int i = lo + (int)threadIdx.x; i < hi; i += bd) {
     qd[i] = qs[i];
     pd[i] = ps[i];
     fd[i] = fs[i];
   }
 }
 
-// One block per replica r.  An exited worker r >= 1 draws u from Philox stream 1 at counter
-// (t_global, replica r), picks survivor number floor(u * |S| / 2^32) in ascending index order among
-// the non-exited workers S (the reference walker when S is empty) and copies q, p, F and the
-// observable accumulators from it.  Sources are never destinations, so the copies do not race.
-// Every exited worker is branched, so the block of the reference walker (r = 0, never branched)
-// stores their number in *n_branched: no counter to clear before the launch, no atomics.
-__device__ __forceinline__ void fv_branch_one(int r, int n_rep, int nd, int nacc, double *q, double *p, double *f,
-                                              double *acc, const uint8_t *exited, int32_t *src, int *n_branched,
-                                              uint64_t seed, long long t_global) {
+// The survivor that exited worker r copies (Section 2.4.1, task 2), called by the whole block:
+// survivors S = the workers 1..n_rep-1 not exited, in ascending order; u from Philox stream 1 at
+// counter (t_global, replica r) picks survivor number floor(u |S| / 2^32); with no survivor, the
+// reference walker (0).  Each thread counts the survivors of its contiguous chunk of the mask; a
+// block-wide scan of the counts gives |S| and the rank of each chunk's first survivor; the thread whose
+// chunk holds rank m walks it to that survivor.  (Three dependent rounds of loads, where a warp scanning
+// the mask 32 workers at a time took n_rep/32 dependent rounds.)  Blocks of at most 256 threads.
+__device__ __forceinline__ int draw_survivor(int r, int n_rep, const uint8_t *exited, uint64_t seed,
+                                             long long t_global) {
   __shared__ int s_src;
   __shared__ int s_cnt[8];
-  if (r == 0) {
-    int ne = 0;
-    for (int w = 1 + threadIdx.x; w < n_rep; w += blockDim.x) ne += exited[w] ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ne += __shfl_down_sync(0xffffffffu, ne, o);
-    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = ne;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_cnt[w];
-      *n_branched = tot;
-      if (src) src[0] = -1;
-    }
-    return;
-  }
-  if (!exited[r]) {
-    if (threadIdx.x == 0 && src) src[r] = -1;
-    return;
-  }
-  // Survivors S = the workers 1..R-1 not exited, in ascending order.  Each thread counts those of its
-  // contiguous chunk; a block-wide scan of the counts gives |S| and the rank of each chunk's first
-  // survivor; the thread whose chunk holds rank m = floor(u |S| / 2^32) walks it to that survivor.
-  // (Three dependent rounds of loads, where a warp scanning the mask 32 workers at a time took
-  // R/32 dependent rounds.)
   const int nt = (int)blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int chunk = (n_rep - 1 + nt - 1) / nt;
   const int lo = 1 + threadIdx.x * chunk, hi = min(n_rep, lo + chunk);
@@ -121,8 +103,47 @@ __device__ __forceinline__ void fv_branch_one(int r, int n_rep, int nd, int nacc
   }
   __syncthreads();
   const int s = s_src;
+  __syncthreads();  // every thread has read s_src before a later call rewrites it
+  return s;
+}
+
+// One block per replica r.  An exited worker r >= 1 draws u from Philox stream 1 at counter
+// (t_global, replica r), picks survivor number floor(u * |S| / 2^32) in ascending index order among
+// the non-exited workers S (the reference walker when S is empty) and copies q, p, F and the
+// observable accumulators from it.  Sources are never destinations, so the copies do not race.
+// Every exited worker is branched, so the block of the reference walker (r = 0, never branched)
+// stores their number in *n_branched: no counter to clear before the launch, no atomics.  Large
+// replicas are copied by `parts` blocks, each drawing the same survivor and copying one slice of the
+// rows (slice 0 also copies the accumulators and records the source), so that the copies of a few
+// hundred branched workers spread evenly over the SMs.
+__device__ __forceinline__ void fv_branch_one(int r, int n_rep, int nd, int nacc, double *q, double *p, double *f,
+                                              double *acc, const uint8_t *exited, int32_t *src, int *n_branched,
+                                              uint64_t seed, long long t_global, int part = 0, int parts = 1) {
+  __shared__ int s_cnt[8];
+  if (r == 0) {
+    if (part != 0) return;
+    int ne = 0;
+    for (int w = 1 + threadIdx.x; w < n_rep; w += blockDim.x) ne += exited[w] ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ne += __shfl_down_sync(0xffffffffu, ne, o);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = ne;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_cnt[w];
+      *n_branched = tot;
+      if (src) src[0] = -1;
+    }
+    return;
+  }
+  if (!exited[r]) {
+    if (threadIdx.x == 0 && src && part == 0) src[r] = -1;
+    return;
+  }
+  const int s = draw_survivor(r, n_rep, exited, seed, t_global);
   const size_t a = (size_t)s * nd, b = (size_t)r * nd;
-  copy_row3(q + b, p + b, f + b, q + a, p + a, f + a, nd);
+  copy_row3(q + b, p + b, f + b, q + a, p + a, f + a, nd, part, parts);
+  if (part != 0) return;
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[(size_t)r * nacc + i] = acc[(size_t)s * nacc + i];
   if (threadIdx.x == 0 && src) src[r] = s;
 }
@@ -131,14 +152,18 @@ __global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int n
                                                         double *f, double *acc, const uint8_t *exited,
                                                         int32_t *src, int *n_branched, uint64_t seed,
                                                         long long t_global) {
-  fv_branch_one(blockIdx.x, n_rep, nd, nacc, q, p, f, acc, exited, src, n_branched, seed, t_global);
+  fv_branch_one(blockIdx.x, n_rep, nd, nacc, q, p, f, acc, exited, src, n_branched, seed, t_global, blockIdx.y,
+                gridDim.y);
 }
 
 cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                              const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
                              long long t_global, cudaStream_t st) {
-  fv_branch_kernel<<<n_rep, 256, 0, st>>>(n_rep, S.nd, S.n_obs * 4, q, p, f, acc, exited, src, n_branched,
-                                          seed, t_global);
+  // slices of about 48 KB (256 threads x twelve 16-byte loads) per block
+  const long long row_bytes = 3ll * S.nd * 8;
+  const int parts = (int)std::min<long long>(16, std::max<long long>(1, (row_bytes + 49151) / 49152));
+  fv_branch_kernel<<<dim3(n_rep, parts), 256, 0, st>>>(n_rep, S.nd, S.n_obs * 4, q, p, f, acc, exited, src,
+                                                      n_branched, seed, t_global);
   return cudaGetLastError();
 }
 
@@ -154,6 +179,59 @@ __global__ void __launch_bounds__(256) fv_branch_batch_kernel(const RunArrays *r
 cudaError_t launch_fv_branch_batch(const RunArrays *d_runs, const uint2 *d_units, int n_units, cudaStream_t st) {
   if (n_units <= 0) return cudaSuccess;
   fv_branch_batch_kernel<<<n_units, 256, 0, st>>>(d_runs, d_units);
+  return cudaGetLastError();
+}
+
+// ---- runs sharded over several processes: the shard holds the global replicas [first, first + n_local)
+// Fleming-Viot sources of the shard's replicas from the exit flags of all n_global replicas: one block per
+// local replica, the survivor drawn exactly as fv_branch_one draws it, with global indices.
+__global__ void __launch_bounds__(256) fv_plan_kernel(int n_local, int first, int n_global,
+                                                      const uint8_t *exited_global, int32_t *src, uint64_t seed,
+                                                      long long t_global) {
+  const int g = first + (int)blockIdx.x;
+  if (g == 0 || !exited_global[g]) {
+    if (threadIdx.x == 0) src[blockIdx.x] = -1;
+    return;
+  }
+  const int s = draw_survivor(g, n_global, exited_global, seed, t_global);
+  if (threadIdx.x == 0) src[blockIdx.x] = s;
+}
+
+cudaError_t launch_fv_plan(int n_local, int first, int n_global, const uint8_t *exited_global, int32_t *src,
+                           uint64_t seed, long long t_global, cudaStream_t st) {
+  if (n_local <= 0) return cudaSuccess;
+  fv_plan_kernel<<<n_local, 256, 0, st>>>(n_local, first, n_global, exited_global, src, seed, t_global);
+  return cudaGetLastError();
+}
+
+// Rows of replicas idx[i] (q, p, F, accumulators) to or from a packed buffer [n][3 nd + nacc]: one
+// block per row.  An index outside [0, n_rep) is skipped and flagged.
+__global__ void __launch_bounds__(256) pack_rows_kernel(int n_rep, int nd, int nacc, double *q, double *p,
+                                                        double *f, double *acc, const int32_t *idx, double *buf,
+                                                        int unpack, int *err) {
+  const int r = idx[blockIdx.x];
+  if (r < 0 || r >= n_rep) {
+    if (threadIdx.x == 0) atomicOr(err, (int)kErrIndex);
+    return;
+  }
+  double *b = buf + (size_t)blockIdx.x * (3 * (size_t)nd + nacc);
+  double *rows[3] = {q + (size_t)r * nd, p + (size_t)r * nd, f + (size_t)r * nd};
+  for (int c = 0; c < 3; ++c)
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+      if (unpack) rows[c][t] = b[(size_t)c * nd + t];
+      else b[(size_t)c * nd + t] = rows[c][t];
+    }
+  double *a = acc + (size_t)r * nacc, *ba = b + 3 * (size_t)nd;
+  for (int t = threadIdx.x; t < nacc; t += blockDim.x) {
+    if (unpack) a[t] = ba[t];
+    else ba[t] = a[t];
+  }
+}
+
+cudaError_t launch_pack_rows(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc, int n,
+                             const int32_t *idx, double *buf, int unpack, int *err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  pack_rows_kernel<<<n, 256, 0, st>>>(n_rep, S.nd, S.n_obs * 4, q, p, f, acc, idx, buf, unpack, err);
   return cudaGetLastError();
 }
 
@@ -203,6 +281,51 @@ __device__ __forceinline__ void gelman_rubin_one(int j, int n_rep, int n_obs, co
   const double W = block_sum_d(sw, scratch) / nw;
   if (threadIdx.x == 0) rhat[j] = (nw < 1 || nbad > 0 || !(W > 0)) ? __longlong_as_double(0x7FF0000000000000LL)
                                                                     : 1.0 + B / W;
+}
+
+// Gelman-Rubin sums of a shard's workers (global index >= 1), one block per observable j, from the
+// shifted accumulators (c, S1, S2, n) as in gelman_rubin_one.  Pass 1: out[3 j ..] = (sum of the worker
+// means O^k, workers with samples, workers without); pass 2, grand = the global mean of the worker
+// means: out[2 j ..] = (sum of (O^k - grand)^2, sum of within-worker variances S2/n - (S1/n)^2).
+__global__ void __launch_bounds__(256) gr_partials_kernel(int n_local, int first, int n_obs, const double *acc,
+                                                          int pass, GrGrand grand, double *out) {
+  __shared__ double scratch[33];
+  const int j = blockIdx.x;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int i = threadIdx.x; i < n_local; i += blockDim.x) {
+    if (first + i == 0) continue;  // the reference walker is not a Fleming-Viot worker
+    const double *a = acc + ((size_t)i * n_obs + j) * 4;
+    if (pass == 1) {
+      if (a[3] < 1.0) {
+        a2 += 1.0;
+      } else {
+        a0 += a[0] + a[1] / a[3];
+        a1 += 1.0;
+      }
+    } else if (a[3] >= 1.0) {
+      const double m1 = a[1] / a[3];
+      const double mk = a[0] + m1;
+      a0 += (mk - grand.v[j]) * (mk - grand.v[j]);
+      a1 += a[2] / a[3] - m1 * m1;
+    }
+  }
+  a0 = block_sum_d(a0, scratch);
+  a1 = block_sum_d(a1, scratch);
+  a2 = block_sum_d(a2, scratch);
+  if (threadIdx.x == 0) {
+    if (pass == 1) {
+      out[3 * j] = a0; out[3 * j + 1] = a1; out[3 * j + 2] = a2;
+    } else {
+      out[2 * j] = a0; out[2 * j + 1] = a1;
+    }
+  }
+}
+
+cudaError_t launch_gr_partials(const SysDev &S, int n_local, int first, const double *acc, int pass,
+                               const GrGrand &grand, double *out, cudaStream_t st) {
+  if (S.n_obs == 0) return cudaSuccess;
+  gr_partials_kernel<<<S.n_obs, 256, 0, st>>>(n_local, first, S.n_obs, acc, pass, grand, out);
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) gelman_rubin_kernel(int n_rep, int n_obs, const double *acc, double *rhat) {

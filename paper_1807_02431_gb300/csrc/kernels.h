@@ -21,6 +21,7 @@ struct SegArgs {
   long long t_global0, t_phase0;
   int k, t_gr;
   int n_active;
+  int rep0;                  // global index of replica 0 of the set (noise stream of a shard)
   int do_check, omega;
   long long M;               // check index written into the exit key
   int skip_if_exit;          // return at once when *exit_key holds an exit of a check before M
@@ -70,6 +71,20 @@ cudaError_t launch_copy_replica(const SysDev &S, int n_rep, double *q, double *p
 cudaError_t launch_dephase(const SysDev &S, int n_rep, double *q, double *p, double *f, double *sq, double *sp,
                            double *sf, const uint8_t *exited, long long *stay, uint8_t *done, int t_check,
                            long long t_phase, int *counters, cudaStream_t st);
+
+// ---- runs sharded over several processes (the shard holds global replicas [first, first + n_local))
+// Fleming-Viot source (global index, -1 = kept) of each local replica from the global exit flags.
+cudaError_t launch_fv_plan(int n_local, int first, int n_global, const uint8_t *exited_global, int32_t *src,
+                           uint64_t seed, long long t_global, cudaStream_t st);
+// Rows (q, p, F, accumulators) of replicas idx[0..n) to (unpack = 0) or from (unpack = 1) buf.
+cudaError_t launch_pack_rows(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc, int n,
+                             const int32_t *idx, double *buf, int unpack, int *err, cudaStream_t st);
+// Gelman-Rubin sums of the shard's workers: pass 1 [n_obs][3], pass 2 [n_obs][2] (see fvgr.cu).
+struct GrGrand {
+  double v[kMaxObs];
+};
+cudaError_t launch_gr_partials(const SysDev &S, int n_local, int first, const double *acc, int pass,
+                               const GrGrand &grand, double *out, cudaStream_t st);
 
 // ---- batched runs (many replica sets, possibly of different systems, in one launch)
 // Device arrays of one run for the batched branching / Gelman-Rubin / status kernels.

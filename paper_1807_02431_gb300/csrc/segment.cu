@@ -409,7 +409,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if (kMode == kModeItems || NB > 0) {
       if (j == NB) j = 0;
       if (j == 0) {
-        gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r, n);
+        gen_noise<T>(xi, min(NB, a.k - s), a.t_global0 + s, a.seed, r + a.rep0, n);
         __syncthreads();
       }
       // one thread per coordinate; with a Verlet list, an atom is taken to have moved more than skin/2
@@ -430,7 +430,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     } else {
       for (int at = threadIdx.x; at < n; at += kThreads) {
         T z[4];
-        normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r, at), z);
+        normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r + a.rep0, at), z);
         st.baoa(at, z, h, c1);
         if (use_list) {  // Verlet list: rebuilt when some atom has moved more than skin/2
           float x[3];
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
   int until = a.t_gr > 0 ? (int)(a.t_gr - a.t_phase0 % a.t_gr) : 0x7fffffff;
   for (int s = 0; s < a.k; ++s) {
     double xi[4];
-    normals4_f64(philox_stream(a.seed, a.t_global0 + s, 0u, r, 0), xi);
+    normals4_f64(philox_stream(a.seed, a.t_global0 + s, 0u, r + a.rep0, 0), xi);
     px += h * fx; py += h * fy;
     x += h * px * im; y += h * py * im;
     px = c1 * px + sd * xi[0]; py = c1 * py + sd * xi[1];

@@ -1,7 +1,6 @@
 """Multi-rank host logic (paper_1807_02431_gb300/ranks.py) on two gloo processes on the CPU: replica
-sharding, the global first exit of Eq. 5 (lowest check, then lowest global replica index), the
-Gelman-Rubin ratio of Eq. 3 from per-rank sums (against the oracle's ratio on the whole sample set) and
-the max-over-ranks time of the benchmark."""
+sharding, the shard layout and the max-over-ranks time of the benchmark.  (The sharded run itself is
+tested in test_sharded_run.py.)"""
 import os
 import socket
 
@@ -28,20 +27,6 @@ def _worker(rank, world, port, samples, out_dir):
     res = {}
     # sharding
     res["shards"] = [ranks.shard(n, world, rank) for n in (1, 7, 256, 1025)]
-    # first exit: rank 0 sees replica 5 at check 3, rank 1 replica 1 at check 3 (global 11): k = 6
-    start, _ = ranks.shard(20, world, rank)
-    local = [(3 << 32) | 5, (3 << 32) | 1][rank]
-    res["exit_same_check"] = ranks.first_exit(local, start)
-    # rank 1 exits one check earlier: its replica wins
-    local = [(3 << 32) | 0, (2 << 32) | 4][rank]
-    res["exit_earlier"] = ranks.first_exit(local, start)
-    res["exit_none"] = ranks.first_exit(ranks.NO_EXIT, start)
-    # Gelman-Rubin from per-rank sums
-    s0, c0 = ranks.shard(samples.shape[0], world, rank)
-    mine = samples[s0:s0 + c0]
-    means = mine.mean(axis=1)
-    variances = (mine * mine).mean(axis=1) - means * means
-    res["rhat"] = float(ranks.gelman_rubin_global(means[:, None], variances[:, None])[0])
     res["tmax"] = ranks.max_over_ranks([0.5, 2.0][rank])
     dist.destroy_process_group()
     with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
@@ -62,10 +47,17 @@ def test_two_rank_host_logic(tmp_path, oracle_mod):
         got = sorted(tuple(r["shards"][i]) for r in res)
         assert got[0][0] == 0 and got[0][0] + got[0][1] == got[1][0] and got[1][0] + got[1][1] == n
     for r in res:
-        assert tuple(r["exit_same_check"]) == (3, 6)
-        assert tuple(r["exit_earlier"]) == (2, 10 + 4 + 1)
-        assert r["exit_none"] is None
         assert r["tmax"] == 2.0
-    ref = oracle_mod.gelman_rubin(samples)
-    for r in res:
-        assert abs(r["rhat"] - ref) < 1e-12 * ref
+
+
+def test_layout():
+    """Shards of a run: contiguous, ordered, covering [0, N); shard_of finds the shard of every index."""
+    from paper_1807_02431_gb300 import ranks
+
+    L = ranks.Layout([10, 7, 15], [0, 1, 1])
+    assert L.first == [0, 10, 17] and L.N == 32
+    assert [L.shard_of(g) for g in (0, 9, 10, 16, 17, 31)] == [0, 0, 1, 1, 2, 2]
+    assert L.of_rank(1) == [1, 2]
+    L2 = ranks.Layout.by_rank(1025, 2, per_rank=2)
+    assert L2.N == 1025 and L2.rank == [0, 0, 1, 1] and sum(L2.count) == 1025
+    assert all(L2.shard_of(L2.first[s]) == s for s in range(4))
