@@ -90,8 +90,17 @@ static void rf_constants(const orc_system *s, double *krf, double *crf) {
  * alpha, beta, gamma = 1, 0.8, 4.85) is 1/B_i = 1/a_i - tanh(alpha psi - beta psi^2 + gamma psi^3) / rho_i.
  * The energy, over all pairs including bonded ones and each atom with itself, is
  *   E = -(1/2) k_e (1/eps_in - 1/eps_out) sum_i sum_j q_i q_j / f_ij,
- *   f_ij = sqrt(r^2 + B_i B_j exp(-r^2 / (4 B_i B_j))), f_ii = B_i. */
+ *   f_ij = sqrt(r^2 + B_i B_j exp(-r^2 / (4 B_i B_j))), f_ii = B_i.
+ * With a cutoff r_c (a system whose nonbonded terms are truncated, as the paper's protein-ligand setup
+ * in a non-periodic cutoff scheme), a pair i != j at r >= r_c enters neither the descreening sums nor
+ * the pair energy (plain truncation, like the Lennard-Jones and Coulomb terms of such a system); the
+ * self terms always count. */
 static const double kGbOffset = 0.009, kGbAlpha = 1.0, kGbBeta = 0.8, kGbGamma = 4.85;
+
+/* Whether the pair at squared distance r2 enters the solvent sums. */
+static int gb_in_range(const orc_system *s, double r2) {
+  return !(s->cutoff > 0 && r2 >= s->cutoff * s->cutoff);
+}
 
 /* h_ij and its derivative dh/dr (L and U depend on r). */
 static double gb_hct(double r, double ai, double sj, double *dh) {
@@ -126,6 +135,7 @@ static void gb_radii(const orc_ctx *c, const double *q, double *born, double *db
       if (j == i) continue;
       double d[3], dh;
       sub3(q + 3 * i, q + 3 * j, d);
+      if (!gb_in_range(s, dot3(d, d))) continue;
       sum += gb_hct(norm3(d), ai, s->gb_scale[j] * (s->gb_radius[j] - kGbOffset), &dh);
     }
     const double I = 0.5 * sum, psi = ai * I;
@@ -158,6 +168,7 @@ static double gb_energy(const orc_ctx *c, const double *q) {
       double d[3];
       sub3(q + 3 * i, q + 3 * j, d);
       const double r2 = dot3(d, d), bb = B[i] * B[j];
+      if (!gb_in_range(s, r2)) continue;
       sum += 2.0 * s->charge[i] * s->charge[j] / sqrt(r2 + bb * exp(-r2 / (4.0 * bb)));
     }
   }
@@ -178,7 +189,9 @@ static void gb_forces(const orc_ctx *c, const double *q, double *f) {
     for (int j = i + 1; j < n; ++j) {
       double d[3];
       sub3(q + 3 * i, q + 3 * j, d);
-      const double r2 = dot3(d, d), r = sqrt(r2), bb = B[i] * B[j], D = r2 / (4.0 * bb), e = exp(-D);
+      const double r2 = dot3(d, d);
+      if (!gb_in_range(s, r2)) continue;
+      const double r = sqrt(r2), bb = B[i] * B[j], D = r2 / (4.0 * bb), e = exp(-D);
       const double fij = sqrt(r2 + bb * e), qq = s->charge[i] * s->charge[j];
       /* E_pair = -tau qq / f: dE/df = tau qq / f^2 */
       const double dEdf = tau * qq / (fij * fij);
@@ -198,6 +211,7 @@ static void gb_forces(const orc_ctx *c, const double *q, double *f) {
       if (j == i) continue;
       double d[3], dh;
       sub3(q + 3 * i, q + 3 * j, d);
+      if (!gb_in_range(s, dot3(d, d))) continue;
       const double r = norm3(d);
       gb_hct(r, ai, s->gb_scale[j] * (s->gb_radius[j] - kGbOffset), &dh);
       const double g = w * dh / r;

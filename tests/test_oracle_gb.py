@@ -119,3 +119,78 @@ def test_forces_are_minus_the_gradient(oracle_mod):
         qm[a, x] -= h
         fd = -(o.potential(qp) - o.potential(qm)) / (2 * h)
         assert fd == pytest.approx(f[a, x], rel=1e-6, abs=1e-4)
+
+
+# ----------------------------------------------------------------------------- with a cutoff
+# A system with a cutoff truncates the solvent sums like its other nonbonded terms: a pair at r >= r_c
+# enters neither the descreening sums nor the pair energy; the self terms always count.
+
+def _with_cutoff(s, rc):
+    t = dataclasses.replace(s, cutoff=rc)
+    t.q0, t.p0 = s.q0, s.p0
+    return t
+
+
+def test_cutoff_beyond_every_pair_changes_nothing(oracle_mod):
+    base = W.chain()
+    rng = np.random.default_rng(3)
+    s = dataclasses.replace(base, gb_radius=rng.uniform(0.14, 0.19, base.n_atoms),
+                            gb_scale=rng.uniform(0.7, 0.9, base.n_atoms))
+    s.q0, s.p0 = base.q0, base.p0
+    q = s.q0 + 0.005 * rng.standard_normal(s.q0.shape)
+    o, oc = oracle_mod.Oracle(s), oracle_mod.Oracle(_with_cutoff(s, 50.0))
+    assert oc.potential(q) == o.potential(q)
+    assert np.array_equal(oc.forces(q), o.forces(q))
+
+
+def test_ions_beyond_the_cutoff_are_lone_born_spheres(oracle_mod):
+    """Two ions 1.5 nm apart with a 1.2 nm cutoff: no descreening, no pair term, no Coulomb: the energy
+    is the two Born energies exactly and there is no force; at 1.0 nm both couplings are back."""
+    q1, q2, rho1, rho2 = 0.6, -0.8, 0.16, 0.18
+    a1, a2 = rho1 - OFFSET, rho2 - OFFSET
+    born_e = -_tau() * (q1 * q1 / a1 + q2 * q2 / a2) / 2
+    far = _with_cutoff(_ions([q1, q2], [rho1, rho2], [0.8, 0.8], [[0, 0, 0], [1.5, 0, 0]]), 1.2)
+    o = oracle_mod.Oracle(far)
+    born, integral = o.gb_born(far.q0)
+    assert np.array_equal(integral, [0.0, 0.0]) and born[0] == pytest.approx(a1, rel=1e-15)
+    assert o.potential(far.q0) == pytest.approx(born_e, rel=1e-14)
+    assert np.all(o.forces(far.q0) == 0.0)
+    near = np.array([[0, 0, 0], [1.0, 0, 0]], float)
+    assert abs(o.potential(near) - born_e) > 1.0
+    assert np.all(o.gb_born(near)[1] > 0)
+
+
+def test_cutoff_truncates_each_pair_separately(oracle_mod):
+    """Three atoms on a line, 1.0 nm apart, cutoff 1.2 nm: atom 0 is descreened by atom 1 alone (its sum
+    equals the two-atom value) while atom 1 is descreened by both; the pair (0, 2) at 2.0 nm is cut."""
+    rho, sc = [0.16, 0.17, 0.15], [0.8, 0.75, 0.85]
+    three = _with_cutoff(_ions([0.3, -0.2, 0.4], rho, sc, [[0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]]), 1.2)
+    _, i3 = oracle_mod.Oracle(three).gb_born(three.q0)
+    pair01 = _ions([0.3, -0.2], rho[:2], sc[:2], [[0, 0, 0], [1.0, 0, 0]])
+    pair12 = _ions([-0.2, 0.4], rho[1:], sc[1:], [[1.0, 0, 0], [2.0, 0, 0]])
+    _, i01 = oracle_mod.Oracle(pair01).gb_born(pair01.q0)
+    _, i12 = oracle_mod.Oracle(pair12).gb_born(pair12.q0)
+    assert i3[0] == i01[0] and i3[2] == i12[1]
+    assert i3[1] == pytest.approx(i01[1] + i12[0], rel=1e-15)
+
+
+def test_forces_are_minus_the_gradient_with_a_cutoff(oracle_mod):
+    """The chain in solvent with a 0.9 nm cutoff (some pairs beyond it): forces = -grad V where no pair
+    lies within 1e-4 nm of the cutoff."""
+    base = W.chain()
+    rng = np.random.default_rng(4)
+    s = dataclasses.replace(base, gb_radius=rng.uniform(0.14, 0.19, base.n_atoms),
+                            gb_scale=rng.uniform(0.7, 0.9, base.n_atoms), cutoff=0.9)
+    s.q0, s.p0 = base.q0, base.p0
+    o = oracle_mod.Oracle(s)
+    q = s.q0 + 0.005 * rng.standard_normal(s.q0.shape)
+    d = np.linalg.norm(q[:, None] - q[None], axis=-1)[np.triu_indices(base.n_atoms, 1)]
+    assert (d > 0.9).any() and (d < 0.9).any() and np.abs(d - 0.9).min() > 1e-4
+    f = o.forces(q)
+    h = 1e-6
+    for a, x in [(0, 0), (4, 1), (11, 2), (16, 0), (21, 1)]:
+        qp, qm = q.copy(), q.copy()
+        qp[a, x] += h
+        qm[a, x] -= h
+        fd = -(o.potential(qp) - o.potential(qm)) / (2 * h)
+        assert fd == pytest.approx(f[a, x], rel=1e-6, abs=1e-4)
