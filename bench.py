@@ -271,7 +271,30 @@ def accelerated_speed(B, s, precision, R, seed, max_steps, max_exits=10 ** 6, un
     return out
 
 
-def multistate_bench(B, max_steps, n_runs=64):
+def same_error_bench(B, max_steps, n_runs=64):
+    """The metric's comparison at the same error: the state-to-state loop on the alkane (81 rotamer
+    states) run on both precision paths with the same seeds.  Mixed and FP64 trajectories decorrelate
+    (chaos), so "same error" is judged on the output of the method, the distribution of residence times
+    per visit: a two-sample Kolmogorov-Smirnov test of mixed against FP64, beside the accelerated time
+    per wall time of each path."""
+    from scipy import stats
+
+    from paper_1807_02431_gb300 import analysis
+
+    out = {}
+    res = {}
+    for prec, name in ((B.GRP_MIXED, "mixed"), (B.GRP_FP64, "fp64")):
+        r = multistate_bench(B, max_steps, n_runs, precision=prec, keep_visits=True)
+        res[name] = r.pop("_residences")
+        out[name] = {"ns_per_day": r["ns_per_day"], "wall_s": r["wall_s"], "visits": r["visits"],
+                     "mean_residence_ps": float(np.mean(res[name]))}
+    out["ks_pvalue_mixed_vs_fp64"] = float(stats.ks_2samp(res["mixed"], res["fp64"]).pvalue)
+    out["speedup_mixed_over_fp64_ns_per_day"] = out["mixed"]["ns_per_day"] / out["fp64"]["ns_per_day"]
+    out["workload"] = f"alkane7, {n_runs} runs x 32 replicas, {max_steps} steps per run, both paths"
+    return out
+
+
+def multistate_bench(B, max_steps, n_runs=64, precision=None, keep_visits=False):
     """The state-to-state loop at scale: n_runs independent Gen. ParRep runs of the 7-bead alkane
     (81 rotamer states, transients between them), 32 replicas each, mixed precision, all advanced by
     grp_batch_run until each run's step counter reaches max_steps.  Reports the summed simulated time
@@ -284,7 +307,7 @@ def multistate_bench(B, max_steps, n_runs=64):
     s = W.alkane()
     reps = []
     for i in range(n_runs):
-        sysh = B.grp_create_system(s, B.GRP_MIXED)
+        sysh = B.grp_create_system(s, B.GRP_MIXED if precision is None else precision)
         reps.append((sysh, B.grp_init_replicas(sysh, s.n_replicas, 9000 + i, s.q0, s.p0)))
     b = B.grp_batch_create([r for _, r in reps])
     torch.cuda.synchronize()
@@ -296,13 +319,17 @@ def multistate_bench(B, max_steps, n_runs=64):
     rep = analysis.state_report(evs, dt=s.dt)
     top = sorted(rep, key=lambda k: -rep[k]["n"])[:3]
     vis = [v for ev in evs for v in analysis.visits(ev)]
-    return {"system": f"alkane7 (81 rotamer states), {n_runs} runs x {s.n_replicas} replicas, mixed, "
-                      f"t_check {s.t_check}, TOL {s.tol}, {max_steps} steps per run",
+    out = {"system": f"alkane7 (81 rotamer states), {n_runs} runs x {s.n_replicas} replicas, "
+                     f"{'FP64' if precision == B.GRP_FP64 else 'mixed'}, "
+                     f"t_check {s.t_check}, TOL {s.tol}, {max_steps} steps per run",
             "wall_s": wall, "t_sim_ns": sim_ns, "ns_per_day": sim_ns / (wall / 86400.0),
             "visits": len(vis), "parallel_exits": sum(1 for v in vis if v[3]),
             "states_visited": len({v[0] for v in vis}),
             "top_states_ps": {str(k): {"n": rep[k]["n"], "mean": rep[k]["mean"], "ci95": list(rep[k]["ci"])}
                               for k in top}}
+    if keep_visits:
+        out["_residences"] = [v[1] * s.dt for v in vis]
+    return out
 
 
 def batched_bench(B, steps, warmup, flush, n_runs=64, R=128):
@@ -363,6 +390,14 @@ def ligand_bench(B, steps, warmup, flush, fp64_steps):
     t_rf = time_steps(step_rf, max(1, steps // 2), 1, flush, step_rf.stream)
     out["reaction_field"] = {"value": units * len(t_rf) / (float(np.sum(t_rf)) / 1e3),
                              "ms_per_step": float(np.mean(t_rf))}
+    # the same system in OBC II implicit solvent with the 1.2 nm cutoff applied to the solvent sums too
+    # (the paper's protein-ligand setup: OBC II, non-periodic cutoff)
+    sgb = W.solvated(s)
+    step_gb = Step(B, sgb, B.GRP_MIXED, R, SEED, 0, omega=0)
+    t_gb = time_steps(step_gb, max(1, steps // 2), 1, flush, step_gb.stream)
+    out["solvent_obc2"] = {"value": units * len(t_gb) / (float(np.sum(t_gb)) / 1e3),
+                           "ms_per_step": float(np.mean(t_gb)),
+                           "solvent_pairs": "Verlet-list pairs and excluded pairs within 1.2 nm, 5 passes per step"}
     if fp64_steps > 0:
         step64 = Step(B, s, B.GRP_FP64, R, SEED, 0, omega=0)
         t64 = time_steps(step64, fp64_steps, 1, flush, step64.stream)
@@ -548,6 +583,7 @@ def main():
     ap.add_argument("--gradient-reps", type=int, default=2)
     ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--branch-reps", type=int, default=20)
+    ap.add_argument("--same-error-steps", type=int, default=40000)
     ap.add_argument("--profile-case", choices=["chain", "pme", "constrained", "solvated", "ligand", "adjoint", "batch",
                                                      "branch"],
                     default=None,
@@ -678,6 +714,7 @@ def main():
             accel["double_well_2d_original"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
                                                                  max_exits=8, unit_ns=False, original=True)
         multistate = multistate_bench(B, args.multistate_steps) if args.multistate_steps > 0 else None
+        same_error = same_error_bench(B, args.same_error_steps) if args.same_error_steps > 0 else None
         branching = branch_bench(B, flush, args.branch_reps) if args.branch_reps > 0 else None
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -703,6 +740,7 @@ def main():
                "gradient": gradient,
                "accelerated": accel,
                "multistate": multistate,
+               "same_error": same_error,
                "branching": branching,
                "e2e": {"value": e2e_value, "unit": "replica-atom-steps/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo},

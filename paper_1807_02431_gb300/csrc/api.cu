@@ -93,6 +93,7 @@ struct grp_replicas {
   // (rep0 = 0, n_global = R for a set that is the whole run)
   int rep0 = 0, n_global = 0;
   double *d_gr = nullptr;  // [3 GRP_MAX_OBS] Gelman-Rubin sums of the shard
+  double *gb_glob = nullptr;  // [R][2n] Born radii and weights (solvent on Verlet lists)
   // one-launch status readback (branch count, reference label and exit flag, ratios, error word,
   // first-exit key): the set's arrays for the status kernel, its output and a pinned copy
   RunArrays *d_run = nullptr;
@@ -504,9 +505,14 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     // Generalized Born implicit solvent (OBC II): every pair, per-atom radii and scales
     if (d->gb_radius) {
       if (!d->gb_scale) { grp_destroy_system(s); return fail(GRP_EINVAL, "gb_scale is null"); }
-      if (n >= 64 || d->cutoff > 0) {
+      // the item table (fewer than 64 atoms, every pair), or Verlet lists with the cutoff applied to the
+      // solvent sums too (eps = 4r Coulomb)
+      const bool gb_items = n < 64 && !(d->cutoff > 0);
+      const bool gb_list = D.use_list && d->coulomb_mode == GRP_COULOMB_EPS4R;
+      if (!gb_items && !gb_list) {
         grp_destroy_system(s);
-        return fail(GRP_ENOTIMPL, "implicit solvent is implemented for systems of fewer than 64 atoms without a cutoff");
+        return fail(GRP_ENOTIMPL, "implicit solvent is implemented for systems of fewer than 64 atoms without a cutoff, "
+                                  "and for systems of 64 atoms or more with a cutoff and the eps = 4r Coulomb model");
       }
       if (!(d->gb_solute_dielectric > 0) || !(d->gb_solvent_dielectric > 0)) {
         grp_destroy_system(s);
@@ -523,19 +529,27 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
         gd[i] = make_double4(a, 1.0 / d->gb_radius[i], d->gb_scale[i] * a, d->charge[i]);
         gf[i] = make_float4((float)gd[i].x, (float)gd[i].y, (float)gd[i].z, (float)gd[i].w);
       }
-      std::vector<uint32_t> gp;
-      gp.reserve((size_t)n * (n - 1) / 2);
-      const int m = n + (n & 1);  // round-robin order, as the nonbonded pairs
-      std::vector<int> ring(m);
-      for (int rr = 0; rr < m - 1; ++rr) {
-        ring[0] = 0;
-        for (int k = 1; k < m; ++k) ring[k] = 1 + (k - 1 + rr) % (m - 1);
-        for (int k = 0; k < m / 2; ++k) {
-          const int i = std::min(ring[k], ring[m - 1 - k]), j = std::max(ring[k], ring[m - 1 - k]);
-          if (j < n) gp.push_back((uint32_t)i | ((uint32_t)j << 16));
+      std::vector<uint32_t> gp, gx;
+      if (gb_items) {
+        gp.reserve((size_t)n * (n - 1) / 2);
+        const int m = n + (n & 1);  // round-robin order, as the nonbonded pairs
+        std::vector<int> ring(m);
+        for (int rr = 0; rr < m - 1; ++rr) {
+          ring[0] = 0;
+          for (int k = 1; k < m; ++k) ring[k] = 1 + (k - 1 + rr) % (m - 1);
+          for (int k = 0; k < m / 2; ++k) {
+            const int i = std::min(ring[k], ring[m - 1 - k]), j = std::max(ring[k], ring[m - 1 - k]);
+            if (j < n) gp.push_back((uint32_t)i | ((uint32_t)j << 16));
+          }
         }
+      } else {  // the solvent term includes the excluded pairs, which the Verlet lists leave out
+        for (int i = 0; i < n; ++i)
+          for (int j = i + 1; j < n; ++j)
+            if (s->excl[(size_t)i * n + j]) gx.push_back((uint32_t)i | ((uint32_t)j << 16));
       }
       D.gb = 1;
+      D.n_gb_xpairs = (int)gx.size();
+      if (!gx.empty()) UP(gx.data(), gx.size(), &D.gb_xpairs);
       D.n_gb_pairs = (int)gp.size();
       D.gb_tau = d->coulomb_k * (1.0 / d->gb_solute_dielectric - 1.0 / d->gb_solvent_dielectric);
       UP(gd.data(), gd.size(), &D.gb_d);
@@ -718,6 +732,7 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
     r->nbl_cap = (int)std::min(all, 2 * cnt + 1024);
     AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
+    if (D.gb) AL(r->gb_glob, R * (size_t)n * 2 * 8);
   }
   AL(r->d_run, sizeof(RunArrays));
   AL(r->d_status, sizeof(BatchStatus));
@@ -767,7 +782,7 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
   cudaFree(r->q); cudaFree(r->p); cudaFree(r->f); cudaFree(r->acc);
   cudaFree(r->labels); cudaFree(r->exited); cudaFree(r->src); cudaFree(r->exit_key);
   cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat); cudaFree(r->d_gr);
-  cudaFree(r->nbl); cudaFree(r->qref);
+  cudaFree(r->nbl); cudaFree(r->qref); cudaFree(r->gb_glob);
   if (r->hb) cudaFreeHost(r->hb);
   cudaFree(r->d_run); cudaFree(r->d_status);
   if (r->h_status) cudaFreeHost(r->h_status);
@@ -784,6 +799,7 @@ static SegArgs seg_args(grp_replicas *r, int k, int t_gr, int n_active) {
   a.nbl = r->nbl;
   a.qref = r->qref;
   a.nbl_cap = r->nbl_cap;
+  a.gb_glob = r->gb_glob;
   a.seed = r->seed;
   a.t_global0 = r->t_global;
   a.t_phase0 = r->t_phase;

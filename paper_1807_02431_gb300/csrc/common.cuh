@@ -60,8 +60,10 @@ struct SysDev {
   const int *cgroup_cons;  // constraint indices of each group, ascending
   const int *cgroup_aoff;  // [n_cgroups + 1] into cgroup_atoms
   const int *cgroup_atoms; // atoms of each group
-  int n_gb_pairs;          // every pair i < j (i | j << 16)
+  int n_gb_pairs;          // every pair i < j (i | j << 16) (systems of the item table)
   const uint32_t *gb_pairs;
+  int n_gb_xpairs;         // the excluded pairs i < j (systems with Verlet lists, whose lists omit them)
+  const uint32_t *gb_xpairs;
   double gb_tau;           // k_e (1/eps_in - 1/eps_out)
   const double4 *gb_d;     // per atom (rho - 0.009, 1/rho, S (rho - 0.009), q)
   const float4 *gb_f;

@@ -147,4 +147,84 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
   }
 }
 
+// The solvent forces of a system with a cutoff (Verlet-list systems, up to thousands of atoms): the five
+// passes of gb_forces over the pairs within the cutoff (plain truncation: a pair at r >= r_c enters
+// neither I_i nor the pair energy; the self terms always count).  `pairs(f)` calls f(i, j) for this
+// thread's share of the candidate pairs (each unordered pair once): the Verlet list, which holds every
+// non-excluded pair within the cutoff, and the excluded pairs, which the solvent term includes.  One
+// shared-memory accumulator per atom serves I_i in passes 1-2 and dE/dB_i in passes 2-4; the Born
+// radii and chain-rule weights of the replica live in `born` and `w` (global memory, [n] each, written
+// and read by this block only).  dh/dr is recomputed in pass 5 instead of kept per pair.  Called by every
+// thread of the block with the positions final; the scratch accumulator is zero on entry and left zero.
+template <class P, class Pairs>
+__device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename P::Acc &fa, const ScalarAcc<P> &acc,
+                              typename P::T *born, typename P::T *w, Pairs pairs, bool want_e, long long &e_fix,
+                              int *err) {
+  using T = typename P::T;
+  const int n = S.n, bd = blockDim.x;
+  const T tau = (T)S.gb_tau, cut2 = (T)S.cutoff2;
+  // 1. descreening sums
+  pairs([&](int i, int j) {
+    const V3<T> d = pos.diff(i, j);
+    const T r2 = dot(d, d);
+    if (!(r2 < cut2)) return;
+    const T r = gsqrt(r2);
+    const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
+    T dh;
+    acc.add(i, gb_hct<T>(r, (T)pi.x, (T)pj.z, dh), err);
+    acc.add(j, gb_hct<T>(r, (T)pj.x, (T)pi.z, dh), err);
+  });
+  __syncthreads();
+  // 2. Born radii, dB/dI, the self terms of E and dE/dB
+  for (int i = threadIdx.x; i < n; i += bd) {
+    const auto p = gb_atom<P>(S, i);
+    const T ai = (T)p.x, irho = (T)p.y, qi = (T)p.w;
+    const T psi = ai * T(0.5) * acc.get(i);
+    const T th = gtanh(psi - T(0.8) * psi * psi + T(4.85) * psi * psi * psi);
+    const T B = T(1) / (T(1) / ai - th * irho);
+    born[i] = B;
+    w[i] = B * B * (T(1) - th * th) * irho * (T(1) - T(1.6) * psi + T(14.55) * psi * psi) * ai;  // dB/dI
+    acc.set(i, T(0.5) * tau * qi * qi / (B * B), err);
+    if (want_e) e_fix += fa.efix(T(-0.5) * tau * qi * qi / B, err);
+  }
+  __syncthreads();
+  // 3. pair terms at fixed Born radii: forces and the pairs' parts of dE/dB
+  pairs([&](int i, int j) {
+    const V3<T> d = pos.diff(i, j);
+    const T r2 = dot(d, d);
+    if (!(r2 < cut2)) return;
+    const T bi = born[i], bj = born[j], bb = bi * bj, D = r2 / (T(4) * bb), e = gexp(-D);
+    const T f2 = r2 + bb * e, f = gsqrt(f2), qq = (T)gb_atom<P>(S, i).w * (T)gb_atom<P>(S, j).w;
+    const T dEdf = tau * qq / f2;
+    const T dBcommon = dEdf * e * (T(1) + D) / (T(2) * f);
+    acc.add(i, dBcommon * bj, err);
+    acc.add(j, dBcommon * bi, err);
+    const T gr = -dEdf * (T(1) - T(0.25) * e) / f;  // -dE/dr / r
+    fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
+    fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
+    if (want_e) e_fix += fa.efix(-tau * qq / f, err);
+  });
+  __syncthreads();
+  // 4. chain-rule weights w_i = dE/dB_i dB_i/dI_i / 2
+  for (int i = threadIdx.x; i < n; i += bd) {
+    w[i] = T(0.5) * acc.get(i) * w[i];
+    acc.zero(i);
+  }
+  __syncthreads();
+  // 5. forces through the Born radii
+  pairs([&](int i, int j) {
+    const V3<T> d = pos.diff(i, j);
+    const T r2 = dot(d, d);
+    if (!(r2 < cut2)) return;
+    const T r = gsqrt(r2);
+    const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
+    T dhij, dhji;
+    gb_hct<T>(r, (T)pi.x, (T)pj.z, dhij);
+    gb_hct<T>(r, (T)pj.x, (T)pi.z, dhji);
+    const T gr = -(w[i] * dhij + w[j] * dhji) / r;
+    fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
+    fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
+  });
+}
+
 }  // namespace grp

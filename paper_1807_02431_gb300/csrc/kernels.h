@@ -31,6 +31,7 @@ struct SegArgs {
   uint32_t *nbl;             // [R][nbl_cap] Verlet lists (systems with use_list), else null
   float4 *qref;              // [R][n] positions at the last list build
   int nbl_cap;
+  double *gb_glob;           // [R][2n] Born radii and chain-rule weights (solvent with Verlet lists)
   double h, c1;              // dt/2 and exp(-gamma dt)
 };
 

@@ -347,6 +347,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
   constexpr bool kGB = kMode == kModeItems && kFF == 2;
+  constexpr bool kGBL = kMode == kModeList && kFF == 2;  // solvent with a cutoff on the Verlet list
   constexpr bool kCon = kMode == kModeItems && kFF == 3;
   constexpr bool kPME = kMode == kModeItems && kFF == 4;
   constexpr int kRF = kFF == 4 ? 2 : (kFF >= 2 ? 0 : kFF);
@@ -355,6 +356,15 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     ptr = align32(ptr);
     gbs.carve(ptr, n);
     for (int i = threadIdx.x; i < 2 * n; i += kThreads) gbs.acc.zero(i);
+  }
+  ScalarAcc<P> gbl_acc;  // solvent with a cutoff: one accumulator per atom; radii and weights in global memory
+  T *gbl_born = nullptr, *gbl_w = nullptr;
+  if constexpr (kGBL) {
+    ptr = align32(ptr);
+    gbl_acc.carve(ptr, n);
+    for (int i = threadIdx.x; i < n; i += kThreads) gbl_acc.zero(i);
+    gbl_born = reinterpret_cast<T *>(a.gb_glob + (size_t)r * 2 * n);
+    gbl_w = gbl_born + n;
   }
   PmeScratch<P> pms;  // particle mesh (item-table systems only)
   if constexpr (kPME) {
@@ -454,6 +464,14 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if (sample) until = a.t_gr;
     long long e_fix = 0;
     if constexpr (kGB) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
+    if constexpr (kGBL) {
+      const int nl = n_list;
+      gb_forces_cut<P>(S, pos, fa, gbl_acc, gbl_born, gbl_w, [&](auto f) {
+        for (int t = threadIdx.x; t < nl; t += kThreads) f((int)(list[t] & 0xFFFFu), (int)(list[t] >> 16));
+        for (int t = threadIdx.x; t < S.n_gb_xpairs; t += kThreads)
+          f((int)(S.gb_xpairs[t] & 0xFFFFu), (int)(S.gb_xpairs[t] >> 16));
+      }, sample, e_fix, &err);
+    }
     if constexpr (kPME) pme_forces<P>(S, pos, par, fa, pms, sample, e_fix, &err);
     auto passes = [&](auto rf) {
       constexpr int R = decltype(rf)::value;
@@ -614,7 +632,8 @@ static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch,
   b += (size_t)noise_batch * 3 * n * real;
   if (S.tiled && S.cutoff2 > 0) b += (size_t)S.n_tiles * 6 * 4;
   if (pairs_in_smem) b += (size_t)(S.n_pairs + S.n_items) * 4 + 32;
-  if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(n) : GbScratch<PathMixed>::bytes(n));
+  if (S.gb && S.use_list) b += 32 + ScalarAcc<PathF64>::bytes(n);  // one 8-byte accumulator per atom
+  else if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(n) : GbScratch<PathMixed>::bytes(n));
   if (S.coulomb_rf == 2)
     b += 32 + (S.precision == GRP_FP64 ? PmeScratch<PathF64>::bytes(S) : PmeScratch<PathMixed>::bytes(S));
   if (S.n_cons > 0 && S.precision != GRP_FP64) b += 32 + (size_t)S.n_cgroups * sizeof(PairDsConst);
@@ -680,7 +699,8 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
             : mode == kModeTiles
                   ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles, 0> : ff_segment_kernel<P, 512, 1, kModeTiles, 0>)
                   : (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 1> : ff_segment_kernel<P, 512, 1, kModeList, 1>)
-                        : (small ? ff_segment_kernel<P, 320, 2, kModeList, 0> : ff_segment_kernel<P, 512, 1, kModeList, 0>));
+                     : gb ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 2> : ff_segment_kernel<P, 512, 1, kModeList, 2>)
+                          : (small ? ff_segment_kernel<P, 320, 2, kModeList, 0> : ff_segment_kernel<P, 512, 1, kModeList, 0>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.n_active, c.threads, c.smem, st>>>(a);
@@ -724,7 +744,7 @@ cudaError_t launch_segment(const SegArgs &a0, const SegConfig &c, cudaStream_t s
 // Energies and forces of independent configurations (one block per configuration).
 template <class P>
 __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const double *q, double *energy,
-                                                            double *forces, int *errp, int lean) {
+                                                            double *forces, int *errp, int lean, double *gb_glob) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = S.n, nd = 3 * n, b = blockIdx.x;
   unsigned char *ptr = smem;
@@ -734,7 +754,12 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   ptr = align32(ptr);
   st.carve(ptr, n, S, lean != 0);
   GbScratch<P> gbs;
-  if (S.gb) {
+  ScalarAcc<P> gbl_acc;  // solvent with a cutoff: radii and weights in global memory (gb_glob [conf][2n])
+  if (S.gb && S.use_list) {
+    ptr = align32(ptr);
+    gbl_acc.carve(ptr, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) gbl_acc.zero(i);
+  } else if (S.gb) {
     ptr = align32(ptr);
     gbs.carve(ptr, n);
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) gbs.acc.zero(i);
@@ -764,7 +789,18 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
   int err = 0;
   long long e_fix = 0;
   const typename P::Acc fa = State<P>::acc(F, n);
-  if (S.gb) gb_forces<P>(S, st.pos(), fa, gbs, energy != nullptr, e_fix, &err);
+  if (S.gb && S.use_list) {
+    // every pair i < j, the cutoff applied inside: rows i, i + blockDim.x, ... per thread
+    using T = typename P::T;
+    T *born = reinterpret_cast<T *>(gb_glob + (size_t)b * 2 * n);
+    gb_forces_cut<P>(S, st.pos(), fa, gbl_acc, born, born + n, [&](auto f) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int j = i + 1; j < n; ++j) f(i, j);
+    }, energy != nullptr, e_fix, &err);
+    __syncthreads();
+  } else if (S.gb) {
+    gb_forces<P>(S, st.pos(), fa, gbs, energy != nullptr, e_fix, &err);
+  }
   if (S.coulomb_rf == 2) pme_forces<P>(S, st.pos(), st.params(S), fa, pms, energy != nullptr, e_fix, &err);
   force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, energy != nullptr, e_fix, &err);
   if (S.tiled) tile_pass<P>(S, st.pos(), st.params(S), fa, nullptr, energy != nullptr, e_fix, &err);
@@ -803,7 +839,8 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
   auto bytes = [&](bool lean) {
     size_t b = (size_t)3 * S.n * 8 + 32 * 8 + 32 +
                (S.precision == GRP_FP64 ? State<PathF64>::bytes(S.n, lean) : State<PathMixed>::bytes(S.n, lean));
-    if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(S.n) : GbScratch<PathMixed>::bytes(S.n));
+    if (S.gb && S.use_list) b += 32 + ScalarAcc<PathF64>::bytes(S.n);
+    else if (S.gb) b += 32 + (S.precision == GRP_FP64 ? GbScratch<PathF64>::bytes(S.n) : GbScratch<PathMixed>::bytes(S.n));
     if (S.coulomb_rf == 2)
       b += 32 + (S.precision == GRP_FP64 ? PmeScratch<PathF64>::bytes(S) : PmeScratch<PathMixed>::bytes(S));
     return b;
@@ -812,16 +849,24 @@ cudaError_t launch_energy_forces(const SysDev &S, int n_conf, const double *q, d
   const size_t smem = bytes(lean);
   if (smem > kMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e;
+  double *gb_glob = nullptr;  // Born radii and weights of every configuration (solvent with a cutoff)
+  if (S.gb && S.use_list) {
+    e = cudaMallocAsync((void **)&gb_glob, (size_t)n_conf * 2 * S.n * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+  }
   if (S.precision == GRP_FP64) {
     e = cudaFuncSetAttribute(energy_forces_kernel<PathF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    energy_forces_kernel<PathF64><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean);
+    if (e == cudaSuccess) energy_forces_kernel<PathF64><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean, gb_glob);
   } else {
     e = cudaFuncSetAttribute(energy_forces_kernel<PathMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    energy_forces_kernel<PathMixed><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean);
+    if (e == cudaSuccess) energy_forces_kernel<PathMixed><<<n_conf, 256, smem, st>>>(S, q, energy, forces, err, lean, gb_glob);
   }
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (gb_glob) {
+    const cudaError_t e2 = cudaFreeAsync(gb_glob, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------------
