@@ -658,6 +658,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
     if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
     if (e & kErrConstraint) return fail(GRP_ETIMEOUT, "SHAKE or RATTLE did not converge within constraint_max_iter sweeps");
     if (e & kErrIndex) return fail(GRP_EINVAL, "a row index outside the replica set");
+    if (e & kErrTimeout) return fail(GRP_ETIMEOUT, "a bulk copy of the branching did not complete within its time limit");
     return fail(GRP_EOVERFLOW, "force or energy term outside the fixed-point range (2^22 FP64, 2^18 mixed) or not finite");
   }
   return GRP_OK;
@@ -854,7 +855,7 @@ extern "C" grp_status grp_fv_branch(grp_replicas *r, const uint8_t *d_exited, in
   cudaStream_t st = (cudaStream_t)stream;
   const SysDev &D = r->sys->dev;
   CU(launch_fv_branch(D, r->R, r->q, r->p, r->f, r->acc, d_exited ? d_exited : r->exited, r->src, r->n_branched,
-                      r->seed, r->t_global, st));
+                      r->seed, r->t_global, st, r->err));
   if (d_src) CU(cudaMemcpyAsync(d_src, r->src, (size_t)r->R * 4, cudaMemcpyDeviceToDevice, st));
   if (h_n_branched) {
     CU(cudaMemcpyAsync(&r->hb->n_branched, r->n_branched, 4, cudaMemcpyDeviceToHost, st));
@@ -1271,7 +1272,8 @@ static grp_status fv_check(grp_replicas *r, int omega, int t_check, int t_gr, do
   const int R = r->R;
   grp_status e = run_steps(r, t_check, t_gr, R, 1, omega, 0, 0, st);
   if (e != GRP_OK) return e;
-  CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st));
+  CU(launch_fv_branch(D, R, r->q, r->p, r->f, r->acc, r->exited, r->src, r->n_branched, r->seed, r->t_global, st,
+                      r->err));
   const bool want_gr = r->t_phase >= min_fv_steps && R > 1 && D.n_obs > 0;
   if (want_gr) CU(launch_gelman_rubin(D, R, r->acc, tol, r->rhat, nullptr, st));
   // the whole status in one launch and one copy

@@ -12,7 +12,7 @@ constexpr int kMaxObs = GRP_MAX_OBS;
 constexpr int kMaxGroups = GRP_MAX_GROUPS;
 
 // Error bits latched by kernels into the replica set's error word.
-enum : int { kErrNaN = 1, kErrOverflow = 2, kErrList = 4, kErrConstraint = 8, kErrIndex = 16 };
+enum : int { kErrNaN = 1, kErrOverflow = 2, kErrList = 4, kErrConstraint = 8, kErrIndex = 16, kErrTimeout = 32 };
 
 // Kinds of force-field work items.
 enum : uint32_t { kItemPair = 0, kItemBond = 1, kItemAngle = 2, kItemDihedral = 3, kItemNone = 15 };

@@ -156,9 +156,130 @@ __global__ void __launch_bounds__(256) fv_branch_kernel(int n_rep, int nd, int n
                 gridDim.y);
 }
 
+// ---- the same branching with the copies done by the bulk-copy (TMA) engine
+// One elected thread moves a row through shared memory in chunks: cp.async.bulk loads (global -> shared,
+// completion counted in bytes on an mbarrier) kBulkStages chunks ahead, cp.async.bulk stores (shared ->
+// global) as each chunk lands; a buffer is reloaded once the store that read it has finished reading.  The
+// bulk copies need 16-byte aligned addresses and sizes: rows of an even number of doubles on 16-byte
+// aligned arrays (checked on the host).  Every wait on an mbarrier is bounded by ~1 s of SM clock, after
+// which the block records kErrTimeout, waits for its issued stores and stops.
+constexpr int kBulkStages = 4;
+constexpr uint32_t kBulkChunk = 12288;  // bytes; 4 stages = 48 KB of shared memory, four blocks per SM
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst_smem)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all_but_one() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Bounded wait for phase `parity` of an mbarrier: false after ~2^31 SM cycles (about one second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+
+// Grid (worker r, row part): part 0, 1, 2 copies the q, p or F row of an exited worker; the survivor is
+// drawn as in fv_branch_one; part 0 also copies the accumulators and records the source.  The reference
+// walker's block (r = 0) stores the branch count.
+__global__ void __launch_bounds__(128) fv_branch_bulk_kernel(int n_rep, int nd, int nacc, double *q, double *p,
+                                                             double *f, double *acc, const uint8_t *exited,
+                                                             int32_t *src, int *n_branched, uint64_t seed,
+                                                             long long t_global, int *err) {
+  extern __shared__ __align__(128) unsigned char stage[];  // kBulkStages x kBulkChunk
+  __shared__ __align__(8) uint64_t bar[kBulkStages];
+  const int r = blockIdx.x, part = blockIdx.y;
+  if (r == 0 || !exited[r]) {  // the count, or a kept worker: no copy
+    fv_branch_one(r, n_rep, nd, nacc, q, p, f, acc, exited, src, n_branched, seed, t_global, part, gridDim.y);
+    return;
+  }
+  const int s = draw_survivor(r, n_rep, exited, seed, t_global);
+  if (part == 0) {
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[(size_t)r * nacc + i] = acc[(size_t)s * nacc + i];
+    if (threadIdx.x == 0 && src) src[r] = s;
+  }
+  if (threadIdx.x == 0) {
+    double *arr = part == 0 ? q : (part == 1 ? p : f);
+    const char *from = reinterpret_cast<const char *>(arr + (size_t)s * nd);
+    char *to = reinterpret_cast<char *>(arr + (size_t)r * nd);
+    const uint32_t row = (uint32_t)nd * 8u;
+    const int nc = (int)((row + kBulkChunk - 1) / kBulkChunk);
+    auto bytes_of = [&](int c) { return min(kBulkChunk, row - (uint32_t)c * kBulkChunk); };
+    for (int b = 0; b < kBulkStages; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
+    for (int c = 0; c < nc && c < kBulkStages; ++c) {
+      mbar_expect_tx(&bar[c], bytes_of(c));
+      bulk_load(stage + (size_t)c * kBulkChunk, from + (size_t)c * kBulkChunk, bytes_of(c), &bar[c]);
+    }
+    bool ok = true;
+    for (int c = 0; c < nc; ++c) {
+      const int b = c % kBulkStages;
+      if (!mbar_wait_bounded(&bar[b], (uint32_t)(c / kBulkStages) & 1u)) {
+        ok = false;
+        break;
+      }
+      bulk_store(to + (size_t)c * kBulkChunk, stage + (size_t)b * kBulkChunk, bytes_of(c));
+      bulk_commit();
+      // refill the buffer of chunk c - 1 with chunk c - 1 + kBulkStages once its store has read it
+      const int nxt = c - 1 + kBulkStages;
+      if (c >= 1 && nxt < nc) {
+        bulk_wait_read_all_but_one();
+        const int bb = (c - 1) % kBulkStages;
+        mbar_expect_tx(&bar[bb], bytes_of(nxt));
+        bulk_load(stage + (size_t)bb * kBulkChunk, from + (size_t)nxt * kBulkChunk, bytes_of(nxt), &bar[bb]);
+      }
+    }
+    if (!ok && err) atomicOr(err, (int)kErrTimeout);
+    bulk_wait_all();  // the stores issued have completed (and read the shared memory)
+  }
+  __syncthreads();  // the block's shared memory outlives thread 0's copies
+}
+
+static bool aligned16(const void *x) { return ((uintptr_t)x & 15u) == 0; }
+
 cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                              const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
-                             long long t_global, cudaStream_t st) {
+                             long long t_global, cudaStream_t st, int *err) {
+  // large rows on 16-byte aligned arrays: the bulk-copy kernel, one block per worker and row
+  if (S.nd % 2 == 0 && S.nd * 8 >= 8192 && aligned16(q) && aligned16(p) && aligned16(f)) {
+    const int smem = kBulkStages * (int)kBulkChunk;
+    cudaError_t e = cudaFuncSetAttribute(fv_branch_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fv_branch_bulk_kernel<<<dim3(n_rep, 3), 128, smem, st>>>(n_rep, S.nd, S.n_obs * 4, q, p, f, acc, exited, src,
+                                                             n_branched, seed, t_global, err);
+    return cudaGetLastError();
+  }
   // slices of about 48 KB (256 threads x twelve 16-byte loads) per block
   const long long row_bytes = 3ll * S.nd * 8;
   const int parts = (int)std::min<long long>(16, std::max<long long>(1, (row_bytes + 49151) / 49152));

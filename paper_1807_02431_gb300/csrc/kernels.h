@@ -54,10 +54,11 @@ cudaError_t launch_segment(const SegArgs &a, const SegConfig &cfg, cudaStream_t 
 cudaError_t launch_check(const SysDev &S, const double *q, int n_rep, int omega, int8_t *labels,
                          uint8_t *exited, unsigned long long *exit_key, long long M, cudaStream_t st);
 
-// Fleming-Viot branching of exited workers; n_branched (device int) receives the number branched.
+// Fleming-Viot branching of exited workers; n_branched (device int) receives the number branched; err
+// (optional) the sticky error word (kErrTimeout when a bulk copy did not complete in time).
 cudaError_t launch_fv_branch(const SysDev &S, int n_rep, double *q, double *p, double *f, double *acc,
                              const uint8_t *exited, int32_t *src, int *n_branched, uint64_t seed,
-                             long long t_global, cudaStream_t st);
+                             long long t_global, cudaStream_t st, int *err = nullptr);
 
 // Gelman-Rubin ratio per observable over workers 1..R-1; rhat[n_obs], converged flag.
 cudaError_t launch_gelman_rubin(const SysDev &S, int n_rep, const double *acc, double tol, double *rhat,
