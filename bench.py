@@ -460,16 +460,17 @@ def measured_hbm_gbs():
         return 6800.0  # the profiling recipe's fallback
 
 
-def gradient_bench(B, reps):
+def gradient_bench(B, reps, precision=None):
     """Differentiation through the dynamics (the gradient workload): 256 replicas of the 22-bead chain,
     one 1,000-step fixed-noise segment with the end-to-end distance sampled every 10 steps, forward
-    pass + checkpoints every 100 steps + adjoint sweep (grp_adjoint_segment), FP64."""
+    pass + checkpoints every 100 steps + adjoint sweep (grp_adjoint_segment), FP64 or mixed (FP32
+    forces and FP32 dual-number tangents in fixed point, FP64 adjoint vectors)."""
     import torch
 
     s = W.chain_gradient()
     R, k, t_gr, ck = s.n_replicas, 1000, 10, 100
     q0, p0 = W.replica_states(s, R, seed=24, spread=0.002)
-    sysh = B.grp_create_system(s, B.GRP_FP64)
+    sysh = B.grp_create_system(s, B.GRP_FP64 if precision is None else precision)
     rep = B.grp_init_replicas(sysh, R, SEED, q0, p0, per_replica=True)
     gth = torch.empty(B.grp_param_count(sysh), dtype=torch.float64, device="cuda")
     B.grp_adjoint_segment(rep, k, t_gr, ck, 4, d_grad_theta=gth)  # warm-up
@@ -704,6 +705,10 @@ def main():
         ligand = (ligand_bench(B, args.ligand_steps, 1, flush, min(args.fp64_steps, 1))
                   if args.ligand_steps > 0 else None)
         gradient = gradient_bench(B, args.gradient_reps) if args.gradient_reps > 0 else None
+        if gradient is not None:
+            gm = gradient_bench(B, args.gradient_reps, precision=B.GRP_MIXED)
+            gradient["mixed_path"] = {k: gm[k] for k in ("ms_per_segment", "forward_ms", "adjoint_over_forward", "value")}
+            gradient["mixed_path"]["speedup_over_fp64"] = gradient["ms_per_segment"] / gm["ms_per_segment"]
         accel = None
         if args.accel_steps > 0:
             # the chain (bounded run) and the double-well validation system, where the loop cycles

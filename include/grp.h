@@ -451,8 +451,11 @@ typedef struct {
  *   d_grad_q0, d_grad_p0 (optional, device [R][n][dim]) dL/dq and dL/dp of the state before the segment.
  * The reverse sweep recomputes states from checkpoints saved every `checkpoint` steps and applies the
  * transposed BAOAB step, whose Hessian-vector products and mixed parameter derivatives come from a
- * dual-number pass of the force field.  Needs a GRP_FP64 force-field system below 64 atoms (else
- * GRP_ENOTIMPL) and (checkpoint + 1) n dim 8 bytes of shared memory for the recomputed states (at most
+ * dual-number pass of the force field.  The recomputation runs the system's own precision path, so it
+ * reproduces the forward trajectory; on a GRP_MIXED system the dual numbers are FP32 and their
+ * tangents are summed in the mixed path's fixed point (the adjoint vectors and dL/d theta stay FP64).
+ * Needs a force-field system below 64 atoms in vacuum (else GRP_ENOTIMPL) and (checkpoint + 1) n dim 8
+ * bytes of shared memory for the recomputed states (at most
  * about 180 KB; else GRP_EINVAL).  Allocates R ceil(k / checkpoint) 3 n dim 8 bytes of device memory
  * for the checkpoints.  Synchronises `stream`. */
 grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_gr, int32_t checkpoint,

@@ -398,6 +398,32 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       bd[b] = make_double2(d->bond_k[b], d->bond_r0[b]);
       bf[b] = make_float2((float)bd[b].x, (float)bd[b].y);
     }
+    // Large systems evaluate their bonds straight from these arrays, 32 consecutive bonds per warp: order
+    // them in greedy rounds of atom-disjoint bonds, so that a warp's fixed-point additions go to distinct
+    // atoms (the elastic network's springs come atom by atom, and consecutive springs of one atom made
+    // the lanes of a warp add to the same words: 90,000 -> 63,000 cycles per step of the ligand's
+    // bonded pass).  The sums are exact, so the order changes no result.
+    if (D.tiled && d->n_bonds > 1) {
+      std::vector<int> left(d->n_bonds), order;
+      for (int b = 0; b < d->n_bonds; ++b) left[b] = b;
+      std::vector<int> used(n, -1);
+      for (int round = 0; !left.empty(); ++round) {
+        std::vector<int> later;
+        for (int b : left) {
+          if (used[bij[b].x] == round || used[bij[b].y] == round) { later.push_back(b); continue; }
+          used[bij[b].x] = used[bij[b].y] = round;
+          order.push_back(b);
+        }
+        left.swap(later);
+      }
+      std::vector<int2> bij2(order.size());
+      std::vector<double2> bd2(order.size());
+      std::vector<float2> bf2(order.size());
+      for (size_t u = 0; u < order.size(); ++u) { bij2[u] = bij[order[u]]; bd2[u] = bd[order[u]]; bf2[u] = bf[order[u]]; }
+      bij.swap(bij2);
+      bd.swap(bd2);
+      bf.swap(bf2);
+    }
     D.n_bonds = d->n_bonds;
     UP(bij.data(), bij.size(), &D.bond_ij);
     UP(bd.data(), bd.size(), &D.bond_d);
@@ -543,9 +569,22 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
           }
         }
       } else {  // the solvent term includes the excluded pairs, which the Verlet lists leave out
+        std::vector<uint32_t> all;
         for (int i = 0; i < n; ++i)
           for (int j = i + 1; j < n; ++j)
-            if (s->excl[(size_t)i * n + j]) gx.push_back((uint32_t)i | ((uint32_t)j << 16));
+            if (s->excl[(size_t)i * n + j]) all.push_back((uint32_t)i | ((uint32_t)j << 16));
+        // in greedy rounds of atom-disjoint pairs, as the bonds of large systems
+        std::vector<int> used(n, -1);
+        for (int round = 0; !all.empty(); ++round) {
+          std::vector<uint32_t> later;
+          for (uint32_t pk : all) {
+            const int i = (int)(pk & 0xFFFFu), j = (int)(pk >> 16);
+            if (used[i] == round || used[j] == round) { later.push_back(pk); continue; }
+            used[i] = used[j] = round;
+            gx.push_back(pk);
+          }
+          all.swap(later);
+        }
       }
       D.gb = 1;
       D.n_gb_xpairs = (int)gx.size();
@@ -1918,9 +1957,8 @@ extern "C" grp_status grp_adjoint_segment(grp_replicas *r, int32_t k, int32_t t_
     return fail(GRP_EINVAL, "grp_adjoint_segment: bad argument");
   const grp_system *s = r->sys;
   const SysDev &D = s->dev;
-  if (D.potential != GRP_POT_FORCE_FIELD || D.precision != GRP_FP64 || D.tiled || D.gb || D.n_cons ||
-      D.coulomb_rf == 2)
-    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs an FP64 force-field system of fewer than 64 atoms in vacuum");
+  if (D.potential != GRP_POT_FORCE_FIELD || D.tiled || D.gb || D.n_cons || D.coulomb_rf == 2)
+    return fail(GRP_ENOTIMPL, "grp_adjoint_segment: needs a force-field system of fewer than 64 atoms in vacuum");
   if (loss->obs < 0 || loss->obs >= D.n_obs) return fail(GRP_EINVAL, "grp_adjoint_segment: bad observable index");
   const int kind = D.obs_kind[loss->obs];
   if (kind != GRP_OBS_COORD && kind != GRP_OBS_GROUP_DISTANCE && kind != GRP_OBS_DIHEDRAL)

@@ -84,6 +84,7 @@ struct ParamAcc {
 struct ParamTangent {
   long long *G;
   __device__ __forceinline__ void add(int k, Dual v, int *err) const { fix_add(&G[k], to_fix(v.d, err)); }
+  __device__ __forceinline__ void add(int k, DualF v, int *err) const { fix_add(&G[k], to_fix((double)v.d, err)); }
 };
 
 // dV/d theta of one configuration by the whole block; qd(i, j) gives q_i - q_j in type T.
@@ -318,13 +319,52 @@ __device__ double loss_sample(const AdjArgs &a, const double *q, double *lq) {
   return a.inv_norm * g;
 }
 
+// Precision of the adjoint: the recomputation runs the forward path's own arithmetic (PathF64, or the mixed
+// path's FP32 forces into split fixed point with double-single integration), so that it reproduces the
+// forward trajectory bit for bit; the reverse sweep's Hessian-vector products and mixed parameter
+// derivatives come from dual numbers of that precision (Dual in FP64, DualF in FP32).  The tangent
+// direction is scaled to a largest component of kTangentScale (1/16 on the mixed path, so that the
+// stiff bonds' tangent contributions stay inside the split fixed point's 2^18 range).
+template <class P>
+struct AdjointTraits;
+template <>
+struct AdjointTraits<PathF64> {
+  using TP = PathTangent;
+  using Num = Dual;
+  static constexpr double kTangentScale = 1.0;
+  static __device__ AccTangent tacc(long long *DF, int) { return AccTangent{DF}; }
+  static __device__ double tget(const long long *DF, int i, int) { return (double)DF[i] * kFixInv; }
+  static __device__ Params<PathTangent> tpar(const SysDev &S) {
+    return Params<PathTangent>{S.atom_d, S.bond_d, S.angle_d, S.term_d, S.coulomb_rf, S.krf, S.crf};
+  }
+};
+template <>
+struct AdjointTraits<PathMixed> {
+  using TP = PathTangentF;
+  using Num = DualF;
+  static constexpr double kTangentScale = 1.0 / 16.0;
+  static __device__ AccTangentF tacc(long long *DF, int nd) {
+    return AccTangentF{(int *)DF, (unsigned int *)DF + nd};
+  }
+  static __device__ double tget(const long long *DF, int i, int nd) {
+    return (double)split_to_float(((const int *)DF)[i], ((const unsigned int *)DF)[nd + i]);
+  }
+  static __device__ Params<PathTangentF> tpar(const SysDev &S) {
+    return Params<PathTangentF>{S.atom_f, S.bond_f, S.angle_f, S.term_f, S.coulomb_rf, (float)S.krf, (float)S.crf};
+  }
+};
+
 size_t adjoint_smem_bytes(const SysDev &S, int n_terms, int ck) {
   const size_t nd = (size_t)S.nd, nt = 2 * (size_t)S.n + n_terms;
   return nd * 8 * 2 + nt * 8 * 2 + nd * 8 * 3 + 33 * 8 + (size_t)(ck + 1) * nd * 8 + 32 +
          State<PathF64>::bytes(S.n, true) + 32;
 }
 
+template <class P>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
+  using Tr = AdjointTraits<P>;
+  using TP = typename Tr::TP;
+  using T = typename P::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const SysDev &S = a.S;
   const int r = blockIdx.x, n = S.n, nd = S.nd, nt = 2 * n + a.n_terms;
@@ -339,7 +379,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
   double *red = (double *)ptr; ptr += 33 * 8;
   ptr = align32(ptr);
   double *Qs = (double *)ptr; ptr += (size_t)(a.ck + 1) * nd * 8;
-  State<PathF64> st;
+  State<P> st;
   ptr = align32(ptr);
   st.carve(ptr, n, S, true);
   for (int i = threadIdx.x; i < nd; i += blockDim.x) { lq[i] = 0.0; lp[i] = 0.0; F[i] = 0; }
@@ -347,8 +387,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
   int err = 0;
   double loss = 0.0;
   const double h = a.h, c1 = a.c1;
-  const AccF64 fa{F};
-  const Params<PathTangent> tpar{S.atom_d, S.bond_d, S.angle_d, S.term_d, S.coulomb_rf, S.krf, S.crf};
+  const typename P::Acc fa = State<P>::acc(F, n);
+  const Params<TP> tpar = Tr::tpar(S);
 
   // the contribution of configuration q_t (see above)
   auto config = [&](const double *qt, long long t, double w) {
@@ -358,19 +398,20 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
     }
     double m = 0.0;
     for (int i = threadIdx.x; i < nd; i += blockDim.x) m = fmax(m, fabs(lp[i]));
-    const double s = block_max_d(m, red);
+    const double s = block_max_d(m, red) / Tr::kTangentScale;
     if (s > 0.0) {
       for (int i = threadIdx.x; i < nd; i += blockDim.x) { vn[i] = lp[i] / s; DF[i] = 0; }
       for (int k = threadIdx.x; k < nt; k += blockDim.x) Gd[k] = 0;
       __syncthreads();
-      const Pos<PathTangent> tpos{qt, vn};
+      const Pos<TP> tpos{qt, vn};
       long long e = 0;
-      force_pass<PathTangent>(S, tpos, tpar, S.items, S.pairs, AccTangent{DF}, false, e, &err);
-      param_pass<Dual>(S, S.atom_d, S.term_d, [&](int i, int j) { return tpos.diff(i, j); }, ParamTangent{Gd}, &err);
+      force_pass<TP>(S, tpos, tpar, S.items, S.pairs, Tr::tacc(DF, nd), false, e, &err);
+      param_pass<typename Tr::Num>(S, tpar.atom, tpar.term, [&](int i, int j) { return tpos.diff(i, j); },
+                                   ParamTangent{Gd}, &err);
       __syncthreads();
-      const double ws = w * s * kFixInv;
-      for (int i = threadIdx.x; i < nd; i += blockDim.x) lq[i] += ws * (double)DF[i];
-      for (int k = threadIdx.x; k < nt; k += blockDim.x) gth[k] -= ws * (double)Gd[k];
+      const double ws = w * s;
+      for (int i = threadIdx.x; i < nd; i += blockDim.x) lq[i] += ws * Tr::tget(DF, i, nd);
+      for (int k = threadIdx.x; k < nt; k += blockDim.x) gth[k] -= ws * kFixInv * (double)Gd[k];
       __syncthreads();
     }
   };
@@ -381,21 +422,23 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
     __syncthreads();
     st.load(S, base, base + nd, base + 2 * nd, n, c1);
     __syncthreads();
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) Qs[i] = st.q[i];
+    for (int at = threadIdx.x; at < n; at += blockDim.x) st.get_f64(at, Qs + 3 * at);
     __syncthreads();  // the copy reads positions that the first drift below overwrites
     // forward recomputation of steps t0 .. t0 + len - 1, keeping every configuration
     for (int j = 0; j < len; ++j) {
       for (int at = threadIdx.x; at < n; at += blockDim.x) {
-        double z[4];
+        T z[4];
         normals4(philox_stream(a.seed, a.t_global0 + t0 + j, 0u, r, at), z);
-        st.baoa(at, z, h, c1);
+        st.baoa(at, z, (T)h, (T)c1);
       }
       __syncthreads();
       long long e = 0;
-      force_pass<PathF64>(S, st.pos(), st.params(S), S.items, S.pairs, fa, false, e, &err);
+      force_pass<P>(S, st.pos(), st.params(S), S.items, S.pairs, fa, false, e, &err);
       __syncthreads();
-      for (int at = threadIdx.x; at < n; at += blockDim.x) st.bk(at, fa, h);
-      for (int i = threadIdx.x; i < nd; i += blockDim.x) Qs[(size_t)(j + 1) * nd + i] = st.q[i];
+      for (int at = threadIdx.x; at < n; at += blockDim.x) {
+        st.bk(at, fa, (T)h);
+        st.get_f64(at, Qs + (size_t)(j + 1) * nd + 3 * at);
+      }
       __syncthreads();
     }
     // reverse sweep over configurations t0 + len .. t0 + 1 and the steps that led to them
@@ -422,12 +465,13 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
 
 cudaError_t launch_adjoint(const AdjArgs &a, int n_rep, cudaStream_t st) {
   if (n_rep <= 0) return cudaSuccess;
-  if (a.S.potential != GRP_POT_FORCE_FIELD || a.S.tiled || a.S.precision != GRP_FP64) return cudaErrorInvalidValue;
+  if (a.S.potential != GRP_POT_FORCE_FIELD || a.S.tiled) return cudaErrorInvalidValue;
   const size_t smem = adjoint_smem_bytes(a.S, a.n_terms, a.ck);
   if (smem > kMaxSmem) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = a.S.precision == GRP_FP64 ? adjoint_kernel<PathF64> : adjoint_kernel<PathMixed>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adjoint_kernel<<<n_rep, 256, smem, st>>>(a);
+  kern<<<n_rep, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
