@@ -398,6 +398,14 @@ def ligand_bench(B, steps, warmup, flush, fp64_steps):
     out["solvent_obc2"] = {"value": units * len(t_gb) / (float(np.sum(t_gb)) / 1e3),
                            "ms_per_step": float(np.mean(t_gb)),
                            "solvent_pairs": "Verlet-list pairs and excluded pairs within 1.2 nm, 5 passes per step"}
+    # the paper's protein-ligand setup in full: OBC II solvent and constrained hydrogens on the ligand
+    sh = W.solvated(W.ligand_receptor_h(n_replicas=R))
+    step_h = Step(B, sh, B.GRP_MIXED, R, SEED, 0, omega=0)
+    t_h = time_steps(step_h, max(1, steps // 2), 1, flush, step_h.stream)
+    out["solvent_obc2_constrained_h"] = {
+        "workload": f"{sh.name}_r{R} ({sh.n_atoms} atoms, {len(sh.constraints)} constrained hydrogen bonds, OBC II)",
+        "value": R * sh.n_atoms * sh.t_check * len(t_h) / (float(np.sum(t_h)) / 1e3),
+        "ms_per_step": float(np.mean(t_h))}
     if fp64_steps > 0:
         step64 = Step(B, s, B.GRP_FP64, R, SEED, 0, omega=0)
         t64 = time_steps(step64, fp64_steps, 1, flush, step64.stream)

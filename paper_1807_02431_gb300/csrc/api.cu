@@ -308,6 +308,19 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
       ad[i] = make_double4(0.5 * d->sigma[i], std::sqrt(d->epsilon[i]), d->charge[i] * ck, 1.0 / d->mass[i]);
       af[i] = make_float4((float)ad[i].x, (float)ad[i].y, (float)ad[i].z, (float)ad[i].w);
     }
+    // noise amplitudes sqrt((1 - c1^2) kT m) per atom, computed on the device as the states compute them
+    {
+      std::vector<double> zd(n, 0.0);
+      std::vector<float> zf(n, 0.f);
+      UP(zd.data(), (size_t)n, &D.sd_d);
+      UP(zf.data(), (size_t)n, &D.sd_f);
+      const cudaError_t e = launch_noise_sd(D, std::exp(-d->gamma * d->dt), const_cast<double *>(D.sd_d),
+                                            const_cast<float *>(D.sd_f), 0);
+      if (e != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        grp_destroy_system(s);
+        return fail(GRP_ECUDA, "noise amplitude table: %s", cudaGetErrorString(e));
+      }
+    }
     UP(ad.data(), (size_t)n, &D.atom_d);
     UP(af.data(), (size_t)n, &D.atom_f);
     // explicit list of non-excluded pairs
@@ -598,10 +611,14 @@ extern "C" grp_status grp_create_system(const grp_system_desc *d, grp_system **o
     // bond constraints: independent groups (connected components of the constraint graph)
     if (d->n_constraints > 0) {
       if (!d->constraint_atoms || !d->constraint_length) { grp_destroy_system(s); return fail(GRP_EINVAL, "constraint arrays null"); }
-      if (D.tiled || D.coulomb_rf || D.gb) {
+      // the item table (eps = 4r, no solvent), or Verlet lists (eps = 4r, with or without the solvent: the
+      // paper's protein-ligand setup)
+      const bool con_items = !D.tiled && !D.coulomb_rf && !D.gb;
+      const bool con_list = D.use_list && !D.coulomb_rf;
+      if (!con_items && !con_list) {
         grp_destroy_system(s);
-        return fail(GRP_ENOTIMPL, "bond constraints are implemented for systems of fewer than 64 atoms with the eps = 4r "
-                                  "Coulomb model and no implicit solvent");
+        return fail(GRP_ENOTIMPL, "bond constraints are implemented with the eps = 4r Coulomb model for systems of fewer "
+                                  "than 64 atoms without implicit solvent, and for systems with Verlet lists");
       }
       if (!(d->constraint_tol > 0) || d->constraint_max_iter < 1) {
         grp_destroy_system(s);

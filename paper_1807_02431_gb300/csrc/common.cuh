@@ -34,6 +34,8 @@ struct SysDev {
   const double *mass;      // [n]
   const double4 *atom_d;   // [n] (sigma/2, sqrt(eps), q sqrt(k_e/4), 1/m)
   const float4 *atom_f;
+  const double *sd_d;      // [n] noise amplitudes sqrt((1 - c1^2) kT m) of the O step (large systems)
+  const float *sd_f;
   int n_pairs;             // explicit non-excluded pair list (i | j << 16), i < j
   const uint32_t *pairs;
   int n_items;             // force-field work items, (kind << 28) | index, each kind padded to a

@@ -347,16 +347,21 @@ __device__ __forceinline__ void pair_a_step_ds(const SysDev &S, const PairDsCons
   if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
 }
 
-// B, A, O, A of one constrained group (the force of the previous step in the state's f, the noise of
-// this step in xs[3 atom + axis]).
-template <class P>
-__device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P::T *xs, double h, double c1,
-                         int *err, const PairDsConst *kds = nullptr) {
+// B, A, O, A of one constrained group (the force of the previous step in the state's f; noise(atom, z)
+// writes the three normals of this step for an atom: from a noise batch, or drawn from the counter-based
+// stream, which give the same values).
+template <class P, class Noise>
+__device__ void con_baoa(const SysDev &S, State<P> &st, int g, Noise noise, double h, double c1, int *err,
+                         const PairDsConst *kds = nullptr) {
+  using T = typename P::T;
   if constexpr (P::kMixed) {
     if (kds && S.cgroup_off[g + 1] - S.cgroup_off[g] == 1) {  // one bond, double-single
       const PairDsConst &K = kds[g];
       ConPairDs C;
       pair_load_ds(S, st, g, C);
+      T za[3], zb[3];
+      noise(C.a, za);
+      noise(C.b, zb);
       const float hf = (float)h, ih = (float)(1.0 / h), c1f = (float)c1;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
@@ -367,8 +372,8 @@ __device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P:
       pair_a_step_ds(S, K, C, ih, err);
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        C.p[0][x] = ds_add(ds_scale(C.p[0][x], c1f), K.sa * xs[3 * C.a + x]);
-        C.p[1][x] = ds_add(ds_scale(C.p[1][x], c1f), K.sb * xs[3 * C.b + x]);
+        C.p[0][x] = ds_add(ds_scale(C.p[0][x], c1f), K.sa * za[x]);
+        C.p[1][x] = ds_add(ds_scale(C.p[1][x], c1f), K.sb * zb[x]);
       }
       if (!pair_rattle_ds(S, K, C)) *err |= kErrConstraint;
       pair_a_step_ds(S, K, C, ih, err);
@@ -387,9 +392,12 @@ __device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P:
     if (!pair_rattle(S, C)) *err |= kErrConstraint;
     pair_a_step(S, C, h, ih, err);
     const double sa = noise_scale(c1, S.kT, S.mass[C.a]), sb = noise_scale(c1, S.kT, S.mass[C.b]);
+    T za[3], zb[3];
+    noise(C.a, za);
+    noise(C.b, zb);
     for (int x = 0; x < 3; ++x) {
-      C.p[0][x] = c1 * C.p[0][x] + sa * (double)xs[3 * C.a + x];
-      C.p[1][x] = c1 * C.p[1][x] + sb * (double)xs[3 * C.b + x];
+      C.p[0][x] = c1 * C.p[0][x] + sa * (double)za[x];
+      C.p[1][x] = c1 * C.p[1][x] + sb * (double)zb[x];
     }
     if (!pair_rattle(S, C)) *err |= kErrConstraint;
     pair_a_step(S, C, h, ih, err);
@@ -409,7 +417,9 @@ __device__ void con_baoa(const SysDev &S, State<P> &st, int g, const typename P:
   con_a_step(S, G, h, err);
   for (int u = 0; u < G.na; ++u) {
     const double sd = noise_scale(c1, S.kT, S.mass[G.atom[u]]);
-    for (int x = 0; x < 3; ++x) G.p[u][x] = c1 * G.p[u][x] + sd * (double)xs[3 * G.atom[u] + x];
+    T z[3];
+    noise(G.atom[u], z);
+    for (int x = 0; x < 3; ++x) G.p[u][x] = c1 * G.p[u][x] + sd * (double)z[x];
   }
   if (!con_rattle(S, G)) *err |= kErrConstraint;
   con_a_step(S, G, h, err);

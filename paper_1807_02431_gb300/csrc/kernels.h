@@ -48,6 +48,8 @@ struct SegConfig {
 constexpr size_t kMaxSmem = 227 * 1024;
 
 SegConfig segment_config(const SysDev &S, int threads_hint);
+// The noise amplitude of every atom in FP64 and FP32 (the system's tables for lean replica states).
+cudaError_t launch_noise_sd(const SysDev &S, double c1, double *sd_d, float *sd_f, cudaStream_t st);
 cudaError_t launch_segment(const SegArgs &a, const SegConfig &cfg, cudaStream_t st);
 
 // State functions at the current state (FP64), writing labels/exited; exit key as above.

@@ -310,6 +310,21 @@ struct ObsAcc<PathMixed> {
   }
 };
 
+// Whether an atom of constraint group g has moved more than skin/2 since the last Verlet-list build.
+template <class P>
+__device__ __forceinline__ int group_moved(const SysDev &S, const State<P> &st, int g, const float4 *qref) {
+  int mv = 0;
+  for (int t = S.cgroup_aoff[g]; t < S.cgroup_aoff[g + 1]; ++t) {
+    const int at = S.cgroup_atoms[t];
+    float x[3];
+    st.get_f32(at, x);
+    const float4 o = qref[at];
+    const float dx = x[0] - o.x, dy = x[1] - o.y, dz = x[2] - o.z;
+    mv |= dx * dx + dy * dy + dz * dz > S.half_skin2;
+  }
+  return mv;
+}
+
 // ------------------------------------------------------------------------------------------------
 // One segment of replica r by the whole thread block (the block's shared memory holds its state).
 // Force-field paths of the segment kernel, fixed at compile time so that each kernel carries only
@@ -346,9 +361,10 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   T *xi = (T *)ptr; ptr += (size_t)NB * nd * sizeof(T);  // NB = 0: noise drawn inline per atom
   float *boxes = nullptr;  // tile bounding boxes, only with tiles and a cutoff
   if (S.tiled && S.cutoff2 > 0) { boxes = (float *)ptr; ptr += (size_t)S.n_tiles * 6 * 4; }
+  // kFF = 5 (Verlet lists only): solvent and bond constraints together, the paper's protein-ligand setup
   constexpr bool kGB = kMode == kModeItems && kFF == 2;
-  constexpr bool kGBL = kMode == kModeList && kFF == 2;  // solvent with a cutoff on the Verlet list
-  constexpr bool kCon = kMode == kModeItems && kFF == 3;
+  constexpr bool kGBL = kMode == kModeList && (kFF == 2 || kFF == 5);  // solvent with a cutoff on the list
+  constexpr bool kCon = (kMode == kModeItems && kFF == 3) || (kMode == kModeList && (kFF == 3 || kFF == 5));
   constexpr bool kPME = kMode == kModeItems && kFF == 4;
   constexpr int kRF = kFF == 4 ? 2 : (kFF >= 2 ? 0 : kFF);
   GbScratch<P> gbs;  // implicit solvent (item-table systems only)
@@ -436,9 +452,25 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
         }
       }
       if constexpr (kCon)
-        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) con_baoa<P>(S, st, g, xs, a.h, a.c1, &err, kds);
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) {
+          con_baoa<P>(S, st, g, [&](int at, T z3[3]) { z3[0] = xs[3 * at]; z3[1] = xs[3 * at + 1]; z3[2] = xs[3 * at + 2]; },
+                      a.h, a.c1, &err, kds);
+          if (use_list) moved |= group_moved(S, st, g, qref);
+        }
     } else {
+      if constexpr (kCon)  // constrained atoms: their groups, with the noise drawn from the same stream
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) {
+          con_baoa<P>(S, st, g, [&](int at, T z3[3]) {
+            T z[4];
+            normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r + a.rep0, at), z);
+            z3[0] = z[0]; z3[1] = z[1]; z3[2] = z[2];
+          }, a.h, a.c1, &err, kds);
+          if (use_list) moved |= group_moved(S, st, g, qref);
+        }
       for (int at = threadIdx.x; at < n; at += kThreads) {
+        if constexpr (kCon) {
+          if (S.con_atom[at]) continue;
+        }
         T z[4];
         normals4(philox_stream(a.seed, a.t_global0 + s, 0u, r + a.rep0, at), z);
         st.baoa(at, z, h, c1);
@@ -504,9 +536,17 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
         }
     } else {  // the same thread owns each atom in both halves of the step
       for (int at = threadIdx.x; at < n; at += kThreads) {
+        if constexpr (kCon) {
+          if (S.con_atom[at]) continue;
+        }
         const T ke = st.bk(at, fa, h);
         if (sample) k_fix += fa.efix(ke, &err);
       }
+      if constexpr (kCon)
+        for (int g = threadIdx.x; g < S.n_cgroups; g += kThreads) {
+          const double ke = con_b<P>(S, st, fa, g, a.h, &err, kds);
+          if (sample) k_fix += fa.efix((T)ke, &err);
+        }
     }
     if (sample) {
       block_sum2_ll(e_fix, k_fix, red);
@@ -543,7 +583,11 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) ff_segment_kernel(con
 // decreasing system size, so that the largest replicas start first and the small ones fill in.
 // Each unit's launch arguments are copied into shared memory before its segment runs.
 template <class P>
-__global__ void __launch_bounds__(512, 1) ff_segment_batch_kernel(const SegArgs *runs, const uint2 *units,
+#ifndef GRP_BATCH_MAXT
+#define GRP_BATCH_MAXT 512
+#define GRP_BATCH_MINB 1
+#endif
+__global__ void __launch_bounds__(GRP_BATCH_MAXT, GRP_BATCH_MINB) ff_segment_batch_kernel(const SegArgs *runs, const uint2 *units,
                                                                   int n_units, int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SegArgs sa;
@@ -623,6 +667,22 @@ __global__ void __launch_bounds__(64) dw_segment_kernel(const SegArgs a) {
   }
 }
 
+// Noise amplitudes of every atom (the tables that lean replica states read), with the arithmetic of
+// the states that keep them in shared memory, so that both give the same bits.
+__global__ void noise_sd_kernel(int n, double c1, double kT, const double *mass, double *sd_d, float *sd_f) {
+  const int at = blockIdx.x * blockDim.x + threadIdx.x;
+  if (at >= n) return;
+  const double v = noise_scale(c1, kT, mass[at]);
+  sd_d[at] = v;
+  sd_f[at] = (float)v;
+}
+
+cudaError_t launch_noise_sd(const SysDev &S, double c1, double *sd_d, float *sd_f, cudaStream_t st) {
+  if (S.n <= 0) return cudaSuccess;
+  noise_sd_kernel<<<(S.n + 127) / 128, 128, 0, st>>>(S.n, c1, S.kT, S.mass, sd_d, sd_f);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------------------
 static size_t ff_smem_bytes(const SysDev &S, int pairs_in_smem, int noise_batch, int lean) {
   const int n = S.n;
@@ -660,7 +720,8 @@ SegConfig segment_config(const SysDev &S, int threads_hint) {
   // lines per transform pass take one round of the block; the constraint groups run on one warp, and
   // two blocks per SM run two such warps at once and 256 replicas in one wave); the FP64 transforms and
   // groups need the registers of the 512-thread variant
-  if ((S.coulomb_rf == 2 || S.n_cons > 0) && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320) t = 320;
+  if ((S.coulomb_rf == 2 || S.n_cons > 0) && S.precision != GRP_FP64 && threads_hint <= 0 && t > 320 && !S.tiled)
+    t = 320;
   c.threads = t;
   // noise for up to 64 steps at a time (one barrier per batch), within 32 KB; beyond 16 steps only where
   // the block keeps to half an SM's shared memory, so that a larger batch costs no occupancy (the
@@ -699,7 +760,9 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
             : mode == kModeTiles
                   ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles, 0> : ff_segment_kernel<P, 512, 1, kModeTiles, 0>)
                   : (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 1> : ff_segment_kernel<P, 512, 1, kModeList, 1>)
+                     : (gb && con) ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 5> : ff_segment_kernel<P, 512, 1, kModeList, 5>)
                      : gb ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 2> : ff_segment_kernel<P, 512, 1, kModeList, 2>)
+                     : con ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 3> : ff_segment_kernel<P, 512, 1, kModeList, 3>)
                           : (small ? ff_segment_kernel<P, 320, 2, kModeList, 0> : ff_segment_kernel<P, 512, 1, kModeList, 0>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;

@@ -42,7 +42,8 @@ struct State<PathF64> {
   double *q, *p, *f, *sd;  // [3n], [3n], [3n], [n]
   const double4 *atom;     // [n] parameters: a shared-memory copy, or the global table when lean
   bool own_atom;
-  static size_t bytes(int n, bool lean) { return (size_t)n * (72 + 8 + (lean ? 0 : 32)); }
+  // lean: the atom parameters and the noise amplitudes are read from the system's global tables
+  static size_t bytes(int n, bool lean) { return (size_t)n * (72 + (lean ? 0 : 8 + 32)); }
   __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
     own_atom = !lean;
     if (lean) atom = S.atom_d;
@@ -50,14 +51,15 @@ struct State<PathF64> {
     q = (double *)ptr; ptr += (size_t)n * 24;
     p = (double *)ptr; ptr += (size_t)n * 24;
     f = (double *)ptr; ptr += (size_t)n * 24;
-    sd = (double *)ptr; ptr += (size_t)n * 8;
+    if (lean) sd = const_cast<double *>(S.sd_d);
+    else { sd = (double *)ptr; ptr += (size_t)n * 8; }
   }
   static __device__ AccF64 acc(long long *F, int n) { return AccF64{F}; }
   __device__ void load(const SysDev &S, const double *gq, const double *gp, const double *gf, int n, double c1) {
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) { q[i] = gq[i]; p[i] = gp[i]; f[i] = gf[i]; }
     for (int at = threadIdx.x; at < n; at += blockDim.x) {
       if (own_atom) const_cast<double4 *>(atom)[at] = S.atom_d[at];
-      sd[at] = noise_scale(c1, S.kT, S.mass[at]);
+      if (own_atom) sd[at] = noise_scale(c1, S.kT, S.mass[at]);
     }
   }
   __device__ void store(double *gq, double *gp, double *gf, int n, int *err) const {
@@ -120,7 +122,7 @@ struct State<PathMixed> {
   float *f, *sd;     // [3n], [n]
   const float4 *atom;  // [n] parameters: a shared-memory copy, or the global table when lean
   bool own_atom;
-  static size_t bytes(int n, bool lean) { return (size_t)n * (32 + 24 + 12 + 4 + (lean ? 0 : 16)); }
+  static size_t bytes(int n, bool lean) { return (size_t)n * (32 + 24 + 12 + (lean ? 0 : 4 + 16)); }
   __device__ void carve(unsigned char *&ptr, int n, const SysDev &S, bool lean) {
     own_atom = !lean;
     qh = (float4 *)ptr; ptr += (size_t)n * 16;
@@ -130,7 +132,8 @@ struct State<PathMixed> {
     ph = (float *)ptr; ptr += (size_t)n * 12;
     pl = (float *)ptr; ptr += (size_t)n * 12;
     f = (float *)ptr; ptr += (size_t)n * 12;
-    sd = (float *)ptr; ptr += (size_t)n * 4;
+    if (lean) sd = const_cast<float *>(S.sd_f);
+    else { sd = (float *)ptr; ptr += (size_t)n * 4; }
   }
   // the 8 bytes per force component hold the hi words [3n] then the lo words [3n]
   static __device__ AccMixed acc(long long *F, int n) {
@@ -144,7 +147,7 @@ struct State<PathMixed> {
       qh[at] = make_float4(x.hi, y.hi, z.hi, pa.x);  // fourth words: sigma/2 and sqrt(eps) (nb_params)
       ql[at] = make_float4(x.lo, y.lo, z.lo, pa.y);
       if (own_atom) const_cast<float4 *>(atom)[at] = pa;
-      sd[at] = (float)noise_scale(c1, S.kT, S.mass[at]);
+      if (own_atom) sd[at] = (float)noise_scale(c1, S.kT, S.mass[at]);
     }
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
       const ds v = ds_from_double(gp[i]);

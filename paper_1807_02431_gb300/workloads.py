@@ -569,6 +569,80 @@ def ligand_receptor(n_receptor: int = 2000, n_ligand: int = 30, seed: int = 1807
     return s
 
 
+def ligand_receptor_h(n_replicas: int = 1024, seed: int = 1807, dyn_seed: int = 2431) -> System:
+    """The ligand-receptor system with one hydrogen (1.008 amu) on every ligand bead, its bond of
+    0.109 nm held by a constraint (the paper's protein-ligand setup constrains the bonds of hydrogens,
+    Section 4.2): 2,030 + 30 atoms.  As in ``chain_h``: each hydrogen carries 0.1 e taken from its bead,
+    LJ sigma 0.25 nm and eps 0.1 kJ/mol, angles H-C-C of k = 300 kJ/mol/rad^2 at 109.5 deg with the bead's
+    neighbours, 1-2 and 1-3 pairs through the hydrogen excluded.  A hydrogen sits opposite the bisector
+    of its bead's bonds, turned about the bead's neighbour axis to the 10-deg step that keeps it furthest
+    (in units of sigma_ij, at least 0.8) from every atom it interacts with.  Groups, states and observables are the ligand's
+    (the centres of mass are those of the heavy beads)."""
+    base = ligand_receptor(n_replicas=n_replicas, seed=seed, dyn_seed=dyn_seed)
+    nb = base.n_atoms
+    L = np.asarray(base.groups[0])
+    nl = len(L)
+    x = base.q0
+    sig_h = 0.25
+    excl = {tuple(sorted(e)) for e in base.excl.tolist()}
+    hpos = np.zeros((nl, 3))
+    for k, i in enumerate(L):
+        nbrs = [L[m] for m in (k - 1, k + 1) if 0 <= m < nl]
+        if len(nbrs) == 2:
+            u = sum((x[i] - x[j]) / np.linalg.norm(x[i] - x[j]) for j in nbrs)
+            axis = x[nbrs[1]] - x[nbrs[0]]
+        else:  # an end bead: 109.5 deg from its one bond
+            b = (x[nbrs[0]] - x[i]) / np.linalg.norm(x[nbrs[0]] - x[i])
+            perp = np.cross(b, [0.3, 0.5, 0.8])
+            perp /= np.linalg.norm(perp)
+            u = math.cos(math.radians(109.5)) * b - math.sin(math.radians(109.5)) * perp
+            axis = b
+        u /= np.linalg.norm(u)
+        axis /= np.linalg.norm(axis)
+        skip = {i} | set(nbrs)  # the bead and its neighbours are excluded partners of the hydrogen
+        others = [j for j in range(nb) if j not in skip]
+        best, best_ratio = None, -1.0
+        for turn in range(36):  # the turn about the axis that keeps the hydrogen furthest from clashes
+            a = math.radians(10.0 * turn)
+            v = u * math.cos(a) + np.cross(axis, u) * math.sin(a) + axis * np.dot(axis, u) * (1 - math.cos(a))
+            ph = x[i] + 0.109 * v
+            ratio = (np.linalg.norm(x[others] - ph, axis=1) / (0.5 * (base.sigma[others] + sig_h))).min()
+            if k:
+                ratio = min(ratio, (np.linalg.norm(hpos[:k] - ph, axis=1) / sig_h).min())
+            if ratio > best_ratio:
+                best, best_ratio = ph, ratio
+        if best_ratio < 0.8:
+            raise RuntimeError("no clash-free hydrogen position")
+        hpos[k] = best
+    n = nb + nl
+    H = nb + np.arange(nl)
+    mass = np.concatenate([base.mass, np.full(nl, 1.008)])
+    charge = np.concatenate([base.charge, np.full(nl, 0.1)])
+    charge[L] -= 0.1
+    sigma = np.concatenate([base.sigma, np.full(nl, sig_h)])
+    epsilon = np.concatenate([base.epsilon, np.full(nl, 0.1)])
+    angles = [list(a) for a in base.angles]
+    angle_k = list(base.angle_k)
+    angle_t0 = list(base.angle_theta0)
+    for k, i in enumerate(L):
+        h = int(H[k])
+        excl.add((min(i, h), max(i, h)))
+        for m in (k - 1, k + 1):
+            if 0 <= m < nl:
+                angles.append([h, int(i), int(L[m])])
+                angle_k.append(300.0)
+                angle_t0.append(math.radians(109.5))
+                excl.add((min(int(L[m]), h), max(int(L[m]), h)))
+    s = dataclasses.replace(
+        base, name=f"ligand_receptor{n}h", n_atoms=n, mass=mass, charge=charge, sigma=sigma, epsilon=epsilon,
+        excl=np.array(sorted(excl), np.int32), angles=np.array(angles, np.int32), angle_k=np.array(angle_k),
+        angle_theta0=np.array(angle_t0),
+        constraints=np.stack([L, H], 1).astype(np.int32), constraint_length=np.full(nl, 0.109))
+    s.q0 = np.concatenate([x, hpos])
+    s.p0 = maxwell_boltzmann(mass, s.kT, 3, np.random.default_rng(dyn_seed))
+    return s
+
+
 def chain_gradient(n_atoms: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replicas: int = 256) -> System:
     """The chain of ``chain`` for differentiation through the dynamics: groups 0 = first bead and
     1 = last bead, and one more observable, their distance (the end-to-end distance, observable 4)."""
