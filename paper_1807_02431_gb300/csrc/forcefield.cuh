@@ -452,9 +452,11 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
   using T = typename P::T;
   const V3<T> b1 = pos.diff(a.y, a.x), b2 = pos.diff(a.z, a.y), b3 = pos.diff(a.w, a.z);
   const V3<T> n1 = cross(b1, b2), n2 = cross(b2, b3);
-  const T b2sq = dot(b2, b2), lb2 = gsqrt(b2sq);
+  // reciprocal square roots (one hardware approximation each in FP32) instead of a square root followed by
+  // a reciprocal: the dihedral terms are the longest items of small systems' force pass
+  const T b2sq = dot(b2, b2), rb2 = grsqrt(b2sq), lb2 = b2sq * rb2;
   const T x = dot(n1, n2), y = lb2 * dot(b1, n2);
-  const T irho = grcp(gsqrt(x * x + y * y));
+  const T irho = grsqrt(x * x + y * y);
   const T cph = x * irho, sph = y * irho;
   T dedphi = T(0), e = T(0);
   for (int t = terms.x; t < terms.y; ++t) {
@@ -471,7 +473,7 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
     if (want_e) e += T(tp.x) * (T(1) + cn * T(tp.z) + sn * T(tp.w));
   }
   const T n1sq = dot(n1, n1), n2sq = dot(n2, n2);
-  const T ib2 = grcp(b2sq);
+  const T ib2 = rb2 * rb2;
   const T f12 = dot(b1, b2) * ib2, f32 = dot(b3, b2) * ib2;
   const T ci = gdiv(lb2, n1sq) * dedphi;   // F_i = -dE/dphi * (-|b2| n1/|n1|^2)
   const T cl = -gdiv(lb2, n2sq) * dedphi;  // F_l = -dE/dphi * ( |b2| n2/|n2|^2)
