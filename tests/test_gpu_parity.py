@@ -5,10 +5,12 @@ position perturbation of 1e-13 grows by x1e5 (median) to x2e6 (worst of 8 replic
 (tests/test_oracle_sensitivity.py pins this).  Hence:
   FP64 path: positions within 1e-9 and momenta within 1e-8 relative (to the largest |q|, |p|) after
              1,000 steps
-             (the library's per-step differences from the oracle are ~1e-16: FMA contraction and the
-             2^-40 fixed-point quantum of the force sum); labels, exit indices, branch sources exact.
-  mixed path: FP32 forces carry ~1e-7 relative rounding every step, which the chain amplifies beyond
-             any fixed tolerance after ~500 steps; so the mixed path is held to (i) the one-step local
+             (the library's per-step differences from the oracle are ~1e-16: FMA contraction, the
+             2^-40 fixed-point quantum of the force sum, and the transcendental functions of the
+             Box-Muller normals, CUDA's log and sincospi against glibc's log, cos and sin, a few ulps
+             apart on identical Philox words); labels, exit indices, branch sources exact.
+  mixed path: FP32 forces and FP32 normals carry ~1e-7 relative rounding every step, which the chain
+             amplifies beyond any fixed tolerance after ~500 steps; so the mixed path is held to (i) the one-step local
              error (positions 1e-9, momenta 1e-6 relative), (ii) positions within 1e-4 relative after
              200 steps, (iii) labels identical to the GPU FP64 path after one 500-step exit-test
              segment from the same FP64 state for every replica whose CV is further than 2 degrees from
