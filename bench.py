@@ -32,9 +32,9 @@ from paper_1807_02431_gb300 import workloads as W  # noqa: E402
 
 WORKLOAD = "chain22_r256"
 # DRAM bytes (read + write) of one launch of the chain's segment kernel in this workload, from an ncu
-# capture of the current kernel (512,000 read, 0 written: the replicas' state is read once and stays on
+# capture of the current kernel (511,744 read, 0 written: the replicas' state is read once and stays on
 # chip); to be re-measured whenever the kernel changes.
-SEGMENT_DRAM_BYTES = 512256  # ncu dram__bytes_read + write of one chain launch (profiles/)
+SEGMENT_DRAM_BYTES = 511744  # ncu dram__bytes_read + write of one chain launch (profiles/)
 SEED = 2431
 
 

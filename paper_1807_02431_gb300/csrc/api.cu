@@ -786,7 +786,8 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
         cnt += d2 < lc2;
       }
     const size_t all = (size_t)n * (n - 1) / 2;
-    r->nbl_cap = (int)std::min(all, 2 * cnt + 1024);
+    // + the padding of the warps' partly filled chunks (16 warps of a 512-thread block, 256 entries each)
+    r->nbl_cap = (int)(std::min(all, 2 * cnt + 1024) + 16 * 256);
     AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
     if (D.gb) AL(r->gb_glob, R * (size_t)n * 2 * 8);

@@ -53,13 +53,14 @@ __device__ __forceinline__ T gb_hct(T r, T ai, T sj, T &dh) {
   const T diff = r - sj, adiff = diff < T(0) ? -diff : diff;
   const bool lfix = ai > adiff;
   const T L = lfix ? ai : adiff, dL = lfix ? T(0) : (diff >= T(0) ? T(1) : T(-1));
-  const T iL = T(1) / L, iU = T(1) / U, iL2 = iL * iL, iU2 = iU * iU, lg = glog(L / U), s2 = sj * sj, ir = T(1) / r;
+  // reciprocals by grcp (the hardware approximation in FP32, an IEEE quotient in FP64)
+  const T iL = grcp(L), iU = grcp(U), iL2 = iL * iL, iU2 = iU * iU, lg = glog(L * iU), s2 = sj * sj, ir = grcp(r);
   T h = iL - iU + T(0.25) * r * (iU2 - iL2) + T(0.5) * ir * lg + T(0.25) * s2 * ir * (iL2 - iU2);
   T d = -dL * iL2 + iU2 + T(0.25) * (iU2 - iL2) + T(0.25) * r * (T(-2) * iU2 * iU + T(2) * dL * iL2 * iL) -
         T(0.5) * ir * ir * lg + T(0.5) * ir * (dL * iL - iU) - T(0.25) * s2 * ir * ir * (iL2 - iU2) +
         T(0.25) * s2 * ir * (T(-2) * dL * iL2 * iL + T(2) * iU2 * iU);
   if (ai < sj - r) {
-    h += T(2) * (T(1) / ai - iL);
+    h += T(2) * (grcp(ai) - iL);
     d += T(2) * dL * iL2;
   }
   dh = d;
@@ -193,16 +194,18 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
     const V3<T> d = pos.diff(i, j);
     const T r2 = dot(d, d);
     if (!(r2 < cut2)) return;
-    const T bi = born[i], bj = born[j], bb = bi * bj, D = r2 / (T(4) * bb), e = gexp(-D);
-    const T f2 = r2 + bb * e, f = gsqrt(f2), qq = (T)gb_atom<P>(S, i).w * (T)gb_atom<P>(S, j).w;
-    const T dEdf = tau * qq / f2;
-    const T dBcommon = dEdf * e * (T(1) + D) / (T(2) * f);
+    const T bi = born[i], bj = born[j], bb = bi * bj, D = T(0.25) * r2 * grcp(bb), e = gexp(-D);
+    const T f2 = r2 + bb * e, rf = grsqrt(f2), qq = (T)gb_atom<P>(S, i).w * (T)gb_atom<P>(S, j).w;
+    const T f = f2 * rf;  // sqrt(f2) and 1/f from one reciprocal square root
+    const T dEdf = tau * qq * rf * rf;
+    const T dBcommon = T(0.5) * dEdf * e * (T(1) + D) * rf;
     acc.add(i, dBcommon * bj, err);
     acc.add(j, dBcommon * bi, err);
-    const T gr = -dEdf * (T(1) - T(0.25) * e) / f;  // -dE/dr / r
+    const T gr = -dEdf * (T(1) - T(0.25) * e) * rf;  // -dE/dr / r
     fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
     fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
-    if (want_e) e_fix += fa.efix(-tau * qq / f, err);
+    if (want_e) e_fix += fa.efix(-tau * qq * rf, err);
+    (void)f;
   });
   __syncthreads();
   // 4. chain-rule weights w_i = dE/dB_i dB_i/dI_i / 2
@@ -221,7 +224,7 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
     T dhij, dhji;
     gb_hct<T>(r, (T)pi.x, (T)pj.z, dhij);
     gb_hct<T>(r, (T)pj.x, (T)pi.z, dhji);
-    const T gr = -(w[i] * dhij + w[j] * dhji) / r;
+    const T gr = -(w[i] * dhij + w[j] * dhji) * grcp(r);
     fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
     fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
   });

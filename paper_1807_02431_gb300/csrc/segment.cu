@@ -202,9 +202,14 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
 
 // Verlet list of one replica (systems with a cutoff): every non-excluded pair closer than cutoff +
 // skin, found by the tiled scan over tile pairs whose bounding boxes are that close (the same lane
-// rotation as tile_pass, so each unordered pair is met once), appended with one shared atomic per warp
-// and step; the positions at the build are kept for the displacement test.  Returns the pair count
-// (a list longer than `cap` sets kErrList and is cut).  Called by every thread of the block.
+// rotation as tile_pass, so each unordered pair is met once).  Each warp appends to chunks of
+// kListChunk entries that it reserves with one shared atomic, so that a rotation step's ballot is
+// written without a round trip to the shared counter (one atomic per step, waited on by every step of
+// every warp, made the build about ten times slower); the unused tail of a warp's last chunk is filled
+// with 0xFFFFFFFF, which the list's readers skip.  The positions at the build are kept for the
+// displacement test.  Returns the entry count, padding included (a list longer than `cap` sets kErrList
+// and is cut).  Called by every thread of the block.
+constexpr int kListChunk = 256;
 template <class P>
 __device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uint32_t *list, int cap,
                           float4 *qref, int *cnt, int *err) {
@@ -218,6 +223,7 @@ __device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uin
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float lc2 = S.list_cut2;
+  int wpos = 0, wleft = 0;  // this warp's next free entry and the room left in its chunk (warp-uniform)
   for (int tp = warp; tp < S.n_tile_pairs; tp += nwarps) {
     const uint32_t e = S.tile_pairs[tp];
     const int I = (int)(e & 0xFFFFu), J = (int)(e >> 16);
@@ -243,14 +249,24 @@ __device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uin
       }
       const unsigned b = __ballot_sync(0xffffffffu, take);
       if (b) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(cnt, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const int idx = base + __popc(b & ((1u << lane) - 1u));
+        const int nb = __popc(b);
+        if (nb > wleft) {  // pad the rest of the chunk and reserve a new one
+          for (int t = lane; t < wleft; t += 32)
+            if (wpos + t < cap) list[wpos + t] = 0xFFFFFFFFu;
+          int base = 0;
+          if (lane == 0) base = atomicAdd(cnt, kListChunk);
+          wpos = __shfl_sync(0xffffffffu, base, 0);
+          wleft = kListChunk;
+        }
+        const int idx = wpos + __popc(b & ((1u << lane) - 1u));
         if (take && idx < cap) list[idx] = (uint32_t)i | ((uint32_t)(J * 32 + m) << 16);
+        wpos += nb;
+        wleft -= nb;
       }
     }
   }
+  for (int t = lane; t < wleft; t += 32)
+    if (wpos + t < cap) list[wpos + t] = 0xFFFFFFFFu;
   __syncthreads();
   int c = *cnt;
   if (c > cap) {
@@ -499,7 +515,8 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if constexpr (kGBL) {
       const int nl = n_list;
       gb_forces_cut<P>(S, pos, fa, gbl_acc, gbl_born, gbl_w, [&](auto f) {
-        for (int t = threadIdx.x; t < nl; t += kThreads) f((int)(list[t] & 0xFFFFu), (int)(list[t] >> 16));
+        for (int t = threadIdx.x; t < nl; t += kThreads)
+          if (list[t] != 0xFFFFFFFFu) f((int)(list[t] & 0xFFFFu), (int)(list[t] >> 16));
         for (int t = threadIdx.x; t < S.n_gb_xpairs; t += kThreads)
           f((int)(S.gb_xpairs[t] & 0xFFFFu), (int)(S.gb_xpairs[t] >> 16));
       }, sample, e_fix, &err);
