@@ -204,8 +204,7 @@ __device__ void tile_boxes(const SysDev &S, const State<P> &st, float *boxes) {
 // skin, found by the tiled scan over tile pairs whose bounding boxes are that close (the same lane
 // rotation as tile_pass, so each unordered pair is met once).  Each warp appends to chunks of
 // kListChunk entries that it reserves with one shared atomic, so that a rotation step's ballot is
-// written without a round trip to the shared counter (one atomic per step, waited on by every step of
-// every warp, made the build about ten times slower); the unused tail of a warp's last chunk is filled
+// written without a round trip to the shared counter; the unused tail of a warp's last chunk is filled
 // with 0xFFFFFFFF, which the list's readers skip.  The positions at the build are kept for the
 // displacement test.  Returns the entry count, padding included (a list longer than `cap` sets kErrList
 // and is cut).  Called by every thread of the block.
