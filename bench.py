@@ -587,6 +587,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--accel-steps", type=int, default=200000)
+    ap.add_argument("--accel-ligand-steps", type=int, default=10000)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--ligand-steps", type=int, default=3)
     ap.add_argument("--gradient-reps", type=int, default=2)
@@ -726,6 +727,12 @@ def main():
                                                         max_exits=8, unit_ns=False)
             accel["double_well_2d_original"] = accelerated_speed(B, dw, B.GRP_FP64, dw.n_replicas, SEED, 10 ** 8,
                                                                  max_exits=8, unit_ns=False, original=True)
+            if args.accel_ligand_steps > 0:
+                # the ligand-receptor system (bounded run): its bound state is left within tens of ps, before
+                # the Fleming-Viot step converges, so the loop cycles through reference exits
+                lg = W.ligand_receptor()
+                accel["ligand_receptor2030"] = accelerated_speed(B, lg, B.GRP_MIXED, lg.n_replicas, seed,
+                                                                 args.accel_ligand_steps)
         multistate = multistate_bench(B, args.multistate_steps) if args.multistate_steps > 0 else None
         same_error = same_error_bench(B, args.same_error_steps) if args.same_error_steps > 0 else None
         branching = branch_bench(B, flush, args.branch_reps) if args.branch_reps > 0 else None

@@ -290,23 +290,26 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
     // Branch-free: a masked pair (excluded, padding, beyond the cutoff) evaluates atom i against itself
     // with r^2 = 1 and contributes g = 0, so that the two independent steps of a pair of steps carry no
     // divergent branches and their dependent chains can interleave (measured on the batched chains:
-    // 12.0 -> 12.7 TFLOP/s).
-    auto meet = [&](int s, V3<T> &fj) {
+    // 12.0 -> 12.7 TFLOP/s).  kDense: every lane's mask is full and there is no cutoff, so the masking
+    // selects drop out; the arithmetic of each pair is the same as on the masked path.
+    auto meet = [&](auto dense, int s, V3<T> &fj) {
+      constexpr bool kDense = decltype(dense)::value;
       const int m = (lane + s) & 31;
-      const bool on0 = (mask >> m) & 1u;
+      const bool on0 = kDense || ((mask >> m) & 1u);
       const int j = on0 ? j0 + m : ic;
       const typename Pos<P>::At pj = pos.at(j);
       const V3<T> d = Pos<P>::diff(pi, pj);
       T r2 = dot(d, d);
       const bool on = on0 && (!kCutoff || !(cut2 > T(0) && r2 >= cut2));
-      r2 = on ? r2 : T(1);
+      if constexpr (!kDense) r2 = on ? r2 : T(1);
       T bsh, bse, bqc;
       nb_params<P>(pj, par, j, bsh, bse, bqc);
       const T sig = ash + bsh, eps = ase * bse, qq = aqc * bqc;
       const T inv_r2 = grcp(r2);
       const T s2 = sig * sig * inv_r2;
       const T s6 = s2 * s2 * s2;
-      const T g = on ? pair_g<kRF>(par, eps, s6, qq, r2, inv_r2) : T(0);
+      T g = pair_g<kRF>(par, eps, s6, qq, r2, inv_r2);
+      if constexpr (!kDense) g = on ? g : T(0);
       const V3<T> f = {g * d.x, g * d.y, g * d.z};
       fi.x += f.x; fi.y += f.y; fi.z += f.z;
       fj.x -= f.x; fj.y -= f.y; fj.z -= f.z;
@@ -315,17 +318,22 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
     // Steps go in pairs: the j forces of even steps ride in fja, those of odd steps in fjb, and both
     // move two lanes down after each pair, so each register waits on one shuffle per two steps
     // instead of one per step.  s1 - s0 is even (32, or 16 on a diagonal tile).
+    auto rotate = [&](auto dense) {
 #pragma unroll 2
-    for (int s = s0; s < s1; s += 2) {
-      meet(s, fja);
-      meet(s + 1, fjb);
-      fja.x = __shfl_sync(0xffffffffu, fja.x, (lane + 2) & 31);
-      fja.y = __shfl_sync(0xffffffffu, fja.y, (lane + 2) & 31);
-      fja.z = __shfl_sync(0xffffffffu, fja.z, (lane + 2) & 31);
-      fjb.x = __shfl_sync(0xffffffffu, fjb.x, (lane + 2) & 31);
-      fjb.y = __shfl_sync(0xffffffffu, fjb.y, (lane + 2) & 31);
-      fjb.z = __shfl_sync(0xffffffffu, fjb.z, (lane + 2) & 31);
-    }
+      for (int s = s0; s < s1; s += 2) {
+        meet(dense, s, fja);
+        meet(dense, s + 1, fjb);
+        fja.x = __shfl_sync(0xffffffffu, fja.x, (lane + 2) & 31);
+        fja.y = __shfl_sync(0xffffffffu, fja.y, (lane + 2) & 31);
+        fja.z = __shfl_sync(0xffffffffu, fja.z, (lane + 2) & 31);
+        fjb.x = __shfl_sync(0xffffffffu, fjb.x, (lane + 2) & 31);
+        fjb.y = __shfl_sync(0xffffffffu, fjb.y, (lane + 2) & 31);
+        fjb.z = __shfl_sync(0xffffffffu, fjb.z, (lane + 2) & 31);
+      }
+    };
+    // tile pairs of whole tiles away from the exclusions (a diagonal tile's mask is never full)
+    if (!kCutoff && __all_sync(0xffffffffu, mask == 0xffffffffu)) rotate(std::true_type{});
+    else rotate(std::false_type{});
     if (i < S.n) acc.add(i, fi, err);
     // after the last pair of steps lane l holds the j forces of atoms (l + s1) and (l + s1 + 1) mod 32
     const int ja = j0 + ((lane + s1) & 31), jb = j0 + ((lane + s1 + 1) & 31);
