@@ -706,6 +706,21 @@ def main():
                         "roofline": {"bound": "alu", "achieved": pach, "peak": peak, "unit": "TFLOP/s",
                                      "frac": pach / peak, "kernel": "ff_segment_kernel<PathMixed, 320, 2, kModeItems, 4>",
                                      "kernel_ms": pk_ms, "flops_per_launch": pflops}}
+            # a larger periodic system on the Verlet-list path: the 100-bead chain with 60 ion pairs, 4.0 nm box
+            sl = W.chain_ions(n_chain=100, n_pairs=60, edge=4.0, n_replicas=R)
+            step_l = Step(B, sl, B.GRP_MIXED, R, seed, local)
+            tl = time_steps(step_l, args.fp64_steps, 1, flush, step_l.stream)
+            lk_ms = segment_kernel_ms(B, step_l, 2)
+            lflops = pme_flops_per_replica_step(sl) * R * sl.t_check
+            lach = lflops / (lk_ms * 1e-3) / 1e12
+            periodic["verlet_list"] = {
+                "workload": f"{sl.name}_r{R} ({sl.n_atoms} atoms, box {sl.box[0]} nm, grid "
+                            f"{'x'.join(str(k) for k in sl.pme_grid)}, cutoff {sl.cutoff} nm, Verlet lists over nearest images)",
+                "value": R * sl.n_atoms * sl.t_check * len(tl) / (float(np.sum(tl)) / 1e3),
+                "unit": "replica-atom-steps/s", "ms_per_step": float(np.mean(tl)),
+                "roofline": {"bound": "alu", "achieved": lach, "peak": peak, "unit": "TFLOP/s", "frac": lach / peak,
+                             "kernel": "ff_segment_kernel<PathMixed, 512, 1, kModeList, 4>", "kernel_ms": lk_ms,
+                             "flops_per_launch": lflops}}
         # end to end through the public API with host buffers
         step.reset()
         e2e_wall, bi, bo = e2e_steps(B, step, args.steps)

@@ -119,8 +119,10 @@ typedef struct {
    * a_i = rho_i - 0.009 nm, pairwise descreening integrals give I_i, psi_i = a_i I_i, Born radii
    * 1/B_i = 1/a_i - tanh(psi - 0.8 psi^2 + 4.85 psi^3)/rho_i, and
    * E = -(1/2) k_e (1/eps_in - 1/eps_out) sum_i sum_j q_i q_j / sqrt(r^2 + B_i B_j exp(-r^2/(4 B_i B_j)))
-   * over all pairs and each atom with itself.  GRP_ENOTIMPL for 64 atoms or more, with a cutoff, in a
-   * batch, and for grp_adjoint_segment. */
+   * over all pairs and each atom with itself.  Systems of 64 atoms or more with a cutoff (Verlet lists)
+   * truncate the descreening sums and the pair terms at the cutoff (each atom with itself kept).
+   * GRP_ENOTIMPL for 64 atoms or more without a cutoff, below 64 atoms with a cutoff, with the reaction
+   * field or particle mesh Ewald, in a batch, and for grp_adjoint_segment. */
   const double *gb_radius, *gb_scale;
   double gb_solute_dielectric, gb_solvent_dielectric;
   /* Bond constraints |q_i - q_j| = d (the paper's MD setups hold the bonds of hydrogens fixed): each
@@ -128,9 +130,9 @@ typedef struct {
    * by RATTLE (no relative velocity along any bond), Gauss-Seidel sweeps until |r^2 - d^2| <= tol d^2
    * and |r . v| <= tol d^2 / dt; GRP_ETIMEOUT (latched) when constraint_max_iter sweeps do not reach
    * that.  A constrained pair should be excluded from the nonbonded terms and carry no bond term.
-   * GRP_ENOTIMPL for 64 atoms or more, with the reaction field, particle mesh Ewald or implicit
-   * solvent, for groups of coupled constraints larger than 16 constraints or atoms, in a batch, and for
-   * grp_adjoint_segment.  On the mixed path a group of one constraint is integrated in double-single
+   * Below 64 atoms without implicit solvent, or with a cutoff (Verlet lists, with or without implicit
+   * solvent); GRP_ENOTIMPL otherwise, with the reaction field or particle mesh Ewald, for groups of
+   * coupled constraints larger than 16 constraints or atoms, in a batch, and for grp_adjoint_segment.  On the mixed path a group of one constraint is integrated in double-single
    * arithmetic, a larger group in FP64; both meet the same tolerances. */
   int32_t n_constraints;
   const int32_t *constraint_atoms;  /* [n_constraints][2] */
@@ -146,9 +148,11 @@ typedef struct {
    * reciprocal space by smooth particle mesh Ewald (Essmann et al. 1995) with cardinal B-splines of
    * order pme_order on a pme_grid[0] x pme_grid[1] x pme_grid[2] grid.  Lennard-Jones takes the same
    * minimum images and cutoff; bonded terms use the positions as they are (molecules are never
-   * wrapped).  Positions may leave the box.  GRP_EINVAL for a non-positive edge or beta, a missing or
-   * too long cutoff; GRP_ENOTIMPL for 64 atoms or more, grid sizes other than 8 or 16, an order other
-   * than 4, with implicit solvent or constraints, in a batch, and for grp_adjoint_segment. */
+   * wrapped).  Positions may leave the box.  Systems of 64 atoms or more keep Verlet lists over nearest
+   * images, so there cutoff + skin (7/6 of the cutoff) must be at most half the shortest edge.
+   * GRP_EINVAL for a non-positive edge or beta, a missing or too long cutoff; GRP_ENOTIMPL for grid
+   * sizes other than 8 or 16, an order other than 4, with implicit solvent or constraints, in a batch,
+   * and for grp_adjoint_segment. */
   double box[3];
   double ewald_beta;
   int32_t pme_grid[3];
@@ -235,7 +239,10 @@ void grp_destroy_replicas(grp_replicas *r);
  * that brings t_phase to a multiple of t_gr (t_gr > 0) every observable of the active replicas is
  * accumulated (Eq. 2 with the time integral replaced by samples every t_GR, Section 2.4.1).
  * Increments t_global and t_phase by k.  Section 3.2: "one code block realising discretisation
- * steps". */
+ * steps".  Systems with a cutoff keep a Verlet list per replica, of capacity twice the pairs within
+ * cutoff + skin of the first configuration (over nearest images in a periodic box), at least 65,536
+ * entries or every pair; a list that outgrows it is cut and GRP_ENOMEM is reported by the next call
+ * that reads the replicas' error flags (grp_get_state, the check and loop calls). */
 grp_status grp_step_k(grp_replicas *r, int64_t k, int32_t t_gr, int32_t n_active, void *stream);
 
 /* State functions of Section 3.3 for every replica: d_labels[r] = state containing replica r

@@ -131,13 +131,16 @@ static grp_status setup_pme(const grp_system_desc *d, const std::vector<uint8_t>
   SysDev &D = s->dev;
   const int n = d->n_atoms;
   const double pi = 3.14159265358979323846;
-  if (n >= 64) return fail(GRP_ENOTIMPL, "particle mesh Ewald is implemented for systems of fewer than 64 atoms");
   for (int x = 0; x < 3; ++x)
     if (!(d->box[x] > 0) || !std::isfinite(d->box[x])) return fail(GRP_EINVAL, "box edge %d must be positive", x);
   if (!(d->ewald_beta > 0) || !std::isfinite(d->ewald_beta)) return fail(GRP_EINVAL, "ewald_beta must be positive");
   const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2]));
   if (!(d->cutoff > 0) || d->cutoff > 0.5 * lmin)
     return fail(GRP_EINVAL, "particle mesh Ewald needs 0 < cutoff <= half the shortest box edge");
+  // systems of 64 atoms and more keep a Verlet list (skin = cutoff / 6) over minimum images: each pair
+  // within cutoff + skin must have one nearest image
+  if (n >= 64 && 7.0 / 6.0 * d->cutoff > 0.5 * lmin)
+    return fail(GRP_EINVAL, "particle mesh Ewald on %d atoms needs cutoff + skin (7/6 cutoff) <= half the shortest box edge", n);
   for (int x = 0; x < 3; ++x)
     if (d->pme_grid[x] != 8 && d->pme_grid[x] != 16)
       return fail(GRP_ENOTIMPL, "particle mesh Ewald grids of 8 or 16 points per axis (axis %d: %d)", x, d->pme_grid[x]);
@@ -711,7 +714,7 @@ static grp_status latch_errors(grp_replicas *r, cudaStream_t st) {
   if (e) {
     CU(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (e & kErrNaN) return fail(GRP_ENAN, "non-finite position or momentum");
-    if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration)");
+    if (e & kErrList) return fail(GRP_ENOMEM, "a Verlet list outgrew its capacity (twice the pairs of the first configuration, at least 65,536 or every pair)");
     if (e & kErrConstraint) return fail(GRP_ETIMEOUT, "SHAKE or RATTLE did not converge within constraint_max_iter sweeps");
     if (e & kErrIndex) return fail(GRP_EINVAL, "a row index outside the replica set");
     if (e & kErrTimeout) return fail(GRP_ETIMEOUT, "a bulk copy of the branching did not complete within its time limit");
@@ -771,23 +774,28 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
   AL(r->rhat, GRP_MAX_OBS * 8);
   AL(r->d_gr, 3 * GRP_MAX_OBS * 8);
   if (D.use_list) {
-    // capacity: twice the non-excluded pairs within cutoff + skin in the first configuration
+    // capacity: twice the non-excluded pairs within cutoff + skin in the first configuration (over
+    // nearest images in a periodic box), see below
     const int n = D.n;
     const double lc2 = (double)D.list_cut2;
+    const bool per = D.coulomb_rf == 2;
     size_t cnt = 0;
     for (int i = 0; i < n; ++i)
       for (int j = i + 1; j < n; ++j) {
         if (s->excl[(size_t)i * n + j]) continue;
         double d2 = 0;
         for (int x = 0; x < 3; ++x) {
-          const double dx = h_q0[3 * i + x] - h_q0[3 * j + x];
+          double dx = h_q0[3 * i + x] - h_q0[3 * j + x];
+          if (per) dx -= D.box[x] * std::nearbyint(dx * D.ibox[x]);
           d2 += dx * dx;
         }
         cnt += d2 < lc2;
       }
     const size_t all = (size_t)n * (n - 1) / 2;
-    // + the padding of the warps' partly filled chunks (16 warps of a 512-thread block, 256 entries each)
-    r->nbl_cap = (int)(std::min(all, 2 * cnt + 1024) + 16 * 256);
+    // at least 65,536 entries (every pair, for systems of up to ~360 atoms, whose density may still
+    // change a lot: ions condensing in a periodic box), + the padding of the warps' partly filled chunks
+    // (16 warps of a 512-thread block, 256 entries each)
+    r->nbl_cap = (int)(std::min(all, std::max(2 * cnt + 1024, (size_t)65536)) + 16 * 256);
     AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
     if (D.gb) AL(r->gb_glob, R * (size_t)n * 2 * 8);

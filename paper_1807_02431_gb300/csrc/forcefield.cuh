@@ -251,7 +251,8 @@ __device__ __forceinline__ void pair_term(const Pos<P> &pos, const Params<P> &pa
 // Tiled nonbonded pass: each warp takes tile pairs (I, J); lane l owns atom i = 32 I + l and, at
 // rotation step s, meets atom j = 32 J + ((l + s) mod 32).  The force on i accumulates in registers;
 // the force on j accumulates in registers that move down the lanes by warp shuffles, so that they
-// always sit in the lane currently meeting atom j and end in known lanes.
+// always sit in the lane currently meeting atom j and end in known lanes.  In a periodic box (Ewald
+// real space) each pair takes its nearest image.
 // Off-diagonal tiles take s = 0..31; a diagonal tile takes s = 1..16 (lanes 16..31 skip s = 16), which
 // meets every unordered pair once.  Per lane and tile pair the FP32 (FP64) sums are converted to fixed
 // point once, so the result does not depend on which warp takes which tile pair, or in which order.
@@ -298,7 +299,7 @@ __device__ __forceinline__ void tile_pass(const SysDev &S, const Pos<P> &pos, co
       const bool on0 = kDense || ((mask >> m) & 1u);
       const int j = on0 ? j0 + m : ic;
       const typename Pos<P>::At pj = pos.at(j);
-      const V3<T> d = Pos<P>::diff(pi, pj);
+      const V3<T> d = pair_image<kRF>(par, Pos<P>::diff(pi, pj));
       T r2 = dot(d, d);
       const bool on = on0 && (!kCutoff || !(cut2 > T(0) && r2 >= cut2));
       if constexpr (!kDense) r2 = on ? r2 : T(1);
@@ -500,7 +501,7 @@ __device__ __forceinline__ void dihedral_term(const Pos<P> &pos, const Params<P>
 }
 
 // Nonbonded pairs of a Verlet list (i | j << 16), strided over the block's threads; pairs beyond the
-// cutoff contribute nothing.  The list lives in global memory (L2): each thread loads its next four
+// cutoff contribute nothing; in a periodic box (Ewald real space) each pair takes its nearest image.  The list lives in global memory (L2): each thread loads its next four
 // entries before evaluating them, so that one load latency covers four pairs.  (Measured on the
 // 2,030-atom ligand workload, this pair list with fixed-point atomics on both atoms beat per-atom
 // neighbour rows evaluated from both ends by 1.36x, and rows holding each pair once by 7x.)
@@ -525,15 +526,15 @@ __device__ __forceinline__ void list_pass(const SysDev &S, const Pos<P> &pos, co
         // the list's pairs beyond the cutoff, about half of them, skip the low-word loads
         pi.h = pos.qh[i];
         pj.h = pos.qh[j];
-        const float hx = pi.h.x - pj.h.x, hy = pi.h.y - pj.h.y, hz = pi.h.z - pj.h.z;
-        if (hx * hx + hy * hy + hz * hz > cut2 * 1.0001f) continue;
+        const V3<float> hd = pair_image<kRF>(par, V3<float>{pi.h.x - pj.h.x, pi.h.y - pj.h.y, pi.h.z - pj.h.z});
+        if (dot(hd, hd) > cut2 * 1.0001f) continue;
         pi.l = pos.ql[i];
         pj.l = pos.ql[j];
       } else {
         pi = pos.at(i);
         pj = pos.at(j);
       }
-      const V3<T> d = Pos<P>::diff(pi, pj);
+      const V3<T> d = pair_image<kRF>(par, Pos<P>::diff(pi, pj));
       const T r2 = dot(d, d);
       if (!(r2 < cut2)) continue;
       T ash, ase, aqc, bsh, bse, bqc;

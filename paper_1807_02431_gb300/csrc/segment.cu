@@ -222,15 +222,29 @@ __device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uin
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float lc2 = S.list_cut2;
+  // periodic box: tile gaps and pair distances over nearest images (cutoff + skin is at most half the
+  // shortest edge, so a pair within it has one nearest image)
+  const bool per = S.coulomb_rf == 2;
+  const float L[3] = {(float)S.box[0], (float)S.box[1], (float)S.box[2]};
+  const float iL[3] = {(float)S.ibox[0], (float)S.ibox[1], (float)S.ibox[2]};
   int wpos = 0, wleft = 0;  // this warp's next free entry and the room left in its chunk (warp-uniform)
   for (int tp = warp; tp < S.n_tile_pairs; tp += nwarps) {
     const uint32_t e = S.tile_pairs[tp];
     const int I = (int)(e & 0xFFFFu), J = (int)(e >> 16);
     const float *ba = boxes + 6 * I, *bb = boxes + 6 * J;
-    const float gx = fmaxf(0.f, fmaxf(ba[0] - bb[3], bb[0] - ba[3]));
-    const float gy = fmaxf(0.f, fmaxf(ba[1] - bb[4], bb[1] - ba[4]));
-    const float gz = fmaxf(0.f, fmaxf(ba[2] - bb[5], bb[2] - ba[5]));
-    if (gx * gx + gy * gy + gz * gz >= lc2) continue;
+    float g2 = 0.f;
+    for (int x = 0; x < 3; ++x) {
+      float g;
+      if (per) {  // centre distance to the nearest image minus both half extents
+        float dc = 0.5f * ((ba[x] + ba[x + 3]) - (bb[x] + bb[x + 3]));
+        dc -= L[x] * rintf(dc * iL[x]);
+        g = fmaxf(0.f, fabsf(dc) - 0.5f * ((ba[x + 3] - ba[x]) + (bb[x + 3] - bb[x])));
+      } else {
+        g = fmaxf(0.f, fmaxf(ba[x] - bb[x + 3], bb[x] - ba[x + 3]));
+      }
+      g2 += g * g;
+    }
+    if (g2 >= lc2) continue;
     const uint32_t mask = S.tile_masks[(size_t)tp * 32 + lane];
     const int i = I * 32 + lane;
     const bool diag = I == J;
@@ -243,7 +257,12 @@ __device__ int build_list(const SysDev &S, const State<P> &st, float *boxes, uin
       if (((mask >> m) & 1u) && !(diag && s == 16 && lane >= 16)) {
         float xj[3];
         st.get_f32(J * 32 + m, xj);
-        const float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+        float dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+        if (per) {
+          dx -= L[0] * rintf(dx * iL[0]);
+          dy -= L[1] * rintf(dy * iL[1]);
+          dz -= L[2] * rintf(dz * iL[2]);
+        }
         take = dx * dx + dy * dy + dz * dz < lc2;
       }
       const unsigned b = __ballot_sync(0xffffffffu, take);
@@ -353,7 +372,8 @@ enum : int {
 
 // kFF: the nonbonded model compiled into the step loop, 0 = Coulomb with eps = 4r, 1 = reaction field,
 // 2 = eps = 4r plus Generalized Born solvent, 3 = eps = 4r with bond constraints, 4 = periodic box with
-// particle mesh Ewald (2, 3 and 4 on the item table only), -1 = eps = 4r or reaction field
+// particle mesh Ewald (2, 3 and 4 on the item table and the Verlet lists), 5 = solvent and constraints
+// (Verlet lists), -1 = eps = 4r or reaction field
 // decided per launch (the batched kernel, whose runs may differ; implicit solvent is not batched).
 // The single-run kernels are compiled for one model, which keeps one copy of the force passes and no
 // unused solvent code in the step loop.
@@ -380,7 +400,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
   constexpr bool kGB = kMode == kModeItems && kFF == 2;
   constexpr bool kGBL = kMode == kModeList && (kFF == 2 || kFF == 5);  // solvent with a cutoff on the list
   constexpr bool kCon = (kMode == kModeItems && kFF == 3) || (kMode == kModeList && (kFF == 3 || kFF == 5));
-  constexpr bool kPME = kMode == kModeItems && kFF == 4;
+  constexpr bool kPME = (kMode == kModeItems || kMode == kModeList) && kFF == 4;
   constexpr int kRF = kFF == 4 ? 2 : (kFF >= 2 ? 0 : kFF);
   GbScratch<P> gbs;  // implicit solvent (item-table systems only)
   if constexpr (kGB) {
@@ -397,7 +417,7 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     gbl_born = reinterpret_cast<T *>(a.gb_glob + (size_t)r * 2 * n);
     gbl_w = gbl_born + n;
   }
-  PmeScratch<P> pms;  // particle mesh (item-table systems only)
+  PmeScratch<P> pms;  // particle mesh (periodic systems: item table or Verlet lists)
   if constexpr (kPME) {
     ptr = align32(ptr);
     pms.carve(ptr, S);
@@ -773,6 +793,7 @@ static cudaError_t launch_ff_p(const SegArgs &a, const SegConfig &c, cudaStream_
                           : (small ? ff_segment_kernel<P, 320, 2, kModeItems, 0> : ff_segment_kernel<P, 512, 1, kModeItems, 0>))
             : mode == kModeTiles
                   ? (small ? ff_segment_kernel<P, 320, 2, kModeTiles, 0> : ff_segment_kernel<P, 512, 1, kModeTiles, 0>)
+                  : pme ? ff_segment_kernel<P, 512, 1, kModeList, 4>  // periodic (the mesh's registers)
                   : (rf ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 1> : ff_segment_kernel<P, 512, 1, kModeList, 1>)
                      : (gb && con) ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 5> : ff_segment_kernel<P, 512, 1, kModeList, 5>)
                      : gb ? (small ? ff_segment_kernel<P, 320, 2, kModeList, 2> : ff_segment_kernel<P, 512, 1, kModeList, 2>)

@@ -389,16 +389,19 @@ def chain_h(n_heavy: int = 22, seed: int = 1807, dyn_seed: int = 2431, n_replica
 
 
 def chain_ions(n_pairs: int = 20, edge=2.6, seed: int = 1807, dyn_seed: int = 2431,
-               n_replicas: int = 256, grid=16, order: int = 4, ewald_rtol: float = 1e-5) -> System:
-    """The 22-bead chain with `n_pairs` ion pairs in a periodic box of edge `edge` nm (or edges), its
-    electrostatics summed over all periodic images by particle mesh Ewald (an optimisation the paper
-    expects of an MD engine, Section 3.2): 62 atoms for 20 pairs.  Ions of 20 amu, LJ sigma 0.3 nm and
+               n_replicas: int = 256, grid=16, order: int = 4, ewald_rtol: float = 1e-5,
+               n_chain: int = 22) -> System:
+    """The `n_chain`-bead chain (22 by default) with `n_pairs` ion pairs in a periodic box of edge `edge`
+    nm (or edges), its electrostatics summed over all periodic images by particle mesh Ewald (an
+    optimisation the paper expects of an MD engine, Section 3.2): 62 atoms for 20 pairs; 220 atoms for
+    the 100-bead chain with 60 pairs in a 4.0 nm box (a system of 64 atoms or more keeps Verlet lists
+    over nearest images).  Ions of 20 amu, LJ sigma 0.3 nm and
     eps 0.5 kJ/mol, charges +-0.3 e, placed uniformly at least 0.3 nm from every atom placed before;
     plain Coulomb (eps = 1) with real-space cutoff 1.2 nm, beta such that erfc(beta r_c) = ewald_rtol
     (2.6 nm^-1 for 1e-5, the usual MD setting), a grid x grid x grid mesh (0.16 nm spacing for 16) and
     B-splines of order `order`; Lennard-Jones cut at the same distance over minimum images.  States,
     observables and the Gen. ParRep parameters are the chain's."""
-    base = chain(seed=seed, dyn_seed=dyn_seed, n_replicas=n_replicas)
+    base = chain(n_atoms=n_chain, seed=seed, dyn_seed=dyn_seed, n_replicas=n_replicas)
     rng = np.random.default_rng(seed + 7)
     box = np.broadcast_to(np.asarray(edge, float), 3)
     grid = tuple(int(g) for g in np.broadcast_to(grid, 3))
