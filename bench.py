@@ -501,8 +501,9 @@ def profile_case(B, case, replicas, steps, launches):
     """A small fixed case for ncu captures: `launches` launches of the case's main kernel."""
     import torch
 
-    if case in ("chain", "pme", "constrained", "solvated"):
+    if case in ("chain", "pme", "pme_list", "constrained", "solvated"):
         s = {"chain": W.chain, "pme": W.chain_ions, "constrained": W.chain_h,
+             "pme_list": lambda: W.chain_ions(n_chain=100, n_pairs=60, edge=4.0),
              "solvated": lambda: W.solvated(W.chain())}[case]()
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0)
         for _ in range(launches):
@@ -594,7 +595,7 @@ def main():
     ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--branch-reps", type=int, default=20)
     ap.add_argument("--same-error-steps", type=int, default=40000)
-    ap.add_argument("--profile-case", choices=["chain", "pme", "constrained", "solvated", "ligand", "adjoint", "batch",
+    ap.add_argument("--profile-case", choices=["chain", "pme", "pme_list", "constrained", "solvated", "ligand", "adjoint", "batch",
                                                      "branch"],
                     default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")

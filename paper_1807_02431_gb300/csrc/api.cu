@@ -153,6 +153,9 @@ static grp_status setup_pme(const grp_system_desc *d, const std::vector<uint8_t>
     D.box[x] = d->box[x];
     D.ibox[x] = 1.0 / d->box[x];
     D.pme_K[x] = d->pme_grid[x];
+    const double kl = d->pme_grid[x] / d->box[x];
+    D.pme_kl[x][0] = (float)kl;
+    D.pme_kl[x][1] = (float)(kl - (double)D.pme_kl[x][0]);
   }
   const double V = d->box[0] * d->box[1] * d->box[2], b = d->ewald_beta, ke = d->coulomb_k;
   double q2 = 0.0, qt = 0.0;

@@ -70,10 +70,11 @@ struct SysDev {
   const double4 *gb_d;     // per atom (rho - 0.009, 1/rho, S (rho - 0.009), q)
   const float4 *gb_f;
   double krf, crf;         // reaction-field constants k_rf, c_rf (per nm^3, per nm)
-  // Periodic electrostatics by smooth particle mesh Ewald (coulomb_rf = 2, item-table systems)
+  // Periodic electrostatics by smooth particle mesh Ewald (coulomb_rf = 2)
   double box[3], ibox[3];  // orthorhombic box edges (nm) and their inverses
   double ewald_beta;       // splitting parameter (per nm)
   int pme_K[3];            // grid points per axis (8 or 16)
+  float pme_kl[3][2];      // K_d / L_d as a double-single pair (the mixed path's grid coordinates)
   double pme_e_const;      // self and neutralising-background energy
   int n_excl_pairs;        // excluded pairs (i | j << 16): minus the smooth part of their Coulomb
   const uint32_t *excl_pairs;

@@ -354,18 +354,44 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   using C2 = typename PmeCplx<P>::type;
   const int n = S.n, bd = blockDim.x;
   const int K0 = S.pme_K[0], K1 = S.pme_K[1], K2 = S.pme_K[2];
-  // 1. grid cell and B-spline weights of every coordinate (u in FP64: unwrapped positions may lie many
-  // boxes out)
+  // 1. grid cell and B-spline weights of every coordinate.  Unwrapped positions may lie many boxes out,
+  // so the grid coordinate u = x K / L is formed at more than FP32 precision: in FP64 on the FP64 path;
+  // on the mixed path in double-single from the position's two words and K / L's two words, with FP32
+  // instructions only (FP64 instructions run at 1/64 of the FP32 rate on this part): t_hi + t_lo with
+  // t_hi = x_hi c_hi and t_lo = its exact rounding error (fma) + x_hi c_lo + x_lo c_hi; the fractional
+  // part t_hi - floor(t_hi) is exact, and adding t_lo leaves w within ~6e-8 of frac(u).
   for (int i = threadIdx.x; i < 3 * n; i += bd) {
     const int at = i / 3, x = i - 3 * at;
-    const double t = pme_coord<P>(pos, at, x) * S.ibox[x];
-    const double u = (t - floor(t)) * (double)S.pme_K[x];
-    const double fl = floor(u);
-    int k = (int)fl;
-    if (k >= S.pme_K[x]) k -= S.pme_K[x];
+    int k;
+    T w;
+    if constexpr (P::kMixed) {
+      const float xh = (&pos.qh[at].x)[x], xl = (&pos.ql[at].x)[x];
+      const float ch = S.pme_kl[x][0], cl = S.pme_kl[x][1];
+      const float th = xh * ch;
+      const float tl = fmaf(xh, ch, -th) + fmaf(xh, cl, xl * ch);
+      float nf = floorf(th);
+      float wv = (th - nf) + tl;
+      if (wv < 0.f) {
+        wv += 1.f;
+        nf -= 1.f;
+      } else if (wv >= 1.f) {
+        wv -= 1.f;
+        nf += 1.f;
+      }
+      k = (int)nf % S.pme_K[x];
+      k += k < 0 ? S.pme_K[x] : 0;
+      w = wv;
+    } else {
+      const double t = pme_coord<P>(pos, at, x) * S.ibox[x];
+      const double u = (t - floor(t)) * (double)S.pme_K[x];
+      const double fl = floor(u);
+      k = (int)fl;
+      if (k >= S.pme_K[x]) k -= S.pme_K[x];
+      w = (T)(u - fl);
+    }
     g.cell[i] = k;
     T m[4], d[4];
-    bspline4((T)(u - fl), m, d);
+    bspline4(w, m, d);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       g.wm[4 * i + t] = m[t];
