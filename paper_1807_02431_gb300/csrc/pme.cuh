@@ -38,21 +38,35 @@ struct PmeCplx<PathMixed> {
 
 // Shared-memory scratch of the mesh: the charge grid's fixed-point accumulators, the complex grid, and
 // per atom and axis the grid cell floor(u) and the B-spline weights and derivatives at u.
+// Strides of the fixed-point charge grid: rows of K2 + 1 words, planes of K1 (K2 + 1) words rounded up
+// to 4 mod 32.  Spreading gives the 16 (t0, t1) offsets of one atom to 16 lanes, which then fall in 16
+// distinct banks (t1 moves a row, 17 or 9 banks; t0 a plane, 4 banks); with planes of K1 K2 words all
+// four t0 and two t1 offsets shared a bank (8-way conflicts on every fixed-point addition).
+__host__ __device__ __forceinline__ void pme_acc_strides(int K1, int K2, int &rs, int &ps) {
+  rs = K2 + 1;
+  const int p = K1 * rs;
+  ps = p + (36 - p % 32) % 32;
+}
+
 template <class P>
 struct PmeScratch {
   using T = typename P::T;
   using C2 = typename PmeCplx<P>::type;
-  ScalarAcc<P> acc;  // [K0 K1 K2]
+  ScalarAcc<P> acc;  // [K0][K1][K2] in padded rows and planes (pme_acc_strides)
   C2 *c;             // [K0][K1][K2 + 1]
   T *wm, *wd;        // [3n][4]: M_4(w + t), M_4'(w + t)
   int *cell;         // [3n]
+  __host__ __device__ static int acc_points(const SysDev &S) {
+    int rs, ps;
+    pme_acc_strides(S.pme_K[1], S.pme_K[2], rs, ps);
+    return S.pme_K[0] * ps;
+  }
   static size_t bytes(const SysDev &S) {
-    const size_t g = (size_t)S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
     const size_t gc = (size_t)S.pme_K[0] * S.pme_K[1] * (S.pme_K[2] + 1);
-    return ScalarAcc<P>::bytes((int)g) + 32 + gc * sizeof(C2) + (size_t)3 * S.n * (4 + 8 * sizeof(T)) + 32;
+    return ScalarAcc<P>::bytes(acc_points(S)) + 32 + gc * sizeof(C2) + (size_t)3 * S.n * (4 + 8 * sizeof(T)) + 32;
   }
   __device__ void carve(unsigned char *&ptr, const SysDev &S) {
-    const int g = S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
+    const int g = acc_points(S);
     acc.carve(ptr, g);
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
     c = (C2 *)ptr;
@@ -66,7 +80,7 @@ struct PmeScratch {
     ptr = (unsigned char *)(((uintptr_t)ptr + 15) & ~(uintptr_t)15);
   }
   __device__ void zero(const SysDev &S) const {
-    const int g = S.pme_K[0] * S.pme_K[1] * S.pme_K[2];
+    const int g = acc_points(S);
     for (int i = threadIdx.x; i < g; i += blockDim.x) acc.zero(i);
   }
 };
@@ -231,12 +245,14 @@ template <int K, class P, class C2, class T>
 __device__ __forceinline__ void fft_first_r2c(const ScalarAcc<P> &acc, C2 *c, int K1, int K2) {
   constexpr int kBits = Log2<K>::value;
   const int rz = K2 + 1, h2 = K2 >> 1;
+  int rs, ps;
+  pme_acc_strides(K1, K2, rs, ps);
   for (int l = threadIdx.x; l < K1 * h2; l += blockDim.x) {
     const int k1 = l / h2, k2 = l - k1 * h2;
     T re[K], im[K];
 #pragma unroll
     for (int e = 0; e < K; ++e) {
-      const int g = (bitrev(e, kBits) * K1 + k1) * K2 + k2;
+      const int g = bitrev(e, kBits) * ps + k1 * rs + k2;
       re[e] = acc.get(g);
       im[e] = acc.get(g + h2);
       acc.zero(g);
@@ -414,6 +430,8 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   if (want_e && threadIdx.x == 0) e_fix += fa.efix((T)S.pme_e_const, err);
   __syncthreads();
   // 2. spread: one thread per (atom, t0, t1), four grid points along the third axis each
+  int acc_rs, acc_ps;
+  pme_acc_strides(K1, K2, acc_rs, acc_ps);
   for (int it = threadIdx.x; it < 16 * n; it += bd) {
     const int at = it >> 4, t0 = (it >> 2) & 3, t1 = it & 3;
     int k0 = g.cell[3 * at] - t0, k1 = g.cell[3 * at + 1] - t1;
@@ -421,7 +439,7 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
     k1 += k1 < 0 ? K1 : 0;
     const T w = T(par.atom[at].z) * g.wm[12 * at + t0] * g.wm[12 * at + 4 + t1];
     const T *m2 = g.wm + 12 * at + 8;
-    const int row = (k0 * K1 + k1) * K2, c2 = g.cell[3 * at + 2];
+    const int row = k0 * acc_ps + k1 * acc_rs, c2 = g.cell[3 * at + 2];
 #pragma unroll
     for (int t2 = 0; t2 < 4; ++t2) {
       const int k2 = c2 - t2 + (c2 - t2 < 0 ? K2 : 0);
@@ -448,35 +466,50 @@ __device__ void pme_forces(const SysDev &S, const Pos<P> &pos, const Params<P> &
   if (K0 == 16) fft_last_c2r<16, C2, T>(g.c, K1, K2);
   else fft_last_c2r<8, C2, T>(g.c, K1, K2);
   __syncthreads();
-  // 4. gather: one thread per (atom, t0); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d
-  for (int it = threadIdx.x; it < 4 * n; it += bd) {
-    const int at = it >> 2, t0 = it & 3;
-    const T *m1 = g.wm + 12 * at + 4, *m2 = g.wm + 12 * at + 8, *d1 = g.wd + 12 * at + 4, *d2 = g.wd + 12 * at + 8;
-    int k0 = g.cell[3 * at] - t0;
-    k0 += k0 < 0 ? K0 : 0;
-    const int c1 = g.cell[3 * at + 1], c2 = g.cell[3 * at + 2];
-    T sx = T(0), sy = T(0), sz = T(0);
+  // 4. gather: one thread per (atom, t1); F_i = -q_i sum_k grad W_i(k) phi(k), dW/dr_d = K_d/L_d dW/du_d.
+  // The four t1 threads of an atom are consecutive lanes reading rows one complex row apart (distinct
+  // banks; with one thread per t0 the four lanes read planes 272 complex values apart, one bank); their
+  // forces are summed by shuffles and added once.  Every thread runs the same number of rounds, so that
+  // whole warps take part in the shuffles.
+  for (int base = 0; base < 4 * n; base += bd) {
+    const int it = base + threadIdx.x;
+    const bool active = it < 4 * n;
+    const int at = active ? it >> 2 : 0, t1 = it & 3;
+    V3<T> f{T(0), T(0), T(0)};
+    if (active) {
+      const T *w0 = g.wm + 12 * at, *dw0 = g.wd + 12 * at, *m2 = g.wm + 12 * at + 8, *d2 = g.wd + 12 * at + 8;
+      const int c0 = g.cell[3 * at], c2 = g.cell[3 * at + 2];
+      int k1 = g.cell[3 * at + 1] - t1;
+      k1 += k1 < 0 ? K1 : 0;
+      T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
-    for (int t1 = 0; t1 < 4; ++t1) {
-      const int k1 = c1 - t1 + (c1 - t1 < 0 ? K1 : 0);
-      const int row = (k0 * K1 + k1) * (K2 + 1);
-      T px = T(0), pz = T(0);  // sum over t2 of phi m2 and phi d2
+      for (int t0 = 0; t0 < 4; ++t0) {
+        const int k0 = c0 - t0 + (c0 - t0 < 0 ? K0 : 0);
+        const int row = (k0 * K1 + k1) * (K2 + 1);
+        T px = T(0), pz = T(0);  // sum over t2 of phi m2 and phi d2
 #pragma unroll
-      for (int t2 = 0; t2 < 4; ++t2) {
-        const int k2 = c2 - t2 + (c2 - t2 < 0 ? K2 : 0);
-        const T ph = g.c[row + k2].x;
-        px += ph * m2[t2];
-        pz += ph * d2[t2];
+        for (int t2 = 0; t2 < 4; ++t2) {
+          const int k2 = c2 - t2 + (c2 - t2 < 0 ? K2 : 0);
+          const T ph = g.c[row + k2].x;
+          px += ph * m2[t2];
+          pz += ph * d2[t2];
+        }
+        ax += dw0[t0] * px;
+        ay += w0[t0] * px;
+        az += w0[t0] * pz;
       }
-      sx += m1[t1] * px;
-      sy += d1[t1] * px;
-      sz += m1[t1] * pz;
+      const T qi = T(par.atom[at].z);
+      const T m1 = g.wm[12 * at + 4 + t1], d1 = g.wd[12 * at + 4 + t1];
+      f = {-qi * m1 * ax * T(K0 * par.ibox[0]), -qi * d1 * ay * T(K1 * par.ibox[1]),
+           -qi * m1 * az * T(K2 * par.ibox[2])};
     }
-    const T qi = T(par.atom[at].z);
-    const T w0 = g.wm[12 * at + t0], dw0 = g.wd[12 * at + t0];
-    const V3<T> f{-qi * dw0 * sx * T(K0 * par.ibox[0]), -qi * w0 * sy * T(K1 * par.ibox[1]),
-                  -qi * w0 * sz * T(K2 * par.ibox[2])};
-    fa.add(at, f, err);
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      f.x += __shfl_xor_sync(0xffffffffu, f.x, o);
+      f.y += __shfl_xor_sync(0xffffffffu, f.y, o);
+      f.z += __shfl_xor_sync(0xffffffffu, f.z, o);
+    }
+    if (active && t1 == 0) fa.add(at, f, err);
   }
 }
 
