@@ -79,3 +79,37 @@ def test_batch_autotune_restores_state(B):
         for x, y in zip(a1[:3], a2[:3]):
             assert np.array_equal(x, y)
         assert a1[3] == a2[3]
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-12)])
+def test_batch_full_size_sampled(B, oracle_mod, prec, tol):
+    """The benchmark's batch at full size and in its launch configuration (64 runs x 128 replicas,
+    chains of 22..400 beads, the autotuned block size): 50 steps of every replica with sampling every
+    10, then sampled replicas -- six runs across the size range, two replicas each -- against the oracle
+    advancing them alone with their own noise indices.  Positions relative to their largest component:
+    FP64 1e-12 (measured ~1e-15: the oracle's arithmetic in another order); mixed 1e-6 (measured 1-3e-8
+    from the FP32 forces; a missing or doubled pair term gives ~1e-3)."""
+    n_runs, R, k = 64, 128, 50
+    systems = W.batched_chains(n_runs=n_runs, n_replicas=R)
+    inits, reps = [], []
+    for i, s in enumerate(systems):
+        sysh = B.grp_create_system(s, prec)
+        q0, p0 = W.replica_states(s, R, seed=3000 + i, spread=0.002)
+        inits.append((q0, p0))
+        reps.append(B.grp_init_replicas(sysh, R, 2431 + i, q0, p0, per_replica=True))
+    b = B.grp_batch_create(reps)
+    B.grp_batch_autotune(b, 10)  # restores every replica's state and counters
+    B.grp_batch_step_k(b, k, 10)
+    order = np.argsort([s.n_atoms for s in systems], kind="stable")
+    for i in order[np.linspace(0, n_runs - 1, 6).astype(int)]:
+        s = systems[i]
+        o = oracle_mod.Oracle(s)
+        q, p, _, ctr = B.grp_get_state(reps[i])
+        assert ctr["t_global"] == k
+        for r in (0, 77):
+            qo, po = inits[i][0][r:r + 1].copy(), inits[i][1][r:r + 1].copy()
+            fo = o.forces(qo[0])[None]
+            o.step_k_from(qo, po, fo, 2431 + i, r, 0, 0, k, 10, cap=k // 10)
+            err = np.abs(q[r] - qo[0]).max() / np.abs(qo[0]).max()
+            print(f"run {i} ({s.n_atoms} beads) replica {r} prec {prec}: q {err:.2e}")
+            assert err < tol
