@@ -221,8 +221,9 @@ def segment_kernel_ms(B, step, n):
 
 
 def e2e_steps(B, step, K):
-    """The same step through the public API with host buffers: H2D of the replica state from pinned
-    host memory, the step, D2H of positions and the Gelman-Rubin ratios, every step."""
+    """The same step through the public API with host buffers: H2D of the replica state (positions and
+    momenta) from pinned host memory, the step, D2H of the positions into pinned memory and of the
+    Gelman-Rubin ratios (read by the step's status), every step."""
     import torch
 
     s, R = step.s, step.R
@@ -236,8 +237,7 @@ def e2e_steps(B, step, K):
     for _ in range(K):
         B.grp_set_state(step.rep, hq.numpy(), hp.numpy(), None, ctr, step.stream)
         step()
-        B.grp_get_state(step.rep, step.stream, q=hout.numpy().reshape(R, s.n_atoms, s.dim),
-                        p=np.empty((R, s.n_atoms, s.dim)))
+        B.grp_get_state(step.rep, step.stream, q=hout.numpy().reshape(R, s.n_atoms, s.dim), copy=("q",))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t
     return wall, 2 * nd * 8, nd * 8 + 8 * len(s.observables)

@@ -373,13 +373,15 @@ def grp_run_original(r: ReplicasHandle, t_check: int, t_corr: int, t_phase: int,
     return events, tsim.value
 
 
-def grp_get_state(r: ReplicasHandle, stream=None, q=None, p=None, acc=None):
-    """Copy the state to host arrays (allocated when not given); returns (q, p, acc, counters)."""
-    q = np.empty(r.shape) if q is None else q
-    p = np.empty(r.shape) if p is None else p
-    acc = np.empty((r.R, r.n_obs, 4)) if acc is None else acc
+def grp_get_state(r: ReplicasHandle, stream=None, q=None, p=None, acc=None, copy=("q", "p", "acc")):
+    """Copy the state to host arrays (allocated when not given); returns (q, p, acc, counters).  Only
+    the parts named in `copy` are read (the others are returned as None)."""
+    q = (np.empty(r.shape) if q is None else q) if "q" in copy else None
+    p = (np.empty(r.shape) if p is None else p) if "p" in copy else None
+    acc = (np.empty((r.R, r.n_obs, 4)) if acc is None else acc) if "acc" in copy else None
     ctr = Counters()
-    _check(_lib.grp_get_state(r.handle, _dp(q), _dp(p), _dp(acc) if r.n_obs else None, C.byref(ctr),
+    _check(_lib.grp_get_state(r.handle, None if q is None else _dp(q), None if p is None else _dp(p),
+                              _dp(acc) if (acc is not None and r.n_obs) else None, C.byref(ctr),
                               _stream(stream)))
     return q, p, acc, {"t_global": ctr.t_global, "t_phase": ctr.t_phase}
 
