@@ -231,6 +231,7 @@ __device__ __forceinline__ void pair_load(const SysDev &S, const State<P> &st, i
 struct PairDsConst {
   ds wa, wb, ha, hb, d2;  // 1/m, h/m (h half a step), d^2
   float tq, tv, sa, sb;   // SHAKE and RATTLE thresholds, noise amplitudes sqrt((1 - c1^2) kT m)
+  float h, ih, c1;        // h, 1/h and c1 in FP32 (no FP64 division or conversion in the step loop)
 };
 __device__ __forceinline__ void pair_ds_const(const SysDev &S, int g, double h, double c1, PairDsConst &K) {
   const int k = S.cgroup_cons[S.cgroup_off[g]];
@@ -245,6 +246,9 @@ __device__ __forceinline__ void pair_ds_const(const SysDev &S, int g, double h, 
   K.tv = (float)(S.con_tol * d * d / S.dt);
   K.sa = (float)noise_scale(c1, S.kT, S.mass[ij.x]);
   K.sb = (float)noise_scale(c1, S.kT, S.mass[ij.y]);
+  K.h = (float)h;
+  K.ih = (float)(1.0 / h);
+  K.c1 = (float)c1;
 }
 
 struct ConPairDs {
@@ -362,7 +366,7 @@ __device__ void con_baoa(const SysDev &S, State<P> &st, int g, Noise noise, doub
       T za[3], zb[3];
       noise(C.a, za);
       noise(C.b, zb);
-      const float hf = (float)h, ih = (float)(1.0 / h), c1f = (float)c1;
+      const float hf = K.h, ih = K.ih, c1f = K.c1;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         C.p[0][x] = ds_add(C.p[0][x], hf * st.f[3 * C.a + x]);
@@ -454,7 +458,7 @@ __device__ double con_b(const SysDev &S, State<P> &st, const typename P::Acc &fa
       const PairDsConst &K = kds[g];
       ConPairDs C;
       pair_load_ds(S, st, g, C);
-      const float hf = (float)h;
+      const float hf = K.h;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         C.p[0][x] = ds_add(C.p[0][x], hf * (float)con_take_force(st, fa, 3 * C.a + x));
