@@ -175,16 +175,28 @@ def test_lennard_jones_through_a_face(oracle_mod):
     assert f[0, 0] == pytest.approx(g, rel=1e-10) and f[1, 0] == pytest.approx(-g, rel=1e-10)
 
 
-@pytest.mark.parametrize("shape", [{}, ORTHO])
+LIST_SHAPE = dict(n_chain=100, n_pairs=60, edge=4.0)  # the Verlet-list variant, 220 atoms
+
+
+@pytest.mark.parametrize("shape", [{}, ORTHO, LIST_SHAPE])
 def test_chain_ions_recipe(shape):
     """The periodic workload as documented: neutral, every ion at least 0.3 nm (minimum image) from
-    every other atom, erfc(beta r_c) = 1e-5, the cutoff within half the shortest edge."""
+    every other atom, erfc(beta r_c) = 1e-5, the cutoff within half the shortest edge; the Verlet-list
+    variant (64 atoms or more) also keeps cutoff + skin (7/6 of the cutoff) within half the shortest
+    edge, and no chain bead comes within 0.25 nm of another bead's periodic image."""
     s = W.chain_ions(**shape)
     box = np.asarray(s.box)
     assert abs(s.charge.sum()) < 1e-12
     assert math.erfc(s.ewald_beta * s.cutoff) == pytest.approx(1e-5, rel=1e-9)
     assert s.cutoff <= 0.5 * box.min()
-    n_chain = 22
+    n_chain = shape.get("n_chain", 22)
+    assert s.n_atoms == n_chain + 2 * shape.get("n_pairs", 20)
+    if s.n_atoms >= 64:
+        assert 7.0 / 6.0 * s.cutoff <= 0.5 * box.min()
+        dc = s.q0[:n_chain, None] - s.q0[None, :n_chain]
+        dc -= box * np.round(dc / box)
+        iu = np.triu_indices(n_chain, 3)
+        assert np.linalg.norm(dc, axis=-1)[iu].min() >= 0.25
     d = s.q0[n_chain:, None] - s.q0[None]
     d -= box * np.round(d / box)
     r = np.linalg.norm(d, axis=-1)
