@@ -27,6 +27,7 @@ from paper_1807_02431_gb300 import workloads as W
 NACL_M = 1.747564595
 CSCL_M = 1.762674773
 ORTHO = dict(edge=(2.6, 2.9, 2.45), grid=(16, 8, 32))  # an orthorhombic box with unequal grids
+LIST_SHAPE = dict(n_chain=100, n_pairs=60, edge=4.0)  # the Verlet-list variant, 220 atoms
 
 
 def _ions(pos, charges, box, mode, beta, cutoff, kmax=0, grid=(16, 16, 16), order=4, sigma=0.0, eps=0.0,
@@ -106,7 +107,7 @@ def test_excluding_a_pair_removes_its_coulomb(oracle_mod):
     assert e1 - e0 == pytest.approx(-W.COULOMB_K * s.charge[i] * s.charge[j] / r, rel=1e-9)
 
 
-@pytest.mark.parametrize("shape", [{}, ORTHO])
+@pytest.mark.parametrize("shape", [{}, ORTHO, LIST_SHAPE])
 def test_mesh_tends_to_the_ewald_sum(oracle_mod, shape):
     s = W.chain_ions(**shape)
     q = s.q0
@@ -120,8 +121,11 @@ def test_mesh_tends_to_the_ewald_sum(oracle_mod, shape):
         errs.append((abs(o.ewald_parts(q)[3] - e_ref) / abs(e_ref), np.abs(o.forces(q) - f_ref).max() / np.abs(f_ref).max()))
     for a, b in zip(errs, errs[1:]):
         assert b[0] < a[0] and b[1] < a[1]
-    assert errs[0][0] < 1e-2 and errs[0][1] < 1e-2
-    assert errs[-1][0] < 1e-6 and errs[-1][1] < 1e-6
+    # the 4.0 nm box has a coarser mesh at the same point counts (0.25 nm spacing at 16 points against
+    # 0.16 nm; measured 1.0e-2 / 1.3e-2 at 16^3, order 4, and 6e-7 / 2.8e-6 at 48^3, order 6)
+    coarse, fine = (2e-2, 5e-6) if shape is LIST_SHAPE else (1e-2, 1e-6)
+    assert errs[0][0] < coarse and errs[0][1] < coarse
+    assert errs[-1][0] < fine and errs[-1][1] < fine
 
 
 @pytest.mark.parametrize("mode", [W.COULOMB_PME, W.COULOMB_EWALD])
@@ -173,9 +177,6 @@ def test_lennard_jones_through_a_face(oracle_mod):
     f = o.forces(pos)
     g = 24 * eps * (2 * sr6 * sr6 - sr6) / 0.2  # repulsive: atom 0 moves away from atom 1's image at x = -1.1
     assert f[0, 0] == pytest.approx(g, rel=1e-10) and f[1, 0] == pytest.approx(-g, rel=1e-10)
-
-
-LIST_SHAPE = dict(n_chain=100, n_pairs=60, edge=4.0)  # the Verlet-list variant, 220 atoms
 
 
 @pytest.mark.parametrize("shape", [{}, ORTHO, LIST_SHAPE])
