@@ -520,8 +520,8 @@ def profile_case(B, case, replicas, steps, launches):
             B.grp_batch_step_k(b, steps, 10)
         torch.cuda.synchronize()
         del b
-    elif case == "ligand":
-        s = W.ligand_receptor()
+    elif case in ("ligand", "ligand_gb"):
+        s = W.ligand_receptor() if case == "ligand" else W.solvated(W.ligand_receptor())
         st = Step(B, s, B.GRP_MIXED, replicas, SEED, 0, omega=0)
         for _ in range(launches):
             B.grp_step_k(st.rep, steps, s.t_gr, 0, st.stream)
@@ -595,7 +595,7 @@ def main():
     ap.add_argument("--multistate-steps", type=int, default=40000)
     ap.add_argument("--branch-reps", type=int, default=20)
     ap.add_argument("--same-error-steps", type=int, default=40000)
-    ap.add_argument("--profile-case", choices=["chain", "pme", "pme_list", "constrained", "solvated", "ligand", "adjoint", "batch",
+    ap.add_argument("--profile-case", choices=["chain", "pme", "pme_list", "constrained", "solvated", "ligand", "ligand_gb", "adjoint", "batch",
                                                      "branch"],
                     default=None,
                     help="run a small case of one kernel for ncu captures and exit (no benchmark line)")

@@ -151,29 +151,44 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
 // The solvent forces of a system with a cutoff (Verlet-list systems, up to thousands of atoms): the five
 // passes of gb_forces over the pairs within the cutoff (plain truncation: a pair at r >= r_c enters
 // neither I_i nor the pair energy; the self terms always count).  `pairs(f)` calls f(i, j) for this
-// thread's share of the candidate pairs (each unordered pair once): the Verlet list, which holds every
-// non-excluded pair within the cutoff, and the excluded pairs, which the solvent term includes.  One
-// shared-memory accumulator per atom serves I_i in passes 1-2 and dE/dB_i in passes 2-4; the Born
-// radii and chain-rule weights of the replica live in `born` and `w` (global memory, [n] each, written
-// and read by this block only).  dh/dr is recomputed in pass 5 instead of kept per pair.  Called by every
-// thread of the block with the positions final; the scratch accumulator is zero on entry and left zero.
+// thread's share of the candidate pairs (each unordered pair once), kGbBatch pairs at a time (slots with
+// i < 0 are empty): the Verlet list, which holds every non-excluded pair within the cutoff, and the
+// excluded pairs, which the solvent term includes.  Each pass loads the positions, parameters and Born
+// quantities of a whole batch before evaluating it, so that the loads' latencies (the parameters and
+// Born radii are in global memory) overlap instead of adding up pair by pair.  One shared-memory
+// accumulator per atom serves I_i in passes 1-2 and dE/dB_i in passes 2-4; the Born radii and chain-rule
+// weights of the replica live in `born` and `w` (global memory, [n] each, written and read by this
+// block only).  dh/dr is recomputed in pass 5 instead of kept per pair.  Called by every thread of the
+// block with the positions final; the scratch accumulator is zero on entry and left zero.
+constexpr int kGbBatch = 4;
 template <class P, class Pairs>
 __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename P::Acc &fa, const ScalarAcc<P> &acc,
                               typename P::T *born, typename P::T *w, Pairs pairs, bool want_e, long long &e_fix,
                               int *err) {
   using T = typename P::T;
+  using GA = decltype(gb_atom<P>(S, 0));
   const int n = S.n, bd = blockDim.x;
   const T tau = (T)S.gb_tau, cut2 = (T)S.cutoff2;
   // 1. descreening sums
-  pairs([&](int i, int j) {
-    const V3<T> d = pos.diff(i, j);
-    const T r2 = dot(d, d);
-    if (!(r2 < cut2)) return;
-    const T r = gsqrt(r2);
-    const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
-    T dh;
-    acc.add(i, gb_hct<T>(r, (T)pi.x, (T)pj.z, dh), err);
-    acc.add(j, gb_hct<T>(r, (T)pj.x, (T)pi.z, dh), err);
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+    V3<T> d[kGbBatch];
+    GA pa[kGbBatch], pb[kGbBatch];
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {  // an empty slot reads atom 0 and is skipped below
+      const int i = I[u] < 0 ? 0 : I[u], j = I[u] < 0 ? 0 : J[u];
+      d[u] = pos.diff(i, j);
+      pa[u] = gb_atom<P>(S, i);
+      pb[u] = gb_atom<P>(S, j);
+    }
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {
+      const T r2 = dot(d[u], d[u]);
+      if (I[u] < 0 || !(r2 < cut2)) continue;
+      const T r = gsqrt(r2);
+      T dh;
+      acc.add(I[u], gb_hct<T>(r, (T)pa[u].x, (T)pb[u].z, dh), err);
+      acc.add(J[u], gb_hct<T>(r, (T)pb[u].x, (T)pa[u].z, dh), err);
+    }
   });
   __syncthreads();
   // 2. Born radii, dB/dI, the self terms of E and dE/dB
@@ -190,22 +205,32 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
   }
   __syncthreads();
   // 3. pair terms at fixed Born radii: forces and the pairs' parts of dE/dB
-  pairs([&](int i, int j) {
-    const V3<T> d = pos.diff(i, j);
-    const T r2 = dot(d, d);
-    if (!(r2 < cut2)) return;
-    const T bi = born[i], bj = born[j], bb = bi * bj, D = T(0.25) * r2 * grcp(bb), e = gexp(-D);
-    const T f2 = r2 + bb * e, rf = grsqrt(f2), qq = (T)gb_atom<P>(S, i).w * (T)gb_atom<P>(S, j).w;
-    const T f = f2 * rf;  // sqrt(f2) and 1/f from one reciprocal square root
-    const T dEdf = tau * qq * rf * rf;
-    const T dBcommon = T(0.5) * dEdf * e * (T(1) + D) * rf;
-    acc.add(i, dBcommon * bj, err);
-    acc.add(j, dBcommon * bi, err);
-    const T gr = -dEdf * (T(1) - T(0.25) * e) * rf;  // -dE/dr / r
-    fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
-    fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
-    if (want_e) e_fix += fa.efix(-tau * qq * rf, err);
-    (void)f;
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+    V3<T> d[kGbBatch];
+    T bi[kGbBatch], bj[kGbBatch], qq[kGbBatch];
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {
+      const int i = I[u] < 0 ? 0 : I[u], j = I[u] < 0 ? 0 : J[u];
+      d[u] = pos.diff(i, j);
+      bi[u] = born[i];
+      bj[u] = born[j];
+      qq[u] = (T)gb_atom<P>(S, i).w * (T)gb_atom<P>(S, j).w;
+    }
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {
+      const T r2 = dot(d[u], d[u]);
+      if (I[u] < 0 || !(r2 < cut2)) continue;
+      const T bb = bi[u] * bj[u], D = T(0.25) * r2 * grcp(bb), e = gexp(-D);
+      const T f2 = r2 + bb * e, rf = grsqrt(f2);
+      const T dEdf = tau * qq[u] * rf * rf;
+      const T dBcommon = T(0.5) * dEdf * e * (T(1) + D) * rf;
+      acc.add(I[u], dBcommon * bj[u], err);
+      acc.add(J[u], dBcommon * bi[u], err);
+      const T gr = -dEdf * (T(1) - T(0.25) * e) * rf;  // -dE/dr / r
+      fa.add(I[u], V3<T>{gr * d[u].x, gr * d[u].y, gr * d[u].z}, err);
+      fa.add(J[u], V3<T>{-gr * d[u].x, -gr * d[u].y, -gr * d[u].z}, err);
+      if (want_e) e_fix += fa.efix(-tau * qq[u] * rf, err);
+    }
   });
   __syncthreads();
   // 4. chain-rule weights w_i = dE/dB_i dB_i/dI_i / 2
@@ -215,18 +240,31 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
   }
   __syncthreads();
   // 5. forces through the Born radii
-  pairs([&](int i, int j) {
-    const V3<T> d = pos.diff(i, j);
-    const T r2 = dot(d, d);
-    if (!(r2 < cut2)) return;
-    const T r = gsqrt(r2);
-    const auto pi = gb_atom<P>(S, i), pj = gb_atom<P>(S, j);
-    T dhij, dhji;
-    gb_hct<T>(r, (T)pi.x, (T)pj.z, dhij);
-    gb_hct<T>(r, (T)pj.x, (T)pi.z, dhji);
-    const T gr = -(w[i] * dhij + w[j] * dhji) * grcp(r);
-    fa.add(i, V3<T>{gr * d.x, gr * d.y, gr * d.z}, err);
-    fa.add(j, V3<T>{-gr * d.x, -gr * d.y, -gr * d.z}, err);
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+    V3<T> d[kGbBatch];
+    GA pa[kGbBatch], pb[kGbBatch];
+    T wi[kGbBatch], wj[kGbBatch];
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {
+      const int i = I[u] < 0 ? 0 : I[u], j = I[u] < 0 ? 0 : J[u];
+      d[u] = pos.diff(i, j);
+      pa[u] = gb_atom<P>(S, i);
+      pb[u] = gb_atom<P>(S, j);
+      wi[u] = w[i];
+      wj[u] = w[j];
+    }
+#pragma unroll
+    for (int u = 0; u < kGbBatch; ++u) {
+      const T r2 = dot(d[u], d[u]);
+      if (I[u] < 0 || !(r2 < cut2)) continue;
+      const T r = gsqrt(r2);
+      T dhij, dhji;
+      gb_hct<T>(r, (T)pa[u].x, (T)pb[u].z, dhij);
+      gb_hct<T>(r, (T)pb[u].x, (T)pa[u].z, dhji);
+      const T gr = -(wi[u] * dhij + wj[u] * dhji) * grcp(r);
+      fa.add(I[u], V3<T>{gr * d[u].x, gr * d[u].y, gr * d[u].z}, err);
+      fa.add(J[u], V3<T>{-gr * d[u].x, -gr * d[u].y, -gr * d[u].z}, err);
+    }
   });
 }
 

@@ -533,11 +533,23 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     if constexpr (kGB) gb_forces<P>(S, pos, fa, gbs, sample, e_fix, &err);
     if constexpr (kGBL) {
       const int nl = n_list;
+      // batches of kGbBatch entries per thread (list entries t, t + kThreads, ...), padding entries and
+      // the tail as empty slots
       gb_forces_cut<P>(S, pos, fa, gbl_acc, gbl_born, gbl_w, [&](auto f) {
-        for (int t = threadIdx.x; t < nl; t += kThreads)
-          if (list[t] != 0xFFFFFFFFu) f((int)(list[t] & 0xFFFFu), (int)(list[t] >> 16));
-        for (int t = threadIdx.x; t < S.n_gb_xpairs; t += kThreads)
-          f((int)(S.gb_xpairs[t] & 0xFFFFu), (int)(S.gb_xpairs[t] >> 16));
+        auto batches = [&](const uint32_t *src, int cnt) {
+          for (int t = threadIdx.x; t < cnt; t += kGbBatch * kThreads) {
+            int I[kGbBatch], J[kGbBatch];
+#pragma unroll
+            for (int u = 0; u < kGbBatch; ++u) {
+              const uint32_t pk = t + u * kThreads < cnt ? src[t + u * kThreads] : 0xFFFFFFFFu;
+              I[u] = pk == 0xFFFFFFFFu ? -1 : (int)(pk & 0xFFFFu);
+              J[u] = (int)(pk >> 16);
+            }
+            f(I, J);
+          }
+        };
+        batches(list, nl);
+        batches(S.gb_xpairs, S.n_gb_xpairs);
       }, sample, e_fix, &err);
     }
     if constexpr (kPME) pme_forces<P>(S, pos, par, fa, pms, sample, e_fix, &err);
@@ -893,7 +905,15 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
     T *born = reinterpret_cast<T *>(gb_glob + (size_t)b * 2 * n);
     gb_forces_cut<P>(S, st.pos(), fa, gbl_acc, born, born + n, [&](auto f) {
       for (int i = threadIdx.x; i < n; i += blockDim.x)
-        for (int j = i + 1; j < n; ++j) f(i, j);
+        for (int j = i + 1; j < n; j += kGbBatch) {
+          int I[kGbBatch], J[kGbBatch];
+#pragma unroll
+          for (int u = 0; u < kGbBatch; ++u) {
+            I[u] = j + u < n ? i : -1;
+            J[u] = j + u;
+          }
+          f(I, J);
+        }
     }, energy != nullptr, e_fix, &err);
     __syncthreads();
   } else if (S.gb) {
