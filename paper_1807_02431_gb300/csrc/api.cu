@@ -94,6 +94,8 @@ struct grp_replicas {
   int rep0 = 0, n_global = 0;
   double *d_gr = nullptr;  // [3 GRP_MAX_OBS] Gelman-Rubin sums of the shard
   double *gb_glob = nullptr;  // [R][2n] Born radii and weights (solvent on Verlet lists)
+  void *gb_gr = nullptr;      // [R][gb_gr_stride] the solvent's pass-3 force factor per candidate pair
+  int gb_gr_stride = 0;
   // one-launch status readback (branch count, reference label and exit flag, ratios, error word,
   // first-exit key): the set's arrays for the status kernel, its output and a pinned copy
   RunArrays *d_run = nullptr;
@@ -801,7 +803,11 @@ extern "C" grp_status grp_init_replicas(grp_system *s, int32_t n_replicas, uint6
     r->nbl_cap = (int)(std::min(all, std::max(2 * cnt + 1024, (size_t)65536)) + 16 * 256);
     AL(r->nbl, R * (size_t)r->nbl_cap * 4);
     AL(r->qref, R * (size_t)n * 16);
-    if (D.gb) AL(r->gb_glob, R * (size_t)n * 2 * 8);
+    if (D.gb) {
+      AL(r->gb_glob, R * (size_t)n * 2 * 8);
+      r->gb_gr_stride = r->nbl_cap + D.n_gb_xpairs;
+      AL(r->gb_gr, R * (size_t)r->gb_gr_stride * (D.precision == GRP_FP64 ? 8 : 4));
+    }
   }
   AL(r->d_run, sizeof(RunArrays));
   AL(r->d_status, sizeof(BatchStatus));
@@ -851,7 +857,7 @@ extern "C" void grp_destroy_replicas(grp_replicas *r) {
   cudaFree(r->q); cudaFree(r->p); cudaFree(r->f); cudaFree(r->acc);
   cudaFree(r->labels); cudaFree(r->exited); cudaFree(r->src); cudaFree(r->exit_key);
   cudaFree(r->err); cudaFree(r->n_branched); cudaFree(r->rhat); cudaFree(r->d_gr);
-  cudaFree(r->nbl); cudaFree(r->qref); cudaFree(r->gb_glob);
+  cudaFree(r->nbl); cudaFree(r->qref); cudaFree(r->gb_glob); cudaFree(r->gb_gr);
   if (r->hb) cudaFreeHost(r->hb);
   cudaFree(r->d_run); cudaFree(r->d_status);
   if (r->h_status) cudaFreeHost(r->h_status);
@@ -869,6 +875,8 @@ static SegArgs seg_args(grp_replicas *r, int k, int t_gr, int n_active) {
   a.qref = r->qref;
   a.nbl_cap = r->nbl_cap;
   a.gb_glob = r->gb_glob;
+  a.gb_gr = r->gb_gr;
+  a.gb_gr_stride = r->gb_gr_stride;
   a.seed = r->seed;
   a.t_global0 = r->t_global;
   a.t_phase0 = r->t_phase;

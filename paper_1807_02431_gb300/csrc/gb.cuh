@@ -150,10 +150,12 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
 
 // The solvent forces of a system with a cutoff (Verlet-list systems, up to thousands of atoms): the five
 // passes of gb_forces over the pairs within the cutoff (plain truncation: a pair at r >= r_c enters
-// neither I_i nor the pair energy; the self terms always count).  `pairs(f)` calls f(i, j) for this
+// neither I_i nor the pair energy; the self terms always count).  `pairs(f)` calls f(i, j, k) for this
 // thread's share of the candidate pairs (each unordered pair once), kGbBatch pairs at a time (slots with
 // i < 0 are empty): the Verlet list, which holds every non-excluded pair within the cutoff, and the
-// excluded pairs, which the solvent term includes.  Each pass loads the positions, parameters and Born
+// excluded pairs, which the solvent term includes; k is the pair's slot in `gr3` (the same in every
+// pass), or -1 when `gr3` is null.  With a slot, pass 3 keeps its force factor -dE/dr / r there and
+// pass 5 adds the pair's two force contributions at once (12 fixed-point additions fewer per pair).  Each pass loads the positions, parameters and Born
 // quantities of a whole batch before evaluating it, so that the loads' latencies (the parameters and
 // Born radii are in global memory) overlap instead of adding up pair by pair.  One shared-memory
 // accumulator per atom serves I_i in passes 1-2 and dE/dB_i in passes 2-4; the Born radii and chain-rule
@@ -163,14 +165,14 @@ __device__ void gb_forces(const SysDev &S, const Pos<P> &pos, const typename P::
 constexpr int kGbBatch = 4;
 template <class P, class Pairs>
 __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename P::Acc &fa, const ScalarAcc<P> &acc,
-                              typename P::T *born, typename P::T *w, Pairs pairs, bool want_e, long long &e_fix,
-                              int *err) {
+                              typename P::T *born, typename P::T *w, typename P::T *gr3, Pairs pairs, bool want_e,
+                              long long &e_fix, int *err) {
   using T = typename P::T;
   using GA = decltype(gb_atom<P>(S, 0));
   const int n = S.n, bd = blockDim.x;
   const T tau = (T)S.gb_tau, cut2 = (T)S.cutoff2;
   // 1. descreening sums
-  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch], const int (&K)[kGbBatch]) {
     V3<T> d[kGbBatch];
     GA pa[kGbBatch], pb[kGbBatch];
 #pragma unroll
@@ -205,7 +207,7 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
   }
   __syncthreads();
   // 3. pair terms at fixed Born radii: forces and the pairs' parts of dE/dB
-  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch], const int (&K)[kGbBatch]) {
     V3<T> d[kGbBatch];
     T bi[kGbBatch], bj[kGbBatch], qq[kGbBatch];
 #pragma unroll
@@ -227,8 +229,12 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
       acc.add(I[u], dBcommon * bj[u], err);
       acc.add(J[u], dBcommon * bi[u], err);
       const T gr = -dEdf * (T(1) - T(0.25) * e) * rf;  // -dE/dr / r
-      fa.add(I[u], V3<T>{gr * d[u].x, gr * d[u].y, gr * d[u].z}, err);
-      fa.add(J[u], V3<T>{-gr * d[u].x, -gr * d[u].y, -gr * d[u].z}, err);
+      if (K[u] >= 0) {
+        gr3[K[u]] = gr;  // added with pass 5's factor
+      } else {
+        fa.add(I[u], V3<T>{gr * d[u].x, gr * d[u].y, gr * d[u].z}, err);
+        fa.add(J[u], V3<T>{-gr * d[u].x, -gr * d[u].y, -gr * d[u].z}, err);
+      }
       if (want_e) e_fix += fa.efix(-tau * qq[u] * rf, err);
     }
   });
@@ -240,10 +246,10 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
   }
   __syncthreads();
   // 5. forces through the Born radii
-  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch]) {
+  pairs([&](const int (&I)[kGbBatch], const int (&J)[kGbBatch], const int (&K)[kGbBatch]) {
     V3<T> d[kGbBatch];
     GA pa[kGbBatch], pb[kGbBatch];
-    T wi[kGbBatch], wj[kGbBatch];
+    T wi[kGbBatch], wj[kGbBatch], g3[kGbBatch];
 #pragma unroll
     for (int u = 0; u < kGbBatch; ++u) {
       const int i = I[u] < 0 ? 0 : I[u], j = I[u] < 0 ? 0 : J[u];
@@ -252,6 +258,7 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
       pb[u] = gb_atom<P>(S, j);
       wi[u] = w[i];
       wj[u] = w[j];
+      g3[u] = K[u] >= 0 ? gr3[K[u]] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kGbBatch; ++u) {
@@ -261,7 +268,7 @@ __device__ void gb_forces_cut(const SysDev &S, const Pos<P> &pos, const typename
       T dhij, dhji;
       gb_hct<T>(r, (T)pa[u].x, (T)pb[u].z, dhij);
       gb_hct<T>(r, (T)pb[u].x, (T)pa[u].z, dhji);
-      const T gr = -(wi[u] * dhij + wj[u] * dhji) * grcp(r);
+      const T gr = g3[u] - (wi[u] * dhij + wj[u] * dhji) * grcp(r);
       fa.add(I[u], V3<T>{gr * d[u].x, gr * d[u].y, gr * d[u].z}, err);
       fa.add(J[u], V3<T>{-gr * d[u].x, -gr * d[u].y, -gr * d[u].z}, err);
     }

@@ -32,6 +32,8 @@ struct SegArgs {
   float4 *qref;              // [R][n] positions at the last list build
   int nbl_cap;
   double *gb_glob;           // [R][2n] Born radii and chain-rule weights (solvent with Verlet lists)
+  void *gb_gr;               // [R][gb_gr_stride] pass-3 force factor of each candidate pair (path precision)
+  int gb_gr_stride;          // nbl_cap + the excluded pairs: list entries first, then excluded pairs
   double h, c1;              // dt/2 and exp(-gamma dt)
 };
 

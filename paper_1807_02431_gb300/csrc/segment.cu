@@ -409,13 +409,14 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
     for (int i = threadIdx.x; i < 2 * n; i += kThreads) gbs.acc.zero(i);
   }
   ScalarAcc<P> gbl_acc;  // solvent with a cutoff: one accumulator per atom; radii and weights in global memory
-  T *gbl_born = nullptr, *gbl_w = nullptr;
+  T *gbl_born = nullptr, *gbl_w = nullptr, *gbl_gr = nullptr;
   if constexpr (kGBL) {
     ptr = align32(ptr);
     gbl_acc.carve(ptr, n);
     for (int i = threadIdx.x; i < n; i += kThreads) gbl_acc.zero(i);
     gbl_born = reinterpret_cast<T *>(a.gb_glob + (size_t)r * 2 * n);
     gbl_w = gbl_born + n;
+    if (a.gb_gr) gbl_gr = reinterpret_cast<T *>(a.gb_gr) + (size_t)r * a.gb_gr_stride;
   }
   PmeScratch<P> pms;  // particle mesh (periodic systems: item table or Verlet lists)
   if constexpr (kPME) {
@@ -535,21 +536,23 @@ __device__ __forceinline__ void segment_body(const SegArgs &a, const int r, unsi
       const int nl = n_list;
       // batches of kGbBatch entries per thread (list entries t, t + kThreads, ...), padding entries and
       // the tail as empty slots
-      gb_forces_cut<P>(S, pos, fa, gbl_acc, gbl_born, gbl_w, [&](auto f) {
-        auto batches = [&](const uint32_t *src, int cnt) {
+      // the slot of a pair in the gr3 row: its list position, or nbl_cap + its index among the excluded pairs
+      gb_forces_cut<P>(S, pos, fa, gbl_acc, gbl_born, gbl_w, gbl_gr, [&](auto f) {
+        auto batches = [&](const uint32_t *src, int cnt, int slot0) {
           for (int t = threadIdx.x; t < cnt; t += kGbBatch * kThreads) {
-            int I[kGbBatch], J[kGbBatch];
+            int I[kGbBatch], J[kGbBatch], K[kGbBatch];
 #pragma unroll
             for (int u = 0; u < kGbBatch; ++u) {
               const uint32_t pk = t + u * kThreads < cnt ? src[t + u * kThreads] : 0xFFFFFFFFu;
               I[u] = pk == 0xFFFFFFFFu ? -1 : (int)(pk & 0xFFFFu);
               J[u] = (int)(pk >> 16);
+              K[u] = (gbl_gr && I[u] >= 0) ? slot0 + t + u * kThreads : -1;  // empty slots and the tail: none
             }
-            f(I, J);
+            f(I, J, K);
           }
         };
-        batches(list, nl);
-        batches(S.gb_xpairs, S.n_gb_xpairs);
+        batches(list, nl, 0);
+        batches(S.gb_xpairs, S.n_gb_xpairs, a.nbl_cap);
       }, sample, e_fix, &err);
     }
     if constexpr (kPME) pme_forces<P>(S, pos, par, fa, pms, sample, e_fix, &err);
@@ -903,16 +906,17 @@ __global__ void __launch_bounds__(256) energy_forces_kernel(SysDev S, const doub
     // every pair i < j, the cutoff applied inside: rows i, i + blockDim.x, ... per thread
     using T = typename P::T;
     T *born = reinterpret_cast<T *>(gb_glob + (size_t)b * 2 * n);
-    gb_forces_cut<P>(S, st.pos(), fa, gbl_acc, born, born + n, [&](auto f) {
+    gb_forces_cut<P>(S, st.pos(), fa, gbl_acc, born, born + n, nullptr, [&](auto f) {
       for (int i = threadIdx.x; i < n; i += blockDim.x)
         for (int j = i + 1; j < n; j += kGbBatch) {
-          int I[kGbBatch], J[kGbBatch];
+          int I[kGbBatch], J[kGbBatch], K[kGbBatch];
 #pragma unroll
           for (int u = 0; u < kGbBatch; ++u) {
             I[u] = j + u < n ? i : -1;
             J[u] = j + u;
+            K[u] = -1;
           }
-          f(I, J);
+          f(I, J, K);
         }
     }, energy != nullptr, e_fix, &err);
     __syncthreads();
